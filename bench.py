@@ -1,0 +1,383 @@
+"""Benchmark of the ESP long-range step on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl esp|reference]
+
+One step = the whole long-range step on the membrane-slab workload (210,240 atoms,
+120 x 120 x 150 A, grid 128 x 128 x 160, P = 6, Delta = 1e-5, r_c = 9 A): wrap + bin/sort,
+spread, forward FFT, fused scaling with the energy and 3x3 virial reduction, inverse FFT
+and force gather, with inputs resident in HBM.  Every timed step is bracketed by CUDA
+events on the plan's stream; the L2 cache is flushed (a 512 MB write) between timed steps
+because the workload's inputs are smaller than L2.  Under torchrun (N > 1) each rank runs
+an independent replica of the workload on its own GPU (the step has no exchange to
+shard), the timed region is bracketed by barriers and rank 0 reports the maximum time.
+
+--impl reference times the FP64 CPU oracle on the host cores instead (see
+``reference_arm``).  Both arms print one JSON line.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synthetic  # noqa: E402
+
+METRIC = "long-range ESP steps/sec and atoms/s at 200k atoms, 1e-5 pressure rel err"
+WORKLOAD = "membrane_slab_210k"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+
+# algorithmic bytes (FP32 path): spread reads (s, q) = 16 B per atom and writes one 4 B
+# value per grid point; gather reads 16 B per atom and 4 B per grid point and writes 12 B
+# of force per atom; scale reads and writes 8 B per half-spectrum mode.
+BYTES_PER_ATOM = {"spread": 16, "gather": 28, "bin": 16, "scatter": 16 + 24}
+BYTES_PER_POINT = {"spread": 4, "gather": 4}
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["esp", "reference"], default="esp")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    ap.add_argument("--no-fp64-compare", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args(argv)
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def aggregate(per_rank_seconds, per_rank_steps):
+    """Whole-job throughput: units all ranks processed over the slowest rank's time."""
+    t = max(per_rank_seconds)
+    return sum(per_rank_steps) / t, t
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def recorded_traffic(kernel: str):
+    """dram bytes per launch from the committed ncu summary, if it matches this source."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{WORKLOAD}.md")
+    src = os.path.join(ROOT, "paper_2601_00161_gb300", "csrc", "esp_kernels.cu")
+    try:
+        text = open(path).read()
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    vals = {}
+    for ln in text.splitlines():
+        if ":" in ln and ln.strip().startswith("- "):
+            k, v = ln.strip()[2:].split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("kernel_source_sha256_16") != digest:
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def cpu_baseline_oracle(S, c):
+    """The FP64 oracle as it stands, one full step of the same workload, 1 host thread."""
+    from threadpoolctl import threadpool_limits
+
+    from oracle.esp_grid import esp_grid
+
+    with threadpool_limits(1):
+        t0 = time.perf_counter()
+        esp_grid(S.pos, S.q, S.cell, S.grid, S.P, c, S.rc, forces=True)
+        dt = time.perf_counter() - t0
+    return {"value": 1.0 / dt, "unit": "steps/s", "cores": 1, "kind": "oracle",
+            "sample": f"one full oracle step (spread, FFT, scaling, inverse FFT, gather) of "
+                      f"{WORKLOAD}, {S.n} atoms, FP64, numpy/pocketfft, 1 thread: {dt:.2f} s"}
+
+
+def esp_arm(args):
+    import torch
+
+    import paper_2601_00161_gb300 as esp
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    S = synthetic.membrane_slab()
+    c = esp.esp_c_from_tolerance(S.delta)
+    fp64 = args.precision == "fp64"
+    dt = torch.float64 if fp64 else torch.float32
+    stream = torch.cuda.current_stream()
+    plan = esp.Plan(S.cell, S.n, S.grid, S.P, c, S.rc, precision=args.precision)
+    pos = torch.tensor(S.pos, dtype=dt, device="cuda")
+    q = torch.tensor(S.q, dtype=dt, device="cuda")
+    F = torch.empty((S.n, 3), dtype=dt, device="cuda")
+    acc = torch.zeros(esp.ESP_ACCUM_LEN, dtype=torch.float64, device="cuda")
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step():
+        esp.esp_step(plan.handle, pos, q, F, acc)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    esp.esp_profile(plan.handle, True)
+    stage_tot = {k: 0.0 for k in esp.STAGES}
+    ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    for i in range(args.steps):
+        flush.zero_()
+        ev0[i].record(stream)
+        step()
+        ev1[i].record(stream)
+        for k, v in esp.esp_profile_read(plan.handle).items():  # synchronises the stream
+            stage_tot[k] += v
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    esp.esp_profile(plan.handle, False)
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    my_seconds = sum(step_ms) / 1e3
+    if world > 1:
+        tt = torch.tensor([my_seconds], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+        value = world * args.steps / t_max
+    else:
+        value, t_max = aggregate([my_seconds], [args.steps])
+    res = esp.esp_result_from_accum(plan.handle, acc.cpu().numpy()).as_dict()
+
+    # dominant kernel of ours and its roofline (algorithmic bytes / event-timed duration)
+    ours = ["bin", "scan", "scatter", "spread", "scale", "gather"]
+    avg = {k: stage_tot[k] / args.steps for k in esp.STAGES}
+    dom = max(ours, key=lambda k: avg[k])
+    Mtot = S.grid[0] * S.grid[1] * S.grid[2]
+    alg = BYTES_PER_ATOM.get(dom, 16) * S.n + BYTES_PER_POINT.get(dom, 0) * Mtot
+    if fp64:
+        alg *= 2
+    peak, peak_kind = measured_peaks()
+    achieved = alg / (avg[dom] * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": recorded_traffic(dom),
+                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.8 TB/s",
+                "algorithmic_bytes": alg, "avg_ms": round(avg[dom], 5)}
+
+    # end to end through the public C ABI with host buffers (H2D + step + D2H every step)
+    npdt = np.float64 if fp64 else np.float32
+    pos_h = torch.tensor(S.pos.astype(npdt)).pin_memory().numpy()
+    q_h = torch.tensor(S.q.astype(npdt)).pin_memory().numpy()
+    F_h = torch.empty((S.n, 3), dtype=dt).pin_memory().numpy()
+    for _ in range(3):
+        esp.esp_compute_host(plan.handle, pos_h, q_h, F_h)
+    n_e2e = max(10, min(args.steps, 50))
+    t0 = time.perf_counter()
+    for _ in range(n_e2e):
+        esp.esp_compute_host(plan.handle, pos_h, q_h, F_h)
+    e2e_s = (time.perf_counter() - t0) / n_e2e
+    e2e = {"value": round(world / e2e_s, 2), "unit": "steps/s",
+           "h2d_bytes_per_step": int(pos_h.nbytes + q_h.nbytes),
+           "d2h_bytes_per_step": int(F_h.nbytes + 8 * esp.ESP_ACCUM_LEN)}
+
+    fp64_value = None
+    if not fp64 and not args.no_fp64_compare:
+        p64 = esp.Plan(S.cell, S.n, S.grid, S.P, c, S.rc, precision="fp64")
+        pos64 = torch.tensor(S.pos, dtype=torch.float64, device="cuda")
+        q64 = torch.tensor(S.q, dtype=torch.float64, device="cuda")
+        F64 = torch.empty((S.n, 3), dtype=torch.float64, device="cuda")
+        for _ in range(3):
+            esp.esp_step(p64.handle, pos64, q64, F64, acc)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        n64 = max(5, min(args.steps, 20))
+        for _ in range(n64):
+            flush.zero_()
+            e0.record(stream)
+            esp.esp_step(p64.handle, pos64, q64, F64, acc)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            tot += e0.elapsed_time(e1)
+        fp64_value = round(1e3 * n64 / tot, 2)
+        p64.close()
+
+    launches_per_step = 6
+    out = None
+    if rank == 0:
+        ms = 1e3 * t_max / args.steps
+        out = {
+            "metric": METRIC, "value": round(value, 2), "unit": "steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if not fp64 else "f64", "data": "synthetic",
+            "atoms_per_s": round(value * S.n, 1),
+            "ns_per_day_equiv_2fs": round(value * 0.1728, 2),
+            "config": {"workload": WORKLOAD, "atoms": S.n, "cell_A": [120, 120, 150],
+                       "grid": list(S.grid), "P": S.P, "delta": S.delta, "c": round(c, 6),
+                       "r_c_A": S.rc, "step": "energy + 3x3 virial + forces",
+                       "l2": "flushed between timed steps (512 MB write)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "stage_ms": {k: round(v, 5) for k, v in avg.items()},
+            "roofline": roofline,
+            "e2e": e2e,
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": clk,
+            "fp64_path_value": fp64_value,
+            "energy_recip": res["energy_recip"],
+        }
+        if not args.no_cpu_baseline and world == 1:
+            out["cpu_baseline"] = cpu_baseline_oracle(S, c)
+    plan.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return out
+
+
+def reference_arm(args):
+    """FP64 CPU oracle on host cores; each step a bounded sample of the workload.
+
+    The sample of one step is a periodic sub-cell of the slab: the atoms whose reduced
+    x and y coordinates lie in [0, 1/4) (a 30 x 30 x 150 A column through both water
+    layers and the slab, ~13k atoms), on the matching 32 x 32 x 160 grid with the same
+    P, c and r_c; one full oracle step on it (spread, FFT, scaling, inverse FFT,
+    gather).  The reported steps/s of the full workload is the sample's atoms/s divided
+    by the workload's atom count (the oracle's cost is linear in the atoms apart from the
+    FFT's log factor).
+    """
+    from threadpoolctl import threadpool_limits
+
+    from oracle.esp_grid import esp_grid
+    from oracle.pswf import c_from_tolerance
+
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return None
+    S = synthetic.membrane_slab()
+    c = c_from_tolerance(S.delta)
+    s = S.pos @ np.linalg.inv(S.cell).T
+    s -= np.floor(s)
+    sel = (s[:, 0] < 0.25) & (s[:, 1] < 0.25)
+    sub_cell = S.cell @ np.diag([0.25, 0.25, 1.0])
+    pos, q = S.pos[sel] - 0.0, S.q[sel]
+    grid = (S.grid[0] // 4, S.grid[1] // 4, S.grid[2])
+    with threadpool_limits(1):
+        for _ in range(args.warmup):
+            esp_grid(pos, q, sub_cell, grid, S.P, c, S.rc)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            esp_grid(pos, q, sub_cell, grid, S.P, c, S.rc)
+        dt = time.perf_counter() - t0
+    atoms_per_s = args.steps * len(q) / dt
+    value = atoms_per_s / S.n
+    sample = (f"per step one full FP64 oracle step on a periodic 1/16 sub-cell column of "
+              f"{WORKLOAD} ({len(q)} atoms, 30x30x150 A, grid {grid[0]}x{grid[1]}x{grid[2]}, same P, c, r_c), "
+              f"1 host thread; value = sample atoms/s / {S.n}")
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "atoms_per_s": atoms_per_s,
+        "config": {"workload": WORKLOAD, "atoms": S.n, "grid": list(S.grid), "P": S.P,
+                   "delta": S.delta, "r_c_A": S.rc},
+        "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    out = reference_arm(args) if args.impl == "reference" else esp_arm(args)
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

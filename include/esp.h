@@ -1,0 +1,179 @@
+/*
+ * esp.h - C ABI of the GB300 (sm_103a) long-range step of Ewald summation with
+ * prolates (ESP): charge spreading with a PSWF window, one forward 3D FFT, the fused
+ * diagonal scaling + energy / 3x3 virial reduction, the inverse FFT and the force
+ * gather with the window gradient.
+ *
+ * Paper: J. Liang, L. Lu, S. Jiang, "Fast Ewald Summation with Prolates for Charged
+ * Systems in the NPT Ensemble" (arXiv:2601.00161).  Citations below name its sections
+ * and equations.
+ *
+ * Conventions shared by every entry point
+ *  - cell[9]: the cell matrix h of Sec. 2.2 in COLUMN-MAJOR order, i.e. cell[0..2] is the
+ *    first cell vector h_1, cell[3..5] is h_2, cell[6..8] is h_3 (Angstrom).  det h > 0.
+ *  - Positions are Cartesian (Angstrom), N x 3 row-major; charges N (e).  They may lie
+ *    anywhere; they are wrapped into the cell through reduced coordinates s = h^{-1} r.
+ *  - Units are Gaussian: energies in e^2/Angstrom, as the paper's 1/r kernel.
+ *  - Tensors are 3x3 row-major.  The virial is W = -(dU/dh) h^T at fixed reduced
+ *    coordinates (eq. (instheta) without the kinetic term), so P = W / det h.
+ *  - Device pointers belong to the caller, must stay valid until the stream has
+ *    finished the call, and are read / written on the plan's stream.  The plan owns all
+ *    of its internal buffers.  A plan is not re-entrant: one call at a time.
+ *  - Every function returns ESP_OK (0) or a negative ESP_ERR_* code, never aborts and
+ *    never traps; esp_last_error() then gives a message.  On an error the outputs are
+ *    unspecified but the plan stays usable (except after ESP_ERR_CUDA, which reports a
+ *    failed CUDA call and leaves the context in whatever state CUDA left it).
+ */
+#ifndef ESP_H_
+#define ESP_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  ESP_OK = 0,
+  ESP_ERR_ARG = -1,       /* bad argument (null pointer, n < 0, P out of range, ...) */
+  ESP_ERR_CELL = -2,      /* det h <= 0 or a non-finite cell entry */
+  ESP_ERR_GRID = -3,      /* a mode with |k| <= c/r_c would reach |m_d| >= M_d/2 */
+  ESP_ERR_SUPPORT = -4,   /* stencil P >= M_d: the window would wrap onto itself */
+  ESP_ERR_NONFINITE = -5, /* a position or charge is NaN or Inf (that atom is skipped) */
+  ESP_ERR_CUDA = -6,      /* a CUDA runtime call failed */
+  ESP_ERR_CUFFT = -7,     /* a cuFFT call failed */
+  ESP_ERR_TIMEOUT = -8,   /* reserved: a bounded device wait gave up */
+  ESP_ERR_STATE = -9      /* call order: e.g. esp_forces_from_spectrum with no spectrum */
+};
+
+/* precision flags for esp_plan */
+enum {
+  ESP_FP64 = 0,      /* spread / FFT / scale / gather in FP64; pos, q, F are double */
+  ESP_FP32 = 1,      /* spread, FFT, gather and per-mode math in FP32; energy and virial
+                        sums in FP64; pos, q, F are float unless ESP_IO_F64 is given */
+  ESP_IO_F64 = 16    /* with ESP_FP32: pos, q and F are double */
+};
+
+typedef struct esp_plan_s* esp_plan_t;
+
+/* Results of one evaluation, host doubles. */
+typedef struct {
+  double energy_recip;      /* U_F, eq. (UF) with the gridded structure factor (Sec. 4.1) */
+  double energy_self;       /* U_self = -psi_0(0)/(2 C_0 r_c) sum q^2, eq. (selfen) */
+  double energy_bg;         /* U_cb + U_bb for a net charge, eq. (Corr) (0 if neutral) */
+  double virial_recip[9];   /* W_F = V P_F, eqs. (UFPree)/(tensoraniso): prefactor +1/(2V^2) */
+  double pressure_recip[9]; /* P_F = W_F / V */
+  double pressure_bg;       /* isotropic background pressure, Sec. 3.4 (times I) */
+  double volume;            /* det h */
+  double qsum;              /* sum q (net charge Q) */
+  double q2sum;             /* sum q^2 */
+} esp_result;
+
+/* Number of doubles in the device accumulator written by esp_step (see there). */
+#define ESP_ACCUM_LEN 16
+
+/*
+ * esp_plan - build a plan for N atoms in cell h on an M1 x M2 x M3 grid.
+ *   grid[3]  M_d >= 2; the real grid is row-major with the third index fastest.
+ *   w        stencil width P (grid points per dimension, Sec. 4.3), 3 <= P <= 12, P < M_d.
+ *   c        PSWF shape parameter c > 0 (Sec. 3.1; see esp_c_from_tolerance).
+ *   alpha    the split radius r_c in Angstrom (Sec. 3.1, eq. (decomposition)); ESP has
+ *            no Gaussian alpha, so this argument carries r_c.
+ *   precision ESP_FP64 or ESP_FP32 (optionally | ESP_IO_F64).
+ *   stream   cudaStream_t to run on (NULL = legacy default stream).
+ * Host set-up (FP64, once): psi_0^c by a Legendre-Galerkin eigen-solve, the piecewise
+ * polynomial window tables of Sec. 4.3 (Horner, degree chosen to the precision), the
+ * radial psi_0 / psi_0' tables for the Fourier kernel (Sec. 4.3), the 1D deconvolution
+ * tables 1/what_d(m)^2 (Sec. 4.2), cuFFT plans and all device workspace.
+ * Errors: ESP_ERR_ARG, ESP_ERR_CELL, ESP_ERR_GRID, ESP_ERR_SUPPORT, ESP_ERR_CUDA,
+ * ESP_ERR_CUFFT.  *out is NULL on failure.
+ */
+int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3], int w,
+             double c, double alpha, int precision, void* stream);
+
+/* NPT: change the cell (same N, grid, P, c, r_c); no allocation.  The spectrum kept for
+ * esp_forces_from_spectrum becomes stale.  Errors: ESP_ERR_CELL, ESP_ERR_GRID. */
+int esp_set_cell(esp_plan_t plan, const double cell[9]);
+
+/* Change the stream subsequent calls run on. */
+int esp_set_stream(esp_plan_t plan, void* stream);
+
+/*
+ * esp_step - the whole long-range step on the plan's stream, asynchronous:
+ * wrap + bin/sort, spread (eq. (gridding)), forward FFT, fused scaling + reduction
+ * (eqs. (diag), (PFfinal)) and, if forces != NULL, the inverse FFT and the gather of
+ * eq. (AD) (Appendix C, analytical differentiation).
+ *   pos, q    device arrays (N x 3 and N) of the plan's I/O type.
+ *   forces    device array N x 3 of the I/O type, original atom order, or NULL.
+ *   d_accum   device array of ESP_ACCUM_LEN doubles or NULL (then the plan's own).
+ *             On completion: [0] U_F, [1..6] W_F xx yy zz xy xz yz, [7] sum q,
+ *             [8] sum q^2, [9] number of skipped non-finite atoms.
+ * No host synchronisation.  Errors found on the host only (arguments); a non-finite
+ * input is reported through d_accum[9] (and by esp_energy_pressure).
+ */
+int esp_step(esp_plan_t plan, const void* pos, const void* q, void* forces, double* d_accum);
+
+/* Energy and pressure only (Algorithm 1: no inverse FFT, Sec. 4.1).  Synchronises the
+ * plan's stream and fills *out.  Keeps the spectrum so that an immediately following
+ * esp_forces_from_spectrum needs no second spread / forward FFT.
+ * Errors: ESP_ERR_ARG, ESP_ERR_NONFINITE, ESP_ERR_CUDA, ESP_ERR_CUFFT. */
+int esp_energy_pressure(esp_plan_t plan, const void* pos, const void* q, esp_result* out);
+
+/* Forces F_i = -dU_F/dr_i into the caller's device array (eq. (AD); the exact gradient of
+ * eq. (UFAnal) carries no factor 1/2, U_F being quadratic in the charges).  Device
+ * array N x 3 of the I/O type, original order.  Runs the full step.  Asynchronous. */
+int esp_forces(esp_plan_t plan, const void* pos, const void* q, void* forces);
+
+/* Forces from the spectrum kept by the last esp_energy_pressure (same pos, q, cell):
+ * scaling, inverse FFT and gather only.  ESP_ERR_STATE if no spectrum is kept. */
+int esp_forces_from_spectrum(esp_plan_t plan, void* forces);
+
+/* End-to-end call with HOST buffers: copies pos, q (I/O type) to the device, runs the
+ * full step, copies forces (may be NULL) back and fills *out (may be NULL).
+ * Synchronous.  pos/q/forces may be pageable or pinned host memory. */
+int esp_compute_host(esp_plan_t plan, const void* pos, const void* q, void* forces,
+                     esp_result* out);
+
+/* Convert a device accumulator (ESP_ACCUM_LEN doubles, already copied to the host) into
+ * an esp_result for this plan's cell and constants. */
+int esp_result_from_accum(esp_plan_t plan, const double accum_host[ESP_ACCUM_LEN],
+                          esp_result* out);
+
+/* Copy the plan's real grid (M1*M2*M3 values of the compute type; after esp_energy_pressure
+ * the spread charge rho_s, after a step with forces the potential phi) or its half
+ * spectrum (M1*M2*(M3/2+1) complex values) into a host buffer.  For tests. */
+int esp_copy_grid(esp_plan_t plan, void* host_dst);
+int esp_copy_spectrum(esp_plan_t plan, void* host_dst);
+
+/* Plan facts: [0] c, [1] r_c, [2] psi_0(0), [3] C_0, [4] lambda_0, [5] window table
+ * degree, [6] radial table degree, [7] max window fit error / psi_0(0), [8] max radial
+ * fit error / psi_0(0), [9] tiles, [10] tile T1, [11] T2, [12] T3, [13] kernel launches
+ * per full step, [14] background constant X = r_c^2/2 - int_0^{r_c} r phi_0.
+ * Writes min(len, 15) values. */
+int esp_plan_info(esp_plan_t plan, double* info, int len);
+
+/* Per-stage timing with CUDA events on the plan's stream.  esp_profile(plan, 1) creates
+ * the events and records one before and after every stage of each later step;
+ * esp_profile_read synchronises the stream and writes the last step's stage durations
+ * in ms, in the order: [0] memsets, [1] bin, [2] scan, [3] scatter, [4] grid zeroing,
+ * [5] spread, [6] forward FFT, [7] scale + reduce, [8] inverse FFT, [9] gather
+ * (stages that did not run read 0).  Writes min(len, 10) values. */
+int esp_profile(esp_plan_t plan, int enable);
+int esp_profile_read(esp_plan_t plan, double* stage_ms, int len);
+
+/* Release the plan (waits for its stream). NULL is accepted. */
+int esp_destroy(esp_plan_t plan);
+
+/* Message for the last error of this plan (or of the last failed esp_plan when plan is
+ * NULL).  Valid until the next call on the plan. */
+const char* esp_last_error(esp_plan_t plan);
+
+/* PSWF shape parameter c with psi_0^c(1) / psi_0^c(0) = delta (Sec. 5.1 tuning rule,
+ * read as a ratio to psi_0(0)), 0 < delta < 1; returns a negative value on bad input. */
+double esp_c_from_tolerance(double delta);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ESP_H_ */

@@ -1,0 +1,727 @@
+// C ABI of the ESP long-range step (declared in include/esp.h): plan construction on
+// the host in FP64 and the per-step launch sequence
+//   bin -> scan -> scatter -> spread -> cuFFT R2C -> scale+reduce [-> cuFFT C2R -> gather]
+// on the plan's stream.
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "esp.h"
+#include "esp_kernels.cuh"
+#include "esp_pswf.h"
+
+namespace {
+
+thread_local std::string g_plan_error;
+
+struct Buffer {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct esp_plan_s {
+  // configuration
+  bool fp64 = true;
+  bool io_double = true;
+  int64_t n = 0;
+  int M[3] = {0, 0, 0};
+  int H2 = 0;
+  int P = 0;
+  double c = 0.0, rc = 0.0;
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  // cell
+  double h[9] = {0};     // row-major h[r][c]
+  double hinv[9] = {0};  // row-major
+  double V = 0.0;
+  // PSWF constants
+  esp::Prolate pswf;
+  double A = 0.0;       // 4 pi / psi_0(0)
+  double selfc = 0.0;   // psi_0(0) / (2 C_0 r_c)
+  double Xbg = 0.0;     // r_c^2/2 - int_0^{r_c} r phi_0(r) dr
+  int deg = 0, rdeg = 0;
+  double fit_err = 0.0, rfit_err = 0.0;
+  // geometry
+  esp::TileGeom tg{};
+  esp::ScaleGeom sg{};
+  esp::GatherGeom gg{};
+  int ntiles = 0;
+  int scale_blocks = 0;
+  // device buffers
+  void* d_wtab = nullptr;
+  void* d_radtab = nullptr;
+  void* d_invw2 = nullptr;
+  void* d_grid = nullptr;
+  void* d_spec = nullptr;
+  int* d_count = nullptr;
+  int* d_offset = nullptr;
+  int* d_ptile = nullptr;
+  int* d_prank = nullptr;
+  int* d_plb = nullptr;
+  void* d_sorted_tq = nullptr;
+  int* d_sorted_lb = nullptr;
+  int* d_sorted_idx = nullptr;
+  double* d_accum = nullptr;
+  double* d_partials = nullptr;
+  unsigned int* d_counter = nullptr;
+  void* d_io_pos = nullptr;
+  void* d_io_q = nullptr;
+  void* d_io_f = nullptr;
+  double* h_accum = nullptr;  // pinned
+  cufftHandle fwd = 0, inv = 0;
+  bool have_fwd = false, have_inv = false;
+  bool spectrum_kept = false;
+  // per-stage CUDA events (esp_profile)
+  bool profiling = false;
+  cudaEvent_t ev[16] = {};
+  bool ev_used[16] = {};
+  std::string err;
+};
+
+namespace {
+
+int fail(esp_plan_t p, int code, const std::string& msg) {
+  if (p)
+    p->err = msg;
+  else
+    g_plan_error = msg;
+  return code;
+}
+
+int cuda_fail(esp_plan_t p, cudaError_t e, const char* what) {
+  return fail(p, ESP_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define ESP_CUDA(p, call)                                          \
+  do {                                                             \
+    cudaError_t e_ = (call);                                       \
+    if (e_ != cudaSuccess) return cuda_fail((p), e_, #call);       \
+  } while (0)
+
+#define ESP_CUFFT(p, call)                                                          \
+  do {                                                                              \
+    cufftResult r_ = (call);                                                        \
+    if (r_ != CUFFT_SUCCESS)                                                        \
+      return fail((p), ESP_ERR_CUFFT, std::string(#call) + " failed, cufftResult " + \
+                                           std::to_string((int)r_));                \
+  } while (0)
+
+// h from the column-major cell[9] (columns are the cell vectors); checks det h > 0.
+int set_cell_matrix(esp_plan_t p, const double cell[9], double h[9], double hinv[9],
+                    double* V) {
+  if (!cell) return fail(p, ESP_ERR_ARG, "cell is NULL");
+  for (int i = 0; i < 9; ++i)
+    if (!std::isfinite(cell[i])) return fail(p, ESP_ERR_CELL, "non-finite cell entry");
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) h[3 * r + c] = cell[3 * c + r];
+  const double c00 = h[4] * h[8] - h[5] * h[7];
+  const double c01 = h[5] * h[6] - h[3] * h[8];
+  const double c02 = h[3] * h[7] - h[4] * h[6];
+  const double det = h[0] * c00 + h[1] * c01 + h[2] * c02;
+  if (!(det > 0.0) || !std::isfinite(det)) return fail(p, ESP_ERR_CELL, "det h must be positive");
+  const double id = 1.0 / det;
+  hinv[0] = c00 * id;
+  hinv[1] = (h[2] * h[7] - h[1] * h[8]) * id;
+  hinv[2] = (h[1] * h[5] - h[2] * h[4]) * id;
+  hinv[3] = c01 * id;
+  hinv[4] = (h[0] * h[8] - h[2] * h[6]) * id;
+  hinv[5] = (h[2] * h[3] - h[0] * h[5]) * id;
+  hinv[6] = c02 * id;
+  hinv[7] = (h[1] * h[6] - h[0] * h[7]) * id;
+  hinv[8] = (h[0] * h[4] - h[1] * h[3]) * id;
+  *V = det;
+  return ESP_OK;
+}
+
+// Every mode with |k| <= K = c/r_c has |m_d| = |h_d . k| / 2pi <= |h_d| K / 2pi; require
+// that bound below M_d/2 so no such mode reaches the Nyquist index.
+int check_grid(esp_plan_t p, const double h[9], const int M[3], double c, double rc,
+               int mmax[3]) {
+  const double K = c / rc;
+  for (int d = 0; d < 3; ++d) {
+    const double len = std::sqrt(h[d] * h[d] + h[3 + d] * h[3 + d] + h[6 + d] * h[6 + d]);
+    const double bound = len * K / (2.0 * M_PI);
+    if (!(bound < 0.5 * M[d])) {
+      char buf[200];
+      std::snprintf(buf, sizeof buf,
+                    "grid too coarse in dimension %d: need M > |h_d| c / (pi r_c) = %.3f", d,
+                    2.0 * bound);
+      return fail(p, ESP_ERR_GRID, buf);
+    }
+    mmax[d] = std::min((int)std::floor(bound), (M[d] - 1) / 2);
+  }
+  return ESP_OK;
+}
+
+void update_cell_constants(esp_plan_t p) {
+  std::memcpy(p->tg.hinv, p->hinv, sizeof p->hinv);
+  for (int d = 0; d < 3; ++d)
+    for (int a = 0; a < 3; ++a) p->sg.b[3 * d + a] = 2.0 * M_PI * p->hinv[3 * d + a];
+  const double Mtot = (double)p->M[0] * p->M[1] * p->M[2];
+  p->sg.scale = 1.0 / (2.0 * p->V * Mtot * Mtot);
+  p->gg.g = p->tg;
+  p->gg.fscale = 1.0 / (p->V * Mtot * Mtot);
+}
+
+template <typename R>
+std::vector<R> to_type(const std::vector<double>& v) {
+  return std::vector<R>(v.begin(), v.end());
+}
+
+int upload(esp_plan_t p, void** dst, const std::vector<double>& src) {
+  const size_t es = p->fp64 ? 8 : 4;
+  ESP_CUDA(p, cudaMalloc(dst, std::max<size_t>(src.size(), 1) * es));
+  if (p->fp64) {
+    ESP_CUDA(p, cudaMemcpy(*dst, src.data(), src.size() * es, cudaMemcpyHostToDevice));
+  } else {
+    std::vector<float> f = to_type<float>(src);
+    ESP_CUDA(p, cudaMemcpy(*dst, f.data(), f.size() * es, cudaMemcpyHostToDevice));
+  }
+  return ESP_OK;
+}
+
+// Window polynomials (Sec. 4.3): for stencil point p and t in [0,1) the window value is
+// psi_0(u) with u = 2 (p + 1 - P/2 - t) / P; coefficients of (t - 1/2)^k, laid out
+// [w: k * P + p][dw: (deg+1) * P + k * P + p].  The degree grows until the fit is below
+// the precision's tolerance.
+int build_window_tables(esp_plan_t p, std::vector<double>& tab) {
+  const esp::Prolate& pr = p->pswf;
+  const int P = p->P;
+  const double tol = p->fp64 ? 3e-15 : 2e-8;
+  double dmax = 0.0;
+  for (int i = 0; i <= 200; ++i) dmax = std::max(dmax, std::fabs(pr.deriv(-1.0 + i / 100.0)));
+  for (int deg = 6; deg <= esp::kMaxDeg; ++deg) {
+    tab.assign(2 * (deg + 1) * P, 0.0);
+    double err = 0.0;
+    std::vector<double> coef(deg + 1);
+    for (int pp = 0; pp < P; ++pp) {
+      auto u_of = [P, pp](double t) { return 2.0 * (pp + 1.0 - 0.5 * P - t) / P; };
+      double e1 = esp::fit_piece([&](double t) { return pr.eval(u_of(t)); }, 0.0, 1.0, deg,
+                                 coef.data());
+      for (int k = 0; k <= deg; ++k) tab[k * P + pp] = coef[k];
+      double e2 = esp::fit_piece([&](double t) { return pr.deriv(u_of(t)); }, 0.0, 1.0, deg,
+                                 coef.data());
+      for (int k = 0; k <= deg; ++k) tab[(deg + 1) * P + k * P + pp] = coef[k];
+      err = std::max(err, std::max(e1 / pr.psi_at_0, e2 / dmax));
+    }
+    if (err <= tol || deg == esp::kMaxDeg) {
+      p->deg = deg;
+      p->fit_err = err;
+      if (err > 50 * tol) return fail(p, ESP_ERR_ARG, "window polynomial fit did not converge");
+      return ESP_OK;
+    }
+  }
+  return ESP_OK;
+}
+
+// Radial psi_0 and psi_0' on x in [0, 1] (the Fourier kernel of eq. (UF) and its
+// derivative in eq. (Far)), kRadialPieces pieces, coefficients of (x - centre)^k.
+int build_radial_tables(esp_plan_t p, std::vector<double>& tab) {
+  const esp::Prolate& pr = p->pswf;
+  const double tol = p->fp64 ? 3e-15 : 2e-8;
+  const int NR = esp::kRadialPieces;
+  double dmax = 0.0;
+  for (int i = 0; i <= 100; ++i) dmax = std::max(dmax, std::fabs(pr.deriv(i / 100.0)));
+  for (int deg = 6; deg <= esp::kMaxDeg; ++deg) {
+    tab.assign(2 * NR * (deg + 1), 0.0);
+    std::vector<double> coef(deg + 1);
+    double err = 0.0;
+    for (int j = 0; j < NR; ++j) {
+      const double lo = (double)j / NR, hi = (double)(j + 1) / NR;
+      double e1 = esp::fit_piece([&](double x) { return pr.eval(x); }, lo, hi, deg, coef.data());
+      for (int k = 0; k <= deg; ++k) tab[j * (deg + 1) + k] = coef[k];
+      double e2 = esp::fit_piece([&](double x) { return pr.deriv(x); }, lo, hi, deg, coef.data());
+      for (int k = 0; k <= deg; ++k) tab[(NR + j) * (deg + 1) + k] = coef[k];
+      err = std::max(err, std::max(e1 / pr.psi_at_0, e2 / std::max(dmax, 1e-300)));
+    }
+    if (err <= tol || deg == esp::kMaxDeg) {
+      p->rdeg = deg;
+      p->rfit_err = err;
+      if (err > 50 * tol) return fail(p, ESP_ERR_ARG, "radial polynomial fit did not converge");
+      return ESP_OK;
+    }
+  }
+  return ESP_OK;
+}
+
+// 1 / what_d(m)^2 with what_d(m) = int w_d(u) e^{-2 pi i m u} du
+//                                = omega_d int_{-1}^{1} psi_0(t) cos(2 pi m omega_d t) dt
+// (Sec. 4.2), evaluated here by Gauss-Legendre quadrature of the integral itself.
+void build_invw2(esp_plan_t p, std::vector<double>& out) {
+  const esp::Prolate& pr = p->pswf;
+  std::vector<double> x, w;
+  esp::gauss_legendre(160 + (int)std::ceil(2.0 * p->c), x, w);
+  std::vector<double> fx(x.size());
+  for (size_t i = 0; i < x.size(); ++i) fx[i] = pr.eval(x[i]) * w[i];
+  out.clear();
+  const int len[3] = {p->M[0], p->M[1], p->H2};
+  for (int d = 0; d < 3; ++d) {
+    const double om = p->P / (2.0 * p->M[d]);
+    for (int i = 0; i < len[d]; ++i) {
+      const int m = (d < 2 && 2 * i > p->M[d]) ? i - p->M[d] : i;
+      double s = 0.0;
+      for (size_t k = 0; k < x.size(); ++k) s += fx[k] * std::cos(2.0 * M_PI * m * om * x[k]);
+      const double wh = om * s;
+      out.push_back(wh != 0.0 ? 1.0 / (wh * wh) : 0.0);
+    }
+  }
+}
+
+void release(esp_plan_t p) {
+  if (!p) return;
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  void* bufs[] = {p->d_wtab,      p->d_radtab,    p->d_invw2,    p->d_grid,      p->d_spec,
+                  p->d_count,     p->d_offset,    p->d_ptile,    p->d_prank,     p->d_plb,
+                  p->d_sorted_tq, p->d_sorted_lb, p->d_sorted_idx, p->d_accum,   p->d_partials,
+                  p->d_counter,   p->d_io_pos,    p->d_io_q,     p->d_io_f};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (p->h_accum) cudaFreeHost(p->h_accum);
+  for (cudaEvent_t e : p->ev)
+    if (e) cudaEventDestroy(e);
+  if (p->have_fwd) cufftDestroy(p->fwd);
+  if (p->have_inv) cufftDestroy(p->inv);
+  delete p;
+}
+
+int fill_result(esp_plan_t p, const double* acc, esp_result* out) {
+  if (!out) return ESP_OK;
+  std::memset(out, 0, sizeof *out);
+  out->energy_recip = acc[0];
+  const double W[9] = {acc[1], acc[4], acc[5], acc[4], acc[2], acc[6], acc[5], acc[6], acc[3]};
+  for (int i = 0; i < 9; ++i) {
+    out->virial_recip[i] = W[i];
+    out->pressure_recip[i] = W[i] / p->V;
+  }
+  out->qsum = acc[7];
+  out->q2sum = acc[8];
+  out->energy_self = -p->selfc * acc[8];
+  out->energy_bg = -2.0 * M_PI * acc[7] * acc[7] / p->V * p->Xbg;
+  out->pressure_bg = out->energy_bg / p->V;
+  out->volume = p->V;
+  return ESP_OK;
+}
+
+// Stage boundaries for esp_profile: event i is recorded before stage i, event i+1 after.
+enum Stage { kPrep, kBin, kScan, kScatter, kZero, kSpread, kFftFwd, kScale, kFftInv, kGather, kNStage };
+
+inline void mark(esp_plan_t p, int i) {
+  if (p->profiling) {
+    cudaEventRecord(p->ev[i], p->stream);
+    p->ev_used[i] = true;
+  }
+}
+
+int run_step(esp_plan_t p, const void* pos, const void* q, void* forces, double* acc) {
+  cudaStream_t st = p->stream;
+  const bool fp64 = p->fp64;
+  const size_t es = fp64 ? 8 : 4;
+  const size_t Mtot = (size_t)p->M[0] * p->M[1] * p->M[2];
+  for (int i = 0; i <= kNStage; ++i) p->ev_used[i] = false;
+  mark(p, kPrep);
+  ESP_CUDA(p, cudaMemsetAsync(p->d_count, 0, sizeof(int) * (size_t)p->ntiles, st));
+  ESP_CUDA(p, cudaMemsetAsync(acc, 0, sizeof(double) * ESP_ACCUM_LEN, st));
+  mark(p, kBin);
+  ESP_CUDA(p, esp::launch_bin(p->io_double, pos, q, p->n, p->tg, p->d_count, p->d_ptile,
+                              p->d_prank, p->d_plb, acc, st));
+  mark(p, kScan);
+  ESP_CUDA(p, esp::launch_scan(p->d_count, p->d_offset, p->ntiles, st));
+  mark(p, kScatter);
+  ESP_CUDA(p, esp::launch_scatter(p->io_double, fp64, pos, q, p->n, p->tg, p->d_ptile,
+                                  p->d_prank, p->d_plb, p->d_offset, p->d_sorted_tq,
+                                  p->d_sorted_lb, p->d_sorted_idx, st));
+  mark(p, kZero);
+  ESP_CUDA(p, cudaMemsetAsync(p->d_grid, 0, es * Mtot, st));
+  mark(p, kSpread);
+  ESP_CUDA(p, esp::launch_spread(fp64, p->tg, p->ntiles, p->d_sorted_tq, p->d_sorted_lb,
+                                 p->d_offset, p->d_wtab, p->d_grid, st));
+  mark(p, kFftFwd);
+  if (fp64)
+    ESP_CUFFT(p, cufftExecD2Z(p->fwd, (cufftDoubleReal*)p->d_grid, (cufftDoubleComplex*)p->d_spec));
+  else
+    ESP_CUFFT(p, cufftExecR2C(p->fwd, (cufftReal*)p->d_grid, (cufftComplex*)p->d_spec));
+  const bool want_f = forces != nullptr;
+  mark(p, kScale);
+  ESP_CUDA(p, esp::launch_scale(fp64, want_f, p->sg, p->d_spec, p->d_invw2, p->d_radtab,
+                                p->d_partials, p->d_counter, acc, p->scale_blocks, st));
+  mark(p, kFftInv);
+  if (want_f) {
+    if (fp64)
+      ESP_CUFFT(p, cufftExecZ2D(p->inv, (cufftDoubleComplex*)p->d_spec, (cufftDoubleReal*)p->d_grid));
+    else
+      ESP_CUFFT(p, cufftExecC2R(p->inv, (cufftComplex*)p->d_spec, (cufftReal*)p->d_grid));
+    mark(p, kGather);
+    ESP_CUDA(p, esp::launch_gather(fp64, p->io_double, p->gg, p->ntiles, p->d_sorted_tq,
+                                   p->d_sorted_lb, p->d_sorted_idx, p->d_offset, p->d_wtab,
+                                   p->d_grid, forces, st));
+  }
+  mark(p, kNStage);
+  p->spectrum_kept = !want_f;
+  return ESP_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3], int w,
+             double c, double alpha, int precision, void* stream) {
+  if (!out) return fail(nullptr, ESP_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!grid) return fail(nullptr, ESP_ERR_ARG, "grid is NULL");
+  if (n < 0 || n > (int64_t)0x3fffffff) return fail(nullptr, ESP_ERR_ARG, "n out of range");
+  if (w < esp::kMinP || w > esp::kMaxP)
+    return fail(nullptr, ESP_ERR_ARG, "stencil width w must be in [3, 12]");
+  if (!(c > 0.0) || !std::isfinite(c)) return fail(nullptr, ESP_ERR_ARG, "c must be positive");
+  if (!(alpha > 0.0) || !std::isfinite(alpha))
+    return fail(nullptr, ESP_ERR_ARG, "alpha (= r_c) must be positive");
+  const int base = precision & 0xf;
+  if (base != ESP_FP64 && base != ESP_FP32) return fail(nullptr, ESP_ERR_ARG, "bad precision");
+  for (int d = 0; d < 3; ++d) {
+    if (grid[d] < 2 || grid[d] > 4096) return fail(nullptr, ESP_ERR_ARG, "grid size out of range");
+    if (w >= grid[d]) return fail(nullptr, ESP_ERR_SUPPORT, "stencil width must be below every M_d");
+  }
+  if ((int64_t)grid[0] * grid[1] * grid[2] > ((int64_t)1 << 31))
+    return fail(nullptr, ESP_ERR_ARG, "grid too large");
+
+  esp_plan_t p = new esp_plan_s();
+  p->fp64 = (base == ESP_FP64);
+  p->io_double = p->fp64 || (precision & ESP_IO_F64);
+  p->n = n;
+  for (int d = 0; d < 3; ++d) p->M[d] = grid[d];
+  p->H2 = grid[2] / 2 + 1;
+  p->P = w;
+  p->c = c;
+  p->rc = alpha;
+  p->stream = (cudaStream_t)stream;
+  int rc;
+  auto bail = [&](int code) {
+    g_plan_error = p->err;
+    release(p);
+    return code;
+  };
+  if ((rc = set_cell_matrix(p, cell, p->h, p->hinv, &p->V)) != ESP_OK) return bail(rc);
+  if ((rc = check_grid(p, p->h, p->M, c, alpha, p->sg.mmax)) != ESP_OK) return bail(rc);
+  if (!p->pswf.solve(c)) return bail(fail(p, ESP_ERR_ARG, "PSWF eigen-solve failed"));
+  const esp::Prolate& pr = p->pswf;
+  p->A = 4.0 * M_PI / pr.psi_at_0;  // 2 pi lambda_0 / C_0 with lambda_0 psi_0(0) = 2 C_0
+  p->selfc = pr.psi_at_0 / (2.0 * pr.C0 * alpha);
+  {
+    std::vector<double> x, wq;
+    esp::gauss_legendre(96, x, wq);
+    double s = 0.0;
+    for (size_t i = 0; i < x.size(); ++i) {
+      const double u = 0.5 * (x[i] + 1.0);
+      s += 0.5 * wq[i] * u * u * pr.eval(u);
+    }
+    p->Xbg = alpha * alpha / (2.0 * pr.C0) * s;
+  }
+  std::vector<double> wtab, rtab, invw2;
+  if ((rc = build_window_tables(p, wtab)) != ESP_OK) return bail(rc);
+  if ((rc = build_radial_tables(p, rtab)) != ESP_OK) return bail(rc);
+  build_invw2(p, invw2);
+
+  // tile geometry: 8 x 8 stencil bases in the first two dimensions; in the third the
+  // padded row T + P - 1 fills a shared-memory pitch of 24 (P <= 9) or 40 words
+  esp::TileGeom& g = p->tg;
+  for (int d = 0; d < 3; ++d) g.M[d] = p->M[d];
+  g.P = w;
+  g.T[0] = std::min(8, p->M[0]);
+  g.T[1] = std::min(8, p->M[1]);
+  g.T[2] = std::min(w <= 9 ? 25 - w : 41 - w, p->M[2]);
+  p->ntiles = 1;
+  for (int d = 0; d < 3; ++d) {
+    g.nt[d] = (p->M[d] + g.T[d] - 1) / g.T[d];
+    g.E[d] = g.T[d] + w - 1;
+    p->ntiles *= g.nt[d];
+  }
+  {
+    int e = (g.E[2] + 7) / 8 * 8;
+    if ((e / 8) % 2 == 0) e += 8;
+    g.E3p = e;
+  }
+  g.deg = p->deg;
+
+  esp::ScaleGeom& s = p->sg;
+  for (int d = 0; d < 3; ++d) s.M[d] = p->M[d];
+  s.H2 = p->H2;
+  s.rdeg = p->rdeg;
+  s.K2 = (c / alpha) * (c / alpha);
+  s.x_per_k = alpha / c;
+  s.A = p->A;
+  update_cell_constants(p);
+
+  int dev = 0;
+  cudaGetDevice(&dev);
+  p->device = dev;
+  int sms = 152;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  p->scale_blocks = sms * 4;
+
+  const size_t es = p->fp64 ? 8 : 4;
+  const size_t io_es = p->io_double ? 8 : 4;
+  const size_t Mtot = (size_t)p->M[0] * p->M[1] * p->M[2];
+  const size_t nspec = (size_t)p->M[0] * p->M[1] * p->H2;
+  const size_t nn = std::max<int64_t>(n, 1);
+  if ((rc = upload(p, &p->d_wtab, wtab)) != ESP_OK) return bail(rc);
+  if ((rc = upload(p, &p->d_radtab, rtab)) != ESP_OK) return bail(rc);
+  if ((rc = upload(p, &p->d_invw2, invw2)) != ESP_OK) return bail(rc);
+#define ALLOC(ptr, bytes)                                                    \
+  do {                                                                       \
+    cudaError_t e_ = cudaMalloc((void**)&(ptr), (bytes));                    \
+    if (e_ != cudaSuccess) return bail(cuda_fail(p, e_, "cudaMalloc " #ptr)); \
+  } while (0)
+  ALLOC(p->d_grid, es * Mtot);
+  ALLOC(p->d_spec, 2 * es * nspec);
+  ALLOC(p->d_count, sizeof(int) * p->ntiles);
+  ALLOC(p->d_offset, sizeof(int) * (p->ntiles + 1));
+  ALLOC(p->d_ptile, sizeof(int) * nn);
+  ALLOC(p->d_prank, sizeof(int) * nn);
+  ALLOC(p->d_plb, sizeof(int) * nn);
+  ALLOC(p->d_sorted_tq, 4 * es * nn);
+  ALLOC(p->d_sorted_lb, sizeof(int) * nn);
+  ALLOC(p->d_sorted_idx, sizeof(int) * nn);
+  ALLOC(p->d_accum, sizeof(double) * ESP_ACCUM_LEN);
+  ALLOC(p->d_partials, sizeof(double) * 8 * p->scale_blocks);
+  ALLOC(p->d_counter, sizeof(unsigned int));
+#undef ALLOC
+  (void)io_es;
+  {
+    cudaError_t e = cudaMemset(p->d_counter, 0, sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemset(p->d_accum, 0, sizeof(double) * ESP_ACCUM_LEN);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_accum, sizeof(double) * ESP_ACCUM_LEN);
+    if (e != cudaSuccess) return bail(cuda_fail(p, e, "plan workspace set-up"));
+  }
+  {
+    cufftResult r1 = cufftPlan3d(&p->fwd, p->M[0], p->M[1], p->M[2], p->fp64 ? CUFFT_D2Z : CUFFT_R2C);
+    if (r1 != CUFFT_SUCCESS) return bail(fail(p, ESP_ERR_CUFFT, "cufftPlan3d (forward) failed"));
+    p->have_fwd = true;
+    cufftResult r2 = cufftPlan3d(&p->inv, p->M[0], p->M[1], p->M[2], p->fp64 ? CUFFT_Z2D : CUFFT_C2R);
+    if (r2 != CUFFT_SUCCESS) return bail(fail(p, ESP_ERR_CUFFT, "cufftPlan3d (inverse) failed"));
+    p->have_inv = true;
+    if (cufftSetStream(p->fwd, p->stream) != CUFFT_SUCCESS ||
+        cufftSetStream(p->inv, p->stream) != CUFFT_SUCCESS)
+      return bail(fail(p, ESP_ERR_CUFFT, "cufftSetStream failed"));
+  }
+  {
+    const size_t ss = esp::spread_smem_bytes(p->fp64, g), gs = esp::gather_smem_bytes(p->fp64, g);
+    if (ss > 227 * 1024 || gs > 227 * 1024)
+      return bail(fail(p, ESP_ERR_ARG, "tile does not fit in shared memory"));
+    cudaError_t e = esp::configure_kernels(p->fp64, w, ss, gs);
+    if (e != cudaSuccess) return bail(cuda_fail(p, e, "cudaFuncSetAttribute"));
+  }
+  *out = p;
+  return ESP_OK;
+}
+
+int esp_set_cell(esp_plan_t p, const double cell[9]) {
+  if (!p) return fail(nullptr, ESP_ERR_ARG, "plan is NULL");
+  double h[9], hinv[9], V;
+  int rc;
+  if ((rc = set_cell_matrix(p, cell, h, hinv, &V)) != ESP_OK) return rc;
+  int mmax[3];
+  if ((rc = check_grid(p, h, p->M, p->c, p->rc, mmax)) != ESP_OK) return rc;
+  std::memcpy(p->h, h, sizeof h);
+  std::memcpy(p->hinv, hinv, sizeof hinv);
+  p->V = V;
+  for (int d = 0; d < 3; ++d) p->sg.mmax[d] = mmax[d];
+  update_cell_constants(p);
+  p->spectrum_kept = false;
+  return ESP_OK;
+}
+
+int esp_set_stream(esp_plan_t p, void* stream) {
+  if (!p) return fail(nullptr, ESP_ERR_ARG, "plan is NULL");
+  p->stream = (cudaStream_t)stream;
+  if (cufftSetStream(p->fwd, p->stream) != CUFFT_SUCCESS ||
+      cufftSetStream(p->inv, p->stream) != CUFFT_SUCCESS)
+    return fail(p, ESP_ERR_CUFFT, "cufftSetStream failed");
+  return ESP_OK;
+}
+
+int esp_step(esp_plan_t p, const void* pos, const void* q, void* forces, double* d_accum) {
+  if (!p) return fail(nullptr, ESP_ERR_ARG, "plan is NULL");
+  if (p->n > 0 && (!pos || !q)) return fail(p, ESP_ERR_ARG, "pos or q is NULL");
+  DeviceGuard guard(p->device);
+  return run_step(p, pos, q, forces, d_accum ? d_accum : p->d_accum);
+}
+
+int esp_energy_pressure(esp_plan_t p, const void* pos, const void* q, esp_result* out) {
+  if (!p) return fail(nullptr, ESP_ERR_ARG, "plan is NULL");
+  if (!out) return fail(p, ESP_ERR_ARG, "out is NULL");
+  if (p->n > 0 && (!pos || !q)) return fail(p, ESP_ERR_ARG, "pos or q is NULL");
+  DeviceGuard guard(p->device);
+  int rc = run_step(p, pos, q, nullptr, p->d_accum);
+  if (rc != ESP_OK) return rc;
+  ESP_CUDA(p, cudaMemcpyAsync(p->h_accum, p->d_accum, sizeof(double) * ESP_ACCUM_LEN,
+                              cudaMemcpyDeviceToHost, p->stream));
+  ESP_CUDA(p, cudaStreamSynchronize(p->stream));
+  fill_result(p, p->h_accum, out);
+  if (p->h_accum[9] > 0.0) {
+    p->spectrum_kept = false;
+    return fail(p, ESP_ERR_NONFINITE, "non-finite position or charge");
+  }
+  return ESP_OK;
+}
+
+int esp_forces(esp_plan_t p, const void* pos, const void* q, void* forces) {
+  if (!p) return fail(nullptr, ESP_ERR_ARG, "plan is NULL");
+  if (p->n > 0 && (!pos || !q || !forces)) return fail(p, ESP_ERR_ARG, "NULL argument");
+  DeviceGuard guard(p->device);
+  return run_step(p, pos, q, forces ? forces : nullptr, p->d_accum);
+}
+
+int esp_forces_from_spectrum(esp_plan_t p, void* forces) {
+  if (!p) return fail(nullptr, ESP_ERR_ARG, "plan is NULL");
+  if (p->n > 0 && !forces) return fail(p, ESP_ERR_ARG, "forces is NULL");
+  if (!p->spectrum_kept) return fail(p, ESP_ERR_STATE, "no spectrum kept for these positions");
+  DeviceGuard guard(p->device);
+  cudaStream_t st = p->stream;
+  const bool fp64 = p->fp64;
+  ESP_CUDA(p, esp::launch_scale(fp64, true, p->sg, p->d_spec, p->d_invw2, p->d_radtab,
+                                p->d_partials, p->d_counter, p->d_accum, p->scale_blocks, st));
+  if (fp64)
+    ESP_CUFFT(p, cufftExecZ2D(p->inv, (cufftDoubleComplex*)p->d_spec, (cufftDoubleReal*)p->d_grid));
+  else
+    ESP_CUFFT(p, cufftExecC2R(p->inv, (cufftComplex*)p->d_spec, (cufftReal*)p->d_grid));
+  ESP_CUDA(p, esp::launch_gather(fp64, p->io_double, p->gg, p->ntiles, p->d_sorted_tq,
+                                 p->d_sorted_lb, p->d_sorted_idx, p->d_offset, p->d_wtab,
+                                 p->d_grid, forces, st));
+  p->spectrum_kept = false;
+  return ESP_OK;
+}
+
+int esp_compute_host(esp_plan_t p, const void* pos, const void* q, void* forces,
+                     esp_result* out) {
+  if (!p) return fail(nullptr, ESP_ERR_ARG, "plan is NULL");
+  if (p->n > 0 && (!pos || !q)) return fail(p, ESP_ERR_ARG, "pos or q is NULL");
+  DeviceGuard guard(p->device);
+  const size_t io_es = p->io_double ? 8 : 4;
+  const size_t nn = (size_t)std::max<int64_t>(p->n, 1);
+  if (!p->d_io_pos) {
+    ESP_CUDA(p, cudaMalloc(&p->d_io_pos, 3 * io_es * nn));
+    ESP_CUDA(p, cudaMalloc(&p->d_io_q, io_es * nn));
+    ESP_CUDA(p, cudaMalloc(&p->d_io_f, 3 * io_es * nn));
+  }
+  cudaStream_t st = p->stream;
+  if (p->n > 0) {
+    ESP_CUDA(p, cudaMemcpyAsync(p->d_io_pos, pos, 3 * io_es * p->n, cudaMemcpyHostToDevice, st));
+    ESP_CUDA(p, cudaMemcpyAsync(p->d_io_q, q, io_es * p->n, cudaMemcpyHostToDevice, st));
+  }
+  int rc = run_step(p, p->d_io_pos, p->d_io_q, forces ? p->d_io_f : nullptr, p->d_accum);
+  if (rc != ESP_OK) return rc;
+  ESP_CUDA(p, cudaMemcpyAsync(p->h_accum, p->d_accum, sizeof(double) * ESP_ACCUM_LEN,
+                              cudaMemcpyDeviceToHost, st));
+  if (forces && p->n > 0)
+    ESP_CUDA(p, cudaMemcpyAsync(forces, p->d_io_f, 3 * io_es * p->n, cudaMemcpyDeviceToHost, st));
+  ESP_CUDA(p, cudaStreamSynchronize(st));
+  fill_result(p, p->h_accum, out);
+  if (p->h_accum[9] > 0.0) return fail(p, ESP_ERR_NONFINITE, "non-finite position or charge");
+  return ESP_OK;
+}
+
+int esp_result_from_accum(esp_plan_t p, const double accum_host[ESP_ACCUM_LEN],
+                          esp_result* out) {
+  if (!p || !accum_host || !out) return fail(p, ESP_ERR_ARG, "NULL argument");
+  return fill_result(p, accum_host, out);
+}
+
+int esp_copy_grid(esp_plan_t p, void* host_dst) {
+  if (!p || !host_dst) return fail(p, ESP_ERR_ARG, "NULL argument");
+  DeviceGuard guard(p->device);
+  const size_t es = p->fp64 ? 8 : 4;
+  const size_t Mtot = (size_t)p->M[0] * p->M[1] * p->M[2];
+  ESP_CUDA(p, cudaStreamSynchronize(p->stream));
+  ESP_CUDA(p, cudaMemcpy(host_dst, p->d_grid, es * Mtot, cudaMemcpyDeviceToHost));
+  return ESP_OK;
+}
+
+int esp_copy_spectrum(esp_plan_t p, void* host_dst) {
+  if (!p || !host_dst) return fail(p, ESP_ERR_ARG, "NULL argument");
+  DeviceGuard guard(p->device);
+  const size_t es = p->fp64 ? 8 : 4;
+  const size_t ns = (size_t)p->M[0] * p->M[1] * p->H2;
+  ESP_CUDA(p, cudaStreamSynchronize(p->stream));
+  ESP_CUDA(p, cudaMemcpy(host_dst, p->d_spec, 2 * es * ns, cudaMemcpyDeviceToHost));
+  return ESP_OK;
+}
+
+int esp_plan_info(esp_plan_t p, double* info, int len) {
+  if (!p || !info || len < 0) return fail(p, ESP_ERR_ARG, "NULL argument");
+  const double v[15] = {p->c,
+                        p->rc,
+                        p->pswf.psi_at_0,
+                        p->pswf.C0,
+                        p->pswf.lambda0,
+                        (double)p->deg,
+                        (double)p->rdeg,
+                        p->fit_err,
+                        p->rfit_err,
+                        (double)p->ntiles,
+                        (double)p->tg.T[0],
+                        (double)p->tg.T[1],
+                        (double)p->tg.T[2],
+                        6.0,
+                        p->Xbg};
+  for (int i = 0; i < std::min(len, 15); ++i) info[i] = v[i];
+  return ESP_OK;
+}
+
+int esp_profile(esp_plan_t p, int enable) {
+  if (!p) return fail(nullptr, ESP_ERR_ARG, "plan is NULL");
+  if (enable && !p->ev[0]) {
+    DeviceGuard guard(p->device);
+    for (int i = 0; i <= kNStage; ++i) ESP_CUDA(p, cudaEventCreate(&p->ev[i]));
+  }
+  p->profiling = enable != 0;
+  return ESP_OK;
+}
+
+int esp_profile_read(esp_plan_t p, double* stage_ms, int len) {
+  if (!p || !stage_ms) return fail(p, ESP_ERR_ARG, "NULL argument");
+  if (!p->profiling) return fail(p, ESP_ERR_STATE, "profiling is off");
+  DeviceGuard guard(p->device);
+  ESP_CUDA(p, cudaStreamSynchronize(p->stream));
+  for (int i = 0; i < std::min(len, (int)kNStage); ++i) {
+    stage_ms[i] = 0.0;
+    int j = i + 1;  // the next recorded boundary ends stage i
+    while (j <= kNStage && !p->ev_used[j]) ++j;
+    if (!p->ev_used[i] || j > kNStage) continue;
+    float ms = 0.f;
+    ESP_CUDA(p, cudaEventElapsedTime(&ms, p->ev[i], p->ev[j]));
+    stage_ms[i] = ms;
+  }
+  return ESP_OK;
+}
+
+int esp_destroy(esp_plan_t p) {
+  release(p);
+  return ESP_OK;
+}
+
+const char* esp_last_error(esp_plan_t p) {
+  return p ? p->err.c_str() : g_plan_error.c_str();
+}
+
+double esp_c_from_tolerance(double delta) { return esp::c_from_tolerance(delta); }
+
+}  // extern "C"

@@ -1,0 +1,687 @@
+// sm_103a kernels of the ESP long-range step (Sec. 4.1 Algorithm 1 and Appendix C):
+//   k_bin      wrap s = h^{-1} r into [0,1), stencil base (Sec. 4.3), tile id, rank
+//   k_scan     exclusive scan of tile counts (one CTA)
+//   k_scatter  counting-sort scatter of (fractional offset t, q) by tile
+//   k_spread   eq. (gridding): each CTA accumulates its tile's padded P^3 footprints in
+//              shared memory, then adds the block to the global grid
+//   k_scale    eqs. (diag)/(PFfinal): per half-spectrum mode the deconvolved weight, the
+//              Fourier kernel and the 3x3 pressure kernel, FP64 reduction; optionally
+//              writes G X for the force path (eq. (UFAnal))
+//   k_gather   eq. (AD): per atom, the P^3 contraction of the potential grid with the
+//              window gradient, staged through a shared-memory tile
+#include "esp_kernels.cuh"
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace esp {
+
+namespace {
+
+template <typename R>
+struct Vec4;
+template <>
+struct Vec4<float> {
+  using T = float4;
+};
+template <>
+struct Vec4<double> {
+  using T = double4;
+};
+
+template <typename R>
+struct Cplx;
+template <>
+struct Cplx<float> {
+  using T = float2;
+};
+template <>
+struct Cplx<double> {
+  using T = double2;
+};
+
+__device__ __forceinline__ int wrap_index(int i, int m) {
+  i %= m;
+  return i < 0 ? i + m : i;
+}
+
+// Reduced coordinate, grid coordinate and stencil base for one dimension (Sec. 4.3):
+// P even: base = floor(x) - P/2 + 1, t = x - floor(x); P odd: base = floor(x + 1/2) -
+// (P-1)/2, t = x + 1/2 - floor(x + 1/2).  Either way the stencil point p sits at offset
+// g - x = p + 1 - P/2 - t from the atom, in grid units.  FP64 on every path so that the
+// integer decision matches the FP64 oracle.
+__device__ __forceinline__ void stencil_base(double s, int M, int P, int* base, double* t) {
+  s = __dsub_rn(s, floor(s));
+  if (s >= 1.0) s = 0.0;
+  double x = __dmul_rn((double)M, s);
+  if (P & 1) x = __dadd_rn(x, 0.5);
+  const double fl = floor(x);
+  *t = x - fl;
+  const int b = (int)fl - ((P & 1) ? (P - 1) / 2 : P / 2 - 1);
+  *base = wrap_index(b, M);
+}
+
+// s_d = (h^{-1} r)_d with explicitly rounded operations, so that every kernel that
+// recomputes it gets the same bits
+__device__ __forceinline__ double reduced_coord(const double* hinv_row, const double r[3]) {
+  return __fma_rn(hinv_row[0], r[0], __fma_rn(hinv_row[1], r[1], __dmul_rn(hinv_row[2], r[2])));
+}
+
+template <typename IO>
+__device__ __forceinline__ bool load_atom(const IO* pos, const IO* q, int64_t i, double r[3],
+                                          double* qi) {
+  r[0] = (double)pos[3 * i + 0];
+  r[1] = (double)pos[3 * i + 1];
+  r[2] = (double)pos[3 * i + 2];
+  *qi = (double)q[i];
+  return isfinite(r[0]) && isfinite(r[1]) && isfinite(r[2]) && isfinite(*qi);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------------------------------
+template <typename IO>
+__global__ void __launch_bounds__(kThreads) k_bin(const IO* __restrict__ pos,
+                                                  const IO* __restrict__ q, int64_t n,
+                                                  TileGeom g, int* __restrict__ tile_count,
+                                                  int* __restrict__ ptile,
+                                                  int* __restrict__ prank,
+                                                  int* __restrict__ plb,
+                                                  double* __restrict__ accum) {
+  double sq = 0.0, sq2 = 0.0, bad = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    double r[3], qi;
+    if (!load_atom(pos, q, i, r, &qi)) {
+      ptile[i] = -1;
+      bad += 1.0;
+      continue;
+    }
+    int tc[3], lb[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      int b;
+      double t;
+      stencil_base(reduced_coord(&g.hinv[3 * d], r), g.M[d], g.P, &b, &t);
+      tc[d] = b / g.T[d];
+      lb[d] = b - tc[d] * g.T[d];
+    }
+    const int tile = (tc[0] * g.nt[1] + tc[1]) * g.nt[2] + tc[2];
+    ptile[i] = tile;
+    plb[i] = lb[0] | (lb[1] << 10) | (lb[2] << 20);
+    prank[i] = atomicAdd(&tile_count[tile], 1);
+    sq += qi;
+    sq2 += qi * qi;
+  }
+  __shared__ double red[3][kThreads / 32];
+  sq = warp_sum(sq);
+  sq2 = warp_sum(sq2);
+  bad = warp_sum(bad);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][wid] = sq;
+    red[1][wid] = sq2;
+    red[2][wid] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0, c = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      a += red[0][w];
+      b += red[1][w];
+      c += red[2][w];
+    }
+    if (a != 0.0) atomicAdd(&accum[7], a);
+    if (b != 0.0) atomicAdd(&accum[8], b);
+    if (c != 0.0) atomicAdd(&accum[9], c);
+  }
+}
+
+// exclusive scan of count[0..n) into offset[0..n], one CTA of kThreads threads
+__global__ void __launch_bounds__(kThreads) k_scan(const int* __restrict__ count,
+                                                   int* __restrict__ offset, int n) {
+  __shared__ int warp_tot[kThreads / 32];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int base = 0; base < n; base += kThreads) {
+    const int i = base + threadIdx.x;
+    const int v = (i < n) ? count[i] : 0;
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int t = (lane < kThreads / 32) ? warp_tot[lane] : 0;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      if (lane < kThreads / 32) warp_tot[lane] = t;  // inclusive prefix of warp totals
+    }
+    __syncthreads();
+    const int before = carry + (wid > 0 ? warp_tot[wid - 1] : 0);
+    if (i < n) offset[i] = before + x - v;
+    __syncthreads();
+    if (threadIdx.x == kThreads - 1) carry = before + x;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) offset[n] = carry;
+}
+
+template <typename IO, typename R>
+__global__ void __launch_bounds__(kThreads) k_scatter(
+    const IO* __restrict__ pos, const IO* __restrict__ q, int64_t n, TileGeom g,
+    const int* __restrict__ ptile, const int* __restrict__ prank, const int* __restrict__ plb,
+    const int* __restrict__ offset, typename Vec4<R>::T* __restrict__ sorted_tq, int* __restrict__ sorted_lb,
+    int* __restrict__ sorted_idx) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int tile = ptile[i];
+    if (tile < 0) continue;
+    double r[3], qi;
+    load_atom(pos, q, i, r, &qi);
+    int b[3];
+    double t[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) stencil_base(reduced_coord(&g.hinv[3 * d], r), g.M[d], g.P, &b[d], &t[d]);
+    const int dst = offset[tile] + prank[i];
+    typename Vec4<R>::T v;
+    v.x = (R)t[0];
+    v.y = (R)t[1];
+    v.z = (R)t[2];
+    v.w = (R)qi;
+    sorted_tq[dst] = v;
+    sorted_lb[dst] = plb[i];  // local base from the binning pass: indices never disagree
+    sorted_idx[dst] = (int)i;
+  }
+}
+
+// Horner evaluation of the window polynomial for stencil point p at offset t in [0,1):
+// coefficients tab[k * P + p] of (t - 1/2)^k.
+template <typename R>
+__device__ __forceinline__ R horner_window(const R* tab, int deg, int P, int p, R t) {
+  const R tau = t - R(0.5);
+  R v = tab[deg * P + p];
+  for (int k = deg - 1; k >= 0; --k) v = fma(v, tau, tab[k * P + p]);
+  return v;
+}
+
+template <typename R>
+__device__ __forceinline__ R tq_comp(const typename Vec4<R>::T& v, int d) {
+  return d == 0 ? v.x : (d == 1 ? v.y : v.z);
+}
+
+// ---------------------------------------------------------------------------------------
+template <typename R, int P>
+__global__ void __launch_bounds__(kThreads) k_spread(
+    const typename Vec4<R>::T* __restrict__ sorted_tq, const int* __restrict__ sorted_lb,
+    const int* __restrict__ offset, TileGeom g, const R* __restrict__ wtab,
+    R* __restrict__ grid) {
+  const int tile = blockIdx.x;
+  const int start = offset[tile], end = offset[tile + 1];
+  if (start == end) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* acc = reinterpret_cast<R*>(smem_raw);
+  const int E0 = g.E[0], E1 = g.E[1], E3p = g.E3p;
+  const int vol = E0 * E1 * E3p;
+  R* tab = acc + vol;
+  R* wbuf = tab + (g.deg + 1) * P;
+  for (int e = threadIdx.x; e < vol; e += blockDim.x) acc[e] = R(0);
+  for (int e = threadIdx.x; e < (g.deg + 1) * P; e += blockDim.x) tab[e] = wtab[e];
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  R* wb = wbuf + wid * 3 * P;
+  for (int j = start + wid; j < end; j += nw) {
+    const typename Vec4<R>::T v = sorted_tq[j];
+    const int lb = sorted_lb[j];
+    for (int e = lane; e < 3 * P; e += 32) {
+      const int d = e / P, p = e - d * P;
+      R w = horner_window(tab, g.deg, P, p, tq_comp<R>(v, d));
+      if (d == 0) w *= v.w;
+      wb[e] = w;
+    }
+    __syncwarp();
+    const int l0 = lb & 1023, l1 = (lb >> 10) & 1023, l2 = (lb >> 20) & 1023;
+    const int base = (l0 * E1 + l1) * E3p + l2;
+#pragma unroll 4
+    for (int nidx = lane; nidx < P * P * P; nidx += 32) {
+      const int i = nidx / (P * P);
+      const int jj = (nidx / P) % P;
+      const int k = nidx % P;
+      atomicAdd(&acc[base + (i * E1 + jj) * E3p + k], wb[i] * wb[P + jj] * wb[2 * P + k]);
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+
+  // add the padded block into the periodic global grid
+  const int t2 = tile % g.nt[2];
+  const int t1 = (tile / g.nt[2]) % g.nt[1];
+  const int t0 = tile / (g.nt[2] * g.nt[1]);
+  const int o0 = t0 * g.T[0], o1 = t1 * g.T[1], o2 = t2 * g.T[2];
+  const int E2 = g.E[2];
+  const int nflush = E0 * E1 * E2;
+  for (int e = threadIdx.x; e < nflush; e += blockDim.x) {
+    const int c = e % E2;
+    const int ab = e / E2;
+    const int b = ab % E1;
+    const int a = ab / E1;
+    const R val = acc[(a * E1 + b) * E3p + c];
+    if (val != R(0)) {
+      const int gi = wrap_index(o0 + a, g.M[0]);
+      const int gj = wrap_index(o1 + b, g.M[1]);
+      const int gk = wrap_index(o2 + c, g.M[2]);
+      atomicAdd(&grid[((int64_t)gi * g.M[1] + gj) * g.M[2] + gk], val);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Radial psi_0 / psi_0' on x in [0, 1] by kRadialPieces Horner pieces in (x - centre).
+template <typename R>
+__device__ __forceinline__ void radial_eval(const R* __restrict__ rt, int rdeg, R x, R* psi,
+                                            R* dpsi) {
+  int piece = (int)(x * R(kRadialPieces));
+  piece = piece < 0 ? 0 : (piece >= kRadialPieces ? kRadialPieces - 1 : piece);
+  const R tau = x - (R(piece) + R(0.5)) / R(kRadialPieces);
+  const R* a = rt + piece * (rdeg + 1);
+  const R* b = rt + (kRadialPieces + piece) * (rdeg + 1);
+  R u = a[rdeg], w = b[rdeg];
+  for (int k = rdeg - 1; k >= 0; --k) {
+    u = fma(u, tau, a[k]);
+    w = fma(w, tau, b[k]);
+  }
+  *psi = u;
+  *dpsi = w;
+}
+
+template <typename R, bool WRITE>
+__global__ void __launch_bounds__(kThreads) k_scale(typename Cplx<R>::T* __restrict__ spec,
+                                                    ScaleGeom s, const R* __restrict__ invw2,
+                                                    const R* __restrict__ radtab,
+                                                    double* __restrict__ partials,
+                                                    unsigned int* __restrict__ counter,
+                                                    double* __restrict__ accum) {
+  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  const int64_t total = (int64_t)s.M[0] * s.M[1] * s.H2;
+  const R* iw0 = invw2;
+  const R* iw1 = invw2 + s.M[0];
+  const R* iw2 = invw2 + s.M[0] + s.M[1];
+  for (int64_t nidx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; nidx < total;
+       nidx += (int64_t)gridDim.x * blockDim.x) {
+    const int i2 = (int)(nidx % s.H2);
+    const int64_t rr = nidx / s.H2;
+    const int i1 = (int)(rr % s.M[1]);
+    const int i0 = (int)(rr / s.M[1]);
+    const int m0 = (2 * i0 <= s.M[0]) ? i0 : i0 - s.M[0];
+    const int m1 = (2 * i1 <= s.M[1]) ? i1 : i1 - s.M[1];
+    const int m2 = i2;
+    bool inside = abs(m0) <= s.mmax[0] && abs(m1) <= s.mmax[1] && m2 <= s.mmax[2] &&
+                  (m0 | m1 | m2) != 0;
+    R kx = R(0), ky = R(0), kz = R(0), k2 = R(0);
+    if (inside) {
+      kx = R(m0 * s.b[0] + m1 * s.b[3] + m2 * s.b[6]);
+      ky = R(m0 * s.b[1] + m1 * s.b[4] + m2 * s.b[7]);
+      kz = R(m0 * s.b[2] + m1 * s.b[5] + m2 * s.b[8]);
+      k2 = kx * kx + ky * ky + kz * kz;
+      // the in-sphere decision is taken in FP64 (FP32 only when far from the boundary)
+      const double K2 = s.K2;
+      if (sizeof(R) == 8 || fabs((double)k2 - K2) <= 1e-5 * K2) {
+        const double dx = m0 * s.b[0] + m1 * s.b[3] + m2 * s.b[6];
+        const double dy = m0 * s.b[1] + m1 * s.b[4] + m2 * s.b[7];
+        const double dz = m0 * s.b[2] + m1 * s.b[5] + m2 * s.b[8];
+        inside = dx * dx + dy * dy + dz * dz <= K2;
+      } else {
+        inside = (double)k2 <= K2;
+      }
+    }
+    if (!inside) {
+      if (WRITE) {
+        typename Cplx<R>::T z;
+        z.x = R(0);
+        z.y = R(0);
+        spec[nidx] = z;
+      }
+      continue;
+    }
+    const typename Cplx<R>::T X = spec[nidx];
+    const R iw = iw0[i0] * iw1[i1] * iw2[i2];
+    const R kmag = sqrt(k2);
+    const R x = kmag * R(s.x_per_k);
+    R psi, dpsi;
+    radial_eval(radtab, s.rdeg, x, &psi, &dpsi);
+    const R Fhat = R(s.A) * psi / k2;
+    const R dterm = R(s.A) * x * dpsi / (k2 * k2);
+    const bool single = (i2 == 0) || ((s.M[2] & 1) == 0 && 2 * i2 == s.M[2]);
+    const double a = (single ? 1.0 : 2.0) * (double)(X.x * X.x + X.y * X.y) * (double)iw * s.scale;
+    const double aF = a * (double)Fhat;
+    const double ck = a * (double)(dterm - R(2) * Fhat / k2);
+    acc[0] += aF;
+    acc[1] += aF + ck * (double)(kx * kx);
+    acc[2] += aF + ck * (double)(ky * ky);
+    acc[3] += aF + ck * (double)(kz * kz);
+    acc[4] += ck * (double)(kx * ky);
+    acc[5] += ck * (double)(kx * kz);
+    acc[6] += ck * (double)(ky * kz);
+    if (WRITE) {
+      const R G = Fhat * iw;
+      typename Cplx<R>::T y;
+      y.x = X.x * G;
+      y.y = X.y * G;
+      spec[nidx] = y;
+    }
+  }
+  // block reduction, then the last block folds the per-block partials in a fixed order
+  __shared__ double red[7][kThreads / 32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < 7; ++j) {
+    const double v = warp_sum(acc[j]);
+    if (lane == 0) red[j][wid] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 7) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
+    partials[blockIdx.x * 8 + threadIdx.x] = v;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (last) {
+    __threadfence();
+    if (threadIdx.x < 7) {
+      double v = 0.0;
+      for (unsigned b = 0; b < gridDim.x; ++b)
+        v += static_cast<volatile double*>(partials)[b * 8 + threadIdx.x];
+      accum[threadIdx.x] = v;
+    }
+    if (threadIdx.x == 0) *counter = 0u;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+template <typename R, typename IO, int P>
+__global__ void __launch_bounds__(kThreads) k_gather(
+    const typename Vec4<R>::T* __restrict__ sorted_tq, const int* __restrict__ sorted_lb,
+    const int* __restrict__ sorted_idx, const int* __restrict__ offset, GatherGeom gg,
+    const R* __restrict__ wtab, const R* __restrict__ grid, IO* __restrict__ forces) {
+  const TileGeom& g = gg.g;
+  const int tile = blockIdx.x;
+  const int start = offset[tile], end = offset[tile + 1];
+  if (start == end) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* phi = reinterpret_cast<R*>(smem_raw);
+  const int E0 = g.E[0], E1 = g.E[1], E2 = g.E[2], E3p = g.E3p;
+  const int vol = E0 * E1 * E3p;
+  R* tab = phi + vol;
+  R* wbuf = tab + 2 * (g.deg + 1) * P;
+  const int t2 = tile % g.nt[2];
+  const int t1 = (tile / g.nt[2]) % g.nt[1];
+  const int t0 = tile / (g.nt[2] * g.nt[1]);
+  const int o0 = t0 * g.T[0], o1 = t1 * g.T[1], o2 = t2 * g.T[2];
+  const int nload = E0 * E1 * E2;
+  for (int e = threadIdx.x; e < nload; e += blockDim.x) {
+    const int c = e % E2;
+    const int ab = e / E2;
+    const int b = ab % E1;
+    const int a = ab / E1;
+    const int gi = wrap_index(o0 + a, g.M[0]);
+    const int gj = wrap_index(o1 + b, g.M[1]);
+    const int gk = wrap_index(o2 + c, g.M[2]);
+    phi[(a * E1 + b) * E3p + c] = grid[((int64_t)gi * g.M[1] + gj) * g.M[2] + gk];
+  }
+  for (int e = threadIdx.x; e < 2 * (g.deg + 1) * P; e += blockDim.x) tab[e] = wtab[e];
+  __syncthreads();
+
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  R* wb = wbuf + wid * 6 * P;  // [w0 w1 w2 | dw0 dw1 dw2]
+  const R* dtab = tab + (g.deg + 1) * P;
+  for (int j = start + wid; j < end; j += nw) {
+    const typename Vec4<R>::T v = sorted_tq[j];
+    const int lb = sorted_lb[j];
+    for (int e = lane; e < 6 * P; e += 32) {
+      const int which = e / (3 * P);
+      const int r = e - which * 3 * P;
+      const int d = r / P, p = r - d * P;
+      const R t = tq_comp<R>(v, d);
+      R val;
+      if (which == 0) {
+        val = horner_window(tab, g.deg, P, p, t);
+      } else {
+        val = horner_window(dtab, g.deg, P, p, t) * R(2.0 * g.M[d] / P);
+      }
+      wb[e] = val;
+    }
+    __syncwarp();
+    const int l0 = lb & 1023, l1 = (lb >> 10) & 1023, l2 = (lb >> 20) & 1023;
+    const int base = (l0 * E1 + l1) * E3p + l2;
+    R gx = R(0), gy = R(0), gz = R(0);
+#pragma unroll 4
+    for (int nidx = lane; nidx < P * P * P; nidx += 32) {
+      const int i = nidx / (P * P);
+      const int jj = (nidx / P) % P;
+      const int k = nidx % P;
+      const R f = phi[base + (i * E1 + jj) * E3p + k];
+      const R w0 = wb[i], w1 = wb[P + jj], w2 = wb[2 * P + k];
+      const R d0 = wb[3 * P + i], d1 = wb[4 * P + jj], d2 = wb[5 * P + k];
+      gx = fma(f * d0, w1 * w2, gx);
+      gy = fma(f * w0, d1 * w2, gy);
+      gz = fma(f * w0, w1 * d2, gz);
+    }
+    gx = warp_sum(gx);
+    gy = warp_sum(gy);
+    gz = warp_sum(gz);
+    if (lane == 0) {
+      // dU/ds = -(q/(V Mtot^2)) (gx, gy, gz);  F = -h^{-T} dU/ds
+      const double f = (double)v.w * gg.fscale;
+      const double a0 = f * (double)gx, a1 = f * (double)gy, a2 = f * (double)gz;
+      const int idx = sorted_idx[j];
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        forces[3 * (int64_t)idx + c] = (IO)(g.hinv[c] * a0 + g.hinv[3 + c] * a1 + g.hinv[6 + c] * a2);
+    }
+    __syncwarp();
+  }
+}
+
+int grid_blocks(int64_t n) {
+  int64_t b = (n + kThreads - 1) / kThreads;
+  if (b < 1) b = 1;
+  if (b > 152 * 16) b = 152 * 16;
+  return (int)b;
+}
+
+template <typename R>
+size_t tile_elems(const TileGeom& g) {
+  return (size_t)g.E[0] * g.E[1] * g.E3p;
+}
+
+// dispatch a functor templated on P
+template <typename F>
+cudaError_t with_P(int P, F&& f) {
+  switch (P) {
+    case 3: return f(std::integral_constant<int, 3>{});
+    case 4: return f(std::integral_constant<int, 4>{});
+    case 5: return f(std::integral_constant<int, 5>{});
+    case 6: return f(std::integral_constant<int, 6>{});
+    case 7: return f(std::integral_constant<int, 7>{});
+    case 8: return f(std::integral_constant<int, 8>{});
+    case 9: return f(std::integral_constant<int, 9>{});
+    case 10: return f(std::integral_constant<int, 10>{});
+    case 11: return f(std::integral_constant<int, 11>{});
+    case 12: return f(std::integral_constant<int, 12>{});
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+// ---- host launchers --------------------------------------------------------------------
+cudaError_t launch_bin(bool io_double, const void* pos, const void* q, int64_t n,
+                       const TileGeom& g, int* tile_count, int* ptile, int* prank, int* plb,
+                       double* accum, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int nb = grid_blocks(n);
+  if (io_double)
+    k_bin<double><<<nb, kThreads, 0, st>>>((const double*)pos, (const double*)q, n, g,
+                                            tile_count, ptile, prank, plb, accum);
+  else
+    k_bin<float><<<nb, kThreads, 0, st>>>((const float*)pos, (const float*)q, n, g,
+                                           tile_count, ptile, prank, plb, accum);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const int* count, int* offset, int ntiles, cudaStream_t st) {
+  k_scan<<<1, kThreads, 0, st>>>(count, offset, ntiles);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scatter(bool io_double, bool fp64, const void* pos, const void* q,
+                           int64_t n, const TileGeom& g, const int* ptile, const int* prank,
+                           const int* plb, const int* offset, void* sorted_tq, int* sorted_lb, int* sorted_idx,
+                           cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int nb = grid_blocks(n);
+  if (io_double && fp64)
+    k_scatter<double, double><<<nb, kThreads, 0, st>>>(
+        (const double*)pos, (const double*)q, n, g, ptile, prank, plb, offset,
+        (double4*)sorted_tq, sorted_lb, sorted_idx);
+  else if (io_double)
+    k_scatter<double, float><<<nb, kThreads, 0, st>>>(
+        (const double*)pos, (const double*)q, n, g, ptile, prank, plb, offset,
+        (float4*)sorted_tq, sorted_lb, sorted_idx);
+  else if (fp64)
+    k_scatter<float, double><<<nb, kThreads, 0, st>>>(
+        (const float*)pos, (const float*)q, n, g, ptile, prank, plb, offset, (double4*)sorted_tq,
+        sorted_lb, sorted_idx);
+  else
+    k_scatter<float, float><<<nb, kThreads, 0, st>>>(
+        (const float*)pos, (const float*)q, n, g, ptile, prank, plb, offset, (float4*)sorted_tq,
+        sorted_lb, sorted_idx);
+  return cudaGetLastError();
+}
+
+size_t spread_smem_bytes(bool fp64, const TileGeom& g) {
+  const size_t es = fp64 ? 8 : 4;
+  return es * ((size_t)g.E[0] * g.E[1] * g.E3p + (size_t)(g.deg + 1) * g.P +
+               (size_t)(kThreads / 32) * 3 * g.P);
+}
+
+size_t gather_smem_bytes(bool fp64, const TileGeom& g) {
+  const size_t es = fp64 ? 8 : 4;
+  return es * ((size_t)g.E[0] * g.E[1] * g.E3p + (size_t)2 * (g.deg + 1) * g.P +
+               (size_t)(kThreads / 32) * 6 * g.P);
+}
+
+cudaError_t configure_kernels(bool fp64, int P, size_t spread_smem, size_t gather_smem) {
+  return with_P(P, [&](auto pc) -> cudaError_t {
+    constexpr int PP = decltype(pc)::value;
+    cudaError_t e;
+    if (fp64) {
+      e = cudaFuncSetAttribute(k_spread<double, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)spread_smem);
+      if (e != cudaSuccess) return e;
+      e = cudaFuncSetAttribute(k_gather<double, double, PP>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gather_smem);
+      if (e != cudaSuccess) return e;
+    } else {
+      e = cudaFuncSetAttribute(k_spread<float, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)spread_smem);
+      if (e != cudaSuccess) return e;
+      e = cudaFuncSetAttribute(k_gather<float, float, PP>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gather_smem);
+      if (e != cudaSuccess) return e;
+      e = cudaFuncSetAttribute(k_gather<float, double, PP>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gather_smem);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  });
+}
+
+cudaError_t launch_spread(bool fp64, const TileGeom& g, int ntiles, const void* sorted_tq,
+                          const int* sorted_lb, const int* offset, const void* wtab,
+                          void* grid, cudaStream_t st) {
+  const size_t smem = spread_smem_bytes(fp64, g);
+  return with_P(g.P, [&](auto pc) -> cudaError_t {
+    constexpr int PP = decltype(pc)::value;
+    if (fp64)
+      k_spread<double, PP><<<ntiles, kThreads, smem, st>>>(
+          (const double4*)sorted_tq, sorted_lb, offset, g, (const double*)wtab, (double*)grid);
+    else
+      k_spread<float, PP><<<ntiles, kThreads, smem, st>>>(
+          (const float4*)sorted_tq, sorted_lb, offset, g, (const float*)wtab, (float*)grid);
+    return cudaGetLastError();
+  });
+}
+
+cudaError_t launch_scale(bool fp64, bool write, const ScaleGeom& s, void* spec,
+                         const void* invw2, const void* radtab, double* partials,
+                         unsigned int* counter, double* accum, int nblocks, cudaStream_t st) {
+  if (fp64) {
+    if (write)
+      k_scale<double, true><<<nblocks, kThreads, 0, st>>>((double2*)spec, s, (const double*)invw2,
+                                                         (const double*)radtab, partials,
+                                                         counter, accum);
+    else
+      k_scale<double, false><<<nblocks, kThreads, 0, st>>>((double2*)spec, s,
+                                                          (const double*)invw2,
+                                                          (const double*)radtab, partials,
+                                                          counter, accum);
+  } else {
+    if (write)
+      k_scale<float, true><<<nblocks, kThreads, 0, st>>>((float2*)spec, s, (const float*)invw2,
+                                                        (const float*)radtab, partials,
+                                                        counter, accum);
+    else
+      k_scale<float, false><<<nblocks, kThreads, 0, st>>>((float2*)spec, s, (const float*)invw2,
+                                                         (const float*)radtab, partials, counter,
+                                                         accum);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather(bool fp64, bool io_double, const GatherGeom& gg, int ntiles,
+                          const void* sorted_tq, const int* sorted_lb, const int* sorted_idx,
+                          const int* offset, const void* wtab, const void* grid, void* forces,
+                          cudaStream_t st) {
+  const size_t smem = gather_smem_bytes(fp64, gg.g);
+  return with_P(gg.g.P, [&](auto pc) -> cudaError_t {
+    constexpr int PP = decltype(pc)::value;
+    if (fp64)
+      k_gather<double, double, PP><<<ntiles, kThreads, smem, st>>>(
+          (const double4*)sorted_tq, sorted_lb, sorted_idx, offset, gg, (const double*)wtab,
+          (const double*)grid, (double*)forces);
+    else if (io_double)
+      k_gather<float, double, PP><<<ntiles, kThreads, smem, st>>>(
+          (const float4*)sorted_tq, sorted_lb, sorted_idx, offset, gg, (const float*)wtab,
+          (const float*)grid, (double*)forces);
+    else
+      k_gather<float, float, PP><<<ntiles, kThreads, smem, st>>>(
+          (const float4*)sorted_tq, sorted_lb, sorted_idx, offset, gg, (const float*)wtab,
+          (const float*)grid, (float*)forces);
+    return cudaGetLastError();
+  });
+}
+
+}  // namespace esp

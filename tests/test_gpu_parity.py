@@ -1,0 +1,214 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle.
+
+Bars: FP64 path within 1e-12 relative of the oracle (normwise for tensors and force
+arrays), FP32 path within 2e-6 relative.  Sizes span several tiles and ragged tails;
+odd and even stencils; cubic, orthorhombic and triclinic cells; empty and one-atom
+inputs; atoms far outside the primary cell.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+import synthetic as sy
+from oracle.esp_grid import esp_grid, spread
+from oracle.pswf import c_from_tolerance
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover - CPU containers
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2601_00161_gb300 as esp  # noqa: E402
+
+TOL = {"fp64": 1e-12, "fp32": 2e-6}
+
+
+def rel(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
+
+
+def run_gpu(S, c, precision, forces=True):
+    plan = esp.Plan(S.cell, S.n, S.grid, S.P, c, S.rc, precision=precision)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    pos = torch.tensor(S.pos, dtype=dt, device="cuda")
+    q = torch.tensor(S.q, dtype=dt, device="cuda")
+    if forces:
+        res, F = plan.compute(pos, q)
+        torch.cuda.synchronize()
+        F = F.double().cpu().numpy()
+    else:
+        res, F = plan.energy_pressure(pos, q), None
+    return plan, res, F, pos.double().cpu().numpy(), q.double().cpu().numpy()
+
+
+def check(S, precision, c=None, forces=True, force_rows=None):
+    c = c_from_tolerance(S.delta) if c is None else c
+    plan, res, F, pos, q = run_gpu(S, c, precision, forces)
+    # the oracle sees exactly the inputs the GPU saw (FP32 rounding included)
+    ref = esp_grid(pos, q, S.cell, S.grid, S.P, c, S.rc, forces=forces, force_rows=force_rows)
+    tol = TOL[precision]
+    assert rel(res["energy_recip"], ref["energy"]) < tol, (res["energy_recip"], ref["energy"])
+    assert rel(res["virial_recip"], ref["virial"]) < tol
+    assert rel(res["pressure_recip"], ref["virial"] / np.linalg.det(S.cell)) < tol
+    if forces:
+        Fg = F if force_rows is None else F[force_rows]
+        assert rel(Fg, ref["forces"]) < tol
+        assert np.max(np.abs(Fg - ref["forces"])) < 10 * tol * np.max(np.abs(ref["forces"]))
+    plan.close()
+    return res, F
+
+
+# -- small and ragged cases ----------------------------------------------------------------
+TRI = np.array([[13.0, 1.3, -0.9], [0.0, 14.0, 1.1], [0.0, 0.0, 12.5]])
+ORTHO = np.diag([11.0, 13.0, 17.0])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_water648(precision):
+    check(sy.water_cubic(), precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("P,grid,cell,n", [
+    (6, (24, 26, 30), TRI, 300),     # ragged tiles in every dimension
+    (5, (17, 23, 29), ORTHO, 211),   # odd P, prime grid sizes
+    (7, (20, 21, 22), TRI, 97),
+    (8, (33, 19, 41), ORTHO, 1000),
+    (3, (12, 12, 12), ORTHO, 50),
+    (12, (40, 36, 44), TRI, 400),    # widest stencil
+    (4, (9, 10, 64), TRI, 123),      # grid smaller than a tile in two dimensions
+])
+def test_ragged_and_odd(precision, P, grid, cell, n):
+    S = sy.small_random(n, cell, seed=7 + n, grid=grid, P=P, delta=1e-6, rc=3.5)
+    check(S, precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_empty_and_single_atom(precision):
+    S0 = sy.small_random(0, ORTHO, seed=1, grid=(16, 16, 16), P=6, rc=3.5)
+    c = c_from_tolerance(1e-6)
+    plan = esp.Plan(S0.cell, 0, S0.grid, 6, c, 3.5, precision=precision)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    r = plan.energy_pressure(torch.zeros((0, 3), dtype=dt, device="cuda"), torch.zeros(0, dtype=dt, device="cuda"))
+    assert r["energy_recip"] == 0.0 and np.all(r["virial_recip"] == 0.0) and r["q2sum"] == 0.0
+    plan.close()
+    S1 = sy.small_random(1, ORTHO, seed=2, grid=(16, 16, 16), P=6, rc=3.5)
+    S1.q[:] = 1.0  # a lone (non-neutral) charge: grid self-interaction plus background
+    res, _ = check(S1, precision)
+    assert res["energy_bg"] < 0.0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_wrapping_of_far_images(precision):
+    S = sy.small_random(200, TRI, seed=3, grid=(24, 24, 24), P=6, rc=3.5)
+    shift = (np.array([5, -3, 2])[None, :] * 1.0) @ TRI.T  # integer combination of cell vectors
+    S2 = sy.System(S.name, S.pos + shift, S.q, S.cell, S.grid, S.P, S.delta, S.rc)
+    r1, F1 = check(S, precision)
+    r2, F2 = check(S2, precision)
+    assert rel(r2["virial_recip"], r1["virial_recip"]) < 10 * TOL[precision]
+
+
+def test_spread_grid_and_spectrum_fp64():
+    S = sy.water_cubic()
+    c = c_from_tolerance(S.delta)
+    plan, res, _, pos, q = run_gpu(S, c, "fp64", forces=False)
+    rho = plan.grid_values()
+    ref = spread(pos, q, S.cell, S.grid, S.P, c)
+    assert np.max(np.abs(rho - ref)) < 1e-12 * np.max(np.abs(ref))
+    X = plan.spectrum()
+    Xr = np.fft.rfftn(ref)
+    assert np.max(np.abs(X - Xr)) < 1e-12 * np.max(np.abs(Xr))
+    plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_forces_from_kept_spectrum_and_host_entry(precision):
+    S = sy.small_random(500, TRI, seed=11, grid=(28, 30, 26), P=7, rc=3.5)
+    c = c_from_tolerance(S.delta)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    plan = esp.Plan(S.cell, S.n, S.grid, S.P, c, S.rc, precision=precision)
+    pos = torch.tensor(S.pos, dtype=dt, device="cuda")
+    q = torch.tensor(S.q, dtype=dt, device="cuda")
+    r = plan.energy_pressure(pos, q)
+    F1 = torch.empty((S.n, 3), dtype=dt, device="cuda")
+    esp.esp_forces_from_spectrum(plan.handle, F1)
+    F2 = plan.forces(pos, q)
+    torch.cuda.synchronize()
+    assert rel(F1.double().cpu().numpy(), F2.double().cpu().numpy()) < TOL[precision]
+    with pytest.raises(esp.ESPError) as ei:
+        esp.esp_forces_from_spectrum(plan.handle, F1)  # spectrum consumed by the force path
+    assert ei.value.code == esp.ESP_ERR_STATE
+    npdt = np.float64 if precision == "fp64" else np.float32
+    Fh = np.empty((S.n, 3), dtype=npdt)
+    rh = esp.esp_compute_host(plan.handle, S.pos.astype(npdt), S.q.astype(npdt), Fh)
+    assert rel(rh.energy_recip, r["energy_recip"]) < TOL[precision]
+    assert rel(Fh, F2.double().cpu().numpy()) < TOL[precision]
+    plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_set_cell_npt(precision):
+    S = sy.small_random(400, TRI, seed=5, grid=(24, 24, 24), P=6, rc=3.5)
+    c = c_from_tolerance(S.delta)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    plan = esp.Plan(S.cell, S.n, S.grid, S.P, c, S.rc, precision=precision)
+    s = S.pos @ np.linalg.inv(S.cell).T
+    for scale in [1.0, 1.02, 0.97]:
+        cell = S.cell * np.array([scale, 1.0, 1.0 / scale])[:, None]
+        pos = s @ cell.T
+        plan.set_cell(cell)
+        res, F = plan.compute(torch.tensor(pos, dtype=dt, device="cuda"), torch.tensor(S.q, dtype=dt, device="cuda"))
+        posd = torch.tensor(pos, dtype=dt).double().numpy()
+        qd = torch.tensor(S.q, dtype=dt).double().numpy()
+        ref = esp_grid(posd, qd, cell, S.grid, S.P, c, S.rc)
+        assert rel(res["virial_recip"], ref["virial"]) < TOL[precision]
+        assert rel(F.double().cpu().numpy(), ref["forces"]) < TOL[precision]
+    with pytest.raises(esp.ESPError) as ei:
+        plan.set_cell(S.cell * 3.0)  # grid now too coarse
+    assert ei.value.code == esp.ESP_ERR_GRID
+    plan.close()
+
+
+def test_nonfinite_input_is_reported_not_faulted():
+    S = sy.small_random(100, ORTHO, seed=9, grid=(16, 16, 16), P=6, rc=3.5)
+    c = c_from_tolerance(S.delta)
+    plan = esp.Plan(S.cell, S.n, S.grid, S.P, c, S.rc, precision="fp64")
+    pos = torch.tensor(S.pos, device="cuda")
+    pos[17, 1] = float("nan")
+    with pytest.raises(esp.ESPError) as ei:
+        plan.energy_pressure(pos, torch.tensor(S.q, device="cuda"))
+    assert ei.value.code == esp.ESP_ERR_NONFINITE
+    # the plan stays usable
+    r = plan.energy_pressure(torch.tensor(S.pos, device="cuda"), torch.tensor(S.q, device="cuda"))
+    assert math.isfinite(r["energy_recip"])
+    plan.close()
+
+
+def test_plan_tables_are_accurate():
+    S = sy.water_cubic()
+    for prec, tol in [("fp64", 3e-15), ("fp32", 2e-8)]:
+        plan = esp.Plan(S.cell, S.n, S.grid, S.P, c_from_tolerance(S.delta), S.rc, precision=prec)
+        info = plan.info()
+        assert info["fit_err"] <= tol and info["rfit_err"] <= tol, info
+        plan.close()
+
+
+# -- full-size workloads ------------------------------------------------------------------
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("name", ["water30k_triclinic", "litfsi16k_ortho"])
+def test_medium_workloads(name, precision):
+    S = sy.WORKLOADS[name]()
+    rows = np.random.default_rng(0).choice(S.n, 3000, replace=False)
+    check(S, precision, force_rows=rows)
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_membrane_slab_full_size(precision):
+    S = sy.membrane_slab()
+    rows = np.random.default_rng(1).choice(S.n, 2000, replace=False)
+    check(S, precision, force_rows=rows)
