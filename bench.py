@@ -159,13 +159,24 @@ def recorded_traffic(kernel: str):
         return None
 
 
+def single_thread():
+    """Limit BLAS / OpenMP pools to one thread (the oracle's own work is single-threaded
+    numpy either way); a no-op where threadpoolctl is not installed."""
+    try:
+        from threadpoolctl import threadpool_limits
+
+        return threadpool_limits(1)
+    except ImportError:
+        import contextlib
+
+        return contextlib.nullcontext()
+
+
 def cpu_baseline_oracle(S, c):
     """The FP64 oracle as it stands, one full step of the same workload, 1 host thread."""
-    from threadpoolctl import threadpool_limits
-
     from oracle.esp_grid import esp_grid
 
-    with threadpool_limits(1):
+    with single_thread():
         t0 = time.perf_counter()
         esp_grid(S.pos, S.q, S.cell, S.grid, S.P, c, S.rc, forces=True)
         dt = time.perf_counter() - t0
@@ -331,8 +342,6 @@ def reference_arm(args):
     by the workload's atom count (the oracle's cost is linear in the atoms apart from the
     FFT's log factor).
     """
-    from threadpoolctl import threadpool_limits
-
     from oracle.esp_grid import esp_grid
     from oracle.pswf import c_from_tolerance
 
@@ -347,7 +356,7 @@ def reference_arm(args):
     sub_cell = S.cell @ np.diag([0.25, 0.25, 1.0])
     pos, q = S.pos[sel] - 0.0, S.q[sel]
     grid = (S.grid[0] // 4, S.grid[1] // 4, S.grid[2])
-    with threadpool_limits(1):
+    with single_thread():
         for _ in range(args.warmup):
             esp_grid(pos, q, sub_cell, grid, S.P, c, S.rc)
         t0 = time.perf_counter()

@@ -66,6 +66,7 @@ struct esp_plan_s {
   int* d_ptile = nullptr;
   int* d_prank = nullptr;
   int* d_plb = nullptr;
+  void* d_tq = nullptr;
   void* d_sorted_tq = nullptr;
   int* d_sorted_lb = nullptr;
   int* d_sorted_idx = nullptr;
@@ -163,8 +164,12 @@ int check_grid(esp_plan_t p, const double h[9], const int M[3], double c, double
 
 void update_cell_constants(esp_plan_t p) {
   std::memcpy(p->tg.hinv, p->hinv, sizeof p->hinv);
+  for (int i = 0; i < 9; ++i) p->tg.hinvf[i] = (float)p->hinv[i];
   for (int d = 0; d < 3; ++d)
-    for (int a = 0; a < 3; ++a) p->sg.b[3 * d + a] = 2.0 * M_PI * p->hinv[3 * d + a];
+    for (int a = 0; a < 3; ++a) {
+      p->sg.b[3 * d + a] = 2.0 * M_PI * p->hinv[3 * d + a];
+      p->sg.bf[3 * d + a] = (float)p->sg.b[3 * d + a];
+    }
   const double Mtot = (double)p->M[0] * p->M[1] * p->M[2];
   p->sg.scale = 1.0 / (2.0 * p->V * Mtot * Mtot);
   p->gg.g = p->tg;
@@ -278,7 +283,7 @@ void build_invw2(esp_plan_t p, std::vector<double>& out) {
 void release(esp_plan_t p) {
   if (!p) return;
   if (p->stream) cudaStreamSynchronize(p->stream);
-  void* bufs[] = {p->d_wtab,      p->d_radtab,    p->d_invw2,    p->d_grid,      p->d_spec,
+  void* bufs[] = {p->d_wtab,      p->d_radtab,    p->d_invw2,    p->d_grid,      p->d_spec,  p->d_tq,
                   p->d_count,     p->d_offset,    p->d_ptile,    p->d_prank,     p->d_plb,
                   p->d_sorted_tq, p->d_sorted_lb, p->d_sorted_idx, p->d_accum,   p->d_partials,
                   p->d_counter,   p->d_io_pos,    p->d_io_q,     p->d_io_f};
@@ -330,14 +335,14 @@ int run_step(esp_plan_t p, const void* pos, const void* q, void* forces, double*
   ESP_CUDA(p, cudaMemsetAsync(p->d_count, 0, sizeof(int) * (size_t)p->ntiles, st));
   ESP_CUDA(p, cudaMemsetAsync(acc, 0, sizeof(double) * ESP_ACCUM_LEN, st));
   mark(p, kBin);
-  ESP_CUDA(p, esp::launch_bin(p->io_double, pos, q, p->n, p->tg, p->d_count, p->d_ptile,
-                              p->d_prank, p->d_plb, acc, st));
+  ESP_CUDA(p, esp::launch_bin(p->io_double, fp64, pos, q, p->n, p->tg, p->d_count, p->d_ptile,
+                              p->d_prank, p->d_plb, p->d_tq, acc, st));
   mark(p, kScan);
   ESP_CUDA(p, esp::launch_scan(p->d_count, p->d_offset, p->ntiles, st));
   mark(p, kScatter);
-  ESP_CUDA(p, esp::launch_scatter(p->io_double, fp64, pos, q, p->n, p->tg, p->d_ptile,
-                                  p->d_prank, p->d_plb, p->d_offset, p->d_sorted_tq,
-                                  p->d_sorted_lb, p->d_sorted_idx, st));
+  ESP_CUDA(p, esp::launch_scatter(fp64, p->n, p->d_ptile, p->d_prank, p->d_plb, p->d_tq,
+                                  p->d_offset, p->d_sorted_tq, p->d_sorted_lb,
+                                  p->d_sorted_idx, st));
   mark(p, kZero);
   ESP_CUDA(p, cudaMemsetAsync(p->d_grid, 0, es * Mtot, st));
   mark(p, kSpread);
@@ -440,25 +445,40 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
   if ((rc = build_radial_tables(p, rtab)) != ESP_OK) return bail(rc);
   build_invw2(p, invw2);
 
-  // tile geometry: 8 x 8 stencil bases in the first two dimensions; in the third the
-  // padded row T + P - 1 fills a shared-memory pitch of 24 (P <= 9) or 40 words
+  // Tile geometry.  A tile holds T0 x T1 x T2 stencil bases; its CTA owns the padded
+  // block (T + P - 1)^3.  T2 is a multiple of 4 so padded rows move as aligned float4
+  // when M2 is too; T0 = T1 = 16 when that still gives two tiles per SM, else 8.
+  int sms = 152;
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
   esp::TileGeom& g = p->tg;
   for (int d = 0; d < 3; ++d) g.M[d] = p->M[d];
   g.P = w;
-  g.T[0] = std::min(8, p->M[0]);
-  g.T[1] = std::min(8, p->M[1]);
-  g.T[2] = std::min(w <= 9 ? 25 - w : 41 - w, p->M[2]);
+  g.T[2] = std::min(w <= 8 ? 16 : 8, p->M[2]);
+  {
+    auto ntile_for = [&](int t) {
+      return ((p->M[0] + t - 1) / t) * ((p->M[1] + t - 1) / t) * ((p->M[2] + g.T[2] - 1) / g.T[2]);
+    };
+    const int t01 = ntile_for(16) >= 2 * sms ? 16 : 8;
+    g.T[0] = std::min(t01, p->M[0]);
+    g.T[1] = std::min(t01, p->M[1]);
+  }
   p->ntiles = 1;
   for (int d = 0; d < 3; ++d) {
     g.nt[d] = (p->M[d] + g.T[d] - 1) / g.T[d];
     g.E[d] = g.T[d] + w - 1;
+    g.dscale[d] = 2.0 * p->M[d] / w;
+    g.dscalef[d] = (float)g.dscale[d];
     p->ntiles *= g.nt[d];
   }
-  {
-    int e = (g.E[2] + 7) / 8 * 8;
-    if ((e / 8) % 2 == 0) e += 8;
-    g.E3p = e;
-  }
+  // row pitch: the smallest value >= E2 that is -P mod 32 (consecutive stencil rows of
+  // one atom then sit on consecutive shared-memory banks)
+  g.E3p = g.E[2];
+  while ((g.E3p + w) % 32 != 0) ++g.E3p;
+  g.vec4 = (!p->fp64 && g.T[2] % 4 == 0 && p->M[2] % 4 == 0 && (g.E[2] + 3) / 4 * 4 <= g.E3p) ? 1 : 0;
   g.deg = p->deg;
 
   esp::ScaleGeom& s = p->sg;
@@ -473,8 +493,6 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
   int dev = 0;
   cudaGetDevice(&dev);
   p->device = dev;
-  int sms = 152;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   p->scale_blocks = sms * 4;
 
   const size_t es = p->fp64 ? 8 : 4;
@@ -497,6 +515,7 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
   ALLOC(p->d_ptile, sizeof(int) * nn);
   ALLOC(p->d_prank, sizeof(int) * nn);
   ALLOC(p->d_plb, sizeof(int) * nn);
+  ALLOC(p->d_tq, 4 * es * nn);
   ALLOC(p->d_sorted_tq, 4 * es * nn);
   ALLOC(p->d_sorted_lb, sizeof(int) * nn);
   ALLOC(p->d_sorted_idx, sizeof(int) * nn);

@@ -1,18 +1,28 @@
 // sm_103a kernels of the ESP long-range step (Sec. 4.1 Algorithm 1 and Appendix C):
-//   k_bin      wrap s = h^{-1} r into [0,1), stencil base (Sec. 4.3), tile id, rank
+//   k_bin      wrap s = h^{-1} r into [0,1), stencil base and fractional offset
+//              (Sec. 4.3), tile id and rank within the tile; FP64 for the coordinate
+//              so the integer stencil decision matches the FP64 oracle
 //   k_scan     exclusive scan of tile counts (one CTA)
-//   k_scatter  counting-sort scatter of (fractional offset t, q) by tile
-//   k_spread   eq. (gridding): each CTA accumulates its tile's padded P^3 footprints in
-//              shared memory, then adds the block to the global grid
+//   k_scatter  counting-sort permutation of (offset t, q), local base and atom index
+//   k_spread   eq. (gridding): a CTA owns one tile of stencil bases; warps take batches
+//              of atoms and spread each atom's P^3 footprint into the tile's padded
+//              shared-memory block; the block is then added to the periodic grid
 //   k_scale    eqs. (diag)/(PFfinal): per half-spectrum mode the deconvolved weight, the
-//              Fourier kernel and the 3x3 pressure kernel, FP64 reduction; optionally
+//              Fourier kernel and the 3x3 pressure kernel, reduced in FP64; optionally
 //              writes G X for the force path (eq. (UFAnal))
-//   k_gather   eq. (AD): per atom, the P^3 contraction of the potential grid with the
-//              window gradient, staged through a shared-memory tile
+//   k_gather   eq. (AD): the CTA stages its tile's padded block of the potential grid in
+//              shared memory; per atom the P^3 contraction with the window gradient
+//
+// Work mapping in spread / gather: a warp handles kBatch atoms at once and splits their
+// P^2 (j, k) stencil rows over its lanes (lane-consecutive k, then j), each lane walking
+// the P points of its row in the first dimension.  With the shared-memory row pitch
+// E3p = -P (mod 32), consecutive rows of one atom fall on consecutive banks.
 #include "esp_kernels.cuh"
 
 #include <cuda_runtime.h>
 #include <math.h>
+
+#include <type_traits>
 
 namespace esp {
 
@@ -47,22 +57,19 @@ __device__ __forceinline__ int wrap_index(int i, int m) {
 
 // Reduced coordinate, grid coordinate and stencil base for one dimension (Sec. 4.3):
 // P even: base = floor(x) - P/2 + 1, t = x - floor(x); P odd: base = floor(x + 1/2) -
-// (P-1)/2, t = x + 1/2 - floor(x + 1/2).  Either way the stencil point p sits at offset
-// g - x = p + 1 - P/2 - t from the atom, in grid units.  FP64 on every path so that the
-// integer decision matches the FP64 oracle.
+// (P-1)/2, t = x + 1/2 - floor(x + 1/2).  Either way stencil point p sits at offset
+// g - x = p + 1 - P/2 - t from the atom, in grid units.  Explicitly rounded FP64.
 __device__ __forceinline__ void stencil_base(double s, int M, int P, int* base, double* t) {
   s = __dsub_rn(s, floor(s));
   if (s >= 1.0) s = 0.0;
   double x = __dmul_rn((double)M, s);
   if (P & 1) x = __dadd_rn(x, 0.5);
   const double fl = floor(x);
-  *t = x - fl;
+  *t = __dsub_rn(x, fl);
   const int b = (int)fl - ((P & 1) ? (P - 1) / 2 : P / 2 - 1);
   *base = wrap_index(b, M);
 }
 
-// s_d = (h^{-1} r)_d with explicitly rounded operations, so that every kernel that
-// recomputes it gets the same bits
 __device__ __forceinline__ double reduced_coord(const double* hinv_row, const double r[3]) {
   return __fma_rn(hinv_row[0], r[0], __fma_rn(hinv_row[1], r[1], __dmul_rn(hinv_row[2], r[2])));
 }
@@ -82,20 +89,27 @@ __device__ __forceinline__ double warp_sum(double v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
 }
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
+
+template <typename R>
+__device__ __forceinline__ R dscale_of(const TileGeom& g, int d);
+template <>
+__device__ __forceinline__ float dscale_of<float>(const TileGeom& g, int d) {
+  return g.dscalef[d];
+}
+template <>
+__device__ __forceinline__ double dscale_of<double>(const TileGeom& g, int d) {
+  return g.dscale[d];
 }
 
 // ---------------------------------------------------------------------------------------
-template <typename IO>
+template <typename IO, typename R>
 __global__ void __launch_bounds__(kThreads) k_bin(const IO* __restrict__ pos,
                                                   const IO* __restrict__ q, int64_t n,
                                                   TileGeom g, int* __restrict__ tile_count,
                                                   int* __restrict__ ptile,
                                                   int* __restrict__ prank,
                                                   int* __restrict__ plb,
+                                                  typename Vec4<R>::T* __restrict__ tq,
                                                   double* __restrict__ accum) {
   double sq = 0.0, sq2 = 0.0, bad = 0.0;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -107,15 +121,21 @@ __global__ void __launch_bounds__(kThreads) k_bin(const IO* __restrict__ pos,
       continue;
     }
     int tc[3], lb[3];
+    double t[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       int b;
-      double t;
-      stencil_base(reduced_coord(&g.hinv[3 * d], r), g.M[d], g.P, &b, &t);
+      stencil_base(reduced_coord(&g.hinv[3 * d], r), g.M[d], g.P, &b, &t[d]);
       tc[d] = b / g.T[d];
       lb[d] = b - tc[d] * g.T[d];
     }
     const int tile = (tc[0] * g.nt[1] + tc[1]) * g.nt[2] + tc[2];
+    typename Vec4<R>::T v;
+    v.x = (R)t[0];
+    v.y = (R)t[1];
+    v.z = (R)t[2];
+    v.w = (R)qi;
+    tq[i] = v;
     ptile[i] = tile;
     plb[i] = lb[0] | (lb[1] << 10) | (lb[2] << 20);
     prank[i] = atomicAdd(&tile_count[tile], 1);
@@ -184,30 +204,18 @@ __global__ void __launch_bounds__(kThreads) k_scan(const int* __restrict__ count
   if (threadIdx.x == 0) offset[n] = carry;
 }
 
-template <typename IO, typename R>
+template <typename V>
 __global__ void __launch_bounds__(kThreads) k_scatter(
-    const IO* __restrict__ pos, const IO* __restrict__ q, int64_t n, TileGeom g,
-    const int* __restrict__ ptile, const int* __restrict__ prank, const int* __restrict__ plb,
-    const int* __restrict__ offset, typename Vec4<R>::T* __restrict__ sorted_tq, int* __restrict__ sorted_lb,
-    int* __restrict__ sorted_idx) {
+    int64_t n, const int* __restrict__ ptile, const int* __restrict__ prank,
+    const int* __restrict__ plb, const V* __restrict__ tq, const int* __restrict__ offset,
+    V* __restrict__ sorted_tq, int* __restrict__ sorted_lb, int* __restrict__ sorted_idx) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int tile = ptile[i];
     if (tile < 0) continue;
-    double r[3], qi;
-    load_atom(pos, q, i, r, &qi);
-    int b[3];
-    double t[3];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) stencil_base(reduced_coord(&g.hinv[3 * d], r), g.M[d], g.P, &b[d], &t[d]);
     const int dst = offset[tile] + prank[i];
-    typename Vec4<R>::T v;
-    v.x = (R)t[0];
-    v.y = (R)t[1];
-    v.z = (R)t[2];
-    v.w = (R)qi;
-    sorted_tq[dst] = v;
-    sorted_lb[dst] = plb[i];  // local base from the binning pass: indices never disagree
+    sorted_tq[dst] = tq[i];
+    sorted_lb[dst] = plb[i];
     sorted_idx[dst] = (int)i;
   }
 }
@@ -227,6 +235,10 @@ __device__ __forceinline__ R tq_comp(const typename Vec4<R>::T& v, int d) {
   return d == 0 ? v.x : (d == 1 ? v.y : v.z);
 }
 
+__device__ __forceinline__ int local_base(int lb, int E1, int E3p) {
+  return (((lb & 1023) * E1 + ((lb >> 10) & 1023)) * E3p) + ((lb >> 20) & 1023);
+}
+
 // ---------------------------------------------------------------------------------------
 template <typename R, int P>
 __global__ void __launch_bounds__(kThreads) k_spread(
@@ -238,34 +250,42 @@ __global__ void __launch_bounds__(kThreads) k_spread(
   if (start == end) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* acc = reinterpret_cast<R*>(smem_raw);
-  const int E0 = g.E[0], E1 = g.E[1], E3p = g.E3p;
+  const int E0 = g.E[0], E1 = g.E[1], E2 = g.E[2], E3p = g.E3p;
   const int vol = E0 * E1 * E3p;
+  const int S1 = E1 * E3p;  // shared-memory stride of the first dimension
   R* tab = acc + vol;
   R* wbuf = tab + (g.deg + 1) * P;
+  const int nw = blockDim.x >> 5;
+  int* bbuf = reinterpret_cast<int*>(wbuf + nw * kBatch * 3 * P);
   for (int e = threadIdx.x; e < vol; e += blockDim.x) acc[e] = R(0);
   for (int e = threadIdx.x; e < (g.deg + 1) * P; e += blockDim.x) tab[e] = wtab[e];
   __syncthreads();
 
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  R* wb = wbuf + wid * 3 * P;
-  for (int j = start + wid; j < end; j += nw) {
-    const typename Vec4<R>::T v = sorted_tq[j];
-    const int lb = sorted_lb[j];
-    for (int e = lane; e < 3 * P; e += 32) {
-      const int d = e / P, p = e - d * P;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  R* W = wbuf + wid * kBatch * 3 * P;  // per atom [w0 | q w1 | w2]
+  int* B = bbuf + wid * kBatch;
+  for (int j0 = start + wid * kBatch; j0 < end; j0 += nw * kBatch) {
+    const int cnt = min(kBatch, end - j0);
+    for (int e = lane; e < cnt * 3 * P; e += 32) {
+      const int a = e / (3 * P);
+      const int r = e - a * 3 * P;
+      const int d = r / P, p = r - d * P;
+      const typename Vec4<R>::T v = sorted_tq[j0 + a];
       R w = horner_window(tab, g.deg, P, p, tq_comp<R>(v, d));
-      if (d == 0) w *= v.w;
-      wb[e] = w;
+      if (d == 1) w *= v.w;
+      W[e] = w;
     }
+    if (lane < cnt) B[lane] = local_base(sorted_lb[j0 + lane], E1, E3p);
     __syncwarp();
-    const int l0 = lb & 1023, l1 = (lb >> 10) & 1023, l2 = (lb >> 20) & 1023;
-    const int base = (l0 * E1 + l1) * E3p + l2;
-#pragma unroll 4
-    for (int nidx = lane; nidx < P * P * P; nidx += 32) {
-      const int i = nidx / (P * P);
-      const int jj = (nidx / P) % P;
-      const int k = nidx % P;
-      atomicAdd(&acc[base + (i * E1 + jj) * E3p + k], wb[i] * wb[P + jj] * wb[2 * P + k]);
+    for (int it = lane; it < cnt * P * P; it += 32) {
+      const int a = it / (P * P);
+      const int pr = it - a * P * P;
+      const int jj = pr / P, k = pr - jj * P;
+      const R* Wa = W + a * 3 * P;
+      const R pw = Wa[P + jj] * Wa[2 * P + k];
+      R* dst = acc + B[a] + jj * E3p + k;
+#pragma unroll
+      for (int i = 0; i < P; ++i) atomicAdd(dst + i * S1, Wa[i] * pw);
     }
     __syncwarp();
   }
@@ -276,7 +296,27 @@ __global__ void __launch_bounds__(kThreads) k_spread(
   const int t1 = (tile / g.nt[2]) % g.nt[1];
   const int t0 = tile / (g.nt[2] * g.nt[1]);
   const int o0 = t0 * g.T[0], o1 = t1 * g.T[1], o2 = t2 * g.T[2];
-  const int E2 = g.E[2];
+  if constexpr (std::is_same<R, float>::value) {
+    if (g.vec4) {
+      const int E2v = (E2 + 3) >> 2;
+      const int nflush = E0 * E1 * E2v;
+      for (int e = threadIdx.x; e < nflush; e += blockDim.x) {
+        const int c4 = e % E2v;
+        const int ab = e / E2v;
+        const int b = ab % E1;
+        const int a = ab / E1;
+        const float* src = acc + (a * E1 + b) * E3p + 4 * c4;
+        const float4 v = make_float4(src[0], src[1], src[2], src[3]);
+        if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) {
+          const int gi = wrap_index(o0 + a, g.M[0]);
+          const int gj = wrap_index(o1 + b, g.M[1]);
+          const int gk = wrap_index(o2 + 4 * c4, g.M[2]);
+          atomicAdd(reinterpret_cast<float4*>(grid + ((int64_t)gi * g.M[1] + gj) * g.M[2] + gk), v);
+        }
+      }
+      return;
+    }
+  }
   const int nflush = E0 * E1 * E2;
   for (int e = threadIdx.x; e < nflush; e += blockDim.x) {
     const int c = e % E2;
@@ -312,6 +352,17 @@ __device__ __forceinline__ void radial_eval(const R* __restrict__ rt, int rdeg, 
   *dpsi = w;
 }
 
+template <typename R>
+__device__ __forceinline__ R bvec(const ScaleGeom& s, int i);
+template <>
+__device__ __forceinline__ float bvec<float>(const ScaleGeom& s, int i) {
+  return s.bf[i];
+}
+template <>
+__device__ __forceinline__ double bvec<double>(const ScaleGeom& s, int i) {
+  return s.b[i];
+}
+
 template <typename R, bool WRITE>
 __global__ void __launch_bounds__(kThreads) k_scale(typename Cplx<R>::T* __restrict__ spec,
                                                     ScaleGeom s, const R* __restrict__ invw2,
@@ -337,11 +388,13 @@ __global__ void __launch_bounds__(kThreads) k_scale(typename Cplx<R>::T* __restr
                   (m0 | m1 | m2) != 0;
     R kx = R(0), ky = R(0), kz = R(0), k2 = R(0);
     if (inside) {
-      kx = R(m0 * s.b[0] + m1 * s.b[3] + m2 * s.b[6]);
-      ky = R(m0 * s.b[1] + m1 * s.b[4] + m2 * s.b[7]);
-      kz = R(m0 * s.b[2] + m1 * s.b[5] + m2 * s.b[8]);
+      const R f0 = R(m0), f1 = R(m1), f2 = R(m2);
+      kx = f0 * bvec<R>(s, 0) + f1 * bvec<R>(s, 3) + f2 * bvec<R>(s, 6);
+      ky = f0 * bvec<R>(s, 1) + f1 * bvec<R>(s, 4) + f2 * bvec<R>(s, 7);
+      kz = f0 * bvec<R>(s, 2) + f1 * bvec<R>(s, 5) + f2 * bvec<R>(s, 8);
       k2 = kx * kx + ky * ky + kz * kz;
-      // the in-sphere decision is taken in FP64 (FP32 only when far from the boundary)
+      // The in-sphere decision is an FP64 one (as in the FP64 oracle): FP32 decides only
+      // when it is far from the boundary.
       const double K2 = s.K2;
       if (sizeof(R) == 8 || fabs((double)k2 - K2) <= 1e-5 * K2) {
         const double dx = m0 * s.b[0] + m1 * s.b[3] + m2 * s.b[6];
@@ -370,16 +423,16 @@ __global__ void __launch_bounds__(kThreads) k_scale(typename Cplx<R>::T* __restr
     const R Fhat = R(s.A) * psi / k2;
     const R dterm = R(s.A) * x * dpsi / (k2 * k2);
     const bool single = (i2 == 0) || ((s.M[2] & 1) == 0 && 2 * i2 == s.M[2]);
-    const double a = (single ? 1.0 : 2.0) * (double)(X.x * X.x + X.y * X.y) * (double)iw * s.scale;
-    const double aF = a * (double)Fhat;
-    const double ck = a * (double)(dterm - R(2) * Fhat / k2);
-    acc[0] += aF;
-    acc[1] += aF + ck * (double)(kx * kx);
-    acc[2] += aF + ck * (double)(ky * ky);
-    acc[3] += aF + ck * (double)(kz * kz);
-    acc[4] += ck * (double)(kx * ky);
-    acc[5] += ck * (double)(kx * kz);
-    acc[6] += ck * (double)(ky * kz);
+    const R a = (single ? R(1) : R(2)) * (X.x * X.x + X.y * X.y) * iw * R(s.scale);
+    const R aF = a * Fhat;
+    const R ck = a * (dterm - R(2) * Fhat / k2);
+    acc[0] += (double)aF;
+    acc[1] += (double)(aF + ck * kx * kx);
+    acc[2] += (double)(aF + ck * ky * ky);
+    acc[3] += (double)(aF + ck * kz * kz);
+    acc[4] += (double)(ck * kx * ky);
+    acc[5] += (double)(ck * kx * kz);
+    acc[6] += (double)(ck * ky * kz);
     if (WRITE) {
       const R G = Fhat * iw;
       typename Cplx<R>::T y;
@@ -433,72 +486,114 @@ __global__ void __launch_bounds__(kThreads) k_gather(
   R* phi = reinterpret_cast<R*>(smem_raw);
   const int E0 = g.E[0], E1 = g.E[1], E2 = g.E[2], E3p = g.E3p;
   const int vol = E0 * E1 * E3p;
+  const int S1 = E1 * E3p;
   R* tab = phi + vol;
   R* wbuf = tab + 2 * (g.deg + 1) * P;
+  const int nw = blockDim.x >> 5;
+  R* fbuf = wbuf + nw * kBatch * 6 * P;
+  int* bbuf = reinterpret_cast<int*>(fbuf + nw * kBatch * 3);
   const int t2 = tile % g.nt[2];
   const int t1 = (tile / g.nt[2]) % g.nt[1];
   const int t0 = tile / (g.nt[2] * g.nt[1]);
   const int o0 = t0 * g.T[0], o1 = t1 * g.T[1], o2 = t2 * g.T[2];
-  const int nload = E0 * E1 * E2;
-  for (int e = threadIdx.x; e < nload; e += blockDim.x) {
-    const int c = e % E2;
-    const int ab = e / E2;
-    const int b = ab % E1;
-    const int a = ab / E1;
-    const int gi = wrap_index(o0 + a, g.M[0]);
-    const int gj = wrap_index(o1 + b, g.M[1]);
-    const int gk = wrap_index(o2 + c, g.M[2]);
-    phi[(a * E1 + b) * E3p + c] = grid[((int64_t)gi * g.M[1] + gj) * g.M[2] + gk];
+  bool loaded = false;
+  if constexpr (std::is_same<R, float>::value) {
+    if (g.vec4) {
+      const int E2v = (E2 + 3) >> 2;
+      const int nload = E0 * E1 * E2v;
+      for (int e = threadIdx.x; e < nload; e += blockDim.x) {
+        const int c4 = e % E2v;
+        const int ab = e / E2v;
+        const int b = ab % E1;
+        const int a = ab / E1;
+        const int gi = wrap_index(o0 + a, g.M[0]);
+        const int gj = wrap_index(o1 + b, g.M[1]);
+        const int gk = wrap_index(o2 + 4 * c4, g.M[2]);
+        const float4 v =
+            *reinterpret_cast<const float4*>(grid + ((int64_t)gi * g.M[1] + gj) * g.M[2] + gk);
+        float* dst = phi + (a * E1 + b) * E3p + 4 * c4;
+        dst[0] = v.x;
+        dst[1] = v.y;
+        dst[2] = v.z;
+        dst[3] = v.w;
+      }
+      loaded = true;
+    }
+  }
+  if (!loaded) {
+    const int nload = E0 * E1 * E2;
+    for (int e = threadIdx.x; e < nload; e += blockDim.x) {
+      const int c = e % E2;
+      const int ab = e / E2;
+      const int b = ab % E1;
+      const int a = ab / E1;
+      const int gi = wrap_index(o0 + a, g.M[0]);
+      const int gj = wrap_index(o1 + b, g.M[1]);
+      const int gk = wrap_index(o2 + c, g.M[2]);
+      phi[(a * E1 + b) * E3p + c] = grid[((int64_t)gi * g.M[1] + gj) * g.M[2] + gk];
+    }
   }
   for (int e = threadIdx.x; e < 2 * (g.deg + 1) * P; e += blockDim.x) tab[e] = wtab[e];
   __syncthreads();
 
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  R* wb = wbuf + wid * 6 * P;  // [w0 w1 w2 | dw0 dw1 dw2]
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  R* W = wbuf + wid * kBatch * 6 * P;  // per atom [w0 w1 w2 | dw0 dw1 dw2]
+  R* Fa = fbuf + wid * kBatch * 3;
+  int* B = bbuf + wid * kBatch;
   const R* dtab = tab + (g.deg + 1) * P;
-  for (int j = start + wid; j < end; j += nw) {
-    const typename Vec4<R>::T v = sorted_tq[j];
-    const int lb = sorted_lb[j];
-    for (int e = lane; e < 6 * P; e += 32) {
-      const int which = e / (3 * P);
-      const int r = e - which * 3 * P;
-      const int d = r / P, p = r - d * P;
+  for (int j0 = start + wid * kBatch; j0 < end; j0 += nw * kBatch) {
+    const int cnt = min(kBatch, end - j0);
+    for (int e = lane; e < cnt * 6 * P; e += 32) {
+      const int a = e / (6 * P);
+      const int r = e - a * 6 * P;
+      const int which = r / (3 * P);
+      const int r2 = r - which * 3 * P;
+      const int d = r2 / P, p = r2 - d * P;
+      const typename Vec4<R>::T v = sorted_tq[j0 + a];
       const R t = tq_comp<R>(v, d);
-      R val;
-      if (which == 0) {
-        val = horner_window(tab, g.deg, P, p, t);
-      } else {
-        val = horner_window(dtab, g.deg, P, p, t) * R(2.0 * g.M[d] / P);
+      W[e] = which == 0 ? horner_window(tab, g.deg, P, p, t)
+                        : horner_window(dtab, g.deg, P, p, t) * dscale_of<R>(g, d);
+    }
+    if (lane < cnt) B[lane] = local_base(sorted_lb[j0 + lane], E1, E3p);
+    if (lane < 3 * cnt) Fa[lane] = R(0);
+    __syncwarp();
+    for (int it = lane; it < cnt * P * P; it += 32) {
+      const int a = it / (P * P);
+      const int pr = it - a * P * P;
+      const int jj = pr / P, k = pr - jj * P;
+      const R* Wa = W + a * 6 * P;
+      const R* src = phi + B[a] + jj * E3p + k;
+      R sx = R(0), sw = R(0);
+#pragma unroll
+      for (int i = 0; i < P; ++i) {
+        const R f = src[i * S1];
+        sx = fma(f, Wa[3 * P + i], sx);
+        sw = fma(f, Wa[i], sw);
       }
-      wb[e] = val;
+      const R w1 = Wa[P + jj], w2 = Wa[2 * P + k];
+      atomicAdd(&Fa[3 * a + 0], w1 * w2 * sx);
+      atomicAdd(&Fa[3 * a + 1], Wa[4 * P + jj] * w2 * sw);
+      atomicAdd(&Fa[3 * a + 2], w1 * Wa[5 * P + k] * sw);
     }
     __syncwarp();
-    const int l0 = lb & 1023, l1 = (lb >> 10) & 1023, l2 = (lb >> 20) & 1023;
-    const int base = (l0 * E1 + l1) * E3p + l2;
-    R gx = R(0), gy = R(0), gz = R(0);
-#pragma unroll 4
-    for (int nidx = lane; nidx < P * P * P; nidx += 32) {
-      const int i = nidx / (P * P);
-      const int jj = (nidx / P) % P;
-      const int k = nidx % P;
-      const R f = phi[base + (i * E1 + jj) * E3p + k];
-      const R w0 = wb[i], w1 = wb[P + jj], w2 = wb[2 * P + k];
-      const R d0 = wb[3 * P + i], d1 = wb[4 * P + jj], d2 = wb[5 * P + k];
-      gx = fma(f * d0, w1 * w2, gx);
-      gy = fma(f * w0, d1 * w2, gy);
-      gz = fma(f * w0, w1 * d2, gz);
-    }
-    gx = warp_sum(gx);
-    gy = warp_sum(gy);
-    gz = warp_sum(gz);
-    if (lane == 0) {
-      // dU/ds = -(q/(V Mtot^2)) (gx, gy, gz);  F = -h^{-T} dU/ds
-      const double f = (double)v.w * gg.fscale;
-      const double a0 = f * (double)gx, a1 = f * (double)gy, a2 = f * (double)gz;
+    if (lane < cnt) {
+      // dU/ds = -(q / (V Mtot^2)) (gx, gy, gz);  F = -h^{-T} dU/ds
+      const int j = j0 + lane;
       const int idx = sorted_idx[j];
+      const R gx = Fa[3 * lane], gy = Fa[3 * lane + 1], gz = Fa[3 * lane + 2];
+      if constexpr (std::is_same<R, float>::value) {
+        const float f = sorted_tq[j].w * (float)gg.fscale;
 #pragma unroll
-      for (int c = 0; c < 3; ++c)
-        forces[3 * (int64_t)idx + c] = (IO)(g.hinv[c] * a0 + g.hinv[3 + c] * a1 + g.hinv[6 + c] * a2);
+        for (int c = 0; c < 3; ++c)
+          forces[3 * (int64_t)idx + c] =
+              (IO)(f * (g.hinvf[c] * gx + g.hinvf[3 + c] * gy + g.hinvf[6 + c] * gz));
+      } else {
+        const double f = sorted_tq[j].w * gg.fscale;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          forces[3 * (int64_t)idx + c] =
+              (IO)(f * (g.hinv[c] * gx + g.hinv[3 + c] * gy + g.hinv[6 + c] * gz));
+      }
     }
     __syncwarp();
   }
@@ -509,11 +604,6 @@ int grid_blocks(int64_t n) {
   if (b < 1) b = 1;
   if (b > 152 * 16) b = 152 * 16;
   return (int)b;
-}
-
-template <typename R>
-size_t tile_elems(const TileGeom& g) {
-  return (size_t)g.E[0] * g.E[1] * g.E3p;
 }
 
 // dispatch a functor templated on P
@@ -537,17 +627,27 @@ cudaError_t with_P(int P, F&& f) {
 }  // namespace
 
 // ---- host launchers --------------------------------------------------------------------
-cudaError_t launch_bin(bool io_double, const void* pos, const void* q, int64_t n,
+cudaError_t launch_bin(bool io_double, bool fp64, const void* pos, const void* q, int64_t n,
                        const TileGeom& g, int* tile_count, int* ptile, int* prank, int* plb,
-                       double* accum, cudaStream_t st) {
+                       void* tq, double* accum, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int nb = grid_blocks(n);
-  if (io_double)
-    k_bin<double><<<nb, kThreads, 0, st>>>((const double*)pos, (const double*)q, n, g,
-                                            tile_count, ptile, prank, plb, accum);
+  if (io_double && fp64)
+    k_bin<double, double><<<nb, kThreads, 0, st>>>((const double*)pos, (const double*)q, n, g,
+                                                    tile_count, ptile, prank, plb,
+                                                    (double4*)tq, accum);
+  else if (io_double)
+    k_bin<double, float><<<nb, kThreads, 0, st>>>((const double*)pos, (const double*)q, n, g,
+                                                   tile_count, ptile, prank, plb, (float4*)tq,
+                                                   accum);
+  else if (fp64)
+    k_bin<float, double><<<nb, kThreads, 0, st>>>((const float*)pos, (const float*)q, n, g,
+                                                   tile_count, ptile, prank, plb, (double4*)tq,
+                                                   accum);
   else
-    k_bin<float><<<nb, kThreads, 0, st>>>((const float*)pos, (const float*)q, n, g,
-                                           tile_count, ptile, prank, plb, accum);
+    k_bin<float, float><<<nb, kThreads, 0, st>>>((const float*)pos, (const float*)q, n, g,
+                                                  tile_count, ptile, prank, plb, (float4*)tq,
+                                                  accum);
   return cudaGetLastError();
 }
 
@@ -556,41 +656,35 @@ cudaError_t launch_scan(const int* count, int* offset, int ntiles, cudaStream_t 
   return cudaGetLastError();
 }
 
-cudaError_t launch_scatter(bool io_double, bool fp64, const void* pos, const void* q,
-                           int64_t n, const TileGeom& g, const int* ptile, const int* prank,
-                           const int* plb, const int* offset, void* sorted_tq, int* sorted_lb, int* sorted_idx,
-                           cudaStream_t st) {
+cudaError_t launch_scatter(bool fp64, int64_t n, const int* ptile, const int* prank,
+                           const int* plb, const void* tq, const int* offset, void* sorted_tq,
+                           int* sorted_lb, int* sorted_idx, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int nb = grid_blocks(n);
-  if (io_double && fp64)
-    k_scatter<double, double><<<nb, kThreads, 0, st>>>(
-        (const double*)pos, (const double*)q, n, g, ptile, prank, plb, offset,
-        (double4*)sorted_tq, sorted_lb, sorted_idx);
-  else if (io_double)
-    k_scatter<double, float><<<nb, kThreads, 0, st>>>(
-        (const double*)pos, (const double*)q, n, g, ptile, prank, plb, offset,
-        (float4*)sorted_tq, sorted_lb, sorted_idx);
-  else if (fp64)
-    k_scatter<float, double><<<nb, kThreads, 0, st>>>(
-        (const float*)pos, (const float*)q, n, g, ptile, prank, plb, offset, (double4*)sorted_tq,
-        sorted_lb, sorted_idx);
+  if (fp64)
+    k_scatter<double4><<<nb, kThreads, 0, st>>>(n, ptile, prank, plb, (const double4*)tq,
+                                                offset, (double4*)sorted_tq, sorted_lb,
+                                                sorted_idx);
   else
-    k_scatter<float, float><<<nb, kThreads, 0, st>>>(
-        (const float*)pos, (const float*)q, n, g, ptile, prank, plb, offset, (float4*)sorted_tq,
-        sorted_lb, sorted_idx);
+    k_scatter<float4><<<nb, kThreads, 0, st>>>(n, ptile, prank, plb, (const float4*)tq, offset,
+                                               (float4*)sorted_tq, sorted_lb, sorted_idx);
   return cudaGetLastError();
 }
 
 size_t spread_smem_bytes(bool fp64, const TileGeom& g) {
   const size_t es = fp64 ? 8 : 4;
+  const size_t nw = kThreads / 32;
   return es * ((size_t)g.E[0] * g.E[1] * g.E3p + (size_t)(g.deg + 1) * g.P +
-               (size_t)(kThreads / 32) * 3 * g.P);
+               nw * kBatch * 3 * g.P) +
+         sizeof(int) * nw * kBatch;
 }
 
 size_t gather_smem_bytes(bool fp64, const TileGeom& g) {
   const size_t es = fp64 ? 8 : 4;
+  const size_t nw = kThreads / 32;
   return es * ((size_t)g.E[0] * g.E[1] * g.E3p + (size_t)2 * (g.deg + 1) * g.P +
-               (size_t)(kThreads / 32) * 6 * g.P);
+               nw * kBatch * 6 * g.P + nw * kBatch * 3) +
+         sizeof(int) * nw * kBatch;
 }
 
 cudaError_t configure_kernels(bool fp64, int P, size_t spread_smem, size_t gather_smem) {

@@ -11,6 +11,7 @@ constexpr int kMaxP = 12;
 constexpr int kMaxDeg = 24;
 constexpr int kRadialPieces = 16;
 constexpr int kThreads = 256;
+constexpr int kBatch = 8;  // atoms a warp handles together in spread / gather
 
 // Geometry shared by the binning, spreading and gathering kernels.
 struct TileGeom {
@@ -19,9 +20,13 @@ struct TileGeom {
   int T[3];     // tile extent (grid points of stencil bases per tile)
   int nt[3];    // tiles per dimension
   int E[3];     // padded tile extent T + P - 1
-  int E3p;      // padded row pitch in shared memory (>= E[2])
+  int E3p;      // shared-memory row pitch >= E[2], chosen with E3p = -P (mod 32)
   int deg;      // degree of the window polynomials
-  double hinv[9];  // h^{-1}, row-major
+  int vec4;     // 1: rows move as aligned float4 between global and shared memory
+  double hinv[9];    // h^{-1}, row-major
+  float hinvf[9];    // the same in FP32 (FP32 force transform)
+  double dscale[3];  // d u / d s factor of the window argument: 2 M_d / P
+  float dscalef[3];
 };
 
 // Constants of the fused scaling + reduction pass over the half spectrum.
@@ -31,6 +36,7 @@ struct ScaleGeom {
   int mmax[3];   // bounding box of the sphere |k| <= K in m
   int rdeg;      // degree of the radial psi_0 / psi_0' polynomials
   double b[9];   // reciprocal vectors: k = m0 b_0 + m1 b_1 + m2 b_2, b_d = 2 pi (row d of h^{-1})
+  float bf[9];
   double K2;     // (c / r_c)^2
   double x_per_k;  // r_c / c
   double A;      // 2 pi lambda_0 / C_0 = 4 pi / psi_0(0)
@@ -43,16 +49,15 @@ struct GatherGeom {
 };
 
 // ---- launchers (return cudaGetLastError() of the launch) -----------------------------
-// io_double: pos/q/F are double (else float).  R: compute type via `fp64`.
+// io_double: pos/q/F are double (else float).  fp64: compute type double (else float).
 
-cudaError_t launch_bin(bool io_double, const void* pos, const void* q, int64_t n,
+cudaError_t launch_bin(bool io_double, bool fp64, const void* pos, const void* q, int64_t n,
                        const TileGeom& g, int* tile_count, int* ptile, int* prank, int* plb,
-                       double* accum, cudaStream_t st);
+                       void* tq, double* accum, cudaStream_t st);
 cudaError_t launch_scan(const int* count, int* offset, int ntiles, cudaStream_t st);
-cudaError_t launch_scatter(bool io_double, bool fp64, const void* pos, const void* q,
-                           int64_t n, const TileGeom& g, const int* ptile, const int* prank,
-                           const int* plb, const int* offset, void* sorted_tq, int* sorted_lb, int* sorted_idx,
-                           cudaStream_t st);
+cudaError_t launch_scatter(bool fp64, int64_t n, const int* ptile, const int* prank,
+                           const int* plb, const void* tq, const int* offset, void* sorted_tq,
+                           int* sorted_lb, int* sorted_idx, cudaStream_t st);
 cudaError_t launch_spread(bool fp64, const TileGeom& g, int ntiles, const void* sorted_tq,
                           const int* sorted_lb, const int* offset, const void* wtab,
                           void* grid, cudaStream_t st);

@@ -32,6 +32,14 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
 
 
+def fitting_rc(cell, grid, delta, floor=3.0):
+    """Smallest split radius (>= floor) for which every in-sphere mode stays below Nyquist."""
+    c = c_from_tolerance(delta)
+    lens = np.linalg.norm(np.asarray(cell), axis=0)
+    need = max(lens[d] * c / (math.pi * (grid[d] - 1.5)) for d in range(3))
+    return max(floor, need)
+
+
 def run_gpu(S, c, precision, forces=True):
     plan = esp.Plan(S.cell, S.n, S.grid, S.P, c, S.rc, precision=precision)
     dt = torch.float64 if precision == "fp64" else torch.float32
@@ -84,23 +92,33 @@ def test_water648(precision):
     (4, (9, 10, 64), TRI, 123),      # grid smaller than a tile in two dimensions
 ])
 def test_ragged_and_odd(precision, P, grid, cell, n):
-    S = sy.small_random(n, cell, seed=7 + n, grid=grid, P=P, delta=1e-6, rc=3.5)
+    rc = fitting_rc(cell, grid, 1e-5)
+    S = sy.small_random(n, cell, seed=7 + n, grid=grid, P=P, delta=1e-5, rc=rc)
     check(S, precision)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_empty_and_single_atom(precision):
-    S0 = sy.small_random(0, ORTHO, seed=1, grid=(16, 16, 16), P=6, rc=3.5)
+    rc = fitting_rc(ORTHO, (16, 16, 16), 1e-6)
+    S0 = sy.small_random(0, ORTHO, seed=1, grid=(16, 16, 16), P=6, rc=rc)
     c = c_from_tolerance(1e-6)
-    plan = esp.Plan(S0.cell, 0, S0.grid, 6, c, 3.5, precision=precision)
+    plan = esp.Plan(S0.cell, 0, S0.grid, 6, c, rc, precision=precision)
     dt = torch.float64 if precision == "fp64" else torch.float32
     r = plan.energy_pressure(torch.zeros((0, 3), dtype=dt, device="cuda"), torch.zeros(0, dtype=dt, device="cuda"))
     assert r["energy_recip"] == 0.0 and np.all(r["virial_recip"] == 0.0) and r["q2sum"] == 0.0
     plan.close()
-    S1 = sy.small_random(1, ORTHO, seed=2, grid=(16, 16, 16), P=6, rc=3.5)
+    S1 = sy.small_random(1, ORTHO, seed=2, grid=(16, 16, 16), P=6, rc=rc)
     S1.q[:] = 1.0  # a lone (non-neutral) charge: grid self-interaction plus background
-    res, _ = check(S1, precision)
+    plan, res, F, pos, q = run_gpu(S1, c, precision)
+    ref = esp_grid(pos, q, S1.cell, S1.grid, 6, c, rc)
+    tol = TOL[precision]
+    assert rel(res["energy_recip"], ref["energy"]) < tol
+    assert rel(res["virial_recip"], ref["virial"]) < tol
+    # the self-force of a lone charge is pure aliasing, ~1e-6 of the sums it cancels out
+    # of; compare on the scale of the field of a unit charge at the split radius
+    assert np.max(np.abs(F - ref["forces"])) < tol / rc ** 2
     assert res["energy_bg"] < 0.0
+    plan.close()
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
@@ -175,7 +193,7 @@ def test_set_cell_npt(precision):
 
 
 def test_nonfinite_input_is_reported_not_faulted():
-    S = sy.small_random(100, ORTHO, seed=9, grid=(16, 16, 16), P=6, rc=3.5)
+    S = sy.small_random(100, ORTHO, seed=9, grid=(16, 16, 16), P=6, rc=fitting_rc(ORTHO, (16, 16, 16), 1e-6))
     c = c_from_tolerance(S.delta)
     plan = esp.Plan(S.cell, S.n, S.grid, S.P, c, S.rc, precision="fp64")
     pos = torch.tensor(S.pos, device="cuda")
