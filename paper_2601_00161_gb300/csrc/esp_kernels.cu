@@ -66,8 +66,9 @@ __device__ __forceinline__ void stencil_base(double s, int M, int P, int* base, 
   if (P & 1) x = __dadd_rn(x, 0.5);
   const double fl = floor(x);
   *t = __dsub_rn(x, fl);
-  const int b = (int)fl - ((P & 1) ? (P - 1) / 2 : P / 2 - 1);
-  *base = wrap_index(b, M);
+  int b = (int)fl - ((P & 1) ? (P - 1) / 2 : P / 2 - 1);  // in [-P/2, M]
+  b = b < 0 ? b + M : (b >= M ? b - M : b);
+  *base = b;
 }
 
 __device__ __forceinline__ double reduced_coord(const double* hinv_row, const double r[3]) {
@@ -142,27 +143,27 @@ __global__ void __launch_bounds__(kThreads) k_bin(const IO* __restrict__ pos,
     sq += qi;
     sq2 += qi * qi;
   }
-  __shared__ double red[3][kThreads / 32];
-  sq = warp_sum(sq);
-  sq2 = warp_sum(sq2);
-  bad = warp_sum(bad);
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (lane == 0) {
-    red[0][wid] = sq;
-    red[1][wid] = sq2;
-    red[2][wid] = bad;
-  }
+  // block sums through shared memory (one warp adds them up), then one FP64 atomic each
+  __shared__ double red[3][kThreads];
+  red[0][threadIdx.x] = sq;
+  red[1][threadIdx.x] = sq2;
+  red[2][threadIdx.x] = bad;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0, b = 0, c = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+  if (threadIdx.x < 32) {
+    double a = 0.0, b = 0.0, c = 0.0;
+    for (int w = threadIdx.x; w < (int)blockDim.x; w += 32) {
       a += red[0][w];
       b += red[1][w];
       c += red[2][w];
     }
-    if (a != 0.0) atomicAdd(&accum[7], a);
-    if (b != 0.0) atomicAdd(&accum[8], b);
-    if (c != 0.0) atomicAdd(&accum[9], c);
+    a = warp_sum(a);
+    b = warp_sum(b);
+    c = warp_sum(c);
+    if (threadIdx.x == 0) {
+      if (a != 0.0) atomicAdd(&accum[7], a);
+      if (b != 0.0) atomicAdd(&accum[8], b);
+      if (c != 0.0) atomicAdd(&accum[9], c);
+    }
   }
 }
 
@@ -235,6 +236,14 @@ __device__ __forceinline__ R tq_comp(const typename Vec4<R>::T& v, int d) {
   return d == 0 ? v.x : (d == 1 ? v.y : v.z);
 }
 
+// Shared-memory accumulation without a return value (red.shared): FP32 by inline PTX,
+// FP64 through atomicAdd.
+__device__ __forceinline__ void smem_add(float* p, float v) {
+  asm volatile("red.shared.add.f32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "f"(v)
+               : "memory");
+}
+__device__ __forceinline__ void smem_add(double* p, double v) { atomicAdd(p, v); }
+
 __device__ __forceinline__ int local_base(int lb, int E1, int E3p) {
   return (((lb & 1023) * E1 + ((lb >> 10) & 1023)) * E3p) + ((lb >> 20) & 1023);
 }
@@ -285,7 +294,7 @@ __global__ void __launch_bounds__(kThreads) k_spread(
       const R pw = Wa[P + jj] * Wa[2 * P + k];
       R* dst = acc + B[a] + jj * E3p + k;
 #pragma unroll
-      for (int i = 0; i < P; ++i) atomicAdd(dst + i * S1, Wa[i] * pw);
+      for (int i = 0; i < P; ++i) smem_add(dst + i * S1, Wa[i] * pw);
     }
     __syncwarp();
   }
@@ -370,81 +379,94 @@ __global__ void __launch_bounds__(kThreads) k_scale(typename Cplx<R>::T* __restr
                                                     double* __restrict__ partials,
                                                     unsigned int* __restrict__ counter,
                                                     double* __restrict__ accum) {
+  // One warp per row (i0, i1) of the half spectrum, lanes along i2.  Rows outside the
+  // bounding box of the sphere |k| <= K and modes beyond mmax[2] hold no in-sphere mode:
+  // they are skipped (energy / pressure only) or zeroed (force path).
   double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-  const int64_t total = (int64_t)s.M[0] * s.M[1] * s.H2;
   const R* iw0 = invw2;
   const R* iw1 = invw2 + s.M[0];
   const R* iw2 = invw2 + s.M[0] + s.M[1];
-  for (int64_t nidx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; nidx < total;
-       nidx += (int64_t)gridDim.x * blockDim.x) {
-    const int i2 = (int)(nidx % s.H2);
-    const int64_t rr = nidx / s.H2;
-    const int i1 = (int)(rr % s.M[1]);
-    const int i0 = (int)(rr / s.M[1]);
+  const int lane = threadIdx.x & 31;
+  const int nrows = s.M[0] * s.M[1];
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  typename Cplx<R>::T zero;
+  zero.x = R(0);
+  zero.y = R(0);
+  for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < nrows; row += warps) {
+    const int i0 = row / s.M[1];
+    const int i1 = row - i0 * s.M[1];
     const int m0 = (2 * i0 <= s.M[0]) ? i0 : i0 - s.M[0];
     const int m1 = (2 * i1 <= s.M[1]) ? i1 : i1 - s.M[1];
-    const int m2 = i2;
-    bool inside = abs(m0) <= s.mmax[0] && abs(m1) <= s.mmax[1] && m2 <= s.mmax[2] &&
-                  (m0 | m1 | m2) != 0;
-    R kx = R(0), ky = R(0), kz = R(0), k2 = R(0);
-    if (inside) {
-      const R f0 = R(m0), f1 = R(m1), f2 = R(m2);
-      kx = f0 * bvec<R>(s, 0) + f1 * bvec<R>(s, 3) + f2 * bvec<R>(s, 6);
-      ky = f0 * bvec<R>(s, 1) + f1 * bvec<R>(s, 4) + f2 * bvec<R>(s, 7);
-      kz = f0 * bvec<R>(s, 2) + f1 * bvec<R>(s, 5) + f2 * bvec<R>(s, 8);
-      k2 = kx * kx + ky * ky + kz * kz;
-      // The in-sphere decision is an FP64 one (as in the FP64 oracle): FP32 decides only
-      // when it is far from the boundary.
-      const double K2 = s.K2;
-      if (sizeof(R) == 8 || fabs((double)k2 - K2) <= 1e-5 * K2) {
-        const double dx = m0 * s.b[0] + m1 * s.b[3] + m2 * s.b[6];
-        const double dy = m0 * s.b[1] + m1 * s.b[4] + m2 * s.b[7];
-        const double dz = m0 * s.b[2] + m1 * s.b[5] + m2 * s.b[8];
-        inside = dx * dx + dy * dy + dz * dz <= K2;
-      } else {
-        inside = (double)k2 <= K2;
-      }
-    }
-    if (!inside) {
-      if (WRITE) {
-        typename Cplx<R>::T z;
-        z.x = R(0);
-        z.y = R(0);
-        spec[nidx] = z;
-      }
+    typename Cplx<R>::T* rowp = spec + (int64_t)row * s.H2;
+    const bool row_in_box = abs(m0) <= s.mmax[0] && abs(m1) <= s.mmax[1];
+    if (!row_in_box) {
+      if (WRITE)
+        for (int i2 = lane; i2 < s.H2; i2 += 32) rowp[i2] = zero;
       continue;
     }
-    const typename Cplx<R>::T X = spec[nidx];
-    const R iw = iw0[i0] * iw1[i1] * iw2[i2];
-    const R kmag = sqrt(k2);
-    const R x = kmag * R(s.x_per_k);
-    R psi, dpsi;
-    radial_eval(radtab, s.rdeg, x, &psi, &dpsi);
-    const R Fhat = R(s.A) * psi / k2;
-    const R dterm = R(s.A) * x * dpsi / (k2 * k2);
-    const bool single = (i2 == 0) || ((s.M[2] & 1) == 0 && 2 * i2 == s.M[2]);
-    const R a = (single ? R(1) : R(2)) * (X.x * X.x + X.y * X.y) * iw * R(s.scale);
-    const R aF = a * Fhat;
-    const R ck = a * (dterm - R(2) * Fhat / k2);
-    acc[0] += (double)aF;
-    acc[1] += (double)(aF + ck * kx * kx);
-    acc[2] += (double)(aF + ck * ky * ky);
-    acc[3] += (double)(aF + ck * kz * kz);
-    acc[4] += (double)(ck * kx * ky);
-    acc[5] += (double)(ck * kx * kz);
-    acc[6] += (double)(ck * ky * kz);
-    if (WRITE) {
-      const R G = Fhat * iw;
-      typename Cplx<R>::T y;
-      y.x = X.x * G;
-      y.y = X.y * G;
-      spec[nidx] = y;
+    const R f0 = R(m0), f1 = R(m1);
+    const R kx0 = f0 * bvec<R>(s, 0) + f1 * bvec<R>(s, 3);
+    const R ky0 = f0 * bvec<R>(s, 1) + f1 * bvec<R>(s, 4);
+    const R kz0 = f0 * bvec<R>(s, 2) + f1 * bvec<R>(s, 5);
+    const R iw01 = iw0[i0] * iw1[i1];
+    for (int i2 = lane; i2 < s.H2; i2 += 32) {
+      const int m2 = i2;
+      bool inside = m2 <= s.mmax[2] && (m0 | m1 | m2) != 0;
+      R kx = R(0), ky = R(0), kz = R(0), k2 = R(0);
+      if (inside) {
+        const R f2 = R(m2);
+        kx = kx0 + f2 * bvec<R>(s, 6);
+        ky = ky0 + f2 * bvec<R>(s, 7);
+        kz = kz0 + f2 * bvec<R>(s, 8);
+        k2 = kx * kx + ky * ky + kz * kz;
+        // The in-sphere decision is an FP64 one (as in the FP64 oracle): FP32 decides
+        // only when it is far from the boundary.
+        const double K2 = s.K2;
+        if (sizeof(R) == 8 || fabs((double)k2 - K2) <= 1e-5 * K2) {
+          const double dx = m0 * s.b[0] + m1 * s.b[3] + m2 * s.b[6];
+          const double dy = m0 * s.b[1] + m1 * s.b[4] + m2 * s.b[7];
+          const double dz = m0 * s.b[2] + m1 * s.b[5] + m2 * s.b[8];
+          inside = dx * dx + dy * dy + dz * dz <= K2;
+        } else {
+          inside = (double)k2 <= K2;
+        }
+      }
+      if (!inside) {
+        if (WRITE) rowp[i2] = zero;
+        continue;
+      }
+      const typename Cplx<R>::T X = rowp[i2];
+      const R iw = iw01 * iw2[i2];
+      const R kmag = sqrt(k2);
+      const R x = kmag * R(s.x_per_k);
+      R psi, dpsi;
+      radial_eval(radtab, s.rdeg, x, &psi, &dpsi);
+      const R Fhat = R(s.A) * psi / k2;
+      const R dterm = R(s.A) * x * dpsi / (k2 * k2);
+      const bool single = (i2 == 0) || ((s.M[2] & 1) == 0 && 2 * i2 == s.M[2]);
+      const R a = (single ? R(1) : R(2)) * (X.x * X.x + X.y * X.y) * iw * R(s.scale);
+      const R aF = a * Fhat;
+      const R ck = a * (dterm - R(2) * Fhat / k2);
+      acc[0] += (double)aF;
+      acc[1] += (double)(aF + ck * kx * kx);
+      acc[2] += (double)(aF + ck * ky * ky);
+      acc[3] += (double)(aF + ck * kz * kz);
+      acc[4] += (double)(ck * kx * ky);
+      acc[5] += (double)(ck * kx * kz);
+      acc[6] += (double)(ck * ky * kz);
+      if (WRITE) {
+        const R G = Fhat * iw;
+        typename Cplx<R>::T y;
+        y.x = X.x * G;
+        y.y = X.y * G;
+        rowp[i2] = y;
+      }
     }
   }
   // block reduction, then the last block folds the per-block partials in a fixed order
   __shared__ double red[7][kThreads / 32];
   __shared__ bool last;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int wid = threadIdx.x >> 5;
 #pragma unroll
   for (int j = 0; j < 7; ++j) {
     const double v = warp_sum(acc[j]);
@@ -557,25 +579,51 @@ __global__ void __launch_bounds__(kThreads) k_gather(
     if (lane < cnt) B[lane] = local_base(sorted_lb[j0 + lane], E1, E3p);
     if (lane < 3 * cnt) Fa[lane] = R(0);
     __syncwarp();
-    for (int it = lane; it < cnt * P * P; it += 32) {
-      const int a = it / (P * P);
-      const int pr = it - a * P * P;
-      const int jj = pr / P, k = pr - jj * P;
-      const R* Wa = W + a * 6 * P;
-      const R* src = phi + B[a] + jj * E3p + k;
-      R sx = R(0), sw = R(0);
+    const int nitem = cnt * P * P;
+    for (int r0 = 0; r0 < nitem; r0 += 32) {
+      const int it = r0 + lane;
+      const bool act = it < nitem;
+      const int a = act ? it / (P * P) : kBatch;
+      R gx = R(0), gy = R(0), gz = R(0);
+      if (act) {
+        const int pr = it - a * P * P;
+        const int jj = pr / P, k = pr - jj * P;
+        const R* Wa = W + a * 6 * P;
+        const R* src = phi + B[a] + jj * E3p + k;
+        R sx = R(0), sw = R(0);
 #pragma unroll
-      for (int i = 0; i < P; ++i) {
-        const R f = src[i * S1];
-        sx = fma(f, Wa[3 * P + i], sx);
-        sw = fma(f, Wa[i], sw);
+        for (int i = 0; i < P; ++i) {
+          const R f = src[i * S1];
+          sx = fma(f, Wa[3 * P + i], sx);
+          sw = fma(f, Wa[i], sw);
+        }
+        const R w1 = Wa[P + jj], w2 = Wa[2 * P + k];
+        gx = w1 * w2 * sx;
+        gy = Wa[4 * P + jj] * w2 * sw;
+        gz = w1 * Wa[5 * P + k] * sw;
       }
-      const R w1 = Wa[P + jj], w2 = Wa[2 * P + k];
-      atomicAdd(&Fa[3 * a + 0], w1 * w2 * sx);
-      atomicAdd(&Fa[3 * a + 1], Wa[4 * P + jj] * w2 * sw);
-      atomicAdd(&Fa[3 * a + 2], w1 * Wa[5 * P + k] * sw);
+      // lanes of one atom are contiguous: segmented inclusive scan, the last lane of
+      // each segment holds the atom's sum for this round
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int ao = __shfl_up_sync(0xffffffffu, a, o);
+        const R x = __shfl_up_sync(0xffffffffu, gx, o);
+        const R y = __shfl_up_sync(0xffffffffu, gy, o);
+        const R z = __shfl_up_sync(0xffffffffu, gz, o);
+        if (lane >= o && ao == a) {
+          gx += x;
+          gy += y;
+          gz += z;
+        }
+      }
+      const int an = __shfl_down_sync(0xffffffffu, a, 1);
+      if (act && (lane == 31 || an != a)) {
+        Fa[3 * a + 0] += gx;
+        Fa[3 * a + 1] += gy;
+        Fa[3 * a + 2] += gz;
+      }
+      __syncwarp();
     }
-    __syncwarp();
     if (lane < cnt) {
       // dU/ds = -(q / (V Mtot^2)) (gx, gy, gz);  F = -h^{-T} dU/ds
       const int j = j0 + lane;
