@@ -195,34 +195,39 @@ int upload(esp_plan_t p, void** dst, const std::vector<double>& src) {
 
 // Window polynomials (Sec. 4.3): for stencil point p and t in [0,1) the window value is
 // psi_0(u) with u = 2 (p + 1 - P/2 - t) / P; coefficients of (t - 1/2)^k, laid out
-// [w: k * P + p][dw: (deg+1) * P + k * P + p].  The degree grows until the fit is below
-// the precision's tolerance.
+// [w: k * P + p][dw: (deg+1) * P + k * P + p].  The degree is fixed per compute type
+// (kDegF32 / kDegF64, so that the kernels keep a lane's coefficients in registers); the
+// plan fails if that degree does not reach the precision's tolerance, which happens only
+// for a stencil far too narrow for c.
 int build_window_tables(esp_plan_t p, std::vector<double>& tab) {
   const esp::Prolate& pr = p->pswf;
   const int P = p->P;
-  const double tol = p->fp64 ? 3e-15 : 2e-8;
+  const double tol = p->fp64 ? 1e-14 : 5e-8;
+  const int deg = p->fp64 ? esp::kDegF64 : esp::kDegF32;
   double dmax = 0.0;
   for (int i = 0; i <= 200; ++i) dmax = std::max(dmax, std::fabs(pr.deriv(-1.0 + i / 100.0)));
-  for (int deg = 6; deg <= esp::kMaxDeg; ++deg) {
-    tab.assign(2 * (deg + 1) * P, 0.0);
-    double err = 0.0;
-    std::vector<double> coef(deg + 1);
-    for (int pp = 0; pp < P; ++pp) {
-      auto u_of = [P, pp](double t) { return 2.0 * (pp + 1.0 - 0.5 * P - t) / P; };
-      double e1 = esp::fit_piece([&](double t) { return pr.eval(u_of(t)); }, 0.0, 1.0, deg,
-                                 coef.data());
-      for (int k = 0; k <= deg; ++k) tab[k * P + pp] = coef[k];
-      double e2 = esp::fit_piece([&](double t) { return pr.deriv(u_of(t)); }, 0.0, 1.0, deg,
-                                 coef.data());
-      for (int k = 0; k <= deg; ++k) tab[(deg + 1) * P + k * P + pp] = coef[k];
-      err = std::max(err, std::max(e1 / pr.psi_at_0, e2 / dmax));
-    }
-    if (err <= tol || deg == esp::kMaxDeg) {
-      p->deg = deg;
-      p->fit_err = err;
-      if (err > 50 * tol) return fail(p, ESP_ERR_ARG, "window polynomial fit did not converge");
-      return ESP_OK;
-    }
+  tab.assign(2 * (deg + 1) * P, 0.0);
+  double err = 0.0;
+  std::vector<double> coef(deg + 1);
+  for (int pp = 0; pp < P; ++pp) {
+    auto u_of = [P, pp](double t) { return 2.0 * (pp + 1.0 - 0.5 * P - t) / P; };
+    double e1 = esp::fit_piece([&](double t) { return pr.eval(u_of(t)); }, 0.0, 1.0, deg,
+                               coef.data());
+    for (int k = 0; k <= deg; ++k) tab[k * P + pp] = coef[k];
+    double e2 = esp::fit_piece([&](double t) { return pr.deriv(u_of(t)); }, 0.0, 1.0, deg,
+                               coef.data());
+    for (int k = 0; k <= deg; ++k) tab[(deg + 1) * P + k * P + pp] = coef[k];
+    err = std::max(err, std::max(e1 / pr.psi_at_0, e2 / dmax));
+  }
+  p->deg = deg;
+  p->fit_err = err;
+  if (err > tol) {
+    char buf[200];
+    std::snprintf(buf, sizeof buf,
+                  "window polynomial fit error %.2e exceeds %.0e: stencil P = %d too narrow "
+                  "for c = %.3f",
+                  err, tol, P, p->c);
+    return fail(p, ESP_ERR_ARG, buf);
   }
   return ESP_OK;
 }
@@ -231,7 +236,7 @@ int build_window_tables(esp_plan_t p, std::vector<double>& tab) {
 // derivative in eq. (Far)), kRadialPieces pieces, coefficients of (x - centre)^k.
 int build_radial_tables(esp_plan_t p, std::vector<double>& tab) {
   const esp::Prolate& pr = p->pswf;
-  const double tol = p->fp64 ? 3e-15 : 2e-8;
+  const double tol = p->fp64 ? 3e-15 : 2e-8;  // converged fits stop early
   const int NR = esp::kRadialPieces;
   double dmax = 0.0;
   for (int i = 0; i <= 100; ++i) dmax = std::max(dmax, std::fabs(pr.deriv(i / 100.0)));
@@ -250,7 +255,8 @@ int build_radial_tables(esp_plan_t p, std::vector<double>& tab) {
     if (err <= tol || deg == esp::kMaxDeg) {
       p->rdeg = deg;
       p->rfit_err = err;
-      if (err > 50 * tol) return fail(p, ESP_ERR_ARG, "radial polynomial fit did not converge");
+      if (err > (p->fp64 ? 1e-14 : 5e-8))
+        return fail(p, ESP_ERR_ARG, "radial polynomial fit did not converge");
       return ESP_OK;
     }
   }

@@ -221,13 +221,24 @@ __global__ void __launch_bounds__(kThreads) k_scatter(
   }
 }
 
-// Horner evaluation of the window polynomial for stencil point p at offset t in [0,1):
-// coefficients tab[k * P + p] of (t - 1/2)^k.
 template <typename R>
-__device__ __forceinline__ R horner_window(const R* tab, int deg, int P, int p, R t) {
+struct WinDeg;
+template <>
+struct WinDeg<float> {
+  static constexpr int value = kDegF32;
+};
+template <>
+struct WinDeg<double> {
+  static constexpr int value = kDegF64;
+};
+
+// Horner with the coefficients of (t - 1/2)^k held in registers
+template <typename R, int D>
+__device__ __forceinline__ R horner_reg(const R (&c)[D + 1], R t) {
   const R tau = t - R(0.5);
-  R v = tab[deg * P + p];
-  for (int k = deg - 1; k >= 0; --k) v = fma(v, tau, tab[k * P + p]);
+  R v = c[D];
+#pragma unroll
+  for (int k = D - 1; k >= 0; --k) v = fma(v, tau, c[k]);
   return v;
 }
 
@@ -262,27 +273,34 @@ __global__ void __launch_bounds__(kThreads) k_spread(
   const int E0 = g.E[0], E1 = g.E[1], E2 = g.E[2], E3p = g.E3p;
   const int vol = E0 * E1 * E3p;
   const int S1 = E1 * E3p;  // shared-memory stride of the first dimension
-  R* tab = acc + vol;
-  R* wbuf = tab + (g.deg + 1) * P;
+  R* wbuf = acc + vol;
   const int nw = blockDim.x >> 5;
   int* bbuf = reinterpret_cast<int*>(wbuf + nw * kBatch * 3 * P);
   for (int e = threadIdx.x; e < vol; e += blockDim.x) acc[e] = R(0);
-  for (int e = threadIdx.x; e < (g.deg + 1) * P; e += blockDim.x) tab[e] = wtab[e];
+
+  // lane l < NPL * P evaluates the window polynomial of stencil point l % P for the
+  // (atom, dimension) pairs l / P, l / P + NPL, ...; its coefficients sit in registers
+  constexpr int D = WinDeg<R>::value;
+  constexpr int NPL = 32 / P;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int p_l = lane % P, slot = lane / P;
+  R cw[D + 1];
+#pragma unroll
+  for (int k = 0; k <= D; ++k) cw[k] = (slot < NPL) ? wtab[k * P + p_l] : R(0);
   __syncthreads();
 
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   R* W = wbuf + wid * kBatch * 3 * P;  // per atom [w0 | q w1 | w2]
   int* B = bbuf + wid * kBatch;
   for (int j0 = start + wid * kBatch; j0 < end; j0 += nw * kBatch) {
     const int cnt = min(kBatch, end - j0);
-    for (int e = lane; e < cnt * 3 * P; e += 32) {
-      const int a = e / (3 * P);
-      const int r = e - a * 3 * P;
-      const int d = r / P, p = r - d * P;
-      const typename Vec4<R>::T v = sorted_tq[j0 + a];
-      R w = horner_window(tab, g.deg, P, p, tq_comp<R>(v, d));
-      if (d == 1) w *= v.w;
-      W[e] = w;
+    if (slot < NPL) {
+      for (int pr = slot; pr < 3 * cnt; pr += NPL) {
+        const int a = pr / 3, d = pr - 3 * a;
+        const typename Vec4<R>::T v = sorted_tq[j0 + a];
+        R w = horner_reg<R, D>(cw, tq_comp<R>(v, d));
+        if (d == 1) w *= v.w;
+        W[a * 3 * P + d * P + p_l] = w;
+      }
     }
     if (lane < cnt) B[lane] = local_base(sorted_lb[j0 + lane], E1, E3p);
     __syncwarp();
@@ -483,13 +501,21 @@ __global__ void __launch_bounds__(kThreads) k_scale(typename Cplx<R>::T* __restr
   if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
   __syncthreads();
   if (last) {
+    // 32 threads per component load the partials in parallel, then a fixed-order tree
     __threadfence();
-    if (threadIdx.x < 7) {
-      double v = 0.0;
-      for (unsigned b = 0; b < gridDim.x; ++b)
-        v += static_cast<volatile double*>(partials)[b * 8 + threadIdx.x];
-      accum[threadIdx.x] = v;
+    const int j = threadIdx.x & 7, part = threadIdx.x >> 3;  // component, 32 parts
+    double v = 0.0;
+    if (j < 7)
+      for (unsigned b = part; b < gridDim.x; b += kThreads / 8)
+        v += static_cast<volatile double*>(partials)[b * 8 + j];
+    __shared__ double fold[kThreads];
+    fold[threadIdx.x] = v;
+    __syncthreads();
+    for (int w = kThreads / 16; w >= 1; w >>= 1) {  // halve the parts: 16, 8, 4, 2, 1
+      if (part < w) fold[threadIdx.x] += fold[threadIdx.x + 8 * w];
+      __syncthreads();
     }
+    if (threadIdx.x < 7) accum[threadIdx.x] = fold[threadIdx.x];
     if (threadIdx.x == 0) *counter = 0u;
   }
 }
@@ -509,8 +535,7 @@ __global__ void __launch_bounds__(kThreads) k_gather(
   const int E0 = g.E[0], E1 = g.E[1], E2 = g.E[2], E3p = g.E3p;
   const int vol = E0 * E1 * E3p;
   const int S1 = E1 * E3p;
-  R* tab = phi + vol;
-  R* wbuf = tab + 2 * (g.deg + 1) * P;
+  R* wbuf = phi + vol;
   const int nw = blockDim.x >> 5;
   R* fbuf = wbuf + nw * kBatch * 6 * P;
   int* bbuf = reinterpret_cast<int*>(fbuf + nw * kBatch * 3);
@@ -555,26 +580,30 @@ __global__ void __launch_bounds__(kThreads) k_gather(
       phi[(a * E1 + b) * E3p + c] = grid[((int64_t)gi * g.M[1] + gj) * g.M[2] + gk];
     }
   }
-  for (int e = threadIdx.x; e < 2 * (g.deg + 1) * P; e += blockDim.x) tab[e] = wtab[e];
+  constexpr int D = WinDeg<R>::value;
+  constexpr int NPL = 32 / P;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int p_l = lane % P, slot = lane / P;
+  R cw[D + 1], cd[D + 1];
+#pragma unroll
+  for (int k = 0; k <= D; ++k) {
+    cw[k] = (slot < NPL) ? wtab[k * P + p_l] : R(0);
+    cd[k] = (slot < NPL) ? wtab[(D + 1) * P + k * P + p_l] : R(0);
+  }
   __syncthreads();
 
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   R* W = wbuf + wid * kBatch * 6 * P;  // per atom [w0 w1 w2 | dw0 dw1 dw2]
   R* Fa = fbuf + wid * kBatch * 3;
   int* B = bbuf + wid * kBatch;
-  const R* dtab = tab + (g.deg + 1) * P;
   for (int j0 = start + wid * kBatch; j0 < end; j0 += nw * kBatch) {
     const int cnt = min(kBatch, end - j0);
-    for (int e = lane; e < cnt * 6 * P; e += 32) {
-      const int a = e / (6 * P);
-      const int r = e - a * 6 * P;
-      const int which = r / (3 * P);
-      const int r2 = r - which * 3 * P;
-      const int d = r2 / P, p = r2 - d * P;
-      const typename Vec4<R>::T v = sorted_tq[j0 + a];
-      const R t = tq_comp<R>(v, d);
-      W[e] = which == 0 ? horner_window(tab, g.deg, P, p, t)
-                        : horner_window(dtab, g.deg, P, p, t) * dscale_of<R>(g, d);
+    if (slot < NPL) {
+      for (int pr = slot; pr < 3 * cnt; pr += NPL) {
+        const int a = pr / 3, d = pr - 3 * a;
+        const R t = tq_comp<R>(sorted_tq[j0 + a], d);
+        W[a * 6 * P + d * P + p_l] = horner_reg<R, D>(cw, t);
+        W[a * 6 * P + 3 * P + d * P + p_l] = horner_reg<R, D>(cd, t) * dscale_of<R>(g, d);
+      }
     }
     if (lane < cnt) B[lane] = local_base(sorted_lb[j0 + lane], E1, E3p);
     if (lane < 3 * cnt) Fa[lane] = R(0);
@@ -722,16 +751,14 @@ cudaError_t launch_scatter(bool fp64, int64_t n, const int* ptile, const int* pr
 size_t spread_smem_bytes(bool fp64, const TileGeom& g) {
   const size_t es = fp64 ? 8 : 4;
   const size_t nw = kThreads / 32;
-  return es * ((size_t)g.E[0] * g.E[1] * g.E3p + (size_t)(g.deg + 1) * g.P +
-               nw * kBatch * 3 * g.P) +
+  return es * ((size_t)g.E[0] * g.E[1] * g.E3p + nw * kBatch * 3 * g.P) +
          sizeof(int) * nw * kBatch;
 }
 
 size_t gather_smem_bytes(bool fp64, const TileGeom& g) {
   const size_t es = fp64 ? 8 : 4;
   const size_t nw = kThreads / 32;
-  return es * ((size_t)g.E[0] * g.E[1] * g.E3p + (size_t)2 * (g.deg + 1) * g.P +
-               nw * kBatch * 6 * g.P + nw * kBatch * 3) +
+  return es * ((size_t)g.E[0] * g.E[1] * g.E3p + nw * kBatch * 6 * g.P + nw * kBatch * 3) +
          sizeof(int) * nw * kBatch;
 }
 

@@ -9,6 +9,10 @@ namespace esp {
 constexpr int kMinP = 3;
 constexpr int kMaxP = 12;
 constexpr int kMaxDeg = 24;
+// Degree of the window polynomials (Sec. 4.3, Horner): fixed per compute type so the
+// coefficients of a lane's stencil point live in registers.
+constexpr int kDegF32 = 13;
+constexpr int kDegF64 = 24;
 constexpr int kRadialPieces = 16;
 constexpr int kThreads = 256;
 constexpr int kBatch = 8;  // atoms a warp handles together in spread / gather
