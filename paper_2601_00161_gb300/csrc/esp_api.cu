@@ -166,6 +166,12 @@ void update_cell_constants(esp_plan_t p) {
   std::memcpy(p->tg.hinv, p->hinv, sizeof p->hinv);
   for (int i = 0; i < 9; ++i) p->tg.hinvf[i] = (float)p->hinv[i];
   for (int d = 0; d < 3; ++d)
+    for (int e = 0; e < 3; ++e) {
+      const double A = (double)p->M[d] * p->hinv[3 * d + e];
+      p->tg.Ahi[3 * d + e] = (float)A;
+      p->tg.Alo[3 * d + e] = (float)(A - (double)(float)A);
+    }
+  for (int d = 0; d < 3; ++d)
     for (int a = 0; a < 3; ++a) {
       p->sg.b[3 * d + a] = 2.0 * M_PI * p->hinv[3 * d + a];
       p->sg.bf[3 * d + a] = (float)p->sg.b[3 * d + a];
@@ -485,6 +491,13 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
   g.E3p = g.E[2];
   while ((g.E3p + w) % 32 != 0) ++g.E3p;
   g.vec4 = (!p->fp64 && g.T[2] % 4 == 0 && p->M[2] % 4 == 0 && (g.E[2] + 3) / 4 * 4 <= g.E3p) ? 1 : 0;
+  {
+    auto magic = [](unsigned int d) {
+      return (unsigned int)((((unsigned long long)1 << 32) + d - 1) / d);
+    };
+    g.div_E1 = magic((unsigned)g.E[1]);
+    g.div_E2v = magic((unsigned)((g.E[2] + 3) / 4));
+  }
   g.deg = p->deg;
 
   esp::ScaleGeom& s = p->sg;

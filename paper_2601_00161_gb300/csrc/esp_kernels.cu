@@ -55,6 +55,39 @@ __device__ __forceinline__ int wrap_index(int i, int m) {
   return i < 0 ? i + m : i;
 }
 
+// floor(x / d) for 0 <= x < 2^16 with m = ceil(2^32 / d), d < 2^16
+__device__ __forceinline__ int fast_div(int x, unsigned int m) {
+  return (int)__umulhi((unsigned int)x, m);
+}
+
+// x in [0, 3 m) -> x mod m
+__device__ __forceinline__ int wrap3(int x, int m) {
+  x = x >= m ? x - m : x;
+  return x >= m ? x - m : x;
+}
+
+// Compensated ("double-float") FP32 arithmetic: a value is hi + lo with |lo| <= ulp(hi)/2.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+struct DF {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float v) {
+    float s, e;
+    two_sum(hi, v, s, e);
+    hi = s;
+    lo += e;
+  }
+  __device__ __forceinline__ void add(const DF& o) {
+    float s, e;
+    two_sum(hi, o.hi, s, e);
+    hi = s;
+    lo += o.lo + e;
+  }
+};
+
 // Reduced coordinate, grid coordinate and stencil base for one dimension (Sec. 4.3):
 // P even: base = floor(x) - P/2 + 1, t = x - floor(x); P odd: base = floor(x + 1/2) -
 // (P-1)/2, t = x + 1/2 - floor(x + 1/2).  Either way stencil point p sits at offset
@@ -75,15 +108,50 @@ __device__ __forceinline__ double reduced_coord(const double* hinv_row, const do
   return __fma_rn(hinv_row[0], r[0], __fma_rn(hinv_row[1], r[1], __dmul_rn(hinv_row[2], r[2])));
 }
 
-template <typename IO>
-__device__ __forceinline__ bool load_atom(const IO* pos, const IO* q, int64_t i, double r[3],
-                                          double* qi) {
-  r[0] = (double)pos[3 * i + 0];
-  r[1] = (double)pos[3 * i + 1];
-  r[2] = (double)pos[3 * i + 2];
-  *qi = (double)q[i];
-  return isfinite(r[0]) && isfinite(r[1]) && isfinite(r[2]) && isfinite(*qi);
+// The grid coordinate x = M_d (h^{-1} r)_d of FP32 positions in compensated FP32: exact
+// products (FMA) of the float pair A = M_d h^{-1}[d][.] with r, compensated sums.  Its
+// error is ~|x| 2^-46, so the integer part agrees with the FP64 computation except when
+// x lies within that distance of an integer; any x within 1e-6 of an integer (or too
+// large for the float pair) returns false and the caller takes the FP64 decision.
+__device__ __forceinline__ bool stencil_base_df(const TileGeom& g, int d, const float* r,
+                                                int* base, double* t_out) {
+  float S = 0.f, err = 0.f;
+#pragma unroll
+  for (int e = 0; e < 3; ++e) {
+    const float hi = g.Ahi[3 * d + e];
+    const float p = hi * r[e];
+    const float pe = fmaf(hi, r[e], -p);  // exact: hi * r = p + pe
+    float s2, e2;
+    two_sum(S, p, s2, e2);
+    S = s2;
+    err += e2 + pe + g.Alo[3 * d + e] * r[e];
+  }
+  if (g.P & 1) {
+    float s2, e2;
+    two_sum(S, 0.5f, s2, e2);
+    S = s2;
+    err += e2;
+  }
+  if (!(fabsf(S) < 1048576.f)) return false;
+  float fl = floorf(S);
+  float t = (S - fl) + err;  // S - fl is exact
+  if (t < 0.f) {
+    t += 1.f;
+    fl -= 1.f;
+  } else if (t >= 1.f) {
+    t -= 1.f;
+    fl += 1.f;
+  }
+  if (t < 1e-6f || t > 1.f - 1e-6f) return false;
+  const int M = g.M[d];
+  int b = (int)fl - ((g.P & 1) ? (g.P - 1) / 2 : g.P / 2 - 1);
+  b %= M;
+  if (b < 0) b += M;
+  *base = b;
+  *t_out = (double)t;
+  return true;
 }
+
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -112,13 +180,16 @@ __global__ void __launch_bounds__(kThreads) k_bin(const IO* __restrict__ pos,
                                                   int* __restrict__ plb,
                                                   typename Vec4<R>::T* __restrict__ tq,
                                                   double* __restrict__ accum) {
-  double sq = 0.0, sq2 = 0.0, bad = 0.0;
+  // FP32 inputs on the FP32 path use the compensated FP32 transform (FP64 only for the
+  // rare coordinate next to a stencil switch); everything else uses FP64.
+  constexpr bool kDF = std::is_same<IO, float>::value && std::is_same<R, float>::value;
+  DF sq, sq2, bad;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
-    double r[3], qi;
-    if (!load_atom(pos, q, i, r, &qi)) {
+    const IO r0 = pos[3 * i], r1 = pos[3 * i + 1], r2 = pos[3 * i + 2], qi = q[i];
+    if (!(isfinite(r0) && isfinite(r1) && isfinite(r2) && isfinite(qi))) {
       ptile[i] = -1;
-      bad += 1.0;
+      bad.add(1.f);
       continue;
     }
     int tc[3], lb[3];
@@ -126,7 +197,15 @@ __global__ void __launch_bounds__(kThreads) k_bin(const IO* __restrict__ pos,
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       int b;
-      stencil_base(reduced_coord(&g.hinv[3 * d], r), g.M[d], g.P, &b, &t[d]);
+      bool done = false;
+      if constexpr (kDF) {
+        const float rf[3] = {(float)r0, (float)r1, (float)r2};
+        done = stencil_base_df(g, d, rf, &b, &t[d]);
+      }
+      if (!done) {
+        const double r[3] = {(double)r0, (double)r1, (double)r2};
+        stencil_base(reduced_coord(&g.hinv[3 * d], r), g.M[d], g.P, &b, &t[d]);
+      }
       tc[d] = b / g.T[d];
       lb[d] = b - tc[d] * g.T[d];
     }
@@ -140,30 +219,52 @@ __global__ void __launch_bounds__(kThreads) k_bin(const IO* __restrict__ pos,
     ptile[i] = tile;
     plb[i] = lb[0] | (lb[1] << 10) | (lb[2] << 20);
     prank[i] = atomicAdd(&tile_count[tile], 1);
-    sq += qi;
-    sq2 += qi * qi;
+    if constexpr (std::is_same<IO, float>::value) {
+      sq.add(qi);
+      sq2.add(qi * qi);
+    } else {
+      // split the double into a float pair so the sums stay accurate to ~2^-48
+      const float qh = (float)qi, ql = (float)(qi - (double)qh);
+      const double q2 = qi * qi;
+      const float q2h = (float)q2, q2l = (float)(q2 - (double)q2h);
+      sq.add(qh);
+      sq.add(ql);
+      sq2.add(q2h);
+      sq2.add(q2l);
+    }
   }
-  // block sums through shared memory (one warp adds them up), then one FP64 atomic each
-  __shared__ double red[3][kThreads];
-  red[0][threadIdx.x] = sq;
-  red[1][threadIdx.x] = sq2;
-  red[2][threadIdx.x] = bad;
+  // compensated warp sums, then one FP64 value per warp and one FP64 atomic per block
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    DF a, b2, c;
+    a.hi = __shfl_xor_sync(0xffffffffu, sq.hi, o);
+    a.lo = __shfl_xor_sync(0xffffffffu, sq.lo, o);
+    b2.hi = __shfl_xor_sync(0xffffffffu, sq2.hi, o);
+    b2.lo = __shfl_xor_sync(0xffffffffu, sq2.lo, o);
+    c.hi = __shfl_xor_sync(0xffffffffu, bad.hi, o);
+    c.lo = __shfl_xor_sync(0xffffffffu, bad.lo, o);
+    sq.add(a);
+    sq2.add(b2);
+    bad.add(c);
+  }
+  __shared__ double red[3][kThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) {
+    red[0][wid] = (double)sq.hi + (double)sq.lo;
+    red[1][wid] = (double)sq2.hi + (double)sq2.lo;
+    red[2][wid] = (double)bad.hi + (double)bad.lo;
+  }
   __syncthreads();
-  if (threadIdx.x < 32) {
-    double a = 0.0, b = 0.0, c = 0.0;
-    for (int w = threadIdx.x; w < (int)blockDim.x; w += 32) {
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0, c = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
       a += red[0][w];
       b += red[1][w];
       c += red[2][w];
     }
-    a = warp_sum(a);
-    b = warp_sum(b);
-    c = warp_sum(c);
-    if (threadIdx.x == 0) {
-      if (a != 0.0) atomicAdd(&accum[7], a);
-      if (b != 0.0) atomicAdd(&accum[8], b);
-      if (c != 0.0) atomicAdd(&accum[9], c);
-    }
+    if (a != 0.0) atomicAdd(&accum[7], a);
+    if (b != 0.0) atomicAdd(&accum[8], b);
+    if (c != 0.0) atomicAdd(&accum[9], c);
   }
 }
 
@@ -328,16 +429,16 @@ __global__ void __launch_bounds__(kThreads) k_spread(
       const int E2v = (E2 + 3) >> 2;
       const int nflush = E0 * E1 * E2v;
       for (int e = threadIdx.x; e < nflush; e += blockDim.x) {
-        const int c4 = e % E2v;
-        const int ab = e / E2v;
-        const int b = ab % E1;
-        const int a = ab / E1;
-        const float* src = acc + (a * E1 + b) * E3p + 4 * c4;
+        const int ab = fast_div(e, g.div_E2v);
+        const int c4 = e - ab * E2v;
+        const int a = fast_div(ab, g.div_E1);
+        const int b = ab - a * E1;
+        const float* src = acc + ab * E3p + 4 * c4;
         const float4 v = make_float4(src[0], src[1], src[2], src[3]);
         if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) {
-          const int gi = wrap_index(o0 + a, g.M[0]);
-          const int gj = wrap_index(o1 + b, g.M[1]);
-          const int gk = wrap_index(o2 + 4 * c4, g.M[2]);
+          const int gi = wrap3(o0 + a, g.M[0]);
+          const int gj = wrap3(o1 + b, g.M[1]);
+          const int gk = wrap3(o2 + 4 * c4, g.M[2]);
           atomicAdd(reinterpret_cast<float4*>(grid + ((int64_t)gi * g.M[1] + gj) * g.M[2] + gk), v);
         }
       }
@@ -400,7 +501,12 @@ __global__ void __launch_bounds__(kThreads) k_scale(typename Cplx<R>::T* __restr
   // One warp per row (i0, i1) of the half spectrum, lanes along i2.  Rows outside the
   // bounding box of the sphere |k| <= K and modes beyond mmax[2] hold no in-sphere mode:
   // they are skipped (energy / pressure only) or zeroed (force path).
-  double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+  // FP64 path: plain FP64 sums.  FP32 path: compensated FP32 sums per lane and across
+  // the warp (about 48 significant bits), FP64 from the warp totals on.
+  using Acc = typename std::conditional<std::is_same<R, double>::value, double, DF>::type;
+  Acc acc[7];
+  if constexpr (std::is_same<R, double>::value)
+    for (int j = 0; j < 7; ++j) acc[j] = 0.0;
   const R* iw0 = invw2;
   const R* iw1 = invw2 + s.M[0];
   const R* iw2 = invw2 + s.M[0] + s.M[1];
@@ -439,14 +545,14 @@ __global__ void __launch_bounds__(kThreads) k_scale(typename Cplx<R>::T* __restr
         k2 = kx * kx + ky * ky + kz * kz;
         // The in-sphere decision is an FP64 one (as in the FP64 oracle): FP32 decides
         // only when it is far from the boundary.
-        const double K2 = s.K2;
-        if (sizeof(R) == 8 || fabs((double)k2 - K2) <= 1e-5 * K2) {
+        const R K2r = R(s.K2);
+        if (sizeof(R) == 8 || fabs(k2 - K2r) <= R(1e-5) * K2r) {
           const double dx = m0 * s.b[0] + m1 * s.b[3] + m2 * s.b[6];
           const double dy = m0 * s.b[1] + m1 * s.b[4] + m2 * s.b[7];
           const double dz = m0 * s.b[2] + m1 * s.b[5] + m2 * s.b[8];
-          inside = dx * dx + dy * dy + dz * dz <= K2;
+          inside = dx * dx + dy * dy + dz * dz <= s.K2;
         } else {
-          inside = (double)k2 <= K2;
+          inside = k2 <= K2r;
         }
       }
       if (!inside) {
@@ -465,13 +571,20 @@ __global__ void __launch_bounds__(kThreads) k_scale(typename Cplx<R>::T* __restr
       const R a = (single ? R(1) : R(2)) * (X.x * X.x + X.y * X.y) * iw * R(s.scale);
       const R aF = a * Fhat;
       const R ck = a * (dterm - R(2) * Fhat / k2);
-      acc[0] += (double)aF;
-      acc[1] += (double)(aF + ck * kx * kx);
-      acc[2] += (double)(aF + ck * ky * ky);
-      acc[3] += (double)(aF + ck * kz * kz);
-      acc[4] += (double)(ck * kx * ky);
-      acc[5] += (double)(ck * kx * kz);
-      acc[6] += (double)(ck * ky * kz);
+      const R contrib[7] = {aF,
+                            aF + ck * kx * kx,
+                            aF + ck * ky * ky,
+                            aF + ck * kz * kz,
+                            ck * kx * ky,
+                            ck * kx * kz,
+                            ck * ky * kz};
+#pragma unroll
+      for (int j = 0; j < 7; ++j) {
+        if constexpr (std::is_same<R, double>::value)
+          acc[j] += contrib[j];
+        else
+          acc[j].add(contrib[j]);
+      }
       if (WRITE) {
         const R G = Fhat * iw;
         typename Cplx<R>::T y;
@@ -487,7 +600,20 @@ __global__ void __launch_bounds__(kThreads) k_scale(typename Cplx<R>::T* __restr
   const int wid = threadIdx.x >> 5;
 #pragma unroll
   for (int j = 0; j < 7; ++j) {
-    const double v = warp_sum(acc[j]);
+    double v;
+    if constexpr (std::is_same<R, double>::value) {
+      v = warp_sum(acc[j]);
+    } else {
+      DF x = acc[j];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        DF y;
+        y.hi = __shfl_xor_sync(0xffffffffu, x.hi, o);
+        y.lo = __shfl_xor_sync(0xffffffffu, x.lo, o);
+        x.add(y);
+      }
+      v = (lane == 0) ? (double)x.hi + (double)x.lo : 0.0;
+    }
     if (lane == 0) red[j][wid] = v;
   }
   __syncthreads();
@@ -549,16 +675,16 @@ __global__ void __launch_bounds__(kThreads) k_gather(
       const int E2v = (E2 + 3) >> 2;
       const int nload = E0 * E1 * E2v;
       for (int e = threadIdx.x; e < nload; e += blockDim.x) {
-        const int c4 = e % E2v;
-        const int ab = e / E2v;
-        const int b = ab % E1;
-        const int a = ab / E1;
-        const int gi = wrap_index(o0 + a, g.M[0]);
-        const int gj = wrap_index(o1 + b, g.M[1]);
-        const int gk = wrap_index(o2 + 4 * c4, g.M[2]);
+        const int ab = fast_div(e, g.div_E2v);
+        const int c4 = e - ab * E2v;
+        const int a = fast_div(ab, g.div_E1);
+        const int b = ab - a * E1;
+        const int gi = wrap3(o0 + a, g.M[0]);
+        const int gj = wrap3(o1 + b, g.M[1]);
+        const int gk = wrap3(o2 + 4 * c4, g.M[2]);
         const float4 v =
             *reinterpret_cast<const float4*>(grid + ((int64_t)gi * g.M[1] + gj) * g.M[2] + gk);
-        float* dst = phi + (a * E1 + b) * E3p + 4 * c4;
+        float* dst = phi + ab * E3p + 4 * c4;
         dst[0] = v.x;
         dst[1] = v.y;
         dst[2] = v.z;

@@ -31,6 +31,10 @@ struct TileGeom {
   float hinvf[9];    // the same in FP32 (FP32 force transform)
   double dscale[3];  // d u / d s factor of the window argument: 2 M_d / P
   float dscalef[3];
+  // M_d h^{-1}[d][e] split into two floats (hi + lo) for the compensated FP32 transform
+  float Ahi[9], Alo[9];
+  // magic multipliers for division by E[1] and by ceil(E[2] / 4)
+  unsigned int div_E1, div_E2v;
 };
 
 // Constants of the fused scaling + reduction pass over the half spectrum.

@@ -131,6 +131,21 @@ def test_wrapping_of_far_images(precision):
     assert rel(r2["virial_recip"], r1["virial_recip"]) < 10 * TOL[precision]
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("P", [5, 6])
+def test_stencil_ties(precision, P):
+    # atoms exactly on grid points and on half points: the stencil base is a floor of an
+    # exactly representable grid coordinate, decided identically by both sides (FP64)
+    L, M = 16.0, 32
+    cell = np.eye(3) * L
+    rng = np.random.default_rng(P)
+    g = rng.integers(0, 2 * M, size=(120, 3)) * 0.25  # multiples of L/(2M): points and half points
+    q = rng.normal(size=120)
+    q -= q.mean()
+    S = sy.System("ties", g, q, cell, (M, M, M), P, 1e-5, fitting_rc(cell, (M, M, M), 1e-5))
+    check(S, precision)
+
+
 def test_spread_grid_and_spectrum_fp64():
     S = sy.water_cubic()
     c = c_from_tolerance(S.delta)
