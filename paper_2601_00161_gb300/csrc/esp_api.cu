@@ -178,6 +178,7 @@ void update_cell_constants(esp_plan_t p) {
     }
   const double Mtot = (double)p->M[0] * p->M[1] * p->M[2];
   p->sg.scale = 1.0 / (2.0 * p->V * Mtot * Mtot);
+  p->sg.scalef = (float)p->sg.scale;
   p->gg.g = p->tg;
   p->gg.fscale = 1.0 / (p->V * Mtot * Mtot);
 }
@@ -507,12 +508,15 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
   s.K2 = (c / alpha) * (c / alpha);
   s.x_per_k = alpha / c;
   s.A = p->A;
+  s.K2f = (float)s.K2;
+  s.x_per_kf = (float)s.x_per_k;
+  s.Af = (float)s.A;
   update_cell_constants(p);
 
   int dev = 0;
   cudaGetDevice(&dev);
   p->device = dev;
-  p->scale_blocks = sms * 4;
+  p->scale_blocks = sms * 2;
 
   const size_t es = p->fp64 ? 8 : 4;
   const size_t io_es = p->io_double ? 8 : 4;

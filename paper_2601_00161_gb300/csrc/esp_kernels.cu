@@ -114,7 +114,7 @@ __device__ __forceinline__ double reduced_coord(const double* hinv_row, const do
 // x lies within that distance of an integer; any x within 1e-6 of an integer (or too
 // large for the float pair) returns false and the caller takes the FP64 decision.
 __device__ __forceinline__ bool stencil_base_df(const TileGeom& g, int d, const float* r,
-                                                int* base, double* t_out) {
+                                                int* base, float* t_out) {
   float S = 0.f, err = 0.f;
 #pragma unroll
   for (int e = 0; e < 3; ++e) {
@@ -148,7 +148,7 @@ __device__ __forceinline__ bool stencil_base_df(const TileGeom& g, int d, const 
   b %= M;
   if (b < 0) b += M;
   *base = b;
-  *t_out = (double)t;
+  *t_out = t;
   return true;
 }
 
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(kThreads) k_bin(const IO* __restrict__ pos,
       continue;
     }
     int tc[3], lb[3];
-    double t[3];
+    R t[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       int b;
@@ -204,16 +204,18 @@ __global__ void __launch_bounds__(kThreads) k_bin(const IO* __restrict__ pos,
       }
       if (!done) {
         const double r[3] = {(double)r0, (double)r1, (double)r2};
-        stencil_base(reduced_coord(&g.hinv[3 * d], r), g.M[d], g.P, &b, &t[d]);
+        double td;
+        stencil_base(reduced_coord(&g.hinv[3 * d], r), g.M[d], g.P, &b, &td);
+        t[d] = (R)td;
       }
       tc[d] = b / g.T[d];
       lb[d] = b - tc[d] * g.T[d];
     }
     const int tile = (tc[0] * g.nt[1] + tc[1]) * g.nt[2] + tc[2];
     typename Vec4<R>::T v;
-    v.x = (R)t[0];
-    v.y = (R)t[1];
-    v.z = (R)t[2];
+    v.x = t[0];
+    v.y = t[1];
+    v.z = t[2];
     v.w = (R)qi;
     tq[i] = v;
     ptile[i] = tile;
@@ -491,6 +493,24 @@ __device__ __forceinline__ double bvec<double>(const ScaleGeom& s, int i) {
   return s.b[i];
 }
 
+template <typename R>
+struct ScaleConst {
+  R K2, x_per_k, A, scale;
+  __device__ __forceinline__ explicit ScaleConst(const ScaleGeom& s) {
+    if constexpr (std::is_same<R, float>::value) {
+      K2 = s.K2f;
+      x_per_k = s.x_per_kf;
+      A = s.Af;
+      scale = s.scalef;
+    } else {
+      K2 = s.K2;
+      x_per_k = s.x_per_k;
+      A = s.A;
+      scale = s.scale;
+    }
+  }
+};
+
 template <typename R, bool WRITE>
 __global__ void __launch_bounds__(kThreads) k_scale(typename Cplx<R>::T* __restrict__ spec,
                                                     ScaleGeom s, const R* __restrict__ invw2,
@@ -510,6 +530,7 @@ __global__ void __launch_bounds__(kThreads) k_scale(typename Cplx<R>::T* __restr
   const R* iw0 = invw2;
   const R* iw1 = invw2 + s.M[0];
   const R* iw2 = invw2 + s.M[0] + s.M[1];
+  const ScaleConst<R> sc(s);
   const int lane = threadIdx.x & 31;
   const int nrows = s.M[0] * s.M[1];
   const int warps = (gridDim.x * blockDim.x) >> 5;
@@ -545,7 +566,7 @@ __global__ void __launch_bounds__(kThreads) k_scale(typename Cplx<R>::T* __restr
         k2 = kx * kx + ky * ky + kz * kz;
         // The in-sphere decision is an FP64 one (as in the FP64 oracle): FP32 decides
         // only when it is far from the boundary.
-        const R K2r = R(s.K2);
+        const R K2r = sc.K2;
         if (sizeof(R) == 8 || fabs(k2 - K2r) <= R(1e-5) * K2r) {
           const double dx = m0 * s.b[0] + m1 * s.b[3] + m2 * s.b[6];
           const double dy = m0 * s.b[1] + m1 * s.b[4] + m2 * s.b[7];
@@ -562,13 +583,13 @@ __global__ void __launch_bounds__(kThreads) k_scale(typename Cplx<R>::T* __restr
       const typename Cplx<R>::T X = rowp[i2];
       const R iw = iw01 * iw2[i2];
       const R kmag = sqrt(k2);
-      const R x = kmag * R(s.x_per_k);
+      const R x = kmag * sc.x_per_k;
       R psi, dpsi;
       radial_eval(radtab, s.rdeg, x, &psi, &dpsi);
-      const R Fhat = R(s.A) * psi / k2;
-      const R dterm = R(s.A) * x * dpsi / (k2 * k2);
+      const R Fhat = sc.A * psi / k2;
+      const R dterm = sc.A * x * dpsi / (k2 * k2);
       const bool single = (i2 == 0) || ((s.M[2] & 1) == 0 && 2 * i2 == s.M[2]);
-      const R a = (single ? R(1) : R(2)) * (X.x * X.x + X.y * X.y) * iw * R(s.scale);
+      const R a = (single ? R(1) : R(2)) * (X.x * X.x + X.y * X.y) * iw * sc.scale;
       const R aF = a * Fhat;
       const R ck = a * (dterm - R(2) * Fhat / k2);
       const R contrib[7] = {aF,
@@ -595,15 +616,26 @@ __global__ void __launch_bounds__(kThreads) k_scale(typename Cplx<R>::T* __restr
     }
   }
   // block reduction, then the last block folds the per-block partials in a fixed order
-  __shared__ double red[7][kThreads / 32];
   __shared__ bool last;
   const int wid = threadIdx.x >> 5;
+  if constexpr (std::is_same<R, double>::value) {
+    __shared__ double red[7][kThreads / 32];
 #pragma unroll
-  for (int j = 0; j < 7; ++j) {
-    double v;
-    if constexpr (std::is_same<R, double>::value) {
-      v = warp_sum(acc[j]);
-    } else {
+    for (int j = 0; j < 7; ++j) {
+      const double v = warp_sum(acc[j]);
+      if (lane == 0) red[j][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 7) {
+      double v = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
+      partials[blockIdx.x * 8 + threadIdx.x] = v;
+    }
+  } else {
+    // compensated sums across the warp and the block; one FP64 conversion per block
+    __shared__ float red[7][kThreads / 32][2];
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
       DF x = acc[j];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
@@ -612,15 +644,22 @@ __global__ void __launch_bounds__(kThreads) k_scale(typename Cplx<R>::T* __restr
         y.lo = __shfl_xor_sync(0xffffffffu, x.lo, o);
         x.add(y);
       }
-      v = (lane == 0) ? (double)x.hi + (double)x.lo : 0.0;
+      if (lane == 0) {
+        red[j][wid][0] = x.hi;
+        red[j][wid][1] = x.lo;
+      }
     }
-    if (lane == 0) red[j][wid] = v;
-  }
-  __syncthreads();
-  if (threadIdx.x < 7) {
-    double v = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
-    partials[blockIdx.x * 8 + threadIdx.x] = v;
+    __syncthreads();
+    if (threadIdx.x < 7) {
+      DF x;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        DF y;
+        y.hi = red[threadIdx.x][w][0];
+        y.lo = red[threadIdx.x][w][1];
+        x.add(y);
+      }
+      partials[blockIdx.x * 8 + threadIdx.x] = (double)x.hi + (double)x.lo;
+    }
   }
   __threadfence();
   __syncthreads();

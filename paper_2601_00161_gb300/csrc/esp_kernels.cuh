@@ -49,6 +49,7 @@ struct ScaleGeom {
   double x_per_k;  // r_c / c
   double A;      // 2 pi lambda_0 / C_0 = 4 pi / psi_0(0)
   double scale;  // 1 / (2 V Mtot^2)
+  float K2f, x_per_kf, Af, scalef;  // FP32 copies
 };
 
 struct GatherGeom {
