@@ -55,14 +55,18 @@ struct esp_plan_s {
   esp::GatherGeom gg{};
   int ntiles = 0;
   int scale_blocks = 0;
+  int bin_blocks = 0;
+  int spread_blocks = 0, gather_blocks = 0;
   // device buffers
   void* d_wtab = nullptr;
   void* d_radtab = nullptr;
   void* d_invw2 = nullptr;
   void* d_grid = nullptr;
   void* d_spec = nullptr;
-  int* d_count = nullptr;
-  int* d_offset = nullptr;
+  int* d_count = nullptr;   // kSub counters per tile, then 2 work counters (spread, gather)
+  int* d_suboff = nullptr;  // exclusive scan of d_count (tile-major)
+  int* d_offset = nullptr;  // first sorted atom of each tile (ntiles + 1)
+  double* d_binpart = nullptr;  // per binning block: sum q, sum q^2, skipped atoms
   int* d_ptile = nullptr;
   int* d_prank = nullptr;
   int* d_plb = nullptr;
@@ -297,7 +301,7 @@ void release(esp_plan_t p) {
   if (!p) return;
   if (p->stream) cudaStreamSynchronize(p->stream);
   void* bufs[] = {p->d_wtab,      p->d_radtab,    p->d_invw2,    p->d_grid,      p->d_spec,  p->d_tq,
-                  p->d_count,     p->d_offset,    p->d_ptile,    p->d_prank,     p->d_plb,
+                  p->d_count,     p->d_offset,    p->d_ptile,    p->d_prank,     p->d_plb,  p->d_suboff, p->d_binpart,
                   p->d_sorted_tq, p->d_sorted_lb, p->d_sorted_idx, p->d_accum,   p->d_partials,
                   p->d_counter,   p->d_io_pos,    p->d_io_q,     p->d_io_f};
   for (void* b : bufs)
@@ -345,22 +349,24 @@ int run_step(esp_plan_t p, const void* pos, const void* q, void* forces, double*
   const size_t Mtot = (size_t)p->M[0] * p->M[1] * p->M[2];
   for (int i = 0; i <= kNStage; ++i) p->ev_used[i] = false;
   mark(p, kPrep);
-  ESP_CUDA(p, cudaMemsetAsync(p->d_count, 0, sizeof(int) * (size_t)p->ntiles, st));
+  int* work = p->d_count + (size_t)p->ntiles * esp::kSub;
+  ESP_CUDA(p, cudaMemsetAsync(p->d_count, 0, sizeof(int) * ((size_t)p->ntiles * esp::kSub + 2), st));
   ESP_CUDA(p, cudaMemsetAsync(acc, 0, sizeof(double) * ESP_ACCUM_LEN, st));
   mark(p, kBin);
   ESP_CUDA(p, esp::launch_bin(p->io_double, fp64, pos, q, p->n, p->tg, p->d_count, p->d_ptile,
-                              p->d_prank, p->d_plb, p->d_tq, acc, st));
+                              p->d_prank, p->d_plb, p->d_tq, p->d_binpart, st));
   mark(p, kScan);
-  ESP_CUDA(p, esp::launch_scan(p->d_count, p->d_offset, p->ntiles, st));
+  ESP_CUDA(p, esp::launch_scan(p->d_count, p->d_suboff, p->d_offset, p->ntiles, p->d_binpart,
+                               p->n > 0 ? p->bin_blocks : 0, acc, st));
   mark(p, kScatter);
   ESP_CUDA(p, esp::launch_scatter(fp64, p->n, p->d_ptile, p->d_prank, p->d_plb, p->d_tq,
-                                  p->d_offset, p->d_sorted_tq, p->d_sorted_lb,
+                                  p->d_suboff, p->d_sorted_tq, p->d_sorted_lb,
                                   p->d_sorted_idx, st));
   mark(p, kZero);
   ESP_CUDA(p, cudaMemsetAsync(p->d_grid, 0, es * Mtot, st));
   mark(p, kSpread);
-  ESP_CUDA(p, esp::launch_spread(fp64, p->tg, p->ntiles, p->d_sorted_tq, p->d_sorted_lb,
-                                 p->d_offset, p->d_wtab, p->d_grid, st));
+  ESP_CUDA(p, esp::launch_spread(fp64, p->tg, p->ntiles, p->spread_blocks, p->d_sorted_tq,
+                                 p->d_sorted_lb, p->d_offset, work, p->d_wtab, p->d_grid, st));
   mark(p, kFftFwd);
   if (fp64)
     ESP_CUFFT(p, cufftExecD2Z(p->fwd, (cufftDoubleReal*)p->d_grid, (cufftDoubleComplex*)p->d_spec));
@@ -377,9 +383,9 @@ int run_step(esp_plan_t p, const void* pos, const void* q, void* forces, double*
     else
       ESP_CUFFT(p, cufftExecC2R(p->inv, (cufftComplex*)p->d_spec, (cufftReal*)p->d_grid));
     mark(p, kGather);
-    ESP_CUDA(p, esp::launch_gather(fp64, p->io_double, p->gg, p->ntiles, p->d_sorted_tq,
-                                   p->d_sorted_lb, p->d_sorted_idx, p->d_offset, p->d_wtab,
-                                   p->d_grid, forces, st));
+    ESP_CUDA(p, esp::launch_gather(fp64, p->io_double, p->gg, p->ntiles, p->gather_blocks,
+                                   p->d_sorted_tq, p->d_sorted_lb, p->d_sorted_idx,
+                                   p->d_offset, work, p->d_wtab, p->d_grid, forces, st));
   }
   mark(p, kNStage);
   p->spectrum_kept = !want_f;
@@ -458,9 +464,10 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
   if ((rc = build_radial_tables(p, rtab)) != ESP_OK) return bail(rc);
   build_invw2(p, invw2);
 
-  // Tile geometry.  A tile holds T0 x T1 x T2 stencil bases; its CTA owns the padded
-  // block (T + P - 1)^3.  T2 is a multiple of 4 so padded rows move as aligned float4
-  // when M2 is too; T0 = T1 = 16 when that still gives two tiles per SM, else 8.
+  // Tile geometry.  A tile holds T0 x T1 x T2 stencil bases; the CTA working on it owns
+  // the padded block (T + P - 1)^3.  T2 is a multiple of 4 so padded rows move as
+  // aligned float4 when M2 is too.  Many small tiles keep the persistent CTAs of spread
+  // and gather busy to the end.
   int sms = 152;
   {
     int dev = 0;
@@ -475,7 +482,8 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
     auto ntile_for = [&](int t) {
       return ((p->M[0] + t - 1) / t) * ((p->M[1] + t - 1) / t) * ((p->M[2] + g.T[2] - 1) / g.T[2]);
     };
-    const int t01 = ntile_for(16) >= 2 * sms ? 16 : 8;
+    // 8 x 8 tiles unless that makes more than ~64 tiles per SM (very large grids)
+    const int t01 = ntile_for(8) > 64 * sms ? 16 : 8;
     g.T[0] = std::min(t01, p->M[0]);
     g.T[1] = std::min(t01, p->M[1]);
   }
@@ -533,8 +541,11 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
   } while (0)
   ALLOC(p->d_grid, es * Mtot);
   ALLOC(p->d_spec, 2 * es * nspec);
-  ALLOC(p->d_count, sizeof(int) * p->ntiles);
+  p->bin_blocks = esp::bin_blocks(n);
+  ALLOC(p->d_count, sizeof(int) * ((size_t)p->ntiles * esp::kSub + 2));
+  ALLOC(p->d_suboff, sizeof(int) * ((size_t)p->ntiles * esp::kSub + 1));
   ALLOC(p->d_offset, sizeof(int) * (p->ntiles + 1));
+  ALLOC(p->d_binpart, sizeof(double) * 3 * p->bin_blocks);
   ALLOC(p->d_ptile, sizeof(int) * nn);
   ALLOC(p->d_prank, sizeof(int) * nn);
   ALLOC(p->d_plb, sizeof(int) * nn);
@@ -570,6 +581,11 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
       return bail(fail(p, ESP_ERR_ARG, "tile does not fit in shared memory"));
     cudaError_t e = esp::configure_kernels(p->fp64, w, ss, gs);
     if (e != cudaSuccess) return bail(cuda_fail(p, e, "cudaFuncSetAttribute"));
+    int occ_s = 1, occ_g = 1;
+    e = esp::occupancy(p->fp64, p->io_double, w, ss, gs, &occ_s, &occ_g);
+    if (e != cudaSuccess) return bail(cuda_fail(p, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor"));
+    p->spread_blocks = std::max(1, std::min(p->ntiles, sms * std::max(occ_s, 1)));
+    p->gather_blocks = std::max(1, std::min(p->ntiles, sms * std::max(occ_g, 1)));
   }
   *out = p;
   return ESP_OK;
@@ -645,9 +661,11 @@ int esp_forces_from_spectrum(esp_plan_t p, void* forces) {
     ESP_CUFFT(p, cufftExecZ2D(p->inv, (cufftDoubleComplex*)p->d_spec, (cufftDoubleReal*)p->d_grid));
   else
     ESP_CUFFT(p, cufftExecC2R(p->inv, (cufftComplex*)p->d_spec, (cufftReal*)p->d_grid));
-  ESP_CUDA(p, esp::launch_gather(fp64, p->io_double, p->gg, p->ntiles, p->d_sorted_tq,
-                                 p->d_sorted_lb, p->d_sorted_idx, p->d_offset, p->d_wtab,
-                                 p->d_grid, forces, st));
+  int* work = p->d_count + (size_t)p->ntiles * esp::kSub;
+  ESP_CUDA(p, cudaMemsetAsync(work + 1, 0, sizeof(int), st));
+  ESP_CUDA(p, esp::launch_gather(fp64, p->io_double, p->gg, p->ntiles, p->gather_blocks,
+                                 p->d_sorted_tq, p->d_sorted_lb, p->d_sorted_idx, p->d_offset,
+                                 work, p->d_wtab, p->d_grid, forces, st));
   p->spectrum_kept = false;
   return ESP_OK;
 }

@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(kThreads) k_bin(const IO* __restrict__ pos,
                                                   int* __restrict__ prank,
                                                   int* __restrict__ plb,
                                                   typename Vec4<R>::T* __restrict__ tq,
-                                                  double* __restrict__ accum) {
+                                                  double* __restrict__ bin_part) {
   // FP32 inputs on the FP32 path use the compensated FP32 transform (FP64 only for the
   // rare coordinate next to a stencil switch); everything else uses FP64.
   constexpr bool kDF = std::is_same<IO, float>::value && std::is_same<R, float>::value;
@@ -220,7 +220,8 @@ __global__ void __launch_bounds__(kThreads) k_bin(const IO* __restrict__ pos,
     tq[i] = v;
     ptile[i] = tile;
     plb[i] = lb[0] | (lb[1] << 10) | (lb[2] << 20);
-    prank[i] = atomicAdd(&tile_count[tile], 1);
+    // kSub counters per tile, chosen by the atom's warp, spread the same-address atomics
+    prank[i] = atomicAdd(&tile_count[tile * kSub + (int)((i >> 5) & (kSub - 1))], 1);
     if constexpr (std::is_same<IO, float>::value) {
       sq.add(qi);
       sq2.add(qi * qi);
@@ -257,24 +258,24 @@ __global__ void __launch_bounds__(kThreads) k_bin(const IO* __restrict__ pos,
     red[2][wid] = (double)bad.hi + (double)bad.lo;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0, b = 0, c = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-      a += red[0][w];
-      b += red[1][w];
-      c += red[2][w];
-    }
-    if (a != 0.0) atomicAdd(&accum[7], a);
-    if (b != 0.0) atomicAdd(&accum[8], b);
-    if (c != 0.0) atomicAdd(&accum[9], c);
+  if (threadIdx.x < 3) {  // per-block partials; the scan kernel adds them up
+    double a = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += red[threadIdx.x][w];
+    bin_part[3 * blockIdx.x + threadIdx.x] = a;
   }
 }
 
-// exclusive scan of count[0..n) into offset[0..n], one CTA of kThreads threads
+// One CTA: exclusive scan of the sub-counter counts (tile-major), the tile offsets
+// toff[t] = suboff[t * kSub], and the fixed-order sum of the binning partials
+// (sum q, sum q^2, skipped atoms) into accum[7..9].
 __global__ void __launch_bounds__(kThreads) k_scan(const int* __restrict__ count,
-                                                   int* __restrict__ offset, int n) {
+                                                   int* __restrict__ suboff,
+                                                   int* __restrict__ toff, int ntiles,
+                                                   const double* __restrict__ bin_part,
+                                                   int nbin, double* __restrict__ accum) {
   __shared__ int warp_tot[kThreads / 32];
   __shared__ int carry;
+  const int n = ntiles * kSub;
   if (threadIdx.x == 0) carry = 0;
   __syncthreads();
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -300,12 +301,32 @@ __global__ void __launch_bounds__(kThreads) k_scan(const int* __restrict__ count
     }
     __syncthreads();
     const int before = carry + (wid > 0 ? warp_tot[wid - 1] : 0);
-    if (i < n) offset[i] = before + x - v;
+    if (i < n) {
+      suboff[i] = before + x - v;
+      if ((i & (kSub - 1)) == 0) toff[i / kSub] = before + x - v;
+    }
     __syncthreads();
     if (threadIdx.x == kThreads - 1) carry = before + x;
     __syncthreads();
   }
-  if (threadIdx.x == 0) offset[n] = carry;
+  if (threadIdx.x == 0) {
+    suboff[n] = carry;
+    toff[ntiles] = carry;
+  }
+  // binning partials: 3 x 32 threads, fixed order
+  __shared__ double part[3][32];
+  if (threadIdx.x < 96) {
+    const int j = threadIdx.x / 32, l = threadIdx.x & 31;
+    double a = 0.0;
+    for (int b = l; b < nbin; b += 32) a += bin_part[3 * b + j];
+    part[j][l] = a;
+  }
+  __syncthreads();
+  if (threadIdx.x < 3) {
+    double a = 0.0;
+    for (int l = 0; l < 32; ++l) a += part[threadIdx.x][l];
+    accum[7 + threadIdx.x] = a;
+  }
 }
 
 template <typename V>
@@ -317,7 +338,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter(
        i += (int64_t)gridDim.x * blockDim.x) {
     const int tile = ptile[i];
     if (tile < 0) continue;
-    const int dst = offset[tile] + prank[i];
+    const int dst = offset[tile * kSub + (int)((i >> 5) & (kSub - 1))] + prank[i];
     sorted_tq[dst] = tq[i];
     sorted_lb[dst] = plb[i];
     sorted_idx[dst] = (int)i;
@@ -363,23 +384,24 @@ __device__ __forceinline__ int local_base(int lb, int E1, int E3p) {
 }
 
 // ---------------------------------------------------------------------------------------
+// Persistent CTAs take tiles from a global work counter (work[0], zeroed every step).
 template <typename R, int P>
 __global__ void __launch_bounds__(kThreads) k_spread(
     const typename Vec4<R>::T* __restrict__ sorted_tq, const int* __restrict__ sorted_lb,
-    const int* __restrict__ offset, TileGeom g, const R* __restrict__ wtab,
-    R* __restrict__ grid) {
-  const int tile = blockIdx.x;
-  const int start = offset[tile], end = offset[tile + 1];
-  if (start == end) return;
+    const int* __restrict__ toff, TileGeom g, int ntiles, int* __restrict__ work,
+    const R* __restrict__ wtab, R* __restrict__ grid) {
+  using V4 = typename Vec4<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* acc = reinterpret_cast<R*>(smem_raw);
   const int E0 = g.E[0], E1 = g.E[1], E2 = g.E[2], E3p = g.E3p;
   const int vol = E0 * E1 * E3p;
   const int S1 = E1 * E3p;  // shared-memory stride of the first dimension
-  R* wbuf = acc + vol;
   const int nw = blockDim.x >> 5;
-  int* bbuf = reinterpret_cast<int*>(wbuf + nw * kBatch * 3 * P);
-  for (int e = threadIdx.x; e < vol; e += blockDim.x) acc[e] = R(0);
+  const SmemLayout L = smem_layout(false, sizeof(R), (size_t)vol, P, nw);
+  R* wbuf = reinterpret_cast<R*>(smem_raw + L.w);
+  V4* vbuf = reinterpret_cast<V4*>(smem_raw + L.v);
+  int* bbuf = reinterpret_cast<int*>(smem_raw + L.b);
+  __shared__ int s_tile;
 
   // lane l < NPL * P evaluates the window polynomial of stencil point l % P for the
   // (atom, dimension) pairs l / P, l / P + NPL, ...; its coefficients sit in registers
@@ -390,75 +412,105 @@ __global__ void __launch_bounds__(kThreads) k_spread(
   R cw[D + 1];
 #pragma unroll
   for (int k = 0; k <= D; ++k) cw[k] = (slot < NPL) ? wtab[k * P + p_l] : R(0);
-  __syncthreads();
-
   R* W = wbuf + wid * kBatch * 3 * P;  // per atom [w0 | q w1 | w2]
+  V4* Vs = vbuf + wid * kBatch;
   int* B = bbuf + wid * kBatch;
-  for (int j0 = start + wid * kBatch; j0 < end; j0 += nw * kBatch) {
-    const int cnt = min(kBatch, end - j0);
-    if (slot < NPL) {
-      for (int pr = slot; pr < 3 * cnt; pr += NPL) {
-        const int a = pr / 3, d = pr - 3 * a;
-        const typename Vec4<R>::T v = sorted_tq[j0 + a];
-        R w = horner_reg<R, D>(cw, tq_comp<R>(v, d));
-        if (d == 1) w *= v.w;
-        W[a * 3 * P + d * P + p_l] = w;
-      }
-    }
-    if (lane < cnt) B[lane] = local_base(sorted_lb[j0 + lane], E1, E3p);
-    __syncwarp();
-    for (int it = lane; it < cnt * P * P; it += 32) {
-      const int a = it / (P * P);
-      const int pr = it - a * P * P;
-      const int jj = pr / P, k = pr - jj * P;
-      const R* Wa = W + a * 3 * P;
-      const R pw = Wa[P + jj] * Wa[2 * P + k];
-      R* dst = acc + B[a] + jj * E3p + k;
-#pragma unroll
-      for (int i = 0; i < P; ++i) smem_add(dst + i * S1, Wa[i] * pw);
-    }
-    __syncwarp();
-  }
-  __syncthreads();
 
-  // add the padded block into the periodic global grid
-  const int t2 = tile % g.nt[2];
-  const int t1 = (tile / g.nt[2]) % g.nt[1];
-  const int t0 = tile / (g.nt[2] * g.nt[1]);
-  const int o0 = t0 * g.T[0], o1 = t1 * g.T[1], o2 = t2 * g.T[2];
-  if constexpr (std::is_same<R, float>::value) {
-    if (g.vec4) {
-      const int E2v = (E2 + 3) >> 2;
-      const int nflush = E0 * E1 * E2v;
-      for (int e = threadIdx.x; e < nflush; e += blockDim.x) {
-        const int ab = fast_div(e, g.div_E2v);
-        const int c4 = e - ab * E2v;
-        const int a = fast_div(ab, g.div_E1);
-        const int b = ab - a * E1;
-        const float* src = acc + ab * E3p + 4 * c4;
-        const float4 v = make_float4(src[0], src[1], src[2], src[3]);
-        if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) {
-          const int gi = wrap3(o0 + a, g.M[0]);
-          const int gj = wrap3(o1 + b, g.M[1]);
-          const int gk = wrap3(o2 + 4 * c4, g.M[2]);
-          atomicAdd(reinterpret_cast<float4*>(grid + ((int64_t)gi * g.M[1] + gj) * g.M[2] + gk), v);
+  for (;;) {
+    __syncthreads();  // the previous tile is flushed and s_tile consumed
+    if (threadIdx.x == 0) s_tile = atomicAdd(&work[0], 1);
+    for (int e = threadIdx.x; e < vol; e += blockDim.x) acc[e] = R(0);
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile >= ntiles) break;
+    const int start = toff[tile], end = toff[tile + 1];
+    if (start == end) continue;
+
+    int j0 = start + wid * kBatch;
+    V4 vnext;
+    int lbnext = 0;
+    if (j0 + lane < end && lane < kBatch) {
+      vnext = sorted_tq[j0 + lane];
+      lbnext = sorted_lb[j0 + lane];
+    }
+    for (; j0 < end; j0 += nw * kBatch) {
+      const int cnt = min(kBatch, end - j0);
+      if (lane < cnt) {
+        Vs[lane] = vnext;
+        B[lane] = local_base(lbnext, E1, E3p);
+      }
+      __syncwarp();
+      const int jn = j0 + nw * kBatch;  // prefetch the warp's next batch
+      if (lane < kBatch && jn + lane < end) {
+        vnext = sorted_tq[jn + lane];
+        lbnext = sorted_lb[jn + lane];
+      }
+      if (slot < NPL) {
+        for (int pr = slot; pr < 3 * cnt; pr += NPL) {
+          const int a = pr / 3, d = pr - 3 * a;
+          const V4 v = Vs[a];
+          R w = horner_reg<R, D>(cw, tq_comp<R>(v, d));
+          if (d == 1) w *= v.w;
+          W[a * 3 * P + d * P + p_l] = w;
         }
       }
-      return;
+      __syncwarp();
+      for (int it = lane; it < cnt * P * P; it += 32) {
+        const int a = it / (P * P);
+        const int pr = it - a * P * P;
+        const int jj = pr / P, k = pr - jj * P;
+        const R* Wa = W + a * 3 * P;
+        const R pw = Wa[P + jj] * Wa[2 * P + k];
+        R* dst = acc + B[a] + jj * E3p + k;
+#pragma unroll
+        for (int i = 0; i < P; ++i) smem_add(dst + i * S1, Wa[i] * pw);
+      }
+      __syncwarp();
     }
-  }
-  const int nflush = E0 * E1 * E2;
-  for (int e = threadIdx.x; e < nflush; e += blockDim.x) {
-    const int c = e % E2;
-    const int ab = e / E2;
-    const int b = ab % E1;
-    const int a = ab / E1;
-    const R val = acc[(a * E1 + b) * E3p + c];
-    if (val != R(0)) {
-      const int gi = wrap_index(o0 + a, g.M[0]);
-      const int gj = wrap_index(o1 + b, g.M[1]);
-      const int gk = wrap_index(o2 + c, g.M[2]);
-      atomicAdd(&grid[((int64_t)gi * g.M[1] + gj) * g.M[2] + gk], val);
+    __syncthreads();
+
+    // add the padded block into the periodic global grid
+    const int t2 = tile % g.nt[2];
+    const int t1 = (tile / g.nt[2]) % g.nt[1];
+    const int t0 = tile / (g.nt[2] * g.nt[1]);
+    const int o0 = t0 * g.T[0], o1 = t1 * g.T[1], o2 = t2 * g.T[2];
+    bool flushed = false;
+    if constexpr (std::is_same<R, float>::value) {
+      if (g.vec4) {
+        const int E2v = (E2 + 3) >> 2;
+        const int nflush = E0 * E1 * E2v;
+        for (int e = threadIdx.x; e < nflush; e += blockDim.x) {
+          const int ab = fast_div(e, g.div_E2v);
+          const int c4 = e - ab * E2v;
+          const int a = fast_div(ab, g.div_E1);
+          const int b = ab - a * E1;
+          const float* src = acc + ab * E3p + 4 * c4;
+          const float4 v = make_float4(src[0], src[1], src[2], src[3]);
+          if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) {
+            const int gi = wrap3(o0 + a, g.M[0]);
+            const int gj = wrap3(o1 + b, g.M[1]);
+            const int gk = wrap3(o2 + 4 * c4, g.M[2]);
+            atomicAdd(reinterpret_cast<float4*>(grid + ((int64_t)gi * g.M[1] + gj) * g.M[2] + gk), v);
+          }
+        }
+        flushed = true;
+      }
+    }
+    if (!flushed) {
+      const int nflush = E0 * E1 * E2;
+      for (int e = threadIdx.x; e < nflush; e += blockDim.x) {
+        const int c = e % E2;
+        const int ab = e / E2;
+        const int b = ab % E1;
+        const int a = ab / E1;
+        const R val = acc[(a * E1 + b) * E3p + c];
+        if (val != R(0)) {
+          const int gi = wrap_index(o0 + a, g.M[0]);
+          const int gj = wrap_index(o1 + b, g.M[1]);
+          const int gk = wrap_index(o2 + c, g.M[2]);
+          atomicAdd(&grid[((int64_t)gi * g.M[1] + gj) * g.M[2] + gk], val);
+        }
+      }
     }
   }
 }
@@ -686,65 +738,29 @@ __global__ void __launch_bounds__(kThreads) k_scale(typename Cplx<R>::T* __restr
 }
 
 // ---------------------------------------------------------------------------------------
+// Persistent CTAs take tiles from a global work counter (work[1], zeroed every step).
 template <typename R, typename IO, int P>
 __global__ void __launch_bounds__(kThreads) k_gather(
     const typename Vec4<R>::T* __restrict__ sorted_tq, const int* __restrict__ sorted_lb,
-    const int* __restrict__ sorted_idx, const int* __restrict__ offset, GatherGeom gg,
-    const R* __restrict__ wtab, const R* __restrict__ grid, IO* __restrict__ forces) {
+    const int* __restrict__ sorted_idx, const int* __restrict__ toff, GatherGeom gg,
+    int ntiles, int* __restrict__ work, const R* __restrict__ wtab,
+    const R* __restrict__ grid, IO* __restrict__ forces) {
+  using V4 = typename Vec4<R>::T;
   const TileGeom& g = gg.g;
-  const int tile = blockIdx.x;
-  const int start = offset[tile], end = offset[tile + 1];
-  if (start == end) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* phi = reinterpret_cast<R*>(smem_raw);
   const int E0 = g.E[0], E1 = g.E[1], E2 = g.E[2], E3p = g.E3p;
   const int vol = E0 * E1 * E3p;
   const int S1 = E1 * E3p;
-  R* wbuf = phi + vol;
   const int nw = blockDim.x >> 5;
-  R* fbuf = wbuf + nw * kBatch * 6 * P;
-  int* bbuf = reinterpret_cast<int*>(fbuf + nw * kBatch * 3);
-  const int t2 = tile % g.nt[2];
-  const int t1 = (tile / g.nt[2]) % g.nt[1];
-  const int t0 = tile / (g.nt[2] * g.nt[1]);
-  const int o0 = t0 * g.T[0], o1 = t1 * g.T[1], o2 = t2 * g.T[2];
-  bool loaded = false;
-  if constexpr (std::is_same<R, float>::value) {
-    if (g.vec4) {
-      const int E2v = (E2 + 3) >> 2;
-      const int nload = E0 * E1 * E2v;
-      for (int e = threadIdx.x; e < nload; e += blockDim.x) {
-        const int ab = fast_div(e, g.div_E2v);
-        const int c4 = e - ab * E2v;
-        const int a = fast_div(ab, g.div_E1);
-        const int b = ab - a * E1;
-        const int gi = wrap3(o0 + a, g.M[0]);
-        const int gj = wrap3(o1 + b, g.M[1]);
-        const int gk = wrap3(o2 + 4 * c4, g.M[2]);
-        const float4 v =
-            *reinterpret_cast<const float4*>(grid + ((int64_t)gi * g.M[1] + gj) * g.M[2] + gk);
-        float* dst = phi + ab * E3p + 4 * c4;
-        dst[0] = v.x;
-        dst[1] = v.y;
-        dst[2] = v.z;
-        dst[3] = v.w;
-      }
-      loaded = true;
-    }
-  }
-  if (!loaded) {
-    const int nload = E0 * E1 * E2;
-    for (int e = threadIdx.x; e < nload; e += blockDim.x) {
-      const int c = e % E2;
-      const int ab = e / E2;
-      const int b = ab % E1;
-      const int a = ab / E1;
-      const int gi = wrap_index(o0 + a, g.M[0]);
-      const int gj = wrap_index(o1 + b, g.M[1]);
-      const int gk = wrap_index(o2 + c, g.M[2]);
-      phi[(a * E1 + b) * E3p + c] = grid[((int64_t)gi * g.M[1] + gj) * g.M[2] + gk];
-    }
-  }
+  const SmemLayout L = smem_layout(true, sizeof(R), (size_t)vol, P, nw);
+  R* wbuf = reinterpret_cast<R*>(smem_raw + L.w);
+  R* fbuf = reinterpret_cast<R*>(smem_raw + L.f);
+  V4* vbuf = reinterpret_cast<V4*>(smem_raw + L.v);
+  int* bbuf = reinterpret_cast<int*>(smem_raw + L.b);
+  int* ibuf = reinterpret_cast<int*>(smem_raw + L.i);
+  __shared__ int s_tile;
+
   constexpr int D = WinDeg<R>::value;
   constexpr int NPL = 32 / P;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -755,89 +771,165 @@ __global__ void __launch_bounds__(kThreads) k_gather(
     cw[k] = (slot < NPL) ? wtab[k * P + p_l] : R(0);
     cd[k] = (slot < NPL) ? wtab[(D + 1) * P + k * P + p_l] : R(0);
   }
-  __syncthreads();
-
   R* W = wbuf + wid * kBatch * 6 * P;  // per atom [w0 w1 w2 | dw0 dw1 dw2]
-  R* Fa = fbuf + wid * kBatch * 3;
+  R* Fa = fbuf + wid * kBatch * 4;     // per atom g_x g_y g_z q
+  V4* Vs = vbuf + wid * kBatch;
   int* B = bbuf + wid * kBatch;
-  for (int j0 = start + wid * kBatch; j0 < end; j0 += nw * kBatch) {
-    const int cnt = min(kBatch, end - j0);
-    if (slot < NPL) {
-      for (int pr = slot; pr < 3 * cnt; pr += NPL) {
-        const int a = pr / 3, d = pr - 3 * a;
-        const R t = tq_comp<R>(sorted_tq[j0 + a], d);
-        W[a * 6 * P + d * P + p_l] = horner_reg<R, D>(cw, t);
-        W[a * 6 * P + 3 * P + d * P + p_l] = horner_reg<R, D>(cd, t) * dscale_of<R>(g, d);
+  int* Ix = ibuf + wid * kBatch;
+
+  for (;;) {
+    __syncthreads();  // the previous tile is done and s_tile consumed
+    if (threadIdx.x == 0) s_tile = atomicAdd(&work[1], 1);
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile >= ntiles) break;
+    const int start = toff[tile], end = toff[tile + 1];
+    if (start == end) continue;
+
+    const int t2 = tile % g.nt[2];
+    const int t1 = (tile / g.nt[2]) % g.nt[1];
+    const int t0 = tile / (g.nt[2] * g.nt[1]);
+    const int o0 = t0 * g.T[0], o1 = t1 * g.T[1], o2 = t2 * g.T[2];
+    bool loaded = false;
+    if constexpr (std::is_same<R, float>::value) {
+      if (g.vec4) {
+        const int E2v = (E2 + 3) >> 2;
+        const int nload = E0 * E1 * E2v;
+        for (int e = threadIdx.x; e < nload; e += blockDim.x) {
+          const int ab = fast_div(e, g.div_E2v);
+          const int c4 = e - ab * E2v;
+          const int a = fast_div(ab, g.div_E1);
+          const int b = ab - a * E1;
+          const int gi = wrap3(o0 + a, g.M[0]);
+          const int gj = wrap3(o1 + b, g.M[1]);
+          const int gk = wrap3(o2 + 4 * c4, g.M[2]);
+          const float4 v =
+              *reinterpret_cast<const float4*>(grid + ((int64_t)gi * g.M[1] + gj) * g.M[2] + gk);
+          float* dst = phi + ab * E3p + 4 * c4;
+          dst[0] = v.x;
+          dst[1] = v.y;
+          dst[2] = v.z;
+          dst[3] = v.w;
+        }
+        loaded = true;
       }
     }
-    if (lane < cnt) B[lane] = local_base(sorted_lb[j0 + lane], E1, E3p);
-    if (lane < 3 * cnt) Fa[lane] = R(0);
-    __syncwarp();
-    const int nitem = cnt * P * P;
-    for (int r0 = 0; r0 < nitem; r0 += 32) {
-      const int it = r0 + lane;
-      const bool act = it < nitem;
-      const int a = act ? it / (P * P) : kBatch;
-      R gx = R(0), gy = R(0), gz = R(0);
-      if (act) {
-        const int pr = it - a * P * P;
-        const int jj = pr / P, k = pr - jj * P;
-        const R* Wa = W + a * 6 * P;
-        const R* src = phi + B[a] + jj * E3p + k;
-        R sx = R(0), sw = R(0);
-#pragma unroll
-        for (int i = 0; i < P; ++i) {
-          const R f = src[i * S1];
-          sx = fma(f, Wa[3 * P + i], sx);
-          sw = fma(f, Wa[i], sw);
-        }
-        const R w1 = Wa[P + jj], w2 = Wa[2 * P + k];
-        gx = w1 * w2 * sx;
-        gy = Wa[4 * P + jj] * w2 * sw;
-        gz = w1 * Wa[5 * P + k] * sw;
+    if (!loaded) {
+      const int nload = E0 * E1 * E2;
+      for (int e = threadIdx.x; e < nload; e += blockDim.x) {
+        const int c = e % E2;
+        const int ab = e / E2;
+        const int b = ab % E1;
+        const int a = ab / E1;
+        const int gi = wrap_index(o0 + a, g.M[0]);
+        const int gj = wrap_index(o1 + b, g.M[1]);
+        const int gk = wrap_index(o2 + c, g.M[2]);
+        phi[(a * E1 + b) * E3p + c] = grid[((int64_t)gi * g.M[1] + gj) * g.M[2] + gk];
       }
-      // lanes of one atom are contiguous: segmented inclusive scan, the last lane of
-      // each segment holds the atom's sum for this round
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int ao = __shfl_up_sync(0xffffffffu, a, o);
-        const R x = __shfl_up_sync(0xffffffffu, gx, o);
-        const R y = __shfl_up_sync(0xffffffffu, gy, o);
-        const R z = __shfl_up_sync(0xffffffffu, gz, o);
-        if (lane >= o && ao == a) {
-          gx += x;
-          gy += y;
-          gz += z;
+    }
+    __syncthreads();
+
+    int j0 = start + wid * kBatch;
+    V4 vnext;
+    int lbnext = 0, idxnext = 0;
+    if (lane < kBatch && j0 + lane < end) {
+      vnext = sorted_tq[j0 + lane];
+      lbnext = sorted_lb[j0 + lane];
+      idxnext = sorted_idx[j0 + lane];
+    }
+    for (; j0 < end; j0 += nw * kBatch) {
+      const int cnt = min(kBatch, end - j0);
+      if (lane < cnt) {
+        Vs[lane] = vnext;
+        B[lane] = local_base(lbnext, E1, E3p);
+        Ix[lane] = idxnext;
+        Fa[4 * lane + 0] = R(0);
+        Fa[4 * lane + 1] = R(0);
+        Fa[4 * lane + 2] = R(0);
+        Fa[4 * lane + 3] = vnext.w;
+      }
+      __syncwarp();
+      const int jn = j0 + nw * kBatch;  // prefetch the warp's next batch
+      if (lane < kBatch && jn + lane < end) {
+        vnext = sorted_tq[jn + lane];
+        lbnext = sorted_lb[jn + lane];
+        idxnext = sorted_idx[jn + lane];
+      }
+      if (slot < NPL) {
+        for (int pr = slot; pr < 3 * cnt; pr += NPL) {
+          const int a = pr / 3, d = pr - 3 * a;
+          const R t = tq_comp<R>(Vs[a], d);
+          W[a * 6 * P + d * P + p_l] = horner_reg<R, D>(cw, t);
+          W[a * 6 * P + 3 * P + d * P + p_l] = horner_reg<R, D>(cd, t) * dscale_of<R>(g, d);
         }
       }
-      const int an = __shfl_down_sync(0xffffffffu, a, 1);
-      if (act && (lane == 31 || an != a)) {
-        Fa[3 * a + 0] += gx;
-        Fa[3 * a + 1] += gy;
-        Fa[3 * a + 2] += gz;
+      __syncwarp();
+      const int nitem = cnt * P * P;
+      for (int r0 = 0; r0 < nitem; r0 += 32) {
+        const int it = r0 + lane;
+        const bool act = it < nitem;
+        const int a = act ? it / (P * P) : kBatch;
+        R gx = R(0), gy = R(0), gz = R(0);
+        if (act) {
+          const int pr = it - a * P * P;
+          const int jj = pr / P, k = pr - jj * P;
+          const R* Wa = W + a * 6 * P;
+          const R* src = phi + B[a] + jj * E3p + k;
+          R sx = R(0), sw = R(0);
+#pragma unroll
+          for (int i = 0; i < P; ++i) {
+            const R f = src[i * S1];
+            sx = fma(f, Wa[3 * P + i], sx);
+            sw = fma(f, Wa[i], sw);
+          }
+          const R w1 = Wa[P + jj], w2 = Wa[2 * P + k];
+          gx = w1 * w2 * sx;
+          gy = Wa[4 * P + jj] * w2 * sw;
+          gz = w1 * Wa[5 * P + k] * sw;
+        }
+        // lanes of one atom are contiguous: segmented inclusive scan, the last lane of
+        // each segment holds the atom's sum for this round
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int ao = __shfl_up_sync(0xffffffffu, a, o);
+          const R x = __shfl_up_sync(0xffffffffu, gx, o);
+          const R y = __shfl_up_sync(0xffffffffu, gy, o);
+          const R z = __shfl_up_sync(0xffffffffu, gz, o);
+          if (lane >= o && ao == a) {
+            gx += x;
+            gy += y;
+            gz += z;
+          }
+        }
+        const int an = __shfl_down_sync(0xffffffffu, a, 1);
+        if (act && (lane == 31 || an != a)) {
+          Fa[4 * a + 0] += gx;
+          Fa[4 * a + 1] += gy;
+          Fa[4 * a + 2] += gz;
+        }
+        __syncwarp();
+      }
+      if (lane < cnt) {
+        // dU/ds = -(q / (V Mtot^2)) (gx, gy, gz);  F = -h^{-T} dU/ds
+        const int idx = Ix[lane];
+        const R gx = Fa[4 * lane], gy = Fa[4 * lane + 1], gz = Fa[4 * lane + 2];
+        const R qa = Fa[4 * lane + 3];
+        if constexpr (std::is_same<R, float>::value) {
+          const float f = qa * (float)gg.fscale;
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            forces[3 * (int64_t)idx + c] =
+                (IO)(f * (g.hinvf[c] * gx + g.hinvf[3 + c] * gy + g.hinvf[6 + c] * gz));
+        } else {
+          const double f = qa * gg.fscale;
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+            forces[3 * (int64_t)idx + c] =
+                (IO)(f * (g.hinv[c] * gx + g.hinv[3 + c] * gy + g.hinv[6 + c] * gz));
+        }
       }
       __syncwarp();
     }
-    if (lane < cnt) {
-      // dU/ds = -(q / (V Mtot^2)) (gx, gy, gz);  F = -h^{-T} dU/ds
-      const int j = j0 + lane;
-      const int idx = sorted_idx[j];
-      const R gx = Fa[3 * lane], gy = Fa[3 * lane + 1], gz = Fa[3 * lane + 2];
-      if constexpr (std::is_same<R, float>::value) {
-        const float f = sorted_tq[j].w * (float)gg.fscale;
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-          forces[3 * (int64_t)idx + c] =
-              (IO)(f * (g.hinvf[c] * gx + g.hinvf[3 + c] * gy + g.hinvf[6 + c] * gz));
-      } else {
-        const double f = sorted_tq[j].w * gg.fscale;
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-          forces[3 * (int64_t)idx + c] =
-              (IO)(f * (g.hinv[c] * gx + g.hinv[3 + c] * gy + g.hinv[6 + c] * gz));
-      }
-    }
-    __syncwarp();
   }
 }
 
@@ -871,32 +963,35 @@ cudaError_t with_P(int P, F&& f) {
 // ---- host launchers --------------------------------------------------------------------
 cudaError_t launch_bin(bool io_double, bool fp64, const void* pos, const void* q, int64_t n,
                        const TileGeom& g, int* tile_count, int* ptile, int* prank, int* plb,
-                       void* tq, double* accum, cudaStream_t st) {
+                       void* tq, double* bin_part, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int nb = grid_blocks(n);
   if (io_double && fp64)
     k_bin<double, double><<<nb, kThreads, 0, st>>>((const double*)pos, (const double*)q, n, g,
                                                     tile_count, ptile, prank, plb,
-                                                    (double4*)tq, accum);
+                                                    (double4*)tq, bin_part);
   else if (io_double)
     k_bin<double, float><<<nb, kThreads, 0, st>>>((const double*)pos, (const double*)q, n, g,
                                                    tile_count, ptile, prank, plb, (float4*)tq,
-                                                   accum);
+                                                   bin_part);
   else if (fp64)
     k_bin<float, double><<<nb, kThreads, 0, st>>>((const float*)pos, (const float*)q, n, g,
                                                    tile_count, ptile, prank, plb, (double4*)tq,
-                                                   accum);
+                                                   bin_part);
   else
     k_bin<float, float><<<nb, kThreads, 0, st>>>((const float*)pos, (const float*)q, n, g,
                                                   tile_count, ptile, prank, plb, (float4*)tq,
-                                                  accum);
+                                                  bin_part);
   return cudaGetLastError();
 }
 
-cudaError_t launch_scan(const int* count, int* offset, int ntiles, cudaStream_t st) {
-  k_scan<<<1, kThreads, 0, st>>>(count, offset, ntiles);
+cudaError_t launch_scan(const int* count, int* suboff, int* toff, int ntiles,
+                        const double* bin_part, int nbin, double* accum, cudaStream_t st) {
+  k_scan<<<1, kThreads, 0, st>>>(count, suboff, toff, ntiles, bin_part, nbin, accum);
   return cudaGetLastError();
 }
+
+int bin_blocks(int64_t n) { return grid_blocks(n); }
 
 cudaError_t launch_scatter(bool fp64, int64_t n, const int* ptile, const int* prank,
                            const int* plb, const void* tq, const int* offset, void* sorted_tq,
@@ -914,17 +1009,13 @@ cudaError_t launch_scatter(bool fp64, int64_t n, const int* ptile, const int* pr
 }
 
 size_t spread_smem_bytes(bool fp64, const TileGeom& g) {
-  const size_t es = fp64 ? 8 : 4;
-  const size_t nw = kThreads / 32;
-  return es * ((size_t)g.E[0] * g.E[1] * g.E3p + nw * kBatch * 3 * g.P) +
-         sizeof(int) * nw * kBatch;
+  return smem_layout(false, fp64 ? 8 : 4, (size_t)g.E[0] * g.E[1] * g.E3p, g.P, kThreads / 32)
+      .total;
 }
 
 size_t gather_smem_bytes(bool fp64, const TileGeom& g) {
-  const size_t es = fp64 ? 8 : 4;
-  const size_t nw = kThreads / 32;
-  return es * ((size_t)g.E[0] * g.E[1] * g.E3p + nw * kBatch * 6 * g.P + nw * kBatch * 3) +
-         sizeof(int) * nw * kBatch;
+  return smem_layout(true, fp64 ? 8 : 4, (size_t)g.E[0] * g.E[1] * g.E3p, g.P, kThreads / 32)
+      .total;
 }
 
 cudaError_t configure_kernels(bool fp64, int P, size_t spread_smem, size_t gather_smem) {
@@ -953,18 +1044,20 @@ cudaError_t configure_kernels(bool fp64, int P, size_t spread_smem, size_t gathe
   });
 }
 
-cudaError_t launch_spread(bool fp64, const TileGeom& g, int ntiles, const void* sorted_tq,
-                          const int* sorted_lb, const int* offset, const void* wtab,
-                          void* grid, cudaStream_t st) {
+cudaError_t launch_spread(bool fp64, const TileGeom& g, int ntiles, int nblocks,
+                          const void* sorted_tq, const int* sorted_lb, const int* toff,
+                          int* work, const void* wtab, void* grid, cudaStream_t st) {
   const size_t smem = spread_smem_bytes(fp64, g);
   return with_P(g.P, [&](auto pc) -> cudaError_t {
     constexpr int PP = decltype(pc)::value;
     if (fp64)
-      k_spread<double, PP><<<ntiles, kThreads, smem, st>>>(
-          (const double4*)sorted_tq, sorted_lb, offset, g, (const double*)wtab, (double*)grid);
+      k_spread<double, PP><<<nblocks, kThreads, smem, st>>>(
+          (const double4*)sorted_tq, sorted_lb, toff, g, ntiles, work, (const double*)wtab,
+          (double*)grid);
     else
-      k_spread<float, PP><<<ntiles, kThreads, smem, st>>>(
-          (const float4*)sorted_tq, sorted_lb, offset, g, (const float*)wtab, (float*)grid);
+      k_spread<float, PP><<<nblocks, kThreads, smem, st>>>(
+          (const float4*)sorted_tq, sorted_lb, toff, g, ntiles, work, (const float*)wtab,
+          (float*)grid);
     return cudaGetLastError();
   });
 }
@@ -996,25 +1089,48 @@ cudaError_t launch_scale(bool fp64, bool write, const ScaleGeom& s, void* spec,
 }
 
 cudaError_t launch_gather(bool fp64, bool io_double, const GatherGeom& gg, int ntiles,
-                          const void* sorted_tq, const int* sorted_lb, const int* sorted_idx,
-                          const int* offset, const void* wtab, const void* grid, void* forces,
-                          cudaStream_t st) {
+                          int nblocks, const void* sorted_tq, const int* sorted_lb,
+                          const int* sorted_idx, const int* toff, int* work, const void* wtab,
+                          const void* grid, void* forces, cudaStream_t st) {
   const size_t smem = gather_smem_bytes(fp64, gg.g);
   return with_P(gg.g.P, [&](auto pc) -> cudaError_t {
     constexpr int PP = decltype(pc)::value;
     if (fp64)
-      k_gather<double, double, PP><<<ntiles, kThreads, smem, st>>>(
-          (const double4*)sorted_tq, sorted_lb, sorted_idx, offset, gg, (const double*)wtab,
-          (const double*)grid, (double*)forces);
+      k_gather<double, double, PP><<<nblocks, kThreads, smem, st>>>(
+          (const double4*)sorted_tq, sorted_lb, sorted_idx, toff, gg, ntiles, work,
+          (const double*)wtab, (const double*)grid, (double*)forces);
     else if (io_double)
-      k_gather<float, double, PP><<<ntiles, kThreads, smem, st>>>(
-          (const float4*)sorted_tq, sorted_lb, sorted_idx, offset, gg, (const float*)wtab,
-          (const float*)grid, (double*)forces);
+      k_gather<float, double, PP><<<nblocks, kThreads, smem, st>>>(
+          (const float4*)sorted_tq, sorted_lb, sorted_idx, toff, gg, ntiles, work,
+          (const float*)wtab, (const float*)grid, (double*)forces);
     else
-      k_gather<float, float, PP><<<ntiles, kThreads, smem, st>>>(
-          (const float4*)sorted_tq, sorted_lb, sorted_idx, offset, gg, (const float*)wtab,
-          (const float*)grid, (float*)forces);
+      k_gather<float, float, PP><<<nblocks, kThreads, smem, st>>>(
+          (const float4*)sorted_tq, sorted_lb, sorted_idx, toff, gg, ntiles, work,
+          (const float*)wtab, (const float*)grid, (float*)forces);
     return cudaGetLastError();
+  });
+}
+
+// resident CTAs per SM for the spread and gather kernels of this configuration
+cudaError_t occupancy(bool fp64, bool io_double, int P, size_t spread_smem, size_t gather_smem,
+                      int* spread_ctas, int* gather_ctas) {
+  return with_P(P, [&](auto pc) -> cudaError_t {
+    constexpr int PP = decltype(pc)::value;
+    cudaError_t e;
+    if (fp64) {
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(spread_ctas, k_spread<double, PP>, kThreads, spread_smem);
+      if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(gather_ctas, k_gather<double, double, PP>, kThreads, gather_smem);
+    } else {
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(spread_ctas, k_spread<float, PP>, kThreads, spread_smem);
+      if (e == cudaSuccess) {
+        if (io_double)
+          e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(gather_ctas, k_gather<float, double, PP>, kThreads, gather_smem);
+        else
+          e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(gather_ctas, k_gather<float, float, PP>, kThreads, gather_smem);
+      }
+    }
+    return e;
   });
 }
 

@@ -16,6 +16,7 @@ constexpr int kDegF64 = 24;
 constexpr int kRadialPieces = 16;
 constexpr int kThreads = 256;
 constexpr int kBatch = 8;  // atoms a warp handles together in spread / gather
+constexpr int kSub = 8;    // binning sub-counters per tile (spreads same-address atomics)
 
 // Geometry shared by the binning, spreading and gathering kernels.
 struct TileGeom {
@@ -57,26 +58,49 @@ struct GatherGeom {
   double fscale;  // 1 / (V Mtot^2)
 };
 
+// Shared-memory layout of spread / gather, byte offsets aligned to 32 bytes (the tile
+// block first, then per-warp staging).  es = element size of the compute type.
+struct SmemLayout {
+  size_t w, f, v, b, i, total;
+};
+__host__ __device__ inline size_t align32(size_t x) { return (x + 31) & ~(size_t)31; }
+__host__ __device__ inline SmemLayout smem_layout(bool gather, size_t es, size_t vol, int P,
+                                                  int nw) {
+  SmemLayout L;
+  const size_t nb = (size_t)nw * kBatch;
+  L.w = align32(vol * es);
+  L.f = align32(L.w + nb * (gather ? 6 : 3) * P * es);
+  L.v = align32(L.f + (gather ? nb * 4 * es : 0));
+  L.b = align32(L.v + nb * 4 * es);
+  L.i = align32(L.b + nb * sizeof(int));
+  L.total = align32(L.i + (gather ? nb * sizeof(int) : 0));
+  return L;
+}
+
 // ---- launchers (return cudaGetLastError() of the launch) -----------------------------
 // io_double: pos/q/F are double (else float).  fp64: compute type double (else float).
 
 cudaError_t launch_bin(bool io_double, bool fp64, const void* pos, const void* q, int64_t n,
                        const TileGeom& g, int* tile_count, int* ptile, int* prank, int* plb,
-                       void* tq, double* accum, cudaStream_t st);
-cudaError_t launch_scan(const int* count, int* offset, int ntiles, cudaStream_t st);
+                       void* tq, double* bin_part, cudaStream_t st);
+int bin_blocks(int64_t n);
+cudaError_t launch_scan(const int* count, int* suboff, int* toff, int ntiles,
+                        const double* bin_part, int nbin, double* accum, cudaStream_t st);
 cudaError_t launch_scatter(bool fp64, int64_t n, const int* ptile, const int* prank,
                            const int* plb, const void* tq, const int* offset, void* sorted_tq,
                            int* sorted_lb, int* sorted_idx, cudaStream_t st);
-cudaError_t launch_spread(bool fp64, const TileGeom& g, int ntiles, const void* sorted_tq,
-                          const int* sorted_lb, const int* offset, const void* wtab,
-                          void* grid, cudaStream_t st);
+cudaError_t launch_spread(bool fp64, const TileGeom& g, int ntiles, int nblocks,
+                          const void* sorted_tq, const int* sorted_lb, const int* toff,
+                          int* work, const void* wtab, void* grid, cudaStream_t st);
 cudaError_t launch_scale(bool fp64, bool write, const ScaleGeom& s, void* spec,
                          const void* invw2, const void* radtab, double* partials,
                          unsigned int* counter, double* accum, int nblocks, cudaStream_t st);
 cudaError_t launch_gather(bool fp64, bool io_double, const GatherGeom& gg, int ntiles,
-                          const void* sorted_tq, const int* sorted_lb, const int* sorted_idx,
-                          const int* offset, const void* wtab, const void* grid, void* forces,
-                          cudaStream_t st);
+                          int nblocks, const void* sorted_tq, const int* sorted_lb,
+                          const int* sorted_idx, const int* toff, int* work, const void* wtab,
+                          const void* grid, void* forces, cudaStream_t st);
+cudaError_t occupancy(bool fp64, bool io_double, int P, size_t spread_smem, size_t gather_smem,
+                      int* spread_ctas, int* gather_ctas);
 
 size_t spread_smem_bytes(bool fp64, const TileGeom& g);
 size_t gather_smem_bytes(bool fp64, const TileGeom& g);
