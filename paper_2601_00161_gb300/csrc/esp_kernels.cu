@@ -265,53 +265,50 @@ __global__ void __launch_bounds__(kThreads) k_bin(const IO* __restrict__ pos,
   }
 }
 
-// One CTA: exclusive scan of the sub-counter counts (tile-major), the tile offsets
-// toff[t] = suboff[t * kSub], and the fixed-order sum of the binning partials
-// (sum q, sum q^2, skipped atoms) into accum[7..9].
-__global__ void __launch_bounds__(kThreads) k_scan(const int* __restrict__ count,
-                                                   int* __restrict__ suboff,
-                                                   int* __restrict__ toff, int ntiles,
-                                                   const double* __restrict__ bin_part,
-                                                   int nbin, double* __restrict__ accum) {
-  __shared__ int warp_tot[kThreads / 32];
-  __shared__ int carry;
+// One CTA of kScanThreads: exclusive scan of the sub-counter counts (tile-major), the
+// tile offsets toff[t] = suboff[t * kSub], and the fixed-order sum of the binning
+// partials (sum q, sum q^2, skipped atoms) into accum[7..9].  Each thread scans a
+// contiguous chunk; the chunk totals are scanned across the block.
+constexpr int kScanThreads = 1024;
+__global__ void __launch_bounds__(kScanThreads) k_scan(const int* __restrict__ count,
+                                                       int* __restrict__ suboff,
+                                                       int* __restrict__ toff, int ntiles,
+                                                       const double* __restrict__ bin_part,
+                                                       int nbin, double* __restrict__ accum) {
+  __shared__ int warp_tot[kScanThreads / 32];
   const int n = ntiles * kSub;
-  if (threadIdx.x == 0) carry = 0;
-  __syncthreads();
+  const int chunk = (n + kScanThreads - 1) / kScanThreads;
+  const int lo = min(n, (int)threadIdx.x * chunk), hi = min(n, lo + chunk);
+  int own = 0;
+  for (int i = lo; i < hi; ++i) own += count[i];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int base = 0; base < n; base += kThreads) {
-    const int i = base + threadIdx.x;
-    const int v = (i < n) ? count[i] : 0;
-    int x = v;
+  int x = own;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int t = warp_tot[lane];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
+      const int y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
     }
-    if (lane == 31) warp_tot[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-      int t = (lane < kThreads / 32) ? warp_tot[lane] : 0;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, t, o);
-        if (lane >= o) t += y;
-      }
-      if (lane < kThreads / 32) warp_tot[lane] = t;  // inclusive prefix of warp totals
-    }
-    __syncthreads();
-    const int before = carry + (wid > 0 ? warp_tot[wid - 1] : 0);
-    if (i < n) {
-      suboff[i] = before + x - v;
-      if ((i & (kSub - 1)) == 0) toff[i / kSub] = before + x - v;
-    }
-    __syncthreads();
-    if (threadIdx.x == kThreads - 1) carry = before + x;
-    __syncthreads();
+    warp_tot[lane] = t;  // inclusive prefix of warp totals
   }
-  if (threadIdx.x == 0) {
-    suboff[n] = carry;
-    toff[ntiles] = carry;
+  __syncthreads();
+  int run = (wid > 0 ? warp_tot[wid - 1] : 0) + x - own;  // exclusive prefix of this chunk
+  for (int i = lo; i < hi; ++i) {
+    suboff[i] = run;
+    if ((i & (kSub - 1)) == 0) toff[i / kSub] = run;
+    run += count[i];
+  }
+  if (threadIdx.x == kScanThreads - 1) {
+    suboff[n] = warp_tot[kScanThreads / 32 - 1];
+    toff[ntiles] = warp_tot[kScanThreads / 32 - 1];
   }
   // binning partials: 3 x 32 threads, fixed order
   __shared__ double part[3][32];
@@ -987,7 +984,7 @@ cudaError_t launch_bin(bool io_double, bool fp64, const void* pos, const void* q
 
 cudaError_t launch_scan(const int* count, int* suboff, int* toff, int ntiles,
                         const double* bin_part, int nbin, double* accum, cudaStream_t st) {
-  k_scan<<<1, kThreads, 0, st>>>(count, suboff, toff, ntiles, bin_part, nbin, accum);
+  k_scan<<<1, kScanThreads, 0, st>>>(count, suboff, toff, ntiles, bin_part, nbin, accum);
   return cudaGetLastError();
 }
 
