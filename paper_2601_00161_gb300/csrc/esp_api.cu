@@ -8,6 +8,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -487,6 +488,13 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
     g.T[0] = std::min(t01, p->M[0]);
     g.T[1] = std::min(t01, p->M[1]);
   }
+  // tuning override: ESP_TILE="T0,T1,T2" (T2 a multiple of 4 keeps the float4 rows)
+  if (const char* env = std::getenv("ESP_TILE")) {
+    int t[3];
+    if (std::sscanf(env, "%d,%d,%d", &t[0], &t[1], &t[2]) == 3)
+      for (int d = 0; d < 3; ++d)
+        if (t[d] >= 1 && t[d] <= 64) g.T[d] = std::min(t[d], p->M[d]);
+  }
   p->ntiles = 1;
   for (int d = 0; d < 3; ++d) {
     g.nt[d] = (p->M[d] + g.T[d] - 1) / g.T[d];
@@ -524,7 +532,7 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
   int dev = 0;
   cudaGetDevice(&dev);
   p->device = dev;
-  p->scale_blocks = sms * 2;
+  p->scale_blocks = (p->M[0] * p->M[1] + esp::kThreads / 32 - 1) / (esp::kThreads / 32);  // a warp per row
 
   const size_t es = p->fp64 ? 8 : 4;
   const size_t io_es = p->io_double ? 8 : 4;

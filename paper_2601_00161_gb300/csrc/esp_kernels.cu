@@ -270,17 +270,23 @@ __global__ void __launch_bounds__(kThreads) k_bin(const IO* __restrict__ pos,
 // partials (sum q, sum q^2, skipped atoms) into accum[7..9].  Each thread scans a
 // contiguous chunk; the chunk totals are scanned across the block.
 constexpr int kScanThreads = 1024;
+constexpr int kScanStageMax = 48 * 1024;  // counts staged in shared memory (192 KB)
 __global__ void __launch_bounds__(kScanThreads) k_scan(const int* __restrict__ count,
                                                        int* __restrict__ suboff,
                                                        int* __restrict__ toff, int ntiles,
                                                        const double* __restrict__ bin_part,
                                                        int nbin, double* __restrict__ accum) {
   __shared__ int warp_tot[kScanThreads / 32];
+  extern __shared__ int cnt_s[];  // n counts staged with coalesced loads (if they fit)
   const int n = ntiles * kSub;
+  const bool staged = n <= kScanStageMax;
+  int* cs = staged ? cnt_s : suboff;  // else scan in place in the output array
+  for (int i = threadIdx.x; i < n; i += kScanThreads) cs[i] = count[i];
+  __syncthreads();
   const int chunk = (n + kScanThreads - 1) / kScanThreads;
   const int lo = min(n, (int)threadIdx.x * chunk), hi = min(n, lo + chunk);
   int own = 0;
-  for (int i = lo; i < hi; ++i) own += count[i];
+  for (int i = lo; i < hi; ++i) own += cs[i];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int x = own;
 #pragma unroll
@@ -302,10 +308,14 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const int* __restrict__ c
   __syncthreads();
   int run = (wid > 0 ? warp_tot[wid - 1] : 0) + x - own;  // exclusive prefix of this chunk
   for (int i = lo; i < hi; ++i) {
-    suboff[i] = run;
-    if ((i & (kSub - 1)) == 0) toff[i / kSub] = run;
-    run += count[i];
+    const int c = cs[i];
+    cs[i] = run;
+    run += c;
   }
+  __syncthreads();
+  if (staged)
+    for (int i = threadIdx.x; i < n; i += kScanThreads) suboff[i] = cs[i];
+  for (int t = threadIdx.x; t < ntiles; t += kScanThreads) toff[t] = cs[t * kSub];
   if (threadIdx.x == kScanThreads - 1) {
     suboff[n] = warp_tot[kScanThreads / 32 - 1];
     toff[ntiles] = warp_tot[kScanThreads / 32 - 1];
@@ -587,6 +597,7 @@ __global__ void __launch_bounds__(kThreads) k_scale(typename Cplx<R>::T* __restr
   zero.x = R(0);
   zero.y = R(0);
   for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < nrows; row += warps) {
+    // (launched with one warp per row; the loop covers any smaller grid)
     const int i0 = row / s.M[1];
     const int i1 = row - i0 * s.M[1];
     const int m0 = (2 * i0 <= s.M[0]) ? i0 : i0 - s.M[0];
@@ -984,7 +995,13 @@ cudaError_t launch_bin(bool io_double, bool fp64, const void* pos, const void* q
 
 cudaError_t launch_scan(const int* count, int* suboff, int* toff, int ntiles,
                         const double* bin_part, int nbin, double* accum, cudaStream_t st) {
-  k_scan<<<1, kScanThreads, 0, st>>>(count, suboff, toff, ntiles, bin_part, nbin, accum);
+  const size_t n = (size_t)ntiles * kSub;
+  const size_t smem = n <= (size_t)kScanStageMax ? sizeof(int) * n : 0;
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(k_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_scan<<<1, kScanThreads, smem, st>>>(count, suboff, toff, ntiles, bin_part, nbin, accum);
   return cudaGetLastError();
 }
 

@@ -15,7 +15,10 @@ constexpr int kDegF32 = 13;
 constexpr int kDegF64 = 24;
 constexpr int kRadialPieces = 16;
 constexpr int kThreads = 256;
-constexpr int kBatch = 8;  // atoms a warp handles together in spread / gather
+#ifndef ESP_BATCH
+#define ESP_BATCH 8
+#endif
+constexpr int kBatch = ESP_BATCH;  // atoms a warp handles together in spread / gather
 constexpr int kSub = 8;    // binning sub-counters per tile (spreads same-address atomics)
 
 // Geometry shared by the binning, spreading and gathering kernels.
