@@ -392,6 +392,10 @@ __device__ __forceinline__ int local_base(int lb, int E1, int E3p) {
 
 // ---------------------------------------------------------------------------------------
 // Persistent CTAs take tiles from a global work counter (work[0], zeroed every step).
+// Per chunk of a tile's atoms: (A) thread t < SP = (kThreads / P) P evaluates the window
+// polynomial of stencil point t % P (coefficients in registers) for (atom, dimension)
+// pairs t / P, t / P + kThreads / P, ...; (B) the chunk's (atom, j, k) rows are shared
+// out over all threads, each adding the P values of its row into the padded block.
 template <typename R, int P>
 __global__ void __launch_bounds__(kThreads) k_spread(
     const typename Vec4<R>::T* __restrict__ sorted_tq, const int* __restrict__ sorted_lb,
@@ -403,25 +407,18 @@ __global__ void __launch_bounds__(kThreads) k_spread(
   const int E0 = g.E[0], E1 = g.E[1], E2 = g.E[2], E3p = g.E3p;
   const int vol = E0 * E1 * E3p;
   const int S1 = E1 * E3p;  // shared-memory stride of the first dimension
-  const int nw = blockDim.x >> 5;
-  const SmemLayout L = smem_layout(false, sizeof(R), (size_t)vol, P, nw);
-  R* wbuf = reinterpret_cast<R*>(smem_raw + L.w);
-  V4* vbuf = reinterpret_cast<V4*>(smem_raw + L.v);
-  int* bbuf = reinterpret_cast<int*>(smem_raw + L.b);
+  const SmemLayout L = smem_layout(false, sizeof(R), (size_t)vol, P);
+  R* W = reinterpret_cast<R*>(smem_raw + L.w);  // per atom [w0 | q w1 | w2]
+  int* B = reinterpret_cast<int*>(smem_raw + L.b);
   __shared__ int s_tile;
 
-  // lane l < NPL * P evaluates the window polynomial of stencil point l % P for the
-  // (atom, dimension) pairs l / P, l / P + NPL, ...; its coefficients sit in registers
   constexpr int D = WinDeg<R>::value;
-  constexpr int NPL = 32 / P;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int p_l = lane % P, slot = lane / P;
+  constexpr int NP = kThreads / P;  // pairs per sweep
+  const int p_t = threadIdx.x % P, pair0 = threadIdx.x / P;
+  const bool evaluator = pair0 < NP;
   R cw[D + 1];
 #pragma unroll
-  for (int k = 0; k <= D; ++k) cw[k] = (slot < NPL) ? wtab[k * P + p_l] : R(0);
-  R* W = wbuf + wid * kBatch * 3 * P;  // per atom [w0 | q w1 | w2]
-  V4* Vs = vbuf + wid * kBatch;
-  int* B = bbuf + wid * kBatch;
+  for (int k = 0; k <= D; ++k) cw[k] = evaluator ? wtab[k * P + p_t] : R(0);
 
   for (;;) {
     __syncthreads();  // the previous tile is flushed and s_tile consumed
@@ -433,36 +430,20 @@ __global__ void __launch_bounds__(kThreads) k_spread(
     const int start = toff[tile], end = toff[tile + 1];
     if (start == end) continue;
 
-    int j0 = start + wid * kBatch;
-    V4 vnext;
-    int lbnext = 0;
-    if (j0 + lane < end && lane < kBatch) {
-      vnext = sorted_tq[j0 + lane];
-      lbnext = sorted_lb[j0 + lane];
-    }
-    for (; j0 < end; j0 += nw * kBatch) {
-      const int cnt = min(kBatch, end - j0);
-      if (lane < cnt) {
-        Vs[lane] = vnext;
-        B[lane] = local_base(lbnext, E1, E3p);
-      }
-      __syncwarp();
-      const int jn = j0 + nw * kBatch;  // prefetch the warp's next batch
-      if (lane < kBatch && jn + lane < end) {
-        vnext = sorted_tq[jn + lane];
-        lbnext = sorted_lb[jn + lane];
-      }
-      if (slot < NPL) {
-        for (int pr = slot; pr < 3 * cnt; pr += NPL) {
+    for (int c0 = start; c0 < end; c0 += kChunk) {
+      const int cnt = min(kChunk, end - c0);
+      if (evaluator) {
+        for (int pr = pair0; pr < 3 * cnt; pr += NP) {
           const int a = pr / 3, d = pr - 3 * a;
-          const V4 v = Vs[a];
+          const V4 v = sorted_tq[c0 + a];
           R w = horner_reg<R, D>(cw, tq_comp<R>(v, d));
           if (d == 1) w *= v.w;
-          W[a * 3 * P + d * P + p_l] = w;
+          W[a * 3 * P + d * P + p_t] = w;
         }
       }
-      __syncwarp();
-      for (int it = lane; it < cnt * P * P; it += 32) {
+      for (int a = threadIdx.x; a < cnt; a += blockDim.x) B[a] = local_base(sorted_lb[c0 + a], E1, E3p);
+      __syncthreads();
+      for (int it = threadIdx.x; it < cnt * P * P; it += blockDim.x) {
         const int a = it / (P * P);
         const int pr = it - a * P * P;
         const int jj = pr / P, k = pr - jj * P;
@@ -472,9 +453,8 @@ __global__ void __launch_bounds__(kThreads) k_spread(
 #pragma unroll
         for (int i = 0; i < P; ++i) smem_add(dst + i * S1, Wa[i] * pw);
       }
-      __syncwarp();
+      __syncthreads();
     }
-    __syncthreads();
 
     // add the padded block into the periodic global grid
     const int t2 = tile % g.nt[2];
@@ -689,7 +669,7 @@ __global__ void __launch_bounds__(kThreads) k_scale(typename Cplx<R>::T* __restr
     if (threadIdx.x < 7) {
       double v = 0.0;
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
-      partials[blockIdx.x * 8 + threadIdx.x] = v;
+      partials[threadIdx.x * gridDim.x + blockIdx.x] = v;
     }
   } else {
     // compensated sums across the warp and the block; one FP64 conversion per block
@@ -718,7 +698,7 @@ __global__ void __launch_bounds__(kThreads) k_scale(typename Cplx<R>::T* __restr
         y.lo = red[threadIdx.x][w][1];
         x.add(y);
       }
-      partials[blockIdx.x * 8 + threadIdx.x] = (double)x.hi + (double)x.lo;
+      partials[threadIdx.x * gridDim.x + blockIdx.x] = (double)x.hi + (double)x.lo;
     }
   }
   __threadfence();
@@ -726,64 +706,57 @@ __global__ void __launch_bounds__(kThreads) k_scale(typename Cplx<R>::T* __restr
   if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
   __syncthreads();
   if (last) {
-    // 32 threads per component load the partials in parallel, then a fixed-order tree
+    // warp j sums component j: coalesced L2 loads (ld.cg: written by other blocks before
+    // their fence), then a fixed-order warp reduction
     __threadfence();
-    const int j = threadIdx.x & 7, part = threadIdx.x >> 3;  // component, 32 parts
-    double v = 0.0;
-    if (j < 7)
-      for (unsigned b = part; b < gridDim.x; b += kThreads / 8)
-        v += static_cast<volatile double*>(partials)[b * 8 + j];
-    __shared__ double fold[kThreads];
-    fold[threadIdx.x] = v;
-    __syncthreads();
-    for (int w = kThreads / 16; w >= 1; w >>= 1) {  // halve the parts: 16, 8, 4, 2, 1
-      if (part < w) fold[threadIdx.x] += fold[threadIdx.x + 8 * w];
-      __syncthreads();
+    const int j = threadIdx.x >> 5;
+    if (j < 7) {
+      double v = 0.0;
+      const double* pj = partials + (size_t)j * gridDim.x;
+      for (unsigned b = lane; b < gridDim.x; b += 32) v += __ldcg(pj + b);
+      v = warp_sum(v);
+      if (lane == 0) accum[j] = v;
     }
-    if (threadIdx.x < 7) accum[threadIdx.x] = fold[threadIdx.x];
     if (threadIdx.x == 0) *counter = 0u;
   }
 }
 
 // ---------------------------------------------------------------------------------------
 // Persistent CTAs take tiles from a global work counter (work[1], zeroed every step).
+// The tile's padded block of the potential grid is staged in shared memory; per chunk of
+// its atoms: (A) window values and derivatives as in k_spread; (B) each (atom, j, k) row
+// contracts its P values with w0 and w0', a segmented warp scan sums the rows of one atom
+// and the last lane of each segment adds the sums into the atom's slot; (C) one thread
+// per atom turns the sums into the force.
 template <typename R, typename IO, int P>
 __global__ void __launch_bounds__(kThreads) k_gather(
     const typename Vec4<R>::T* __restrict__ sorted_tq, const int* __restrict__ sorted_lb,
     const int* __restrict__ sorted_idx, const int* __restrict__ toff, GatherGeom gg,
     int ntiles, int* __restrict__ work, const R* __restrict__ wtab,
     const R* __restrict__ grid, IO* __restrict__ forces) {
-  using V4 = typename Vec4<R>::T;
   const TileGeom& g = gg.g;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* phi = reinterpret_cast<R*>(smem_raw);
   const int E0 = g.E[0], E1 = g.E[1], E2 = g.E[2], E3p = g.E3p;
   const int vol = E0 * E1 * E3p;
   const int S1 = E1 * E3p;
-  const int nw = blockDim.x >> 5;
-  const SmemLayout L = smem_layout(true, sizeof(R), (size_t)vol, P, nw);
-  R* wbuf = reinterpret_cast<R*>(smem_raw + L.w);
-  R* fbuf = reinterpret_cast<R*>(smem_raw + L.f);
-  V4* vbuf = reinterpret_cast<V4*>(smem_raw + L.v);
-  int* bbuf = reinterpret_cast<int*>(smem_raw + L.b);
-  int* ibuf = reinterpret_cast<int*>(smem_raw + L.i);
+  const SmemLayout L = smem_layout(true, sizeof(R), (size_t)vol, P);
+  R* W = reinterpret_cast<R*>(smem_raw + L.w);   // per atom [w0 w1 w2 | dw0 dw1 dw2]
+  R* Fa = reinterpret_cast<R*>(smem_raw + L.f);  // per atom g_x g_y g_z
+  int* B = reinterpret_cast<int*>(smem_raw + L.b);
   __shared__ int s_tile;
 
   constexpr int D = WinDeg<R>::value;
-  constexpr int NPL = 32 / P;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int p_l = lane % P, slot = lane / P;
+  constexpr int NP = kThreads / P;
+  const int lane = threadIdx.x & 31;
+  const int p_t = threadIdx.x % P, pair0 = threadIdx.x / P;
+  const bool evaluator = pair0 < NP;
   R cw[D + 1], cd[D + 1];
 #pragma unroll
   for (int k = 0; k <= D; ++k) {
-    cw[k] = (slot < NPL) ? wtab[k * P + p_l] : R(0);
-    cd[k] = (slot < NPL) ? wtab[(D + 1) * P + k * P + p_l] : R(0);
+    cw[k] = evaluator ? wtab[k * P + p_t] : R(0);
+    cd[k] = evaluator ? wtab[(D + 1) * P + k * P + p_t] : R(0);
   }
-  R* W = wbuf + wid * kBatch * 6 * P;  // per atom [w0 w1 w2 | dw0 dw1 dw2]
-  R* Fa = fbuf + wid * kBatch * 4;     // per atom g_x g_y g_z q
-  V4* Vs = vbuf + wid * kBatch;
-  int* B = bbuf + wid * kBatch;
-  int* Ix = ibuf + wid * kBatch;
 
   for (;;) {
     __syncthreads();  // the previous tile is done and s_tile consumed
@@ -835,48 +808,30 @@ __global__ void __launch_bounds__(kThreads) k_gather(
         phi[(a * E1 + b) * E3p + c] = grid[((int64_t)gi * g.M[1] + gj) * g.M[2] + gk];
       }
     }
-    __syncthreads();
 
-    int j0 = start + wid * kBatch;
-    V4 vnext;
-    int lbnext = 0, idxnext = 0;
-    if (lane < kBatch && j0 + lane < end) {
-      vnext = sorted_tq[j0 + lane];
-      lbnext = sorted_lb[j0 + lane];
-      idxnext = sorted_idx[j0 + lane];
-    }
-    for (; j0 < end; j0 += nw * kBatch) {
-      const int cnt = min(kBatch, end - j0);
-      if (lane < cnt) {
-        Vs[lane] = vnext;
-        B[lane] = local_base(lbnext, E1, E3p);
-        Ix[lane] = idxnext;
-        Fa[4 * lane + 0] = R(0);
-        Fa[4 * lane + 1] = R(0);
-        Fa[4 * lane + 2] = R(0);
-        Fa[4 * lane + 3] = vnext.w;
-      }
-      __syncwarp();
-      const int jn = j0 + nw * kBatch;  // prefetch the warp's next batch
-      if (lane < kBatch && jn + lane < end) {
-        vnext = sorted_tq[jn + lane];
-        lbnext = sorted_lb[jn + lane];
-        idxnext = sorted_idx[jn + lane];
-      }
-      if (slot < NPL) {
-        for (int pr = slot; pr < 3 * cnt; pr += NPL) {
+    for (int c0 = start; c0 < end; c0 += kChunk) {
+      const int cnt = min(kChunk, end - c0);
+      if (evaluator) {
+        for (int pr = pair0; pr < 3 * cnt; pr += NP) {
           const int a = pr / 3, d = pr - 3 * a;
-          const R t = tq_comp<R>(Vs[a], d);
-          W[a * 6 * P + d * P + p_l] = horner_reg<R, D>(cw, t);
-          W[a * 6 * P + 3 * P + d * P + p_l] = horner_reg<R, D>(cd, t) * dscale_of<R>(g, d);
+          const R t = tq_comp<R>(sorted_tq[c0 + a], d);
+          W[a * 6 * P + d * P + p_t] = horner_reg<R, D>(cw, t);
+          W[a * 6 * P + 3 * P + d * P + p_t] = horner_reg<R, D>(cd, t) * dscale_of<R>(g, d);
         }
       }
-      __syncwarp();
+      for (int a = threadIdx.x; a < cnt; a += blockDim.x) {
+        B[a] = local_base(sorted_lb[c0 + a], E1, E3p);
+        Fa[3 * a + 0] = R(0);
+        Fa[3 * a + 1] = R(0);
+        Fa[3 * a + 2] = R(0);
+      }
+      __syncthreads();  // also covers the staging of phi for the first chunk
       const int nitem = cnt * P * P;
-      for (int r0 = 0; r0 < nitem; r0 += 32) {
-        const int it = r0 + lane;
+      const int nround = (nitem + blockDim.x - 1) / blockDim.x;
+      for (int r = 0; r < nround; ++r) {
+        const int it = r * blockDim.x + threadIdx.x;
         const bool act = it < nitem;
-        const int a = act ? it / (P * P) : kBatch;
+        const int a = act ? it / (P * P) : kChunk;
         R gx = R(0), gy = R(0), gz = R(0);
         if (act) {
           const int pr = it - a * P * P;
@@ -895,8 +850,8 @@ __global__ void __launch_bounds__(kThreads) k_gather(
           gy = Wa[4 * P + jj] * w2 * sw;
           gz = w1 * Wa[5 * P + k] * sw;
         }
-        // lanes of one atom are contiguous: segmented inclusive scan, the last lane of
-        // each segment holds the atom's sum for this round
+        // rows of one atom are contiguous in the warp: segmented inclusive scan, the last
+        // lane of each segment adds the atom's partial sums
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
           const int ao = __shfl_up_sync(0xffffffffu, a, o);
@@ -911,17 +866,18 @@ __global__ void __launch_bounds__(kThreads) k_gather(
         }
         const int an = __shfl_down_sync(0xffffffffu, a, 1);
         if (act && (lane == 31 || an != a)) {
-          Fa[4 * a + 0] += gx;
-          Fa[4 * a + 1] += gy;
-          Fa[4 * a + 2] += gz;
+          smem_add(&Fa[3 * a + 0], gx);
+          smem_add(&Fa[3 * a + 1], gy);
+          smem_add(&Fa[3 * a + 2], gz);
         }
-        __syncwarp();
       }
-      if (lane < cnt) {
+      __syncthreads();
+      for (int a = threadIdx.x; a < cnt; a += blockDim.x) {
         // dU/ds = -(q / (V Mtot^2)) (gx, gy, gz);  F = -h^{-T} dU/ds
-        const int idx = Ix[lane];
-        const R gx = Fa[4 * lane], gy = Fa[4 * lane + 1], gz = Fa[4 * lane + 2];
-        const R qa = Fa[4 * lane + 3];
+        const int j = c0 + a;
+        const int idx = sorted_idx[j];
+        const R gx = Fa[3 * a], gy = Fa[3 * a + 1], gz = Fa[3 * a + 2];
+        const R qa = sorted_tq[j].w;
         if constexpr (std::is_same<R, float>::value) {
           const float f = qa * (float)gg.fscale;
 #pragma unroll
@@ -936,7 +892,7 @@ __global__ void __launch_bounds__(kThreads) k_gather(
                 (IO)(f * (g.hinv[c] * gx + g.hinv[3 + c] * gy + g.hinv[6 + c] * gz));
         }
       }
-      __syncwarp();
+      __syncthreads();
     }
   }
 }
@@ -1023,13 +979,11 @@ cudaError_t launch_scatter(bool fp64, int64_t n, const int* ptile, const int* pr
 }
 
 size_t spread_smem_bytes(bool fp64, const TileGeom& g) {
-  return smem_layout(false, fp64 ? 8 : 4, (size_t)g.E[0] * g.E[1] * g.E3p, g.P, kThreads / 32)
-      .total;
+  return smem_layout(false, fp64 ? 8 : 4, (size_t)g.E[0] * g.E[1] * g.E3p, g.P).total;
 }
 
 size_t gather_smem_bytes(bool fp64, const TileGeom& g) {
-  return smem_layout(true, fp64 ? 8 : 4, (size_t)g.E[0] * g.E[1] * g.E3p, g.P, kThreads / 32)
-      .total;
+  return smem_layout(true, fp64 ? 8 : 4, (size_t)g.E[0] * g.E[1] * g.E3p, g.P).total;
 }
 
 cudaError_t configure_kernels(bool fp64, int P, size_t spread_smem, size_t gather_smem) {

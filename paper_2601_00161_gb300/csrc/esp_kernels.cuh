@@ -15,10 +15,6 @@ constexpr int kDegF32 = 13;
 constexpr int kDegF64 = 24;
 constexpr int kRadialPieces = 16;
 constexpr int kThreads = 256;
-#ifndef ESP_BATCH
-#define ESP_BATCH 8
-#endif
-constexpr int kBatch = ESP_BATCH;  // atoms a warp handles together in spread / gather
 constexpr int kSub = 8;    // binning sub-counters per tile (spreads same-address atomics)
 
 // Geometry shared by the binning, spreading and gathering kernels.
@@ -61,22 +57,23 @@ struct GatherGeom {
   double fscale;  // 1 / (V Mtot^2)
 };
 
-// Shared-memory layout of spread / gather, byte offsets aligned to 32 bytes (the tile
-// block first, then per-warp staging).  es = element size of the compute type.
+// Atoms a CTA takes from its tile per chunk in spread / gather: all warps compute the
+// window values of a chunk, then share out its (atom, stencil row) items.
+constexpr int kChunk = 128;
+
+// Shared-memory layout of spread / gather, byte offsets aligned to 32 bytes: the padded
+// tile block, then the chunk's window values, force sums (gather) and local bases.
+// es = element size of the compute type.
 struct SmemLayout {
-  size_t w, f, v, b, i, total;
+  size_t w, f, b, total;
 };
 __host__ __device__ inline size_t align32(size_t x) { return (x + 31) & ~(size_t)31; }
-__host__ __device__ inline SmemLayout smem_layout(bool gather, size_t es, size_t vol, int P,
-                                                  int nw) {
+__host__ __device__ inline SmemLayout smem_layout(bool gather, size_t es, size_t vol, int P) {
   SmemLayout L;
-  const size_t nb = (size_t)nw * kBatch;
   L.w = align32(vol * es);
-  L.f = align32(L.w + nb * (gather ? 6 : 3) * P * es);
-  L.v = align32(L.f + (gather ? nb * 4 * es : 0));
-  L.b = align32(L.v + nb * 4 * es);
-  L.i = align32(L.b + nb * sizeof(int));
-  L.total = align32(L.i + (gather ? nb * sizeof(int) : 0));
+  L.f = align32(L.w + (size_t)kChunk * (gather ? 6 : 3) * P * es);
+  L.b = align32(L.f + (gather ? (size_t)kChunk * 3 * es : 0));
+  L.total = align32(L.b + (size_t)kChunk * sizeof(int));
   return L;
 }
 
