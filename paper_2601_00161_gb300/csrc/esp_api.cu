@@ -478,22 +478,11 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
   esp::TileGeom& g = p->tg;
   for (int d = 0; d < 3; ++d) g.M[d] = p->M[d];
   g.P = w;
-  g.T[2] = std::min(w <= 8 ? 16 : 8, p->M[2]);
   {
-    auto ntile_for = [&](int t) {
-      return ((p->M[0] + t - 1) / t) * ((p->M[1] + t - 1) / t) * ((p->M[2] + g.T[2] - 1) / g.T[2]);
-    };
-    // 8 x 8 tiles unless that makes more than ~64 tiles per SM (very large grids)
-    const int t01 = ntile_for(8) > 64 * sms ? 16 : 8;
-    g.T[0] = std::min(t01, p->M[0]);
-    g.T[1] = std::min(t01, p->M[1]);
-  }
-  // tuning override: ESP_TILE="T0,T1,T2" (T2 a multiple of 4 keeps the float4 rows)
-  if (const char* env = std::getenv("ESP_TILE")) {
-    int t[3];
-    if (std::sscanf(env, "%d,%d,%d", &t[0], &t[1], &t[2]) == 3)
-      for (int d = 0; d < 3; ++d)
-        if (t[d] >= 1 && t[d] <= 64) g.T[d] = std::min(t[d], p->M[d]);
+    int Tc[3], E3p, vol;
+    esp::tile_shape(w, Tc, &E3p, &vol);
+    for (int d = 0; d < 3; ++d) g.T[d] = std::min(Tc[d], p->M[d]);
+    g.E3p = E3p;
   }
   p->ntiles = 1;
   for (int d = 0; d < 3; ++d) {
@@ -503,10 +492,6 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
     g.dscalef[d] = (float)g.dscale[d];
     p->ntiles *= g.nt[d];
   }
-  // row pitch: the smallest value >= E2 that is -P mod 32 (consecutive stencil rows of
-  // one atom then sit on consecutive shared-memory banks)
-  g.E3p = g.E[2];
-  while ((g.E3p + w) % 32 != 0) ++g.E3p;
   g.vec4 = (!p->fp64 && g.T[2] % 4 == 0 && p->M[2] % 4 == 0 && (g.E[2] + 3) / 4 * 4 <= g.E3p) ? 1 : 0;
   {
     auto magic = [](unsigned int d) {

@@ -23,6 +23,7 @@
 #include <math.h>
 
 #include <type_traits>
+#include <utility>
 
 namespace esp {
 
@@ -396,17 +397,35 @@ __device__ __forceinline__ int local_base(int lb, int E1, int E3p) {
 // polynomial of stencil point t % P (coefficients in registers) for (atom, dimension)
 // pairs t / P, t / P + kThreads / P, ...; (B) the chunk's (atom, j, k) rows are shared
 // out over all threads, each adding the P values of its row into the padded block.
+// One stencil row of an atom: the P values w0[i] * pw added at the compile-time offsets
+// i * S1 from the row start (shared-space address).
+template <int OFF>
+__device__ __forceinline__ void red_shared_f32(unsigned addr, float v) {
+  asm volatile("red.shared.add.f32 [%0+%2], %1;" ::"r"(addr), "f"(v), "n"(OFF) : "memory");
+}
+
+template <typename R, int S1, int... I>
+__device__ __forceinline__ void spread_row(unsigned addr, const R* w0, R pw,
+                                           std::integer_sequence<int, I...>) {
+  if constexpr (std::is_same<R, float>::value) {
+    (red_shared_f32<I * S1 * 4>(addr, w0[I] * pw), ...);
+  } else {
+    R* base = reinterpret_cast<R*>(__cvta_shared_to_generic(addr));
+    (atomicAdd(base + I * S1, w0[I] * pw), ...);
+  }
+}
+
 template <typename R, int P>
 __global__ void __launch_bounds__(kThreads) k_spread(
     const typename Vec4<R>::T* __restrict__ sorted_tq, const int* __restrict__ sorted_lb,
     const int* __restrict__ toff, TileGeom g, int ntiles, int* __restrict__ work,
     const R* __restrict__ wtab, R* __restrict__ grid) {
   using V4 = typename Vec4<R>::T;
+  using TC = TileC<P>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* acc = reinterpret_cast<R*>(smem_raw);
-  const int E0 = g.E[0], E1 = g.E[1], E2 = g.E[2], E3p = g.E3p;
-  const int vol = E0 * E1 * E3p;
-  const int S1 = E1 * E3p;  // shared-memory stride of the first dimension
+  constexpr int E1 = TC::E1, E3p = TC::E3p, vol = TC::VOL, S1 = TC::S1;
+  const int E0 = g.E[0], E2 = g.E[2];  // this plan's tiles (<= TC)
   const SmemLayout L = smem_layout(false, sizeof(R), (size_t)vol, P);
   R* W = reinterpret_cast<R*>(smem_raw + L.w);  // per atom [w0 | q w1 | w2]
   int* B = reinterpret_cast<int*>(smem_raw + L.b);
@@ -449,9 +468,11 @@ __global__ void __launch_bounds__(kThreads) k_spread(
         const int jj = pr / P, k = pr - jj * P;
         const R* Wa = W + a * 3 * P;
         const R pw = Wa[P + jj] * Wa[2 * P + k];
-        R* dst = acc + B[a] + jj * E3p + k;
+        R w0[P];
 #pragma unroll
-        for (int i = 0; i < P; ++i) smem_add(dst + i * S1, Wa[i] * pw);
+        for (int i = 0; i < P; ++i) w0[i] = Wa[i];
+        const unsigned addr = (unsigned)__cvta_generic_to_shared(acc + B[a] + jj * E3p + k);
+        spread_row<R, S1>(addr, w0, pw, std::make_integer_sequence<int, P>{});
       }
       __syncthreads();
     }
@@ -469,8 +490,9 @@ __global__ void __launch_bounds__(kThreads) k_spread(
         for (int e = threadIdx.x; e < nflush; e += blockDim.x) {
           const int ab = fast_div(e, g.div_E2v);
           const int c4 = e - ab * E2v;
-          const int a = fast_div(ab, g.div_E1);
+          const int a = ab / E1;
           const int b = ab - a * E1;
+          if (b >= g.E[1]) continue;
           const float* src = acc + ab * E3p + 4 * c4;
           const float4 v = make_float4(src[0], src[1], src[2], src[3]);
           if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) {
@@ -484,12 +506,13 @@ __global__ void __launch_bounds__(kThreads) k_spread(
       }
     }
     if (!flushed) {
-      const int nflush = E0 * E1 * E2;
+      const int E1r = g.E[1];
+      const int nflush = E0 * E1r * E2;
       for (int e = threadIdx.x; e < nflush; e += blockDim.x) {
         const int c = e % E2;
         const int ab = e / E2;
-        const int b = ab % E1;
-        const int a = ab / E1;
+        const int b = ab % E1r;
+        const int a = ab / E1r;
         const R val = acc[(a * E1 + b) * E3p + c];
         if (val != R(0)) {
           const int gi = wrap_index(o0 + a, g.M[0]);
@@ -735,11 +758,11 @@ __global__ void __launch_bounds__(kThreads) k_gather(
     int ntiles, int* __restrict__ work, const R* __restrict__ wtab,
     const R* __restrict__ grid, IO* __restrict__ forces) {
   const TileGeom& g = gg.g;
+  using TC = TileC<P>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* phi = reinterpret_cast<R*>(smem_raw);
-  const int E0 = g.E[0], E1 = g.E[1], E2 = g.E[2], E3p = g.E3p;
-  const int vol = E0 * E1 * E3p;
-  const int S1 = E1 * E3p;
+  constexpr int E1 = TC::E1, E3p = TC::E3p, vol = TC::VOL, S1 = TC::S1;
+  const int E0 = g.E[0], E2 = g.E[2];  // this plan's tiles (<= TC)
   const SmemLayout L = smem_layout(true, sizeof(R), (size_t)vol, P);
   R* W = reinterpret_cast<R*>(smem_raw + L.w);   // per atom [w0 w1 w2 | dw0 dw1 dw2]
   R* Fa = reinterpret_cast<R*>(smem_raw + L.f);  // per atom g_x g_y g_z
@@ -779,8 +802,9 @@ __global__ void __launch_bounds__(kThreads) k_gather(
         for (int e = threadIdx.x; e < nload; e += blockDim.x) {
           const int ab = fast_div(e, g.div_E2v);
           const int c4 = e - ab * E2v;
-          const int a = fast_div(ab, g.div_E1);
+          const int a = ab / E1;
           const int b = ab - a * E1;
+          if (b >= g.E[1]) continue;
           const int gi = wrap3(o0 + a, g.M[0]);
           const int gj = wrap3(o1 + b, g.M[1]);
           const int gk = wrap3(o2 + 4 * c4, g.M[2]);
@@ -796,12 +820,13 @@ __global__ void __launch_bounds__(kThreads) k_gather(
       }
     }
     if (!loaded) {
-      const int nload = E0 * E1 * E2;
+      const int E1r = g.E[1];
+      const int nload = E0 * E1r * E2;
       for (int e = threadIdx.x; e < nload; e += blockDim.x) {
         const int c = e % E2;
         const int ab = e / E2;
-        const int b = ab % E1;
-        const int a = ab / E1;
+        const int b = ab % E1r;
+        const int a = ab / E1r;
         const int gi = wrap_index(o0 + a, g.M[0]);
         const int gj = wrap_index(o1 + b, g.M[1]);
         const int gk = wrap_index(o2 + c, g.M[2]);
@@ -979,11 +1004,15 @@ cudaError_t launch_scatter(bool fp64, int64_t n, const int* ptile, const int* pr
 }
 
 size_t spread_smem_bytes(bool fp64, const TileGeom& g) {
-  return smem_layout(false, fp64 ? 8 : 4, (size_t)g.E[0] * g.E[1] * g.E3p, g.P).total;
+  int T[3], E3p, vol;
+  tile_shape(g.P, T, &E3p, &vol);
+  return smem_layout(false, fp64 ? 8 : 4, (size_t)vol, g.P).total;
 }
 
 size_t gather_smem_bytes(bool fp64, const TileGeom& g) {
-  return smem_layout(true, fp64 ? 8 : 4, (size_t)g.E[0] * g.E[1] * g.E3p, g.P).total;
+  int T[3], E3p, vol;
+  tile_shape(g.P, T, &E3p, &vol);
+  return smem_layout(true, fp64 ? 8 : 4, (size_t)vol, g.P).total;
 }
 
 cudaError_t configure_kernels(bool fp64, int P, size_t spread_smem, size_t gather_smem) {

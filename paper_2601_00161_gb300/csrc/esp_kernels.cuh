@@ -23,8 +23,8 @@ struct TileGeom {
   int P;        // stencil width
   int T[3];     // tile extent (grid points of stencil bases per tile)
   int nt[3];    // tiles per dimension
-  int E[3];     // padded tile extent T + P - 1
-  int E3p;      // shared-memory row pitch >= E[2], chosen with E3p = -P (mod 32)
+  int E[3];     // padded extent T + P - 1 of this plan's tiles (<= the TileC<P> block)
+  int E3p;      // shared-memory row pitch (TileC<P>::E3p)
   int deg;      // degree of the window polynomials
   int vec4;     // 1: rows move as aligned float4 between global and shared memory
   double hinv[9];    // h^{-1}, row-major
@@ -56,6 +56,31 @@ struct GatherGeom {
   TileGeom g;
   double fscale;  // 1 / (V Mtot^2)
 };
+
+// Tile block of spread / gather, fixed per stencil width P so that all shared-memory
+// strides are compile-time constants: a tile holds T0 x T1 x T2 stencil bases and its CTA
+// owns the padded block E = T + P - 1; rows are padded to the pitch E3p >= E2 with
+// E3p = -P (mod 32), which puts consecutive stencil rows of one atom on consecutive banks.
+constexpr int tile_pitch(int e2, int p) {
+  int x = e2;
+  while ((x + p) % 32 != 0) ++x;
+  return x;
+}
+template <int P>
+struct TileC {
+  static constexpr int T0 = 8, T1 = 8, T2 = (P <= 8) ? 16 : 8;
+  static constexpr int E0 = T0 + P - 1, E1 = T1 + P - 1, E2 = T2 + P - 1;
+  static constexpr int E3p = tile_pitch(E2, P);
+  static constexpr int S1 = E1 * E3p;
+  static constexpr int VOL = E0 * S1;
+};
+inline void tile_shape(int P, int T[3], int* E3p, int* vol) {
+  T[0] = 8;
+  T[1] = 8;
+  T[2] = P <= 8 ? 16 : 8;
+  *E3p = tile_pitch(T[2] + P - 1, P);
+  *vol = (T[0] + P - 1) * (T[1] + P - 1) * *E3p;
+}
 
 // Atoms a CTA takes from its tile per chunk in spread / gather: all warps compute the
 // window values of a chunk, then share out its (atom, stencil row) items.
