@@ -200,8 +200,12 @@ def esp_arm(args):
     c = esp.esp_c_from_tolerance(S.delta)
     fp64 = args.precision == "fp64"
     dt = torch.float64 if fp64 else torch.float32
-    stream = torch.cuda.current_stream()
-    plan = esp.Plan(S.cell, S.n, S.grid, S.P, c, S.rc, precision=args.precision)
+    # a stream of its own: the library captures the step in a CUDA graph (the legacy
+    # default stream cannot be captured)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    plan = esp.Plan(S.cell, S.n, S.grid, S.P, c, S.rc, precision=args.precision,
+                    stream=stream.cuda_stream)
     pos = torch.tensor(S.pos, dtype=dt, device="cuda")
     q = torch.tensor(S.q, dtype=dt, device="cuda")
     F = torch.empty((S.n, 3), dtype=dt, device="cuda")
@@ -280,7 +284,8 @@ def esp_arm(args):
 
     fp64_value = None
     if not fp64 and not args.no_fp64_compare:
-        p64 = esp.Plan(S.cell, S.n, S.grid, S.P, c, S.rc, precision="fp64")
+        p64 = esp.Plan(S.cell, S.n, S.grid, S.P, c, S.rc, precision="fp64",
+                       stream=stream.cuda_stream)
         pos64 = torch.tensor(S.pos, dtype=torch.float64, device="cuda")
         q64 = torch.tensor(S.q, dtype=torch.float64, device="cuda")
         F64 = torch.empty((S.n, 3), dtype=torch.float64, device="cuda")

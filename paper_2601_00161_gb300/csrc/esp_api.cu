@@ -55,7 +55,8 @@ struct esp_plan_s {
   esp::ScaleGeom sg{};
   esp::GatherGeom gg{};
   int ntiles = 0;
-  int scale_blocks = 0;
+  int scale_blocks = 0;  // sizes the partials: one block per 8 spectrum rows at most
+  int zero_blocks = 0;
   int bin_blocks = 0;
   int spread_blocks = 0, gather_blocks = 0;
   // device buffers
@@ -85,6 +86,14 @@ struct esp_plan_s {
   cufftHandle fwd = 0, inv = 0;
   bool have_fwd = false, have_inv = false;
   bool spectrum_kept = false;
+  // CUDA graph of the last esp_step (re-captured when its arguments or the cell change)
+  bool use_graph = true;
+  cudaGraphExec_t graph_exec = nullptr;
+  const void* g_pos = nullptr;
+  const void* g_q = nullptr;
+  void* g_f = nullptr;
+  double* g_acc = nullptr;
+  bool g_prof = false;
   // per-stage CUDA events (esp_profile)
   bool profiling = false;
   cudaEvent_t ev[16] = {};
@@ -308,6 +317,7 @@ void release(esp_plan_t p) {
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (p->h_accum) cudaFreeHost(p->h_accum);
+  if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
   for (cudaEvent_t e : p->ev)
     if (e) cudaEventDestroy(e);
   if (p->have_fwd) cufftDestroy(p->fwd);
@@ -376,7 +386,7 @@ int run_step(esp_plan_t p, const void* pos, const void* q, void* forces, double*
   const bool want_f = forces != nullptr;
   mark(p, kScale);
   ESP_CUDA(p, esp::launch_scale(fp64, want_f, p->sg, p->d_spec, p->d_invw2, p->d_radtab,
-                                p->d_partials, p->d_counter, acc, p->scale_blocks, st));
+                                p->d_partials, p->d_counter, acc, p->zero_blocks, st));
   mark(p, kFftInv);
   if (want_f) {
     if (fp64)
@@ -390,6 +400,58 @@ int run_step(esp_plan_t p, const void* pos, const void* q, void* forces, double*
   }
   mark(p, kNStage);
   p->spectrum_kept = !want_f;
+  return ESP_OK;
+}
+
+void drop_graph(esp_plan_t p) {
+  if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+  p->graph_exec = nullptr;
+}
+
+// esp_step through a CUDA graph: the launch sequence of run_step is captured once per
+// argument set (the kernels take the cell constants by value, so esp_set_cell drops the
+// graph) and replayed with one launch.  The legacy default stream cannot be captured;
+// there, and if capture fails, the kernels launch one by one.
+int run_step_graph(esp_plan_t p, const void* pos, const void* q, void* forces, double* acc) {
+  if (!p->use_graph || p->stream == nullptr) return run_step(p, pos, q, forces, acc);
+  if (!(p->graph_exec && p->g_pos == pos && p->g_q == q && p->g_f == forces && p->g_acc == acc &&
+        p->g_prof == p->profiling)) {
+    drop_graph(p);
+    cudaStreamCaptureStatus cs;
+    if (cudaStreamIsCapturing(p->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+      return run_step(p, pos, q, forces, acc);  // the caller is capturing: just enqueue
+    if (cudaStreamBeginCapture(p->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      return run_step(p, pos, q, forces, acc);
+    }
+    const int rc = run_step(p, pos, q, forces, acc);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(p->stream, &graph);
+    if (rc != ESP_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rc;
+    }
+    if (e != cudaSuccess || !graph) {
+      cudaGetLastError();
+      p->use_graph = false;
+      return run_step(p, pos, q, forces, acc);
+    }
+    const cudaError_t ei = cudaGraphInstantiate(&p->graph_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+      cudaGetLastError();
+      p->graph_exec = nullptr;
+      p->use_graph = false;
+      return run_step(p, pos, q, forces, acc);
+    }
+    p->g_pos = pos;
+    p->g_q = q;
+    p->g_f = forces;
+    p->g_acc = acc;
+    p->g_prof = p->profiling;
+  }
+  ESP_CUDA(p, cudaGraphLaunch(p->graph_exec, p->stream));
+  p->spectrum_kept = forces == nullptr;
   return ESP_OK;
 }
 
@@ -517,7 +579,8 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
   int dev = 0;
   cudaGetDevice(&dev);
   p->device = dev;
-  p->scale_blocks = (p->M[0] * p->M[1] + esp::kThreads / 32 - 1) / (esp::kThreads / 32);  // a warp per row
+  p->scale_blocks = (p->M[0] * p->M[1] + esp::kThreads / 32 - 1) / (esp::kThreads / 32) + 1;
+  p->zero_blocks = 2 * sms;
 
   const size_t es = p->fp64 ? 8 : 4;
   const size_t io_es = p->io_double ? 8 : 4;
@@ -597,12 +660,14 @@ int esp_set_cell(esp_plan_t p, const double cell[9]) {
   for (int d = 0; d < 3; ++d) p->sg.mmax[d] = mmax[d];
   update_cell_constants(p);
   p->spectrum_kept = false;
+  drop_graph(p);
   return ESP_OK;
 }
 
 int esp_set_stream(esp_plan_t p, void* stream) {
   if (!p) return fail(nullptr, ESP_ERR_ARG, "plan is NULL");
   p->stream = (cudaStream_t)stream;
+  drop_graph(p);
   if (cufftSetStream(p->fwd, p->stream) != CUFFT_SUCCESS ||
       cufftSetStream(p->inv, p->stream) != CUFFT_SUCCESS)
     return fail(p, ESP_ERR_CUFFT, "cufftSetStream failed");
@@ -613,7 +678,7 @@ int esp_step(esp_plan_t p, const void* pos, const void* q, void* forces, double*
   if (!p) return fail(nullptr, ESP_ERR_ARG, "plan is NULL");
   if (p->n > 0 && (!pos || !q)) return fail(p, ESP_ERR_ARG, "pos or q is NULL");
   DeviceGuard guard(p->device);
-  return run_step(p, pos, q, forces, d_accum ? d_accum : p->d_accum);
+  return run_step_graph(p, pos, q, forces, d_accum ? d_accum : p->d_accum);
 }
 
 int esp_energy_pressure(esp_plan_t p, const void* pos, const void* q, esp_result* out) {
@@ -649,7 +714,7 @@ int esp_forces_from_spectrum(esp_plan_t p, void* forces) {
   cudaStream_t st = p->stream;
   const bool fp64 = p->fp64;
   ESP_CUDA(p, esp::launch_scale(fp64, true, p->sg, p->d_spec, p->d_invw2, p->d_radtab,
-                                p->d_partials, p->d_counter, p->d_accum, p->scale_blocks, st));
+                                p->d_partials, p->d_counter, p->d_accum, p->zero_blocks, st));
   if (fp64)
     ESP_CUFFT(p, cufftExecZ2D(p->inv, (cufftDoubleComplex*)p->d_spec, (cufftDoubleReal*)p->d_grid));
   else

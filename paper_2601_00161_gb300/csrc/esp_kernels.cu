@@ -579,13 +579,35 @@ __global__ void __launch_bounds__(kThreads) k_scale(typename Cplx<R>::T* __restr
                                                     const R* __restrict__ radtab,
                                                     double* __restrict__ partials,
                                                     unsigned int* __restrict__ counter,
-                                                    double* __restrict__ accum) {
-  // One warp per row (i0, i1) of the half spectrum, lanes along i2.  Rows outside the
-  // bounding box of the sphere |k| <= K and modes beyond mmax[2] hold no in-sphere mode:
-  // they are skipped (energy / pressure only) or zeroed (force path).
+                                                    double* __restrict__ accum, int nred) {
+  // Blocks [0, nred): one warp per row (m0, m1) of the bounding box of the sphere
+  // |k| <= K, lanes along i2; they scale (force path) and reduce.  Blocks from nred on
+  // (force path only) zero the rows outside the box, which hold no in-sphere mode.
   // FP64 path: plain FP64 sums.  FP32 path: compensated FP32 sums per lane and across
-  // the warp (about 48 significant bits), FP64 from the warp totals on.
+  // the warp (about 48 significant bits), FP64 from the block totals on.
   using Acc = typename std::conditional<std::is_same<R, double>::value, double, DF>::type;
+  const int lane = threadIdx.x & 31;
+  typename Cplx<R>::T zero;
+  zero.x = R(0);
+  zero.y = R(0);
+  const int w0box = 2 * s.mmax[0] + 1, w1box = 2 * s.mmax[1] + 1;
+  if ((int)blockIdx.x >= nred) {
+    if (WRITE) {
+      const int nrows = s.M[0] * s.M[1];
+      const int warps = ((gridDim.x - nred) * blockDim.x) >> 5;
+      for (int row = (((int)blockIdx.x - nred) * blockDim.x + threadIdx.x) >> 5; row < nrows;
+           row += warps) {
+        const int i0 = row / s.M[1];
+        const int i1 = row - i0 * s.M[1];
+        const int m0 = (2 * i0 <= s.M[0]) ? i0 : i0 - s.M[0];
+        const int m1 = (2 * i1 <= s.M[1]) ? i1 : i1 - s.M[1];
+        if (abs(m0) <= s.mmax[0] && abs(m1) <= s.mmax[1]) continue;
+        typename Cplx<R>::T* rowp = spec + (int64_t)row * s.H2;
+        for (int i2 = lane; i2 < s.H2; i2 += 32) rowp[i2] = zero;
+      }
+    }
+    return;
+  }
   Acc acc[7];
   if constexpr (std::is_same<R, double>::value)
     for (int j = 0; j < 7; ++j) acc[j] = 0.0;
@@ -593,25 +615,13 @@ __global__ void __launch_bounds__(kThreads) k_scale(typename Cplx<R>::T* __restr
   const R* iw1 = invw2 + s.M[0];
   const R* iw2 = invw2 + s.M[0] + s.M[1];
   const ScaleConst<R> sc(s);
-  const int lane = threadIdx.x & 31;
-  const int nrows = s.M[0] * s.M[1];
-  const int warps = (gridDim.x * blockDim.x) >> 5;
-  typename Cplx<R>::T zero;
-  zero.x = R(0);
-  zero.y = R(0);
-  for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < nrows; row += warps) {
-    // (launched with one warp per row; the loop covers any smaller grid)
-    const int i0 = row / s.M[1];
-    const int i1 = row - i0 * s.M[1];
-    const int m0 = (2 * i0 <= s.M[0]) ? i0 : i0 - s.M[0];
-    const int m1 = (2 * i1 <= s.M[1]) ? i1 : i1 - s.M[1];
-    typename Cplx<R>::T* rowp = spec + (int64_t)row * s.H2;
-    const bool row_in_box = abs(m0) <= s.mmax[0] && abs(m1) <= s.mmax[1];
-    if (!row_in_box) {
-      if (WRITE)
-        for (int i2 = lane; i2 < s.H2; i2 += 32) rowp[i2] = zero;
-      continue;
-    }
+  const int r = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  if (r < w0box * w1box) {
+    const int u0 = r / w1box;
+    const int m0 = u0 - s.mmax[0], m1 = r - u0 * w1box - s.mmax[1];
+    const int i0 = m0 >= 0 ? m0 : m0 + s.M[0];
+    const int i1 = m1 >= 0 ? m1 : m1 + s.M[1];
+    typename Cplx<R>::T* rowp = spec + ((int64_t)i0 * s.M[1] + i1) * s.H2;
     const R f0 = R(m0), f1 = R(m1);
     const R kx0 = f0 * bvec<R>(s, 0) + f1 * bvec<R>(s, 3);
     const R ky0 = f0 * bvec<R>(s, 1) + f1 * bvec<R>(s, 4);
@@ -692,7 +702,7 @@ __global__ void __launch_bounds__(kThreads) k_scale(typename Cplx<R>::T* __restr
     if (threadIdx.x < 7) {
       double v = 0.0;
       for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
-      partials[threadIdx.x * gridDim.x + blockIdx.x] = v;
+      partials[threadIdx.x * nred + blockIdx.x] = v;
     }
   } else {
     // compensated sums across the warp and the block; one FP64 conversion per block
@@ -721,12 +731,12 @@ __global__ void __launch_bounds__(kThreads) k_scale(typename Cplx<R>::T* __restr
         y.lo = red[threadIdx.x][w][1];
         x.add(y);
       }
-      partials[threadIdx.x * gridDim.x + blockIdx.x] = (double)x.hi + (double)x.lo;
+      partials[threadIdx.x * nred + blockIdx.x] = (double)x.hi + (double)x.lo;
     }
   }
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == (unsigned)nred - 1);
   __syncthreads();
   if (last) {
     // warp j sums component j: coalesced L2 loads (ld.cg: written by other blocks before
@@ -735,8 +745,8 @@ __global__ void __launch_bounds__(kThreads) k_scale(typename Cplx<R>::T* __restr
     const int j = threadIdx.x >> 5;
     if (j < 7) {
       double v = 0.0;
-      const double* pj = partials + (size_t)j * gridDim.x;
-      for (unsigned b = lane; b < gridDim.x; b += 32) v += __ldcg(pj + b);
+      const double* pj = partials + (size_t)j * nred;
+      for (int b = lane; b < nred; b += 32) v += __ldcg(pj + b);
       v = warp_sum(v);
       if (lane == 0) accum[j] = v;
     }
@@ -1061,26 +1071,29 @@ cudaError_t launch_spread(bool fp64, const TileGeom& g, int ntiles, int nblocks,
 
 cudaError_t launch_scale(bool fp64, bool write, const ScaleGeom& s, void* spec,
                          const void* invw2, const void* radtab, double* partials,
-                         unsigned int* counter, double* accum, int nblocks, cudaStream_t st) {
+                         unsigned int* counter, double* accum, int zero_blocks,
+                         cudaStream_t st) {
+  const int nbox = (2 * s.mmax[0] + 1) * (2 * s.mmax[1] + 1);
+  const int nred = (nbox + kThreads / 32 - 1) / (kThreads / 32);
+  const int nb = nred + (write ? zero_blocks : 0);
   if (fp64) {
     if (write)
-      k_scale<double, true><<<nblocks, kThreads, 0, st>>>((double2*)spec, s, (const double*)invw2,
-                                                         (const double*)radtab, partials,
-                                                         counter, accum);
+      k_scale<double, true><<<nb, kThreads, 0, st>>>((double2*)spec, s, (const double*)invw2,
+                                                    (const double*)radtab, partials, counter,
+                                                    accum, nred);
     else
-      k_scale<double, false><<<nblocks, kThreads, 0, st>>>((double2*)spec, s,
-                                                          (const double*)invw2,
-                                                          (const double*)radtab, partials,
-                                                          counter, accum);
+      k_scale<double, false><<<nb, kThreads, 0, st>>>((double2*)spec, s, (const double*)invw2,
+                                                     (const double*)radtab, partials, counter,
+                                                     accum, nred);
   } else {
     if (write)
-      k_scale<float, true><<<nblocks, kThreads, 0, st>>>((float2*)spec, s, (const float*)invw2,
-                                                        (const float*)radtab, partials,
-                                                        counter, accum);
+      k_scale<float, true><<<nb, kThreads, 0, st>>>((float2*)spec, s, (const float*)invw2,
+                                                   (const float*)radtab, partials, counter,
+                                                   accum, nred);
     else
-      k_scale<float, false><<<nblocks, kThreads, 0, st>>>((float2*)spec, s, (const float*)invw2,
-                                                         (const float*)radtab, partials, counter,
-                                                         accum);
+      k_scale<float, false><<<nb, kThreads, 0, st>>>((float2*)spec, s, (const float*)invw2,
+                                                    (const float*)radtab, partials, counter,
+                                                    accum, nred);
   }
   return cudaGetLastError();
 }

@@ -117,9 +117,12 @@ cudaError_t launch_scatter(bool fp64, int64_t n, const int* ptile, const int* pr
 cudaError_t launch_spread(bool fp64, const TileGeom& g, int ntiles, int nblocks,
                           const void* sorted_tq, const int* sorted_lb, const int* toff,
                           int* work, const void* wtab, void* grid, cudaStream_t st);
+// Blocks: one warp per spectrum row of the sphere's bounding box, plus zero_blocks that
+// clear the other rows on the force path.  partials needs 7 x (rows / 8 + 1) doubles.
 cudaError_t launch_scale(bool fp64, bool write, const ScaleGeom& s, void* spec,
                          const void* invw2, const void* radtab, double* partials,
-                         unsigned int* counter, double* accum, int nblocks, cudaStream_t st);
+                         unsigned int* counter, double* accum, int zero_blocks,
+                         cudaStream_t st);
 cudaError_t launch_gather(bool fp64, bool io_double, const GatherGeom& gg, int ntiles,
                           int nblocks, const void* sorted_tq, const int* sorted_lb,
                           const int* sorted_idx, const int* toff, int* work, const void* wtab,

@@ -207,6 +207,34 @@ def test_set_cell_npt(precision):
     plan.close()
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_graph_replay_on_own_stream(precision):
+    # on a non-default stream esp_step captures its launches in a CUDA graph and replays
+    # it; a new cell drops the graph
+    S = sy.small_random(700, TRI, seed=21, grid=(28, 28, 28), P=6, rc=3.5)
+    c = c_from_tolerance(S.delta)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        plan = esp.Plan(S.cell, S.n, S.grid, S.P, c, S.rc, precision=precision, stream=st.cuda_stream)
+        s = S.pos @ np.linalg.inv(S.cell).T
+        for scale in [1.0, 1.0, 1.03, 1.03]:
+            cell = S.cell * np.array([1.0, scale, 1.0])[:, None]
+            plan.set_cell(cell)
+            pos = torch.tensor(s @ cell.T, dtype=dt, device="cuda")
+            q = torch.tensor(S.q, dtype=dt, device="cuda")
+            F = torch.empty((S.n, 3), dtype=dt, device="cuda")
+            acc = torch.zeros(esp.ESP_ACCUM_LEN, dtype=torch.float64, device="cuda")
+            for _ in range(2):
+                plan.step(pos, q, F, acc)
+            st.synchronize()
+            res = esp.esp_result_from_accum(plan.handle, acc.cpu().numpy()).as_dict()
+            ref = esp_grid(pos.double().cpu().numpy(), q.double().cpu().numpy(), cell, S.grid, S.P, c, S.rc)
+            assert rel(res["virial_recip"], ref["virial"]) < TOL[precision]
+            assert rel(F.double().cpu().numpy(), ref["forces"]) < TOL[precision]
+        plan.close()
+
+
 def test_nonfinite_input_is_reported_not_faulted():
     S = sy.small_random(100, ORTHO, seed=9, grid=(16, 16, 16), P=6, rc=fitting_rc(ORTHO, (16, 16, 16), 1e-6))
     c = c_from_tolerance(S.delta)
