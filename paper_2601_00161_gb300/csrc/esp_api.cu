@@ -348,7 +348,8 @@ enum Stage { kPrep, kBin, kScan, kScatter, kZero, kSpread, kFftFwd, kScale, kFft
 
 inline void mark(esp_plan_t p, int i) {
   if (p->profiling) {
-    cudaEventRecord(p->ev[i], p->stream);
+    // "external" records stay timing events when the step is captured in a graph
+    cudaEventRecordWithFlags(p->ev[i], p->stream, cudaEventRecordExternal);
     p->ev_used[i] = true;
   }
 }
