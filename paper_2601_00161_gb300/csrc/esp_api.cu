@@ -362,14 +362,14 @@ int run_step(esp_plan_t p, const void* pos, const void* q, void* forces, double*
   for (int i = 0; i <= kNStage; ++i) p->ev_used[i] = false;
   mark(p, kPrep);
   int* work = p->d_count + (size_t)p->ntiles * esp::kSub;
-  ESP_CUDA(p, cudaMemsetAsync(p->d_count, 0, sizeof(int) * ((size_t)p->ntiles * esp::kSub + 2), st));
-  ESP_CUDA(p, cudaMemsetAsync(acc, 0, sizeof(double) * ESP_ACCUM_LEN, st));
+  // d_count and the work counters are zero here: set at plan time, re-zeroed by the scan
+  // kernel of every step.  acc[0..6] is written by the scale kernel, acc[7..9] by scan.
   mark(p, kBin);
   ESP_CUDA(p, esp::launch_bin(p->io_double, fp64, pos, q, p->n, p->tg, p->d_count, p->d_ptile,
                               p->d_prank, p->d_plb, p->d_tq, p->d_binpart, st));
   mark(p, kScan);
   ESP_CUDA(p, esp::launch_scan(p->d_count, p->d_suboff, p->d_offset, p->ntiles, p->d_binpart,
-                               p->n > 0 ? p->bin_blocks : 0, acc, st));
+                               p->n > 0 ? p->bin_blocks : 0, acc, work, st));
   mark(p, kScatter);
   ESP_CUDA(p, esp::launch_scatter(fp64, p->n, p->d_ptile, p->d_prank, p->d_plb, p->d_tq,
                                   p->d_suboff, p->d_sorted_tq, p->d_sorted_lb,
@@ -617,6 +617,8 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
   (void)io_es;
   {
     cudaError_t e = cudaMemset(p->d_counter, 0, sizeof(unsigned int));
+    if (e == cudaSuccess)
+      e = cudaMemset(p->d_count, 0, sizeof(int) * ((size_t)p->ntiles * esp::kSub + 2));
     if (e == cudaSuccess) e = cudaMemset(p->d_accum, 0, sizeof(double) * ESP_ACCUM_LEN);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_accum, sizeof(double) * ESP_ACCUM_LEN);
     if (e != cudaSuccess) return bail(cuda_fail(p, e, "plan workspace set-up"));

@@ -272,17 +272,25 @@ __global__ void __launch_bounds__(kThreads) k_bin(const IO* __restrict__ pos,
 // contiguous chunk; the chunk totals are scanned across the block.
 constexpr int kScanThreads = 1024;
 constexpr int kScanStageMax = 48 * 1024;  // counts staged in shared memory (192 KB)
-__global__ void __launch_bounds__(kScanThreads) k_scan(const int* __restrict__ count,
+__global__ void __launch_bounds__(kScanThreads) k_scan(int* __restrict__ count,
                                                        int* __restrict__ suboff,
                                                        int* __restrict__ toff, int ntiles,
                                                        const double* __restrict__ bin_part,
-                                                       int nbin, double* __restrict__ accum) {
+                                                       int nbin, double* __restrict__ accum,
+                                                       int* __restrict__ work) {
   __shared__ int warp_tot[kScanThreads / 32];
   extern __shared__ int cnt_s[];  // n counts staged with coalesced loads (if they fit)
   const int n = ntiles * kSub;
   const bool staged = n <= kScanStageMax;
   int* cs = staged ? cnt_s : suboff;  // else scan in place in the output array
-  for (int i = threadIdx.x; i < n; i += kScanThreads) cs[i] = count[i];
+  // the counts are read once and left at zero for the next step (with the work
+  // counters of spread and gather)
+#pragma unroll 8
+  for (int i = threadIdx.x; i < n; i += kScanThreads) {
+    cs[i] = count[i];
+    count[i] = 0;
+  }
+  if (threadIdx.x < 2) work[threadIdx.x] = 0;
   __syncthreads();
   const int chunk = (n + kScanThreads - 1) / kScanThreads;
   const int lo = min(n, (int)threadIdx.x * chunk), hi = min(n, lo + chunk);
@@ -326,6 +334,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const int* __restrict__ c
   if (threadIdx.x < 96) {
     const int j = threadIdx.x / 32, l = threadIdx.x & 31;
     double a = 0.0;
+#pragma unroll 8
     for (int b = l; b < nbin; b += 32) a += bin_part[3 * b + j];
     part[j][l] = a;
   }
@@ -861,50 +870,38 @@ __global__ void __launch_bounds__(kThreads) k_gather(
         Fa[3 * a + 2] = R(0);
       }
       __syncthreads();  // also covers the staging of phi for the first chunk
-      const int nitem = cnt * P * P;
-      const int nround = (nitem + blockDim.x - 1) / blockDim.x;
-      for (int r = 0; r < nround; ++r) {
-        const int it = r * blockDim.x + threadIdx.x;
-        const bool act = it < nitem;
-        const int a = act ? it / (P * P) : kChunk;
-        R gx = R(0), gy = R(0), gz = R(0);
-        if (act) {
-          const int pr = it - a * P * P;
-          const int jj = pr / P, k = pr - jj * P;
-          const R* Wa = W + a * 6 * P;
-          const R* src = phi + B[a] + jj * E3p + k;
+      // one item per (atom, j): the P x P points (i, k) of row j, contracted in registers
+      //   gx = w1[j] sum_k w2[k] sum_i phi w0'[i],  gy = w1'[j] sum_k w2[k] sum_i phi w0[i],
+      //   gz = w1[j] sum_k w2'[k] sum_i phi w0[i]
+      for (int it = threadIdx.x; it < cnt * P; it += blockDim.x) {
+        const int a = it / P, jj = it - a * P;
+        const R* Wa = W + a * 6 * P;
+        R w0[P], d0[P], w2[P], d2[P];
+#pragma unroll
+        for (int i = 0; i < P; ++i) {
+          w0[i] = Wa[i];
+          d0[i] = Wa[3 * P + i];
+          w2[i] = Wa[2 * P + i];
+          d2[i] = Wa[5 * P + i];
+        }
+        const R* src = phi + B[a] + jj * E3p;
+        R ax = R(0), ay = R(0), az = R(0);
+#pragma unroll
+        for (int kk = 0; kk < P; ++kk) {
           R sx = R(0), sw = R(0);
 #pragma unroll
           for (int i = 0; i < P; ++i) {
-            const R f = src[i * S1];
-            sx = fma(f, Wa[3 * P + i], sx);
-            sw = fma(f, Wa[i], sw);
+            const R f = src[i * S1 + kk];
+            sx = fma(f, d0[i], sx);
+            sw = fma(f, w0[i], sw);
           }
-          const R w1 = Wa[P + jj], w2 = Wa[2 * P + k];
-          gx = w1 * w2 * sx;
-          gy = Wa[4 * P + jj] * w2 * sw;
-          gz = w1 * Wa[5 * P + k] * sw;
+          ax = fma(w2[kk], sx, ax);
+          ay = fma(w2[kk], sw, ay);
+          az = fma(d2[kk], sw, az);
         }
-        // rows of one atom are contiguous in the warp: segmented inclusive scan, the last
-        // lane of each segment adds the atom's partial sums
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int ao = __shfl_up_sync(0xffffffffu, a, o);
-          const R x = __shfl_up_sync(0xffffffffu, gx, o);
-          const R y = __shfl_up_sync(0xffffffffu, gy, o);
-          const R z = __shfl_up_sync(0xffffffffu, gz, o);
-          if (lane >= o && ao == a) {
-            gx += x;
-            gy += y;
-            gz += z;
-          }
-        }
-        const int an = __shfl_down_sync(0xffffffffu, a, 1);
-        if (act && (lane == 31 || an != a)) {
-          smem_add(&Fa[3 * a + 0], gx);
-          smem_add(&Fa[3 * a + 1], gy);
-          smem_add(&Fa[3 * a + 2], gz);
-        }
+        smem_add(&Fa[3 * a + 0], Wa[P + jj] * ax);
+        smem_add(&Fa[3 * a + 1], Wa[4 * P + jj] * ay);
+        smem_add(&Fa[3 * a + 2], Wa[P + jj] * az);
       }
       __syncthreads();
       for (int a = threadIdx.x; a < cnt; a += blockDim.x) {
@@ -984,15 +981,16 @@ cudaError_t launch_bin(bool io_double, bool fp64, const void* pos, const void* q
   return cudaGetLastError();
 }
 
-cudaError_t launch_scan(const int* count, int* suboff, int* toff, int ntiles,
-                        const double* bin_part, int nbin, double* accum, cudaStream_t st) {
+cudaError_t launch_scan(int* count, int* suboff, int* toff, int ntiles,
+                        const double* bin_part, int nbin, double* accum, int* work,
+                        cudaStream_t st) {
   const size_t n = (size_t)ntiles * kSub;
   const size_t smem = n <= (size_t)kScanStageMax ? sizeof(int) * n : 0;
   if (smem > 48 * 1024) {
     const cudaError_t e = cudaFuncSetAttribute(k_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_scan<<<1, kScanThreads, smem, st>>>(count, suboff, toff, ntiles, bin_part, nbin, accum);
+  k_scan<<<1, kScanThreads, smem, st>>>(count, suboff, toff, ntiles, bin_part, nbin, accum, work);
   return cudaGetLastError();
 }
 

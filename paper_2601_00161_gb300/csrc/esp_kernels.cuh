@@ -109,8 +109,10 @@ cudaError_t launch_bin(bool io_double, bool fp64, const void* pos, const void* q
                        const TileGeom& g, int* tile_count, int* ptile, int* prank, int* plb,
                        void* tq, double* bin_part, cudaStream_t st);
 int bin_blocks(int64_t n);
-cudaError_t launch_scan(const int* count, int* suboff, int* toff, int ntiles,
-                        const double* bin_part, int nbin, double* accum, cudaStream_t st);
+// count: zero on entry (bin adds into it), zero again on exit; work[0..1] zeroed too
+cudaError_t launch_scan(int* count, int* suboff, int* toff, int ntiles,
+                        const double* bin_part, int nbin, double* accum, int* work,
+                        cudaStream_t st);
 cudaError_t launch_scatter(bool fp64, int64_t n, const int* ptile, const int* prank,
                            const int* plb, const void* tq, const int* offset, void* sorted_tq,
                            int* sorted_lb, int* sorted_idx, cudaStream_t st);
