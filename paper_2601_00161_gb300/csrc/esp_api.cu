@@ -368,10 +368,10 @@ int run_step(esp_plan_t p, const void* pos, const void* q, void* forces, double*
   ESP_CUDA(p, esp::launch_bin(p->io_double, fp64, pos, q, p->n, p->tg, p->d_count, p->d_ptile,
                               p->d_prank, p->d_plb, p->d_tq, p->d_binpart, st));
   mark(p, kScan);
-  ESP_CUDA(p, esp::launch_scan(p->d_count, p->d_suboff, p->d_offset, p->ntiles, p->d_binpart,
-                               p->n > 0 ? p->bin_blocks : 0, acc, work, st));
+  ESP_CUDA(p, esp::launch_scan(p->d_count, p->d_suboff, p->d_offset, p->ntiles, p->tg.ksub,
+                               p->d_binpart, p->n > 0 ? p->bin_blocks : 0, acc, work, st));
   mark(p, kScatter);
-  ESP_CUDA(p, esp::launch_scatter(fp64, p->n, p->d_ptile, p->d_prank, p->d_plb, p->d_tq,
+  ESP_CUDA(p, esp::launch_scatter(fp64, p->n, p->tg.ksub, p->d_ptile, p->d_prank, p->d_plb, p->d_tq,
                                   p->d_suboff, p->d_sorted_tq, p->d_sorted_lb,
                                   p->d_sorted_idx, st));
   mark(p, kZero);
@@ -555,6 +555,9 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
     g.dscalef[d] = (float)g.dscale[d];
     p->ntiles *= g.nt[d];
   }
+  g.ksub = (int64_t)p->ntiles * esp::kSub <= esp::kMaxScan ? esp::kSub : 1;
+  if ((int64_t)p->ntiles * g.ksub > esp::kMaxScan)
+    return bail(fail(p, ESP_ERR_ARG, "grid too large: more tiles than the binning scan handles"));
   g.vec4 = (!p->fp64 && g.T[2] % 4 == 0 && p->M[2] % 4 == 0 && (g.E[2] + 3) / 4 * 4 <= g.E3p) ? 1 : 0;
   {
     auto magic = [](unsigned int d) {

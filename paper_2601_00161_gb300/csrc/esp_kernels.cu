@@ -222,7 +222,7 @@ __global__ void __launch_bounds__(kThreads) k_bin(const IO* __restrict__ pos,
     ptile[i] = tile;
     plb[i] = lb[0] | (lb[1] << 10) | (lb[2] << 20);
     // kSub counters per tile, chosen by the atom's warp, spread the same-address atomics
-    prank[i] = atomicAdd(&tile_count[tile * kSub + (int)((i >> 5) & (kSub - 1))], 1);
+    prank[i] = atomicAdd(&tile_count[tile * g.ksub + (int)((i >> 5) & (g.ksub - 1))], 1);
     if constexpr (std::is_same<IO, float>::value) {
       sq.add(qi);
       sq2.add(qi * qi);
@@ -266,68 +266,82 @@ __global__ void __launch_bounds__(kThreads) k_bin(const IO* __restrict__ pos,
   }
 }
 
-// One CTA of kScanThreads: exclusive scan of the sub-counter counts (tile-major), the
-// tile offsets toff[t] = suboff[t * kSub], and the fixed-order sum of the binning
-// partials (sum q, sum q^2, skipped atoms) into accum[7..9].  Each thread scans a
-// contiguous chunk; the chunk totals are scanned across the block.
+// One CTA of kScanThreads: exclusive scan of the sub-counter counts (tile-major, ksub per
+// tile), the tile offsets toff[t] = suboff[t * ksub], and the fixed-order sum of the
+// binning partials (sum q, sum q^2, skipped atoms) into accum[7..9].  Counts move as
+// coalesced int4 in passes of 4 * kScanThreads with a running carry; they are left at
+// zero for the next step, as are the work counters of spread and gather.
 constexpr int kScanThreads = 1024;
-constexpr int kScanStageMax = 48 * 1024;  // counts staged in shared memory (192 KB)
 __global__ void __launch_bounds__(kScanThreads) k_scan(int* __restrict__ count,
                                                        int* __restrict__ suboff,
                                                        int* __restrict__ toff, int ntiles,
+                                                       int ksub,
                                                        const double* __restrict__ bin_part,
                                                        int nbin, double* __restrict__ accum,
                                                        int* __restrict__ work) {
-  __shared__ int warp_tot[kScanThreads / 32];
-  extern __shared__ int cnt_s[];  // n counts staged with coalesced loads (if they fit)
-  const int n = ntiles * kSub;
-  const bool staged = n <= kScanStageMax;
-  int* cs = staged ? cnt_s : suboff;  // else scan in place in the output array
-  // the counts are read once and left at zero for the next step (with the work
-  // counters of spread and gather)
-#pragma unroll 8
-  for (int i = threadIdx.x; i < n; i += kScanThreads) {
-    cs[i] = count[i];
-    count[i] = 0;
-  }
+  __shared__ int wsum[kScanThreads / 32];
+  __shared__ int carry_s;
+  const int n = ntiles * ksub;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry_s = 0;
   if (threadIdx.x < 2) work[threadIdx.x] = 0;
   __syncthreads();
-  const int chunk = (n + kScanThreads - 1) / kScanThreads;
-  const int lo = min(n, (int)threadIdx.x * chunk), hi = min(n, lo + chunk);
-  int own = 0;
-  for (int i = lo; i < hi; ++i) own += cs[i];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int x = own;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) warp_tot[wid] = x;
-  __syncthreads();
-  if (wid == 0) {
-    int t = warp_tot[lane];
+  for (int base = 0; base < n; base += 4 * kScanThreads) {
+    const int idx = base + 4 * threadIdx.x;
+    int v[4] = {0, 0, 0, 0};
+    const bool full = idx + 3 < n;
+    if (full) {
+      const int4 c = *reinterpret_cast<const int4*>(count + idx);
+      v[0] = c.x;
+      v[1] = c.y;
+      v[2] = c.z;
+      v[3] = c.w;
+      *reinterpret_cast<int4*>(count + idx) = make_int4(0, 0, 0, 0);
+    } else {
+      for (int e = 0; e < 4; ++e)
+        if (idx + e < n) {
+          v[e] = count[idx + e];
+          count[idx + e] = 0;
+        }
+    }
+    const int s4 = v[0] + v[1] + v[2] + v[3];
+    int x = s4;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, t, o);
-      if (lane >= o) t += y;
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
     }
-    warp_tot[lane] = t;  // inclusive prefix of warp totals
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int t = wsum[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      wsum[lane] = t;  // inclusive prefix of warp totals
+    }
+    __syncthreads();
+    int run = carry_s + (wid > 0 ? wsum[wid - 1] : 0) + x - s4;
+    int out[4];
+    for (int e = 0; e < 4; ++e) {
+      out[e] = run;
+      if (idx + e < n && (idx + e) % ksub == 0) toff[(idx + e) / ksub] = run;
+      run += v[e];
+    }
+    if (full)
+      *reinterpret_cast<int4*>(suboff + idx) = make_int4(out[0], out[1], out[2], out[3]);
+    else
+      for (int e = 0; e < 4; ++e)
+        if (idx + e < n) suboff[idx + e] = out[e];
+    __syncthreads();
+    if (threadIdx.x == 0) carry_s += wsum[kScanThreads / 32 - 1];
+    __syncthreads();
   }
-  __syncthreads();
-  int run = (wid > 0 ? warp_tot[wid - 1] : 0) + x - own;  // exclusive prefix of this chunk
-  for (int i = lo; i < hi; ++i) {
-    const int c = cs[i];
-    cs[i] = run;
-    run += c;
-  }
-  __syncthreads();
-  if (staged)
-    for (int i = threadIdx.x; i < n; i += kScanThreads) suboff[i] = cs[i];
-  for (int t = threadIdx.x; t < ntiles; t += kScanThreads) toff[t] = cs[t * kSub];
-  if (threadIdx.x == kScanThreads - 1) {
-    suboff[n] = warp_tot[kScanThreads / 32 - 1];
-    toff[ntiles] = warp_tot[kScanThreads / 32 - 1];
+  if (threadIdx.x == 0) {
+    suboff[n] = carry_s;
+    toff[ntiles] = carry_s;
   }
   // binning partials: 3 x 32 threads, fixed order
   __shared__ double part[3][32];
@@ -348,14 +362,14 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(int* __restrict__ count,
 
 template <typename V>
 __global__ void __launch_bounds__(kThreads) k_scatter(
-    int64_t n, const int* __restrict__ ptile, const int* __restrict__ prank,
+    int64_t n, int ksub, const int* __restrict__ ptile, const int* __restrict__ prank,
     const int* __restrict__ plb, const V* __restrict__ tq, const int* __restrict__ offset,
     V* __restrict__ sorted_tq, int* __restrict__ sorted_lb, int* __restrict__ sorted_idx) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int tile = ptile[i];
     if (tile < 0) continue;
-    const int dst = offset[tile * kSub + (int)((i >> 5) & (kSub - 1))] + prank[i];
+    const int dst = offset[tile * ksub + (int)((i >> 5) & (ksub - 1))] + prank[i];
     sorted_tq[dst] = tq[i];
     sorted_lb[dst] = plb[i];
     sorted_idx[dst] = (int)i;
@@ -981,32 +995,27 @@ cudaError_t launch_bin(bool io_double, bool fp64, const void* pos, const void* q
   return cudaGetLastError();
 }
 
-cudaError_t launch_scan(int* count, int* suboff, int* toff, int ntiles,
+cudaError_t launch_scan(int* count, int* suboff, int* toff, int ntiles, int ksub,
                         const double* bin_part, int nbin, double* accum, int* work,
                         cudaStream_t st) {
-  const size_t n = (size_t)ntiles * kSub;
-  const size_t smem = n <= (size_t)kScanStageMax ? sizeof(int) * n : 0;
-  if (smem > 48 * 1024) {
-    const cudaError_t e = cudaFuncSetAttribute(k_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  k_scan<<<1, kScanThreads, smem, st>>>(count, suboff, toff, ntiles, bin_part, nbin, accum, work);
+  k_scan<<<1, kScanThreads, 0, st>>>(count, suboff, toff, ntiles, ksub, bin_part, nbin, accum,
+                                     work);
   return cudaGetLastError();
 }
 
 int bin_blocks(int64_t n) { return grid_blocks(n); }
 
-cudaError_t launch_scatter(bool fp64, int64_t n, const int* ptile, const int* prank,
+cudaError_t launch_scatter(bool fp64, int64_t n, int ksub, const int* ptile, const int* prank,
                            const int* plb, const void* tq, const int* offset, void* sorted_tq,
                            int* sorted_lb, int* sorted_idx, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int nb = grid_blocks(n);
   if (fp64)
-    k_scatter<double4><<<nb, kThreads, 0, st>>>(n, ptile, prank, plb, (const double4*)tq,
+    k_scatter<double4><<<nb, kThreads, 0, st>>>(n, ksub, ptile, prank, plb, (const double4*)tq,
                                                 offset, (double4*)sorted_tq, sorted_lb,
                                                 sorted_idx);
   else
-    k_scatter<float4><<<nb, kThreads, 0, st>>>(n, ptile, prank, plb, (const float4*)tq, offset,
+    k_scatter<float4><<<nb, kThreads, 0, st>>>(n, ksub, ptile, prank, plb, (const float4*)tq, offset,
                                                (float4*)sorted_tq, sorted_lb, sorted_idx);
   return cudaGetLastError();
 }

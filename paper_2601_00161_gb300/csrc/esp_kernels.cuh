@@ -16,6 +16,7 @@ constexpr int kDegF64 = 24;
 constexpr int kRadialPieces = 16;
 constexpr int kThreads = 256;
 constexpr int kSub = 8;    // binning sub-counters per tile (spreads same-address atomics)
+constexpr int kMaxScan = 1 << 20;  // most counters the single-CTA scan is sized for
 
 // Geometry shared by the binning, spreading and gathering kernels.
 struct TileGeom {
@@ -27,6 +28,7 @@ struct TileGeom {
   int E3p;      // shared-memory row pitch (TileC<P>::E3p)
   int deg;      // degree of the window polynomials
   int vec4;     // 1: rows move as aligned float4 between global and shared memory
+  int ksub;     // binning sub-counters per tile (kSub, or 1 for very many tiles)
   double hinv[9];    // h^{-1}, row-major
   float hinvf[9];    // the same in FP32 (FP32 force transform)
   double dscale[3];  // d u / d s factor of the window argument: 2 M_d / P
@@ -110,10 +112,10 @@ cudaError_t launch_bin(bool io_double, bool fp64, const void* pos, const void* q
                        void* tq, double* bin_part, cudaStream_t st);
 int bin_blocks(int64_t n);
 // count: zero on entry (bin adds into it), zero again on exit; work[0..1] zeroed too
-cudaError_t launch_scan(int* count, int* suboff, int* toff, int ntiles,
+cudaError_t launch_scan(int* count, int* suboff, int* toff, int ntiles, int ksub,
                         const double* bin_part, int nbin, double* accum, int* work,
                         cudaStream_t st);
-cudaError_t launch_scatter(bool fp64, int64_t n, const int* ptile, const int* prank,
+cudaError_t launch_scatter(bool fp64, int64_t n, int ksub, const int* ptile, const int* prank,
                            const int* plb, const void* tq, const int* offset, void* sorted_tq,
                            int* sorted_lb, int* sorted_idx, cudaStream_t st);
 cudaError_t launch_spread(bool fp64, const TileGeom& g, int ntiles, int nblocks,
