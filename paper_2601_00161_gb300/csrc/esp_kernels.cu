@@ -268,10 +268,12 @@ __global__ void __launch_bounds__(kThreads) k_bin(const IO* __restrict__ pos,
 
 // One CTA of kScanThreads: exclusive scan of the sub-counter counts (tile-major, ksub per
 // tile), the tile offsets toff[t] = suboff[t * ksub], and the fixed-order sum of the
-// binning partials (sum q, sum q^2, skipped atoms) into accum[7..9].  Counts move as
-// coalesced int4 in passes of 4 * kScanThreads with a running carry; they are left at
-// zero for the next step, as are the work counters of spread and gather.
+// binning partials (sum q, sum q^2, skipped atoms) into accum[7..9].  In each pass of up
+// to kScanThreads * kScanPer counts, every thread loads its contiguous chunk at once (one
+// memory round trip per pass), scans it, and the chunk totals are scanned across the
+// block.  Counts are left at zero for the next step, as are the work counters.
 constexpr int kScanThreads = 1024;
+constexpr int kScanPer = 32;  // counts per thread per pass (a multiple of 4)
 __global__ void __launch_bounds__(kScanThreads) k_scan(int* __restrict__ count,
                                                        int* __restrict__ suboff,
                                                        int* __restrict__ toff, int ntiles,
@@ -286,25 +288,35 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(int* __restrict__ count,
   if (threadIdx.x == 0) carry_s = 0;
   if (threadIdx.x < 2) work[threadIdx.x] = 0;
   __syncthreads();
-  for (int base = 0; base < n; base += 4 * kScanThreads) {
-    const int idx = base + 4 * threadIdx.x;
-    int v[4] = {0, 0, 0, 0};
-    const bool full = idx + 3 < n;
-    if (full) {
-      const int4 c = *reinterpret_cast<const int4*>(count + idx);
-      v[0] = c.x;
-      v[1] = c.y;
-      v[2] = c.z;
-      v[3] = c.w;
-      *reinterpret_cast<int4*>(count + idx) = make_int4(0, 0, 0, 0);
-    } else {
-      for (int e = 0; e < 4; ++e)
-        if (idx + e < n) {
-          v[e] = count[idx + e];
-          count[idx + e] = 0;
+  for (int base = 0; base < n; base += kScanThreads * kScanPer) {
+    // chunk per thread: a multiple of 4, at most kScanPer
+    const int span = min(n - base, kScanThreads * kScanPer);
+    const int chunk = min(kScanPer, ((span + kScanThreads - 1) / kScanThreads + 3) & ~3);
+    const int lo = base + threadIdx.x * chunk;
+    int v[kScanPer];
+    int s4 = 0;
+#pragma unroll
+    for (int e = 0; e < kScanPer; e += 4) {
+      int4 c = make_int4(0, 0, 0, 0);
+      const int i = lo + e;
+      if (e < chunk && i < base + span) {
+        if (i + 3 < n) {
+          c = *reinterpret_cast<const int4*>(count + i);
+          *reinterpret_cast<int4*>(count + i) = make_int4(0, 0, 0, 0);
+        } else {
+          c.x = i < n ? count[i] : 0;
+          c.y = i + 1 < n ? count[i + 1] : 0;
+          c.z = i + 2 < n ? count[i + 2] : 0;
+          for (int f = 0; f < 3; ++f)
+            if (i + f < n) count[i + f] = 0;
         }
+      }
+      v[e] = c.x;
+      v[e + 1] = c.y;
+      v[e + 2] = c.z;
+      v[e + 3] = c.w;
+      s4 += c.x + c.y + c.z + c.w;
     }
-    const int s4 = v[0] + v[1] + v[2] + v[3];
     int x = s4;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -324,17 +336,25 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(int* __restrict__ count,
     }
     __syncthreads();
     int run = carry_s + (wid > 0 ? wsum[wid - 1] : 0) + x - s4;
-    int out[4];
-    for (int e = 0; e < 4; ++e) {
-      out[e] = run;
-      if (idx + e < n && (idx + e) % ksub == 0) toff[(idx + e) / ksub] = run;
-      run += v[e];
+#pragma unroll
+    for (int e = 0; e < kScanPer; e += 4) {
+      const int i = lo + e;
+      int o4[4];
+      for (int f = 0; f < 4; ++f) {
+        o4[f] = run;
+        run += v[e + f];
+      }
+      if (e < chunk && i < base + span) {
+        if (i + 3 < n) {
+          *reinterpret_cast<int4*>(suboff + i) = make_int4(o4[0], o4[1], o4[2], o4[3]);
+        } else {
+          for (int f = 0; f < 4; ++f)
+            if (i + f < n) suboff[i + f] = o4[f];
+        }
+        for (int f = 0; f < 4; ++f)
+          if (i + f < n && (i + f) % ksub == 0) toff[(i + f) / ksub] = o4[f];
+      }
     }
-    if (full)
-      *reinterpret_cast<int4*>(suboff + idx) = make_int4(out[0], out[1], out[2], out[3]);
-    else
-      for (int e = 0; e < 4; ++e)
-        if (idx + e < n) suboff[idx + e] = out[e];
     __syncthreads();
     if (threadIdx.x == 0) carry_s += wsum[kScanThreads / 32 - 1];
     __syncthreads();
@@ -785,7 +805,7 @@ __global__ void __launch_bounds__(kThreads) k_scale(typename Cplx<R>::T* __restr
 // and the last lane of each segment adds the sums into the atom's slot; (C) one thread
 // per atom turns the sums into the force.
 template <typename R, typename IO, int P>
-__global__ void __launch_bounds__(kThreads) k_gather(
+__global__ void __launch_bounds__(kThreads, 4) k_gather(
     const typename Vec4<R>::T* __restrict__ sorted_tq, const int* __restrict__ sorted_lb,
     const int* __restrict__ sorted_idx, const int* __restrict__ toff, GatherGeom gg,
     int ntiles, int* __restrict__ work, const R* __restrict__ wtab,
