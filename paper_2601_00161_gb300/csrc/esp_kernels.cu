@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(kThreads) k_bin(const IO* __restrict__ pos,
                                                   int* __restrict__ prank,
                                                   int* __restrict__ plb,
                                                   typename Vec4<R>::T* __restrict__ tq,
-                                                  double* __restrict__ bin_part) {
+                                                  float2* __restrict__ bin_part) {
   // FP32 inputs on the FP32 path use the compensated FP32 transform (FP64 only for the
   // rare coordinate next to a stencil switch); everything else uses FP64.
   constexpr bool kDF = std::is_same<IO, float>::value && std::is_same<R, float>::value;
@@ -251,18 +251,23 @@ __global__ void __launch_bounds__(kThreads) k_bin(const IO* __restrict__ pos,
     sq2.add(b2);
     bad.add(c);
   }
-  __shared__ double red[3][kThreads / 32];
+  __shared__ float2 red[3][kThreads / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {
-    red[0][wid] = (double)sq.hi + (double)sq.lo;
-    red[1][wid] = (double)sq2.hi + (double)sq2.lo;
-    red[2][wid] = (double)bad.hi + (double)bad.lo;
+    red[0][wid] = make_float2(sq.hi, sq.lo);
+    red[1][wid] = make_float2(sq2.hi, sq2.lo);
+    red[2][wid] = make_float2(bad.hi, bad.lo);
   }
   __syncthreads();
-  if (threadIdx.x < 3) {  // per-block partials; the scan kernel adds them up
-    double a = 0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) a += red[threadIdx.x][w];
-    bin_part[3 * blockIdx.x + threadIdx.x] = a;
+  if (threadIdx.x < 3) {  // compensated per-block partials; the scan kernel adds them up
+    DF a;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      DF y;
+      y.hi = red[threadIdx.x][w].x;
+      y.lo = red[threadIdx.x][w].y;
+      a.add(y);
+    }
+    bin_part[3 * blockIdx.x + threadIdx.x] = make_float2(a.hi, a.lo);
   }
 }
 
@@ -278,7 +283,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(int* __restrict__ count,
                                                        int* __restrict__ suboff,
                                                        int* __restrict__ toff, int ntiles,
                                                        int ksub,
-                                                       const double* __restrict__ bin_part,
+                                                       const float2* __restrict__ bin_part,
                                                        int nbin, double* __restrict__ accum,
                                                        int* __restrict__ work) {
   __shared__ int wsum[kScanThreads / 32];
@@ -363,20 +368,26 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(int* __restrict__ count,
     suboff[n] = carry_s;
     toff[ntiles] = carry_s;
   }
-  // binning partials: 3 x 32 threads, fixed order
-  __shared__ double part[3][32];
-  if (threadIdx.x < 96) {
-    const int j = threadIdx.x / 32, l = threadIdx.x & 31;
-    double a = 0.0;
-#pragma unroll 8
-    for (int b = l; b < nbin; b += 32) a += bin_part[3 * b + j];
-    part[j][l] = a;
-  }
-  __syncthreads();
-  if (threadIdx.x < 3) {
-    double a = 0.0;
-    for (int l = 0; l < 32; ++l) a += part[threadIdx.x][l];
-    accum[7 + threadIdx.x] = a;
+  // binning partials: warp j adds component j in compensated FP32 (fixed order); one
+  // FP64 conversion at the end (dependent FP64 chains are slow on this part)
+  if (wid < 3) {
+    DF a;
+#pragma unroll 4
+    for (int b = lane; b < nbin; b += 32) {
+      const float2 v = bin_part[3 * b + wid];
+      DF y;
+      y.hi = v.x;
+      y.lo = v.y;
+      a.add(y);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      DF y;
+      y.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
+      y.lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
+      a.add(y);
+    }
+    if (lane == 0) accum[7 + wid] = (double)a.hi + (double)a.lo;
   }
 }
 
@@ -774,7 +785,7 @@ __global__ void __launch_bounds__(kThreads) k_scale(typename Cplx<R>::T* __restr
         y.lo = red[threadIdx.x][w][1];
         x.add(y);
       }
-      partials[threadIdx.x * nred + blockIdx.x] = (double)x.hi + (double)x.lo;
+      reinterpret_cast<float2*>(partials)[threadIdx.x * nred + blockIdx.x] = make_float2(x.hi, x.lo);
     }
   }
   __threadfence();
@@ -787,11 +798,32 @@ __global__ void __launch_bounds__(kThreads) k_scale(typename Cplx<R>::T* __restr
     __threadfence();
     const int j = threadIdx.x >> 5;
     if (j < 7) {
-      double v = 0.0;
-      const double* pj = partials + (size_t)j * nred;
-      for (int b = lane; b < nred; b += 32) v += __ldcg(pj + b);
-      v = warp_sum(v);
-      if (lane == 0) accum[j] = v;
+      if constexpr (std::is_same<R, double>::value) {
+        double v = 0.0;
+        const double* pj = partials + (size_t)j * nred;
+        for (int b = lane; b < nred; b += 32) v += __ldcg(pj + b);
+        v = warp_sum(v);
+        if (lane == 0) accum[j] = v;
+      } else {
+        // compensated FP32 to the end, one FP64 conversion
+        DF x;
+        const float2* pj = reinterpret_cast<const float2*>(partials) + (size_t)j * nred;
+        for (int b = lane; b < nred; b += 32) {
+          const float2 v = __ldcg(pj + b);
+          DF y;
+          y.hi = v.x;
+          y.lo = v.y;
+          x.add(y);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          DF y;
+          y.hi = __shfl_xor_sync(0xffffffffu, x.hi, o);
+          y.lo = __shfl_xor_sync(0xffffffffu, x.lo, o);
+          x.add(y);
+        }
+        if (lane == 0) accum[j] = (double)x.hi + (double)x.lo;
+      }
     }
     if (threadIdx.x == 0) *counter = 0u;
   }
@@ -993,8 +1025,9 @@ cudaError_t with_P(int P, F&& f) {
 // ---- host launchers --------------------------------------------------------------------
 cudaError_t launch_bin(bool io_double, bool fp64, const void* pos, const void* q, int64_t n,
                        const TileGeom& g, int* tile_count, int* ptile, int* prank, int* plb,
-                       void* tq, double* bin_part, cudaStream_t st) {
+                       void* tq, void* bin_part_v, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
+  float2* bin_part = (float2*)bin_part_v;
   const int nb = grid_blocks(n);
   if (io_double && fp64)
     k_bin<double, double><<<nb, kThreads, 0, st>>>((const double*)pos, (const double*)q, n, g,
@@ -1016,10 +1049,10 @@ cudaError_t launch_bin(bool io_double, bool fp64, const void* pos, const void* q
 }
 
 cudaError_t launch_scan(int* count, int* suboff, int* toff, int ntiles, int ksub,
-                        const double* bin_part, int nbin, double* accum, int* work,
+                        const void* bin_part, int nbin, double* accum, int* work,
                         cudaStream_t st) {
-  k_scan<<<1, kScanThreads, 0, st>>>(count, suboff, toff, ntiles, ksub, bin_part, nbin, accum,
-                                     work);
+  k_scan<<<1, kScanThreads, 0, st>>>(count, suboff, toff, ntiles, ksub,
+                                     (const float2*)bin_part, nbin, accum, work);
   return cudaGetLastError();
 }
 

@@ -109,11 +109,12 @@ __host__ __device__ inline SmemLayout smem_layout(bool gather, size_t es, size_t
 
 cudaError_t launch_bin(bool io_double, bool fp64, const void* pos, const void* q, int64_t n,
                        const TileGeom& g, int* tile_count, int* ptile, int* prank, int* plb,
-                       void* tq, double* bin_part, cudaStream_t st);
+                       void* tq, void* bin_part, cudaStream_t st);
 int bin_blocks(int64_t n);
 // count: zero on entry (bin adds into it), zero again on exit; work[0..1] zeroed too
+// bin_part: per binning block 3 compensated sums (float pairs)
 cudaError_t launch_scan(int* count, int* suboff, int* toff, int ntiles, int ksub,
-                        const double* bin_part, int nbin, double* accum, int* work,
+                        const void* bin_part, int nbin, double* accum, int* work,
                         cudaStream_t st);
 cudaError_t launch_scatter(bool fp64, int64_t n, int ksub, const int* ptile, const int* prank,
                            const int* plb, const void* tq, const int* offset, void* sorted_tq,
