@@ -304,7 +304,7 @@ def esp_arm(args):
         fp64_value = round(1e3 * n64 / tot, 2)
         p64.close()
 
-    launches_per_step = 6
+    launches_per_step = 7  # bin, scan (2), scatter, spread, scale, gather
     out = None
     if rank == 0:
         ms = 1e3 * t_max / args.steps

@@ -68,6 +68,7 @@ struct esp_plan_s {
   int* d_count = nullptr;   // kSub counters per tile, then 2 work counters (spread, gather)
   int* d_suboff = nullptr;  // exclusive scan of d_count (tile-major)
   int* d_offset = nullptr;  // first sorted atom of each tile (ntiles + 1)
+  int* d_bsum = nullptr;    // per scan block totals
   double* d_binpart = nullptr;  // per binning block: sum q, sum q^2, skipped atoms
   int* d_ptile = nullptr;
   int* d_prank = nullptr;
@@ -311,7 +312,7 @@ void release(esp_plan_t p) {
   if (!p) return;
   if (p->stream) cudaStreamSynchronize(p->stream);
   void* bufs[] = {p->d_wtab,      p->d_radtab,    p->d_invw2,    p->d_grid,      p->d_spec,  p->d_tq,
-                  p->d_count,     p->d_offset,    p->d_ptile,    p->d_prank,     p->d_plb,  p->d_suboff, p->d_binpart,
+                  p->d_count,     p->d_offset,    p->d_ptile,    p->d_prank,     p->d_plb,  p->d_suboff, p->d_binpart, p->d_bsum,
                   p->d_sorted_tq, p->d_sorted_lb, p->d_sorted_idx, p->d_accum,   p->d_partials,
                   p->d_counter,   p->d_io_pos,    p->d_io_q,     p->d_io_f};
   for (void* b : bufs)
@@ -368,8 +369,9 @@ int run_step(esp_plan_t p, const void* pos, const void* q, void* forces, double*
   ESP_CUDA(p, esp::launch_bin(p->io_double, fp64, pos, q, p->n, p->tg, p->d_count, p->d_ptile,
                               p->d_prank, p->d_plb, p->d_tq, p->d_binpart, st));
   mark(p, kScan);
-  ESP_CUDA(p, esp::launch_scan(p->d_count, p->d_suboff, p->d_offset, p->ntiles, p->tg.ksub,
-                               p->d_binpart, p->n > 0 ? p->bin_blocks : 0, acc, work, st));
+  ESP_CUDA(p, esp::launch_scan(p->d_count, p->d_suboff, p->d_offset, p->d_bsum, p->ntiles,
+                               p->tg.ksub, p->d_binpart, p->n > 0 ? p->bin_blocks : 0, acc,
+                               work, st));
   mark(p, kScatter);
   ESP_CUDA(p, esp::launch_scatter(fp64, p->n, p->tg.ksub, p->d_ptile, p->d_prank, p->d_plb, p->d_tq,
                                   p->d_suboff, p->d_sorted_tq, p->d_sorted_lb,
@@ -606,6 +608,7 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
   ALLOC(p->d_suboff, sizeof(int) * ((size_t)p->ntiles * esp::kSub + 1));
   ALLOC(p->d_offset, sizeof(int) * (p->ntiles + 1));
   ALLOC(p->d_binpart, sizeof(double) * 3 * p->bin_blocks);
+  ALLOC(p->d_bsum, sizeof(int) * esp::scan_blocks(p->ntiles, g.ksub));
   ALLOC(p->d_ptile, sizeof(int) * nn);
   ALLOC(p->d_prank, sizeof(int) * nn);
   ALLOC(p->d_plb, sizeof(int) * nn);

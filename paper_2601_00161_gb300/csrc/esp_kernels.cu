@@ -271,123 +271,131 @@ __global__ void __launch_bounds__(kThreads) k_bin(const IO* __restrict__ pos,
   }
 }
 
-// One CTA of kScanThreads: exclusive scan of the sub-counter counts (tile-major, ksub per
-// tile), the tile offsets toff[t] = suboff[t * ksub], and the fixed-order sum of the
-// binning partials (sum q, sum q^2, skipped atoms) into accum[7..9].  In each pass of up
-// to kScanThreads * kScanPer counts, every thread loads its contiguous chunk at once (one
-// memory round trip per pass), scans it, and the chunk totals are scanned across the
-// block.  Counts are left at zero for the next step, as are the work counters.
-constexpr int kScanThreads = 1024;
-constexpr int kScanPer = 32;  // counts per thread per pass (a multiple of 4)
-__global__ void __launch_bounds__(kScanThreads) k_scan(int* __restrict__ count,
-                                                       int* __restrict__ suboff,
-                                                       int* __restrict__ toff, int ntiles,
-                                                       int ksub,
+// Exclusive scan of the binning sub-counters (tile-major, ksub per tile) in two
+// multi-block kernels of kScanBlock counts per block:
+//   k_scan_local  each block scans its counts (int4 per thread), writes the local
+//                 exclusive prefix to suboff and its total to bsum, and zeroes the counts
+//                 for the next step;
+//   k_scan_fix    each block adds the sum of the totals of the blocks before it and
+//                 writes the tile offsets toff[t] = suboff[t * ksub]; block 0 also adds
+//                 up the binning partials (sum q, sum q^2, skipped atoms) into accum[7..9]
+//                 and resets the work counters of spread and gather.
+constexpr int kScanBlock = 4 * kThreads;
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int* wsum, int* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int t = lane < kThreads / 32 ? wsum[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < kThreads / 32) wsum[lane] = t;
+  }
+  __syncthreads();
+  *total = wsum[kThreads / 32 - 1];
+  return (wid > 0 ? wsum[wid - 1] : 0) + x - v;
+}
+
+__global__ void __launch_bounds__(kThreads) k_scan_local(int* __restrict__ count,
+                                                         int* __restrict__ suboff,
+                                                         int* __restrict__ bsum, int n) {
+  __shared__ int wsum[kThreads / 32];
+  const int i = blockIdx.x * kScanBlock + 4 * threadIdx.x;
+  int v[4] = {0, 0, 0, 0};
+  if (i + 3 < n) {
+    const int4 c = *reinterpret_cast<const int4*>(count + i);
+    v[0] = c.x;
+    v[1] = c.y;
+    v[2] = c.z;
+    v[3] = c.w;
+    *reinterpret_cast<int4*>(count + i) = make_int4(0, 0, 0, 0);
+  } else {
+    for (int f = 0; f < 4; ++f)
+      if (i + f < n) {
+        v[f] = count[i + f];
+        count[i + f] = 0;
+      }
+  }
+  int total;
+  int run = block_exclusive_scan(v[0] + v[1] + v[2] + v[3], wsum, &total);
+  int o[4];
+  for (int f = 0; f < 4; ++f) {
+    o[f] = run;
+    run += v[f];
+  }
+  if (i + 3 < n)
+    *reinterpret_cast<int4*>(suboff + i) = make_int4(o[0], o[1], o[2], o[3]);
+  else
+    for (int f = 0; f < 4; ++f)
+      if (i + f < n) suboff[i + f] = o[f];
+  if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kThreads) k_scan_fix(int* __restrict__ suboff,
+                                                       int* __restrict__ toff,
+                                                       const int* __restrict__ bsum,
+                                                       int ntiles, int ksub,
                                                        const float2* __restrict__ bin_part,
                                                        int nbin, double* __restrict__ accum,
                                                        int* __restrict__ work) {
-  __shared__ int wsum[kScanThreads / 32];
-  __shared__ int carry_s;
+  __shared__ int red[kThreads / 32];
   const int n = ntiles * ksub;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  if (threadIdx.x == 0) carry_s = 0;
-  if (threadIdx.x < 2) work[threadIdx.x] = 0;
+  // sum of the totals of the blocks before this one
+  int pre = 0;
+  for (int b = threadIdx.x; b < (int)blockIdx.x; b += blockDim.x) pre += bsum[b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) pre += __shfl_xor_sync(0xffffffffu, pre, o);
+  if (lane == 0) red[wid] = pre;
   __syncthreads();
-  for (int base = 0; base < n; base += kScanThreads * kScanPer) {
-    // chunk per thread: a multiple of 4, at most kScanPer
-    const int span = min(n - base, kScanThreads * kScanPer);
-    const int chunk = min(kScanPer, ((span + kScanThreads - 1) / kScanThreads + 3) & ~3);
-    const int lo = base + threadIdx.x * chunk;
-    int v[kScanPer];
-    int s4 = 0;
-#pragma unroll
-    for (int e = 0; e < kScanPer; e += 4) {
-      int4 c = make_int4(0, 0, 0, 0);
-      const int i = lo + e;
-      if (e < chunk && i < base + span) {
-        if (i + 3 < n) {
-          c = *reinterpret_cast<const int4*>(count + i);
-          *reinterpret_cast<int4*>(count + i) = make_int4(0, 0, 0, 0);
-        } else {
-          c.x = i < n ? count[i] : 0;
-          c.y = i + 1 < n ? count[i + 1] : 0;
-          c.z = i + 2 < n ? count[i + 2] : 0;
-          for (int f = 0; f < 3; ++f)
-            if (i + f < n) count[i + f] = 0;
-        }
-      }
-      v[e] = c.x;
-      v[e + 1] = c.y;
-      v[e + 2] = c.z;
-      v[e + 3] = c.w;
-      s4 += c.x + c.y + c.z + c.w;
+  pre = 0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) pre += red[w];
+  const int i = blockIdx.x * kScanBlock + 4 * threadIdx.x;
+  for (int f = 0; f < 4; ++f) {
+    if (i + f < n) {
+      const int v = suboff[i + f] + pre;
+      suboff[i + f] = v;
+      if ((i + f) % ksub == 0) toff[(i + f) / ksub] = v;
     }
-    int x = s4;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, x, o);
-      if (lane >= o) x += y;
-    }
-    if (lane == 31) wsum[wid] = x;
-    __syncthreads();
-    if (wid == 0) {
-      int t = wsum[lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, t, o);
-        if (lane >= o) t += y;
-      }
-      wsum[lane] = t;  // inclusive prefix of warp totals
-    }
-    __syncthreads();
-    int run = carry_s + (wid > 0 ? wsum[wid - 1] : 0) + x - s4;
-#pragma unroll
-    for (int e = 0; e < kScanPer; e += 4) {
-      const int i = lo + e;
-      int o4[4];
-      for (int f = 0; f < 4; ++f) {
-        o4[f] = run;
-        run += v[e + f];
-      }
-      if (e < chunk && i < base + span) {
-        if (i + 3 < n) {
-          *reinterpret_cast<int4*>(suboff + i) = make_int4(o4[0], o4[1], o4[2], o4[3]);
-        } else {
-          for (int f = 0; f < 4; ++f)
-            if (i + f < n) suboff[i + f] = o4[f];
-        }
-        for (int f = 0; f < 4; ++f)
-          if (i + f < n && (i + f) % ksub == 0) toff[(i + f) / ksub] = o4[f];
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) carry_s += wsum[kScanThreads / 32 - 1];
-    __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    suboff[n] = carry_s;
-    toff[ntiles] = carry_s;
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
+    const int last = blockIdx.x;
+    const int tot = pre + bsum[last];
+    suboff[n] = tot;
+    toff[ntiles] = tot;
   }
-  // binning partials: warp j adds component j in compensated FP32 (fixed order); one
-  // FP64 conversion at the end (dependent FP64 chains are slow on this part)
-  if (wid < 3) {
-    DF a;
-#pragma unroll 4
-    for (int b = lane; b < nbin; b += 32) {
-      const float2 v = bin_part[3 * b + wid];
-      DF y;
-      y.hi = v.x;
-      y.lo = v.y;
-      a.add(y);
-    }
+  if (blockIdx.x == 0) {
+    if (threadIdx.x < 2) work[threadIdx.x] = 0;
+    // binning partials: warp j adds component j in compensated FP32 (fixed order); one
+    // FP64 conversion at the end (dependent FP64 chains are slow on this part)
+    if (wid < 3) {
+      DF a;
+      for (int b = lane; b < nbin; b += 32) {
+        const float2 v = bin_part[3 * b + wid];
+        DF y;
+        y.hi = v.x;
+        y.lo = v.y;
+        a.add(y);
+      }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      DF y;
-      y.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
-      y.lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
-      a.add(y);
+      for (int o = 16; o > 0; o >>= 1) {
+        DF y;
+        y.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
+        y.lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
+        a.add(y);
+      }
+      if (lane == 0) accum[7 + wid] = (double)a.hi + (double)a.lo;
     }
-    if (lane == 0) accum[7 + wid] = (double)a.hi + (double)a.lo;
   }
 }
 
@@ -1048,13 +1056,20 @@ cudaError_t launch_bin(bool io_double, bool fp64, const void* pos, const void* q
   return cudaGetLastError();
 }
 
-cudaError_t launch_scan(int* count, int* suboff, int* toff, int ntiles, int ksub,
+cudaError_t launch_scan(int* count, int* suboff, int* toff, int* bsum, int ntiles, int ksub,
                         const void* bin_part, int nbin, double* accum, int* work,
                         cudaStream_t st) {
-  k_scan<<<1, kScanThreads, 0, st>>>(count, suboff, toff, ntiles, ksub,
-                                     (const float2*)bin_part, nbin, accum, work);
+  const int n = ntiles * ksub;
+  const int nb = (n + kScanBlock - 1) / kScanBlock;
+  k_scan_local<<<nb, kThreads, 0, st>>>(count, suboff, bsum, n);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_scan_fix<<<nb, kThreads, 0, st>>>(suboff, toff, bsum, ntiles, ksub, (const float2*)bin_part,
+                                      nbin, accum, work);
   return cudaGetLastError();
 }
+
+int scan_blocks(int ntiles, int ksub) { return (ntiles * ksub + kScanBlock - 1) / kScanBlock; }
 
 int bin_blocks(int64_t n) { return grid_blocks(n); }
 

@@ -16,7 +16,7 @@ constexpr int kDegF64 = 24;
 constexpr int kRadialPieces = 16;
 constexpr int kThreads = 256;
 constexpr int kSub = 8;    // binning sub-counters per tile (spreads same-address atomics)
-constexpr int kMaxScan = 1 << 20;  // most counters the single-CTA scan is sized for
+constexpr int kMaxScan = 1 << 24;  // most binning counters supported
 
 // Geometry shared by the binning, spreading and gathering kernels.
 struct TileGeom {
@@ -112,10 +112,12 @@ cudaError_t launch_bin(bool io_double, bool fp64, const void* pos, const void* q
                        void* tq, void* bin_part, cudaStream_t st);
 int bin_blocks(int64_t n);
 // count: zero on entry (bin adds into it), zero again on exit; work[0..1] zeroed too
-// bin_part: per binning block 3 compensated sums (float pairs)
-cudaError_t launch_scan(int* count, int* suboff, int* toff, int ntiles, int ksub,
+// count: zero on entry (bin adds into it), zero again on exit; work[0..1] zeroed too.
+// bin_part: per binning block 3 compensated sums (float pairs); bsum: scan_blocks() ints.
+cudaError_t launch_scan(int* count, int* suboff, int* toff, int* bsum, int ntiles, int ksub,
                         const void* bin_part, int nbin, double* accum, int* work,
                         cudaStream_t st);
+int scan_blocks(int ntiles, int ksub);
 cudaError_t launch_scatter(bool fp64, int64_t n, int ksub, const int* ptile, const int* prank,
                            const int* plb, const void* tq, const int* offset, void* sorted_tq,
                            int* sorted_lb, int* sorted_idx, cudaStream_t st);
