@@ -168,6 +168,31 @@ int esp_destroy(esp_plan_t plan);
  * NULL).  Valid until the next call on the plan. */
 const char* esp_last_error(esp_plan_t plan);
 
+/*
+ * esp_spread_noalloc - the spreading of eq. (gridding) without any device allocation, for
+ * callers that cannot allocate device memory at this point (code running while a CUDA
+ * graph is being captured by someone else, allocators that forbid cudaMalloc, embedded
+ * runtimes with a fixed memory budget).  There is no counterpart in the paper: it is the
+ * bin/sort and spread kernels of the plan path with their scratch (binning counters,
+ * sorted atoms, the window table) in one static device array of the library, about 5.8 MB
+ * that every GPU which loads the library keeps until the process exits.
+ *   cell, grid, w, c, precision: as for esp_plan (no split radius is needed here).
+ *   n <= ESP_NOALLOC_MAX_ATOMS, and the grid at most ESP_NOALLOC_MAX_TILES tiles of
+ *        8 x 8 x 16 points (8 x 8 x 8 for w > 8); larger inputs return ESP_ERR_ARG.
+ *   pos, q     device arrays (N x 3 and N) of the I/O type; grid_out the caller's device
+ *              array of M1*M2*M3 values of the compute type, overwritten with rho_s.
+ *   stream     cudaStream_t to run on.  Asynchronous; non-finite atoms are skipped.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture.  All calls share the one array, so
+ * calls that overlap on the GPU (other streams, other host threads) race: serialise them.
+ * Errors: ESP_ERR_ARG, ESP_ERR_CELL, ESP_ERR_SUPPORT, ESP_ERR_CUDA (esp_last_error(NULL)).
+ */
+#define ESP_NOALLOC_MAX_ATOMS 65536
+#define ESP_NOALLOC_MAX_TILES 4096
+int esp_spread_noalloc(const double cell[9], int64_t n, const int grid[3], int w, double c,
+                       int precision, const void* pos, const void* q, void* grid_out,
+                       void* stream);
+
 /* PSWF shape parameter c with psi_0^c(1) / psi_0^c(0) = delta (Sec. 5.1 tuning rule,
  * read as a ratio to psi_0(0)), 0 < delta < 1; returns a negative value on bad input. */
 double esp_c_from_tolerance(double delta);

@@ -38,8 +38,11 @@ EXPORTS = (
     "esp_plan", "esp_set_cell", "esp_set_stream", "esp_step", "esp_energy_pressure",
     "esp_forces", "esp_forces_from_spectrum", "esp_compute_host", "esp_result_from_accum",
     "esp_copy_grid", "esp_copy_spectrum", "esp_plan_info", "esp_destroy", "esp_last_error",
-    "esp_c_from_tolerance", "esp_profile", "esp_profile_read",
+    "esp_c_from_tolerance", "esp_profile", "esp_profile_read", "esp_spread_noalloc",
 )
+
+ESP_NOALLOC_MAX_ATOMS = 65536
+ESP_NOALLOC_MAX_TILES = 4096
 
 STAGES = ("memset", "bin", "scan", "scatter", "zero_grid", "spread", "fft_fwd", "scale",
           "fft_inv", "gather")
@@ -104,6 +107,7 @@ def _load():
         "esp_c_from_tolerance": (cd, [cd]),
         "esp_profile": (ci, [vp, ci]),
         "esp_profile_read": (ci, [vp, dptr, ci]),
+        "esp_spread_noalloc": (ci, [dptr, i64, ctypes.POINTER(ci), ci, cd, ci, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -222,6 +226,14 @@ def esp_profile_read(plan) -> dict:
     v = (ctypes.c_double * len(STAGES))()
     _check(_lib.esp_profile_read(plan, v, len(STAGES)), plan)
     return dict(zip(STAGES, list(v)))
+
+
+def esp_spread_noalloc(cell, n, grid, w, c, precision, pos, q, grid_out, stream=None):
+    """Spreading with the library's static scratch (no device allocation); see esp.h."""
+    g = (ctypes.c_int * 3)(*[int(x) for x in grid])
+    _check(_lib.esp_spread_noalloc(_cell_colmajor(cell), int(n), g, int(w), float(c),
+                                   int(precision), _ptr(pos), _ptr(q), _ptr(grid_out),
+                                   ctypes.c_void_p(stream) if stream else None), None)
 
 
 # ---- convenience wrapper over torch tensors ----------------------------------------------

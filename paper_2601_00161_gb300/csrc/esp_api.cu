@@ -10,6 +10,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -852,3 +853,184 @@ const char* esp_last_error(esp_plan_t p) {
 double esp_c_from_tolerance(double delta) { return esp::c_from_tolerance(delta); }
 
 }  // extern "C"
+
+// ---- allocation-free spreading ------------------------------------------------------------
+// Scratch for esp_spread_noalloc: one file-scope device array with fixed offsets.  Host
+// code must not take the array's name as a device address: each device's address comes
+// from cudaGetSymbolAddress, once, with that device current.
+namespace {
+
+constexpr size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct NoAllocLayout {
+  size_t count, suboff, toff, bsum, binpart, acc, ptile, prank, plb, tq, stq, slb, sidx, wtab,
+      total;
+};
+
+constexpr NoAllocLayout noalloc_layout() {
+  const size_t N = ESP_NOALLOC_MAX_ATOMS, T = ESP_NOALLOC_MAX_TILES;
+  const size_t nsub = T * esp::kSub;
+  const size_t nbin = (N + esp::kThreads - 1) / esp::kThreads;
+  NoAllocLayout L{};
+  size_t o = 0;
+  L.count = o;   o = al256(o + sizeof(int) * (nsub + 2));
+  L.suboff = o;  o = al256(o + sizeof(int) * (nsub + 1));
+  L.toff = o;    o = al256(o + sizeof(int) * (T + 1));
+  L.bsum = o;    o = al256(o + sizeof(int) * (nsub / (4 * esp::kThreads) + 1));
+  L.binpart = o; o = al256(o + 3 * 8 * nbin);
+  L.acc = o;     o = al256(o + sizeof(double) * ESP_ACCUM_LEN);
+  L.ptile = o;   o = al256(o + sizeof(int) * N);
+  L.prank = o;   o = al256(o + sizeof(int) * N);
+  L.plb = o;     o = al256(o + sizeof(int) * N);
+  L.tq = o;      o = al256(o + 32 * N);
+  L.stq = o;     o = al256(o + 32 * N);
+  L.slb = o;     o = al256(o + sizeof(int) * N);
+  L.sidx = o;    o = al256(o + sizeof(int) * N);
+  L.wtab = o;    o = al256(o + sizeof(double) * 2 * (esp::kMaxDeg + 1) * esp::kMaxP);
+  L.total = o;
+  return L;
+}
+
+constexpr NoAllocLayout kNoAlloc = noalloc_layout();
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAlloc.total];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_addr[kMaxDevices] = {};
+
+// device address of the scratch array for the current device (set up on first use)
+int noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDevice");
+  if (dev < 0 || dev >= kMaxDevices) return fail(nullptr, ESP_ERR_ARG, "device index out of range");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr) return cuda_fail(nullptr, e, "cudaGetSymbolAddress");
+    g_noalloc_addr[dev] = static_cast<unsigned char*>(ptr);
+  }
+  *out = g_noalloc_addr[dev];
+  return ESP_OK;
+}
+
+}  // namespace
+
+extern "C" int esp_spread_noalloc(const double cell[9], int64_t n, const int grid[3], int w,
+                                  double c, int precision, const void* pos, const void* q,
+                                  void* grid_out, void* stream) {
+  if (!grid || !grid_out) return fail(nullptr, ESP_ERR_ARG, "grid or grid_out is NULL");
+  if (n < 0 || n > ESP_NOALLOC_MAX_ATOMS)
+    return fail(nullptr, ESP_ERR_ARG, "n exceeds ESP_NOALLOC_MAX_ATOMS for esp_spread_noalloc");
+  if (n > 0 && (!pos || !q)) return fail(nullptr, ESP_ERR_ARG, "pos or q is NULL");
+  if (w < esp::kMinP || w > esp::kMaxP)
+    return fail(nullptr, ESP_ERR_ARG, "stencil width w must be in [3, 12]");
+  if (!(c > 0.0) || !std::isfinite(c)) return fail(nullptr, ESP_ERR_ARG, "c must be positive");
+  const int base = precision & 0xf;
+  if (base != ESP_FP64 && base != ESP_FP32) return fail(nullptr, ESP_ERR_ARG, "bad precision");
+  for (int d = 0; d < 3; ++d) {
+    if (grid[d] < 2 || grid[d] > 4096) return fail(nullptr, ESP_ERR_ARG, "grid size out of range");
+    if (w >= grid[d]) return fail(nullptr, ESP_ERR_SUPPORT, "stencil width must be below every M_d");
+  }
+  // host-side set-up in a plan object that owns no device memory
+  esp_plan_s tmp;
+  esp_plan_t p = &tmp;
+  p->fp64 = (base == ESP_FP64);
+  p->io_double = p->fp64 || (precision & ESP_IO_F64);
+  p->n = n;
+  for (int d = 0; d < 3; ++d) p->M[d] = grid[d];
+  p->H2 = grid[2] / 2 + 1;
+  p->P = w;
+  p->c = c;
+  p->stream = (cudaStream_t)stream;
+  auto report = [&](int code) {
+    g_plan_error = p->err;
+    return code;
+  };
+  int rc;
+  if ((rc = set_cell_matrix(p, cell, p->h, p->hinv, &p->V)) != ESP_OK) return report(rc);
+  if (!p->pswf.solve(c)) return report(fail(p, ESP_ERR_ARG, "PSWF eigen-solve failed"));
+  std::vector<double> wtab;
+  if ((rc = build_window_tables(p, wtab)) != ESP_OK) return report(rc);
+  esp::TileGeom& g = p->tg;
+  for (int d = 0; d < 3; ++d) g.M[d] = p->M[d];
+  g.P = w;
+  {
+    int Tc[3], E3p, vol;
+    esp::tile_shape(w, Tc, &E3p, &vol);
+    for (int d = 0; d < 3; ++d) g.T[d] = std::min(Tc[d], p->M[d]);
+    g.E3p = E3p;
+  }
+  p->ntiles = 1;
+  for (int d = 0; d < 3; ++d) {
+    g.nt[d] = (p->M[d] + g.T[d] - 1) / g.T[d];
+    g.E[d] = g.T[d] + w - 1;
+    g.dscale[d] = 2.0 * p->M[d] / w;
+    g.dscalef[d] = (float)g.dscale[d];
+    p->ntiles *= g.nt[d];
+  }
+  if (p->ntiles > ESP_NOALLOC_MAX_TILES)
+    return report(fail(p, ESP_ERR_ARG, "grid exceeds ESP_NOALLOC_MAX_TILES tiles for esp_spread_noalloc"));
+  g.ksub = esp::kSub;
+  g.vec4 = (!p->fp64 && g.T[2] % 4 == 0 && p->M[2] % 4 == 0 && (g.E[2] + 3) / 4 * 4 <= g.E3p) ? 1 : 0;
+  g.div_E1 = (unsigned int)((((unsigned long long)1 << 32) + g.E[1] - 1) / g.E[1]);
+  g.div_E2v = (unsigned int)((((unsigned long long)1 << 32) + (g.E[2] + 3) / 4 - 1) / ((g.E[2] + 3) / 4));
+  g.deg = p->deg;
+  update_cell_constants(p);
+
+  unsigned char* S = nullptr;
+  if ((rc = noalloc_scratch(&S)) != ESP_OK) return rc;
+  int* count = reinterpret_cast<int*>(S + kNoAlloc.count);
+  int* work = count + (size_t)p->ntiles * esp::kSub;
+  int* suboff = reinterpret_cast<int*>(S + kNoAlloc.suboff);
+  int* toff = reinterpret_cast<int*>(S + kNoAlloc.toff);
+  int* bsum = reinterpret_cast<int*>(S + kNoAlloc.bsum);
+  void* binpart = S + kNoAlloc.binpart;
+  double* acc = reinterpret_cast<double*>(S + kNoAlloc.acc);
+  int* ptile = reinterpret_cast<int*>(S + kNoAlloc.ptile);
+  int* prank = reinterpret_cast<int*>(S + kNoAlloc.prank);
+  int* plb = reinterpret_cast<int*>(S + kNoAlloc.plb);
+  void* tq = S + kNoAlloc.tq;
+  void* stq = S + kNoAlloc.stq;
+  int* slb = reinterpret_cast<int*>(S + kNoAlloc.slb);
+  int* sidx = reinterpret_cast<int*>(S + kNoAlloc.sidx);
+  void* dwtab = S + kNoAlloc.wtab;
+
+  cudaStream_t st = p->stream;
+  const size_t es = p->fp64 ? 8 : 4;
+  const size_t Mtot = (size_t)p->M[0] * p->M[1] * p->M[2];
+  // the window table (a pageable source: the copy is staged before the call returns)
+  if (p->fp64) {
+    ESP_CUDA(nullptr, cudaMemcpyAsync(dwtab, wtab.data(), es * wtab.size(), cudaMemcpyHostToDevice, st));
+  } else {
+    std::vector<float> f(wtab.begin(), wtab.end());
+    ESP_CUDA(nullptr, cudaMemcpyAsync(dwtab, f.data(), es * f.size(), cudaMemcpyHostToDevice, st));
+  }
+  // the array keeps the last call's contents: the counters must start at zero
+  ESP_CUDA(nullptr, cudaMemsetAsync(count, 0, sizeof(int) * ((size_t)p->ntiles * esp::kSub + 2), st));
+  ESP_CUDA(nullptr, esp::launch_bin(p->io_double, p->fp64, pos, q, n, g, count, ptile, prank, plb,
+                                    tq, binpart, st));
+  ESP_CUDA(nullptr, esp::launch_scan(count, suboff, toff, bsum, p->ntiles, g.ksub, binpart,
+                                     n > 0 ? esp::bin_blocks(n) : 0, acc, work, st));
+  ESP_CUDA(nullptr, esp::launch_scatter(p->fp64, n, g.ksub, ptile, prank, plb, tq, suboff, stq,
+                                        slb, sidx, st));
+  ESP_CUDA(nullptr, cudaMemsetAsync(grid_out, 0, es * Mtot, st));
+  const size_t ss = esp::spread_smem_bytes(p->fp64, g), gs = esp::gather_smem_bytes(p->fp64, g);
+  if (ss > 227 * 1024 || gs > 227 * 1024)
+    return fail(nullptr, ESP_ERR_ARG, "tile does not fit in shared memory");
+  ESP_CUDA(nullptr, esp::configure_kernels(p->fp64, w, ss, gs));
+  int dev = 0, sms = 152, occ_s = 1, occ_g = 1;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  ESP_CUDA(nullptr, esp::occupancy(p->fp64, p->io_double, w, ss, gs, &occ_s, &occ_g));
+  const int nblocks = std::max(1, std::min(p->ntiles, sms * std::max(occ_s, 1)));
+  ESP_CUDA(nullptr, esp::launch_spread(p->fp64, g, p->ntiles, nblocks, stq, slb, toff, work,
+                                       dwtab, grid_out, st));
+  return ESP_OK;
+}
