@@ -45,6 +45,27 @@ FALLBACK_HBM_GBS = 6800.0
 # of force per atom; scale reads and writes 8 B per half-spectrum mode.
 BYTES_PER_ATOM = {"spread": 16, "gather": 28, "bin": 16, "scatter": 16 + 24}
 BYTES_PER_POINT = {"spread": 4, "gather": 4}
+# FP32 window polynomial degree of the library (Horner, Sec. 4.3)
+WINDOW_DEG_F32 = 13
+# GB300: 152 SMs, 128 FP32 lanes per SM (one FMA = 2 FLOP per lane and clock); one shared
+# memory wavefront (32 lanes of 4 B) per SM and clock
+SMS, FP32_LANES = 152, 128
+
+
+def algorithmic_ops(kernel: str, P: int):
+    """(FLOP, shared-memory accumulations) per atom of spread / gather (FP32 path).
+
+    spread: 3P window values by Horner (2 FLOP per degree), the P^2 products q w1 w2, and
+    P^3 products w0 (q w1 w2) accumulated into the tile (P^3 adds).
+    gather: 3P values and 3P derivatives by Horner, then for each of the P^3 points the
+    potential times three products (w0' w1 w2, w0 w1' w2, w0 w1 w2'), about 8 FLOP.
+    """
+    d = WINDOW_DEG_F32
+    if kernel == "spread":
+        return 3 * P * 2 * d + 2 * P * P + 2 * P ** 3, P ** 3
+    if kernel == "gather":
+        return 6 * P * 2 * d + 8 * P ** 3, 0
+    return None, None
 
 
 def parse_args(argv=None):
@@ -265,6 +286,27 @@ def esp_arm(args):
                 "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": recorded_traffic(dom),
                 "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.8 TB/s",
                 "algorithmic_bytes": alg, "avg_ms": round(avg[dom], 5)}
+    # the same kernels against the FP32 FMA and shared-memory accumulation ceilings (nominal
+    # unit counts at the sampled SM clock), and cuFFT against the HBM copy bandwidth
+    sm_hz = 1e6 * (clk.get("sm_mhz") or 2070.0)
+    other = {}
+    for kern in ("spread", "gather"):
+        flop, red = algorithmic_ops(kern, S.P)
+        t = avg[kern] * 1e-3
+        fp32_peak = SMS * FP32_LANES * 2 * sm_hz
+        other[kern] = {"ms": round(avg[kern], 5),
+                       "fp32_tflops": round(flop * S.n / t / 1e12, 3),
+                       "fp32_frac": round(flop * S.n / t / fp32_peak, 4)}
+        if red:
+            red_peak = SMS * 32 * sm_hz
+            other[kern]["smem_red_per_s"] = round(red * S.n / t, 1)
+            other[kern]["smem_red_frac"] = round(red * S.n / t / red_peak, 4)
+    H = S.grid[0] * S.grid[1] * (S.grid[2] // 2 + 1)
+    fft_bytes = (4 if not fp64 else 8) * Mtot + (8 if not fp64 else 16) * H
+    for kern in ("fft_fwd", "fft_inv"):
+        gbs = fft_bytes / (avg[kern] * 1e-3) / 1e9
+        other[kern] = {"ms": round(avg[kern], 5), "bytes": fft_bytes,
+                       "achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / peak, 4)}
 
     # end to end through the public C ABI with host buffers (H2D + step + D2H every step)
     npdt = np.float64 if fp64 else np.float32
@@ -304,6 +346,25 @@ def esp_arm(args):
         fp64_value = round(1e3 * n64 / tot, 2)
         p64.close()
 
+    # energy and pressure only (no inverse FFT, no gather: Sec. 4.1), on a plan of its own
+    pe = esp.Plan(S.cell, S.n, S.grid, S.P, c, S.rc, precision=args.precision,
+                  stream=stream.cuda_stream)
+    for _ in range(max(3, args.warmup)):
+        esp.esp_step(pe.handle, pos, q, None, acc)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tot = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0.record(stream)
+        esp.esp_step(pe.handle, pos, q, None, acc)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    pe.close()
+    energy_pressure = {"value": round(1e3 * args.steps / tot, 2), "unit": "steps/s",
+                       "ms_per_step": round(tot / args.steps, 5),
+                       "step": "bin/sort, spread, forward FFT, scaling + energy/virial reduction"}
+
     launches_per_step = 7  # bin, scan (2), scatter, spread, scale, gather
     out = None
     if rank == 0:
@@ -322,6 +383,8 @@ def esp_arm(args):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "stage_ms": {k: round(v, 5) for k, v in avg.items()},
             "roofline": roofline,
+            "other_bounds": other,
+            "energy_pressure_only": energy_pressure,
             "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,
