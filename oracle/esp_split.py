@@ -59,7 +59,8 @@ def fourier_kernel(k2, c, rc):
     return Fhat, dterm
 
 
-def esp_split(pos, q, h, c, rc, truncate=True, kmax=None, forces=True, near=True):
+def esp_split(pos, q, h, c, rc, truncate=True, kmax=None, forces=True, near=True, far=True,
+              cell_list=False):
     h = lattice.check_cell(h)
     pos = np.asarray(pos, dtype=np.float64)
     q = np.asarray(q, dtype=np.float64)
@@ -73,7 +74,8 @@ def esp_split(pos, q, h, c, rc, truncate=True, kmax=None, forces=True, near=True
     W_N = np.zeros((3, 3))
     F_N = np.zeros((N, 3))
     if near:
-        for i, j, rv, r in lattice.pair_images(pos, h, rc):
+        pairs = lattice.pair_cells if cell_list else lattice.pair_images
+        for i, j, rv, r in pairs(pos, h, rc):
             qq = q[i] * q[j]
             u = r / rc
             phi0 = p.int_psi(u) / p.C0
@@ -85,23 +87,27 @@ def esp_split(pos, q, h, c, rc, truncate=True, kmax=None, forces=True, near=True
                 np.add.at(F_N, i, f[:, None] * rv)
 
     # -- far field -------------------------------------------------------------------
-    K = c / rc
-    m, k, wt = lattice.kvectors(h, K if truncate else (kmax or 2.0 * K), half=True)
-    k2 = np.einsum("ij,ij->i", k, k)
-    Fhat, dterm = fourier_kernel(k2, c, rc)
-    S = lattice.structure_factor(k, pos, q)
-    a = wt * np.abs(S) ** 2 / (2.0 * V)
-    U_F = float(np.sum(a * Fhat))
-    W_F = np.sum(a * Fhat) * np.eye(3) + np.einsum("p,pa,pb->ab", a * (dterm - 2.0 * Fhat / k2), k, k)
-    F_F = np.zeros((N, 3))
-    if forces:
-        for s0 in range(0, len(k), 2048):
-            kk = k[s0:s0 + 2048]
-            ph = np.exp(1j * (pos @ kk.T))
-            im = np.imag(np.conj(S[s0:s0 + 2048])[None, :] * ph)
-            F_F += (q / V)[:, None] * ((im * (wt[s0:s0 + 2048] * Fhat[s0:s0 + 2048])[None, :]) @ kk)
-    # the ξ-defect of eq. (UFS): U_F - tr W_F = -sum a A x psi0'(x) / k^2
-    defect_F = -float(np.sum(a * dterm * k2))
+    U_F, W_F, F_F, defect_F, n_modes = 0.0, np.zeros((3, 3)), np.zeros((N, 3)), 0.0, 0
+    if far:
+        K = c / rc
+        m, k, wt = lattice.kvectors(h, K if truncate else (kmax or 2.0 * K), half=True)
+        k2 = np.einsum("ij,ij->i", k, k)
+        Fhat, dterm = fourier_kernel(k2, c, rc)
+        S = lattice.structure_factor(k, pos, q)
+        a = wt * np.abs(S) ** 2 / (2.0 * V)
+        U_F = float(np.sum(a * Fhat))
+        W_F = np.sum(a * Fhat) * np.eye(3) + np.einsum("p,pa,pb->ab", a * (dterm - 2.0 * Fhat / k2), k, k)
+        F_F = np.zeros((N, 3))
+        if forces:
+            for s0 in range(0, len(k), 2048):
+                kk = k[s0:s0 + 2048]
+                ph = np.exp(1j * (pos @ kk.T))
+                im = np.imag(np.conj(S[s0:s0 + 2048])[None, :] * ph)
+                F_F += (q / V)[:, None] * ((im * (wt[s0:s0 + 2048] * Fhat[s0:s0 + 2048])[None, :]) @ kk)
+        # the ξ-defect of eq. (UFS): U_F - tr W_F = -sum a A x psi0'(x) / k^2
+        defect_F = -float(np.sum(a * dterm * k2))
+
+        n_modes = len(k)
 
     U_self = -p.psi_at_0 / (2.0 * p.C0 * rc) * float(np.sum(q * q))
     Q = float(np.sum(q))
@@ -115,6 +121,6 @@ def esp_split(pos, q, h, c, rc, truncate=True, kmax=None, forces=True, near=True
         pressure=(W_N + W_F + W_bg) / V,
         forces_near=F_N if forces else None, forces_far=F_F if forces else None,
         forces=(F_N + F_F) if forces else None,
-        defect_far=defect_F, n_modes=len(k),
+        defect_far=defect_F, n_modes=n_modes,
     )
     return out

@@ -94,3 +94,53 @@ def pair_images(pos, h, rcut: float, rows=None, chunk: int = 64):
             bi, bj = np.nonzero(mask)
             if len(bi):
                 yield ii[bi], bj, rv[bi, bj], np.sqrt(r2[bi, bj])
+
+
+def pair_cells(pos, h, rcut: float, rows=None):
+    """The pairs of ``pair_images`` (each ordered (i, j, image) once, same rvec) found
+    through a cell list, for systems too large for the all-pairs loop.
+
+    The cell is cut into n_d = floor(width_d / rcut) slabs along each reduced axis, so a
+    slab is at least rcut thick and two atoms closer than rcut lie in neighbouring bins
+    (index difference -1, 0 or +1 per axis, with the periodic image given by the wrap of
+    the index).  With n_d >= 3 the 27 neighbour bins of a bin are distinct, so no pair is
+    visited twice; smaller cells fall back to ``pair_images``.
+    """
+    h = check_cell(h)
+    wd = widths(h)
+    nc = np.array([int(wd[d] // rcut) for d in range(3)])
+    if np.any(nc < 3):
+        yield from pair_images(pos, h, rcut, rows=rows)
+        return
+    s = reduced(pos, h)
+    N = len(s)
+    b = np.minimum((s * nc).astype(np.int64), nc - 1)
+    bid = (b[:, 0] * nc[1] + b[:, 1]) * nc[2] + b[:, 2]
+    order = np.argsort(bid, kind="stable")
+    start = np.concatenate([[0], np.cumsum(np.bincount(bid, minlength=int(np.prod(nc))))])
+    want = np.ones(N, dtype=bool) if rows is None else np.isin(np.arange(N), np.asarray(rows))
+    offsets = np.array(list(itertools.product((-1, 0, 1), repeat=3)))
+    r2max = rcut * rcut
+    for b0 in range(nc[0]):
+        for b1 in range(nc[1]):
+            for b2 in range(nc[2]):
+                home = (b0 * nc[1] + b1) * nc[2] + b2
+                ii = order[start[home]:start[home + 1]]
+                ii = ii[want[ii]]
+                if len(ii) == 0:
+                    continue
+                nb = np.array([b0, b1, b2]) + offsets  # unwrapped neighbour bins
+                shift = np.floor_divide(nb, nc)         # image of the neighbour bin
+                nbw = nb - shift * nc
+                nid = (nbw[:, 0] * nc[1] + nbw[:, 1]) * nc[2] + nbw[:, 2]
+                jj = np.concatenate([order[start[x]:start[x + 1]] for x in nid])
+                sh = np.concatenate([np.repeat(shift[o:o + 1], start[nid[o] + 1] - start[nid[o]], axis=0)
+                                     for o in range(27)]).astype(np.float64)
+                # rvec = r_i - (r_j + h shift) = h (s_i - s_j - shift)
+                d = s[ii, None, :] - (s[None, jj, :] + sh[None, :, :])
+                rv = d @ h.T
+                r2 = np.einsum("ijk,ijk->ij", rv, rv)
+                mask = (r2 <= r2max) & (r2 > 0.0)
+                bi, bj = np.nonzero(mask)
+                if len(bi):
+                    yield ii[bi], jj[bj], rv[bi, bj], np.sqrt(r2[bi, bj])
