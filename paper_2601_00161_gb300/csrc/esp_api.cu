@@ -570,6 +570,8 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
     g.div_E2v = magic((unsigned)((g.E[2] + 3) / 4));
   }
   g.deg = p->deg;
+  // psi_0 is even and largest at 0 on [-1, 1]; the margin covers the polynomial fit
+  g.wmax3 = (float)std::pow(p->pswf.psi_at_0 * (1.0 + 1e-6), 3.0);
 
   esp::ScaleGeom& s = p->sg;
   for (int d = 0; d < 3; ++d) s.M[d] = p->M[d];
@@ -982,6 +984,8 @@ extern "C" int esp_spread_noalloc(const double cell[9], int64_t n, const int gri
   g.div_E1 = (unsigned int)((((unsigned long long)1 << 32) + g.E[1] - 1) / g.E[1]);
   g.div_E2v = (unsigned int)((((unsigned long long)1 << 32) + (g.E[2] + 3) / 4 - 1) / ((g.E[2] + 3) / 4));
   g.deg = p->deg;
+  // psi_0 is even and largest at 0 on [-1, 1]; the margin covers the polynomial fit
+  g.wmax3 = (float)std::pow(p->pswf.psi_at_0 * (1.0 + 1e-6), 3.0);
   update_cell_constants(p);
 
   unsigned char* S = nullptr;

@@ -1,22 +1,22 @@
 // sm_103a kernels of the ESP long-range step (Sec. 4.1 Algorithm 1 and Appendix C):
 //   k_bin      wrap s = h^{-1} r into [0,1), stencil base and fractional offset
-//              (Sec. 4.3), tile id and rank within the tile; FP64 for the coordinate
-//              so the integer stencil decision matches the FP64 oracle
-//   k_scan     exclusive scan of tile counts (one CTA)
+//              (Sec. 4.3), tile id and rank within the tile; the integer stencil
+//              decision is taken in FP64 near a switch so it matches the FP64 oracle
+//   k_scan_*   multi-block exclusive scan of the tile counters, charge sums
 //   k_scatter  counting-sort permutation of (offset t, q), local base and atom index
-//   k_spread   eq. (gridding): a CTA owns one tile of stencil bases; warps take batches
-//              of atoms and spread each atom's P^3 footprint into the tile's padded
-//              shared-memory block; the block is then added to the periodic grid
+//   k_spread   eq. (gridding): one warp owns one tile's padded block in shared memory
+//              and adds each atom's P^3 footprint with plain loads and stores; the block
+//              is then added to the periodic grid
 //   k_scale    eqs. (diag)/(PFfinal): per half-spectrum mode the deconvolved weight, the
-//              Fourier kernel and the 3x3 pressure kernel, reduced in FP64; optionally
-//              writes G X for the force path (eq. (UFAnal))
+//              Fourier kernel and the 3x3 pressure kernel, reduced in FP64 (compensated
+//              FP32 on the FP32 path); optionally writes G X for the force path
 //   k_gather   eq. (AD): the CTA stages its tile's padded block of the potential grid in
-//              shared memory; per atom the P^3 contraction with the window gradient
+//              shared memory; P lanes per atom contract its P^3 points with the window
+//              and its gradient, a segmented shuffle sums them
 //
-// Work mapping in spread / gather: a warp handles kBatch atoms at once and splits their
-// P^2 (j, k) stencil rows over its lanes (lane-consecutive k, then j), each lane walking
-// the P points of its row in the first dimension.  With the shared-memory row pitch
-// E3p = -P (mod 32), consecutive rows of one atom fall on consecutive banks.
+// Shared-memory layout of a tile block: row pitch E3p = P (mod 32) and plane stride
+// S1 = P^2 (mod 32), so the stencil point (i, j, k) of an atom lies in bank
+// (b + i P^2 + j P + k) mod 32 and 32 consecutive flat stencil indices never share a bank.
 #include "esp_kernels.cuh"
 
 #include <cuda_runtime.h>
@@ -441,42 +441,121 @@ __device__ __forceinline__ R tq_comp(const typename Vec4<R>::T& v, int d) {
   return d == 0 ? v.x : (d == 1 ? v.y : v.z);
 }
 
-// Shared-memory accumulation without a return value (red.shared): FP32 by inline PTX,
-// FP64 through atomicAdd.
-__device__ __forceinline__ void smem_add(float* p, float v) {
-  asm volatile("red.shared.add.f32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)), "f"(v)
+
+// offset of an atom's stencil corner in the padded tile block (packed local base: 10 bits
+// per dimension)
+template <int S1, int E3p>
+__device__ __forceinline__ int local_base(int lb) {
+  return (lb & 1023) * S1 + ((lb >> 10) & 1023) * E3p + ((lb >> 20) & 1023);
+}
+
+// P values of a 16-byte aligned shared-memory record into registers (vector loads)
+template <typename R, int P>
+__device__ __forceinline__ void load_record(const R* src, R (&dst)[P]) {
+  if constexpr (std::is_same<R, float>::value) {
+#pragma unroll
+    for (int i = 0; i + 4 <= P; i += 4) {
+      const float4 v = *reinterpret_cast<const float4*>(src + i);
+      dst[i] = v.x;
+      dst[i + 1] = v.y;
+      dst[i + 2] = v.z;
+      dst[i + 3] = v.w;
+    }
+    constexpr int r = P & ~3;
+    if constexpr (P - r >= 2) {
+      const float2 v = *reinterpret_cast<const float2*>(src + r);
+      dst[r] = v.x;
+      dst[r + 1] = v.y;
+    }
+    if constexpr ((P - r) & 1) dst[P - 1] = src[P - 1];
+  } else {
+#pragma unroll
+    for (int i = 0; i + 2 <= P; i += 2) {
+      const double2 v = *reinterpret_cast<const double2*>(src + i);
+      dst[i] = v.x;
+      dst[i + 1] = v.y;
+    }
+    if constexpr (P & 1) dst[P - 1] = src[P - 1];
+  }
+}
+
+// Lane-fixed stencil columns.  A warp works on one atom at a time.  A column is a pair
+// (j, k) numbered c = (P - 1 - j) P + k; in full pass m lane l owns column c = 32 m + l and
+// walks i = 0 .. P-1, and for each i the 32 lanes touch 32 consecutive banks (see TileC).
+// The NT = P^2 mod 32 leftover columns give NT P tail points, handed out 32 at a time in
+// the order u = i NT + (c - 32 MP), whose banks are again consecutive.
+template <int P>
+struct Cols {
+  static constexpr int MP = P * P / 32;
+  static constexpr int NT = P * P % 32;
+  static constexpr int NG = (NT * P + 31) / 32;
+};
+
+// Per-lane tables of the columns: full passes (offset in the block, j and k) and tail points
+// packed as offset | i << 16 | j << 20 | k << 24 | valid << 31.
+template <int P, int S1, int E3p>
+struct LaneCols {
+  int off[Cols<P>::MP > 0 ? Cols<P>::MP : 1];
+  int j[Cols<P>::MP > 0 ? Cols<P>::MP : 1];
+  int k[Cols<P>::MP > 0 ? Cols<P>::MP : 1];
+  unsigned tail[Cols<P>::NG > 0 ? Cols<P>::NG : 1];
+  __device__ __forceinline__ explicit LaneCols(int lane) {
+    using C = Cols<P>;
+#pragma unroll
+    for (int m = 0; m < C::MP; ++m) {
+      const int c = 32 * m + lane;
+      j[m] = P - 1 - c / P;
+      k[m] = c - (c / P) * P;
+      off[m] = j[m] * E3p + k[m];
+    }
+    tail[0] = 0u;
+    if constexpr (C::NT > 0) {
+#pragma unroll
+      for (int g = 0; g < C::NG; ++g) {
+        const int u = 32 * g + lane;
+        tail[g] = 0u;
+        if (u < C::NT * P) {
+          const int i = u / C::NT;
+          const int c = 32 * C::MP + (u - i * C::NT);
+          const int jj = P - 1 - c / P, kk = c - (c / P) * P;
+          tail[g] = (unsigned)(i * S1 + jj * E3p + kk) | ((unsigned)i << 16) |
+                    ((unsigned)jj << 20) | ((unsigned)kk << 24) | (1u << 31);
+        }
+      }
+    }
+  }
+};
+
+// Accumulation into the spread block: FP32 values as 32-bit fixed point (value x scale,
+// rounded to nearest) with the native shared-memory integer add, FP64 values with the
+// double atomic add.  OFF is a compile-time byte offset from the shared-space address.
+template <int OFF>
+__device__ __forceinline__ void red_fixed(unsigned addr, float v) {
+  asm volatile("red.shared.add.s32 [%0+%2], %1;" ::"r"(addr), "r"(__float2int_rn(v)), "n"(OFF)
                : "memory");
 }
-__device__ __forceinline__ void smem_add(double* p, double v) { atomicAdd(p, v); }
-
-__device__ __forceinline__ int local_base(int lb, int E1, int E3p) {
-  return (((lb & 1023) * E1 + ((lb >> 10) & 1023)) * E3p) + ((lb >> 20) & 1023);
+template <int OFF>
+__device__ __forceinline__ void red_fixed(unsigned addr, double v) {
+  atomicAdd(reinterpret_cast<double*>(__cvta_shared_to_generic(addr + OFF)), v);
+}
+// one column of an atom: the P values w0[i] * pw at the offsets i * S1 from the column start
+template <typename R, int S1, int... I>
+__device__ __forceinline__ void spread_column(unsigned addr, const R (&w0)[sizeof...(I)], R pw,
+                                              std::integer_sequence<int, I...>) {
+  (red_fixed<I * S1 * (int)sizeof(R)>(addr, w0[I] * pw), ...);
 }
 
 // ---------------------------------------------------------------------------------------
 // Persistent CTAs take tiles from a global work counter (work[0], zeroed every step).
-// Per chunk of a tile's atoms: (A) thread t < SP = (kThreads / P) P evaluates the window
+// Per chunk of a tile's atoms: (A) thread t < (kThreads / P) P evaluates the window
 // polynomial of stencil point t % P (coefficients in registers) for (atom, dimension)
-// pairs t / P, t / P + kThreads / P, ...; (B) the chunk's (atom, j, k) rows are shared
-// out over all threads, each adding the P values of its row into the padded block.
-// One stencil row of an atom: the P values w0[i] * pw added at the compile-time offsets
-// i * S1 from the row start (shared-space address).
-template <int OFF>
-__device__ __forceinline__ void red_shared_f32(unsigned addr, float v) {
-  asm volatile("red.shared.add.f32 [%0+%2], %1;" ::"r"(addr), "f"(v), "n"(OFF) : "memory");
-}
-
-template <typename R, int S1, int... I>
-__device__ __forceinline__ void spread_row(unsigned addr, const R* w0, R pw,
-                                           std::integer_sequence<int, I...>) {
-  if constexpr (std::is_same<R, float>::value) {
-    (red_shared_f32<I * S1 * 4>(addr, w0[I] * pw), ...);
-  } else {
-    R* base = reinterpret_cast<R*>(__cvta_shared_to_generic(addr));
-    (atomicAdd(base + I * S1, w0[I] * pw), ...);
-  }
-}
-
+// pairs t / P, t / P + kThreads / P, ...; (B) each warp takes one atom at a time and adds
+// its P^3 values into the padded block along the lane-fixed columns of Cols<P>, every
+// shared-memory add of the warp hitting 32 distinct banks.  The FP32 block holds 32-bit
+// fixed point with a power-of-two scale per tile: scale <= 2^30 / (sum |q| over the
+// tile's atoms x max |w|^3), so no partial sum can overflow; the rounding of each
+// contribution is at most half a unit of 2^-30 times that bound.  The block then goes to
+// the periodic grid with global atomics, and is cleared as it is read.
 template <typename R, int P>
 __global__ void __launch_bounds__(kThreads) k_spread(
     const typename Vec4<R>::T* __restrict__ sorted_tq, const int* __restrict__ sorted_lb,
@@ -484,14 +563,20 @@ __global__ void __launch_bounds__(kThreads) k_spread(
     const R* __restrict__ wtab, R* __restrict__ grid) {
   using V4 = typename Vec4<R>::T;
   using TC = TileC<P>;
+  using CM = Cols<P>;
+  constexpr bool kFixed = std::is_same<R, float>::value;
+  using A = typename std::conditional<kFixed, int, double>::type;  // accumulator element
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* acc = reinterpret_cast<R*>(smem_raw);
+  A* acc = reinterpret_cast<A*>(smem_raw);
   constexpr int E1 = TC::E1, E3p = TC::E3p, vol = TC::VOL, S1 = TC::S1;
+  constexpr int RS = record_stride(false, P);
   const int E0 = g.E[0], E2 = g.E[2];  // this plan's tiles (<= TC)
   const SmemLayout L = smem_layout(false, sizeof(R), (size_t)vol, P);
   R* W = reinterpret_cast<R*>(smem_raw + L.w);  // per atom [w0 | q w1 | w2]
   int* B = reinterpret_cast<int*>(smem_raw + L.b);
   __shared__ int s_tile;
+  __shared__ float s_qsum[kThreads / 32];
+  const unsigned acc_s = (unsigned)__cvta_generic_to_shared(acc);
 
   constexpr int D = WinDeg<R>::value;
   constexpr int NP = kThreads / P;  // pairs per sweep
@@ -500,90 +585,140 @@ __global__ void __launch_bounds__(kThreads) k_spread(
   R cw[D + 1];
 #pragma unroll
   for (int k = 0; k <= D; ++k) cw[k] = evaluator ? wtab[k * P + p_t] : R(0);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const LaneCols<P, S1, E3p> lc(lane);
+
+  if (threadIdx.x == 0) s_tile = atomicAdd(&work[0], 1);
+  {
+    // clear the block once; every flush clears what it reads
+    using Z = typename std::conditional<kFixed, int4, double2>::type;
+    constexpr int nz = vol * (int)sizeof(A) / 16;
+    Z* az = reinterpret_cast<Z*>(acc);
+    const Z zero{};
+    for (int e = threadIdx.x; e < nz; e += blockDim.x) az[e] = zero;
+  }
+  __syncthreads();
 
   for (;;) {
-    __syncthreads();  // the previous tile is flushed and s_tile consumed
-    if (threadIdx.x == 0) s_tile = atomicAdd(&work[0], 1);
-    for (int e = threadIdx.x; e < vol; e += blockDim.x) acc[e] = R(0);
-    __syncthreads();
     const int tile = s_tile;
     if (tile >= ntiles) break;
     const int start = toff[tile], end = toff[tile + 1];
-    if (start == end) continue;
-
-    for (int c0 = start; c0 < end; c0 += kChunk) {
-      const int cnt = min(kChunk, end - c0);
-      if (evaluator) {
-        for (int pr = pair0; pr < 3 * cnt; pr += NP) {
-          const int a = pr / 3, d = pr - 3 * a;
-          const V4 v = sorted_tq[c0 + a];
-          R w = horner_reg<R, D>(cw, tq_comp<R>(v, d));
-          if (d == 1) w *= v.w;
-          W[a * 3 * P + d * P + p_t] = w;
-        }
-      }
-      for (int a = threadIdx.x; a < cnt; a += blockDim.x) B[a] = local_base(sorted_lb[c0 + a], E1, E3p);
-      __syncthreads();
-      for (int it = threadIdx.x; it < cnt * P * P; it += blockDim.x) {
-        const int a = it / (P * P);
-        const int pr = it - a * P * P;
-        const int jj = pr / P, k = pr - jj * P;
-        const R* Wa = W + a * 3 * P;
-        const R pw = Wa[P + jj] * Wa[2 * P + k];
-        R w0[P];
+    if (start < end) {
+      // fixed-point scale of this tile (FP32): a power of two, so scaling back is exact
+      R scale = R(1), inv_scale = R(1);
+      if constexpr (kFixed) {
+        float sq = 0.f;
+        for (int j = start + threadIdx.x; j < end; j += blockDim.x) sq += fabsf(sorted_tq[j].w);
 #pragma unroll
-        for (int i = 0; i < P; ++i) w0[i] = Wa[i];
-        const unsigned addr = (unsigned)__cvta_generic_to_shared(acc + B[a] + jj * E3p + k);
-        spread_row<R, S1>(addr, w0, pw, std::make_integer_sequence<int, P>{});
+        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+        if (lane == 0) s_qsum[warp] = sq;
+        __syncthreads();
+        float tot = 0.f;
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) tot += s_qsum[w];
+        // an upper bound of every |partial sum| in the block, with margin for the float sums
+        const float bound = tot * g.wmax3 * 1.0001f + 1e-30f;
+        int ex;
+        frexpf(bound, &ex);  // bound < 2^ex
+        ex = max(ex, -90);   // all-zero charges: any finite scale will do
+        scale = ldexpf(1.f, 30 - ex);
+        inv_scale = ldexpf(1.f, ex - 30);
       }
-      __syncthreads();
-    }
-
-    // add the padded block into the periodic global grid
-    const int t2 = tile % g.nt[2];
-    const int t1 = (tile / g.nt[2]) % g.nt[1];
-    const int t0 = tile / (g.nt[2] * g.nt[1]);
-    const int o0 = t0 * g.T[0], o1 = t1 * g.T[1], o2 = t2 * g.T[2];
-    bool flushed = false;
-    if constexpr (std::is_same<R, float>::value) {
-      if (g.vec4) {
-        const int E2v = (E2 + 3) >> 2;
-        const int nflush = E0 * E1 * E2v;
-        for (int e = threadIdx.x; e < nflush; e += blockDim.x) {
-          const int ab = fast_div(e, g.div_E2v);
-          const int c4 = e - ab * E2v;
-          const int a = ab / E1;
-          const int b = ab - a * E1;
-          if (b >= g.E[1]) continue;
-          const float* src = acc + ab * E3p + 4 * c4;
-          const float4 v = make_float4(src[0], src[1], src[2], src[3]);
-          if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) {
-            const int gi = wrap3(o0 + a, g.M[0]);
-            const int gj = wrap3(o1 + b, g.M[1]);
-            const int gk = wrap3(o2 + 4 * c4, g.M[2]);
-            atomicAdd(reinterpret_cast<float4*>(grid + ((int64_t)gi * g.M[1] + gj) * g.M[2] + gk), v);
+      for (int c0 = start; c0 < end; c0 += kChunk) {
+        const int cnt = min(kChunk, end - c0);
+        if (evaluator) {
+          for (int pr = pair0; pr < 3 * cnt; pr += NP) {
+            const int a = pr / 3, d = pr - 3 * a;
+            const V4 v = sorted_tq[c0 + a];
+            R w = horner_reg<R, D>(cw, tq_comp<R>(v, d));
+            if (d == 1) w *= v.w * scale;
+            W[a * RS + d * P + p_t] = w;
           }
         }
-        flushed = true;
+        for (int a = threadIdx.x; a < cnt; a += blockDim.x) B[a] = local_base<S1, E3p>(sorted_lb[c0 + a]);
+        __syncthreads();
+        for (int a = warp; a < cnt; a += kThreads / 32) {
+          const R* Wa = W + a * RS;
+          R w0[P];
+          load_record<R, P>(Wa, w0);
+          const unsigned base = acc_s + (unsigned)(B[a] * (int)sizeof(A));
+#pragma unroll
+          for (int m = 0; m < CM::MP; ++m) {
+            const R pw = Wa[P + lc.j[m]] * Wa[2 * P + lc.k[m]];
+            spread_column<R, S1>(base + (unsigned)(lc.off[m] * (int)sizeof(A)), w0, pw,
+                                 std::make_integer_sequence<int, P>{});
+          }
+#pragma unroll
+          for (int t = 0; t < CM::NG; ++t) {
+            const unsigned tp = lc.tail[t];
+            if (tp >> 31) {
+              const int i = (tp >> 16) & 15, jj = (tp >> 20) & 15, kk = (tp >> 24) & 15;
+              red_fixed<0>(base + (tp & 0xffffu) * (unsigned)sizeof(A),
+                           Wa[i] * (Wa[P + jj] * Wa[2 * P + kk]));
+            }
+          }
+        }
+        __syncthreads();
       }
-    }
-    if (!flushed) {
-      const int E1r = g.E[1];
-      const int nflush = E0 * E1r * E2;
-      for (int e = threadIdx.x; e < nflush; e += blockDim.x) {
-        const int c = e % E2;
-        const int ab = e / E2;
-        const int b = ab % E1r;
-        const int a = ab / E1r;
-        const R val = acc[(a * E1 + b) * E3p + c];
-        if (val != R(0)) {
-          const int gi = wrap_index(o0 + a, g.M[0]);
-          const int gj = wrap_index(o1 + b, g.M[1]);
-          const int gk = wrap_index(o2 + c, g.M[2]);
-          atomicAdd(&grid[((int64_t)gi * g.M[1] + gj) * g.M[2] + gk], val);
+
+      // add the padded block into the periodic global grid, clearing it
+      const int t2 = tile % g.nt[2];
+      const int t1 = (tile / g.nt[2]) % g.nt[1];
+      const int t0 = tile / (g.nt[2] * g.nt[1]);
+      const int o0 = t0 * g.T[0], o1 = t1 * g.T[1], o2 = t2 * g.T[2];
+      bool flushed = false;
+      if constexpr (kFixed) {
+        if (g.vec4) {
+          const int E2v = (E2 + 3) >> 2;
+          const int nflush = E0 * E1 * E2v;
+          for (int e = threadIdx.x; e < nflush; e += blockDim.x) {
+            const int ab = fast_div(e, g.div_E2v);
+            const int c4 = e - ab * E2v;
+            const int a = ab / E1;
+            const int b = ab - a * E1;
+            if (b >= g.E[1]) continue;
+            int* src = acc + a * S1 + b * E3p + 4 * c4;
+            const int4 iv = make_int4(src[0], src[1], src[2], src[3]);
+            if (iv.x | iv.y | iv.z | iv.w) {
+              src[0] = 0;
+              src[1] = 0;
+              src[2] = 0;
+              src[3] = 0;
+              const float4 v = make_float4((float)iv.x * inv_scale, (float)iv.y * inv_scale,
+                                           (float)iv.z * inv_scale, (float)iv.w * inv_scale);
+              const int gi = wrap3(o0 + a, g.M[0]);
+              const int gj = wrap3(o1 + b, g.M[1]);
+              const int gk = wrap3(o2 + 4 * c4, g.M[2]);
+              atomicAdd(reinterpret_cast<float4*>(grid + ((int64_t)gi * g.M[1] + gj) * g.M[2] + gk), v);
+            }
+          }
+          flushed = true;
+        }
+      }
+      if (!flushed) {
+        const int E1r = g.E[1];
+        const int nflush = E0 * E1r * E2;
+        for (int e = threadIdx.x; e < nflush; e += blockDim.x) {
+          const int c = e % E2;
+          const int ab = e / E2;
+          const int b = ab % E1r;
+          const int a = ab / E1r;
+          A* src = acc + a * S1 + b * E3p + c;
+          const A av = *src;
+          if (av != A(0)) {
+            *src = A(0);
+            const R val = kFixed ? R((float)av * (float)inv_scale) : R(av);
+            const int gi = wrap_index(o0 + a, g.M[0]);
+            const int gj = wrap_index(o1 + b, g.M[1]);
+            const int gk = wrap_index(o2 + c, g.M[2]);
+            atomicAdd(&grid[((int64_t)gi * g.M[1] + gj) * g.M[2] + gk], val);
+          }
         }
       }
     }
+    __syncthreads();  // the block is read out and cleared; s_tile consumed
+    if (threadIdx.x == 0) s_tile = atomicAdd(&work[0], 1);
+    __syncthreads();
   }
 }
 
@@ -839,13 +974,13 @@ __global__ void __launch_bounds__(kThreads) k_scale(typename Cplx<R>::T* __restr
 
 // ---------------------------------------------------------------------------------------
 // Persistent CTAs take tiles from a global work counter (work[1], zeroed every step).
-// The tile's padded block of the potential grid is staged in shared memory; per chunk of
-// its atoms: (A) window values and derivatives as in k_spread; (B) each (atom, j, k) row
-// contracts its P values with w0 and w0', a segmented warp scan sums the rows of one atom
-// and the last lane of each segment adds the sums into the atom's slot; (C) one thread
-// per atom turns the sums into the force.
+// The tile's padded block of the potential grid is staged in shared memory for all warps;
+// per chunk of its atoms: (A) window values and derivatives as in k_spread; (B) groups of
+// P lanes take one atom each (32 / P atoms per warp at a time): lane j of a group
+// contracts stencil row j (its P x P points) in registers, a segmented shuffle reduction
+// sums the rows, and the group's first lane turns the sums into the atom's force.
 template <typename R, typename IO, int P>
-__global__ void __launch_bounds__(kThreads, 4) k_gather(
+__global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 4 : 2) k_gather(
     const typename Vec4<R>::T* __restrict__ sorted_tq, const int* __restrict__ sorted_lb,
     const int* __restrict__ sorted_idx, const int* __restrict__ toff, GatherGeom gg,
     int ntiles, int* __restrict__ work, const R* __restrict__ wtab,
@@ -855,16 +990,18 @@ __global__ void __launch_bounds__(kThreads, 4) k_gather(
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* phi = reinterpret_cast<R*>(smem_raw);
   constexpr int E1 = TC::E1, E3p = TC::E3p, vol = TC::VOL, S1 = TC::S1;
+  constexpr int PS = round_up4(P), RS = record_stride(true, P);
   const int E0 = g.E[0], E2 = g.E[2];  // this plan's tiles (<= TC)
   const SmemLayout L = smem_layout(true, sizeof(R), (size_t)vol, P);
-  R* W = reinterpret_cast<R*>(smem_raw + L.w);   // per atom [w0 w1 w2 | dw0 dw1 dw2]
-  R* Fa = reinterpret_cast<R*>(smem_raw + L.f);  // per atom g_x g_y g_z
+  R* W = reinterpret_cast<R*>(smem_raw + L.w);  // per atom [w0|w1|w2|w0'|w1'|w2'], slots of PS
   int* B = reinterpret_cast<int*>(smem_raw + L.b);
   __shared__ int s_tile;
 
   constexpr int D = WinDeg<R>::value;
   constexpr int NP = kThreads / P;
-  const int lane = threadIdx.x & 31;
+  constexpr int G = 32 / P;  // atoms per warp at a time
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int slot = lane / P, jj = lane - slot * P;
   const int p_t = threadIdx.x % P, pair0 = threadIdx.x / P;
   const bool evaluator = pair0 < NP;
   R cw[D + 1], cd[D + 1];
@@ -903,7 +1040,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_gather(
           const int gk = wrap3(o2 + 4 * c4, g.M[2]);
           const float4 v =
               *reinterpret_cast<const float4*>(grid + ((int64_t)gi * g.M[1] + gj) * g.M[2] + gk);
-          float* dst = phi + ab * E3p + 4 * c4;
+          float* dst = phi + a * S1 + b * E3p + 4 * c4;
           dst[0] = v.x;
           dst[1] = v.y;
           dst[2] = v.z;
@@ -923,7 +1060,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_gather(
         const int gi = wrap_index(o0 + a, g.M[0]);
         const int gj = wrap_index(o1 + b, g.M[1]);
         const int gk = wrap_index(o2 + c, g.M[2]);
-        phi[(a * E1 + b) * E3p + c] = grid[((int64_t)gi * g.M[1] + gj) * g.M[2] + gk];
+        phi[a * S1 + b * E3p + c] = grid[((int64_t)gi * g.M[1] + gj) * g.M[2] + gk];
       }
     }
 
@@ -933,69 +1070,75 @@ __global__ void __launch_bounds__(kThreads, 4) k_gather(
         for (int pr = pair0; pr < 3 * cnt; pr += NP) {
           const int a = pr / 3, d = pr - 3 * a;
           const R t = tq_comp<R>(sorted_tq[c0 + a], d);
-          W[a * 6 * P + d * P + p_t] = horner_reg<R, D>(cw, t);
-          W[a * 6 * P + 3 * P + d * P + p_t] = horner_reg<R, D>(cd, t) * dscale_of<R>(g, d);
+          W[a * RS + d * PS + p_t] = horner_reg<R, D>(cw, t);
+          W[a * RS + (3 + d) * PS + p_t] = horner_reg<R, D>(cd, t) * dscale_of<R>(g, d);
         }
       }
-      for (int a = threadIdx.x; a < cnt; a += blockDim.x) {
-        B[a] = local_base(sorted_lb[c0 + a], E1, E3p);
-        Fa[3 * a + 0] = R(0);
-        Fa[3 * a + 1] = R(0);
-        Fa[3 * a + 2] = R(0);
-      }
+      for (int a = threadIdx.x; a < cnt; a += blockDim.x) B[a] = local_base<S1, E3p>(sorted_lb[c0 + a]);
       __syncthreads();  // also covers the staging of phi for the first chunk
-      // one item per (atom, j): the P x P points (i, k) of row j, contracted in registers
+      // lane j of an atom's group: the P x P points (i, k) of row j, contracted in registers
       //   gx = w1[j] sum_k w2[k] sum_i phi w0'[i],  gy = w1'[j] sum_k w2[k] sum_i phi w0[i],
       //   gz = w1[j] sum_k w2'[k] sum_i phi w0[i]
-      for (int it = threadIdx.x; it < cnt * P; it += blockDim.x) {
-        const int a = it / P, jj = it - a * P;
-        const R* Wa = W + a * 6 * P;
-        R w0[P], d0[P], w2[P], d2[P];
-#pragma unroll
-        for (int i = 0; i < P; ++i) {
-          w0[i] = Wa[i];
-          d0[i] = Wa[3 * P + i];
-          w2[i] = Wa[2 * P + i];
-          d2[i] = Wa[5 * P + i];
-        }
-        const R* src = phi + B[a] + jj * E3p;
+      for (int a0 = warp * G; a0 < cnt; a0 += (kThreads / 32) * G) {
+        const int a = a0 + slot;
+        const bool valid = slot < G && a < cnt;
         R ax = R(0), ay = R(0), az = R(0);
+        if (valid) {
+          const R* Wa = W + a * RS;
+          R w0[P], d0[P], w2[P], d2[P];
+          load_record<R, P>(Wa, w0);
+          load_record<R, P>(Wa + 2 * PS, w2);
+          load_record<R, P>(Wa + 3 * PS, d0);
+          load_record<R, P>(Wa + 5 * PS, d2);
+          const R* src = phi + B[a] + jj * E3p;
 #pragma unroll
-        for (int kk = 0; kk < P; ++kk) {
-          R sx = R(0), sw = R(0);
+          for (int kk = 0; kk < P; ++kk) {
+            R sx = R(0), sw = R(0);
 #pragma unroll
-          for (int i = 0; i < P; ++i) {
-            const R f = src[i * S1 + kk];
-            sx = fma(f, d0[i], sx);
-            sw = fma(f, w0[i], sw);
+            for (int i = 0; i < P; ++i) {
+              const R f = src[i * S1 + kk];
+              sx = fma(f, d0[i], sx);
+              sw = fma(f, w0[i], sw);
+            }
+            ax = fma(w2[kk], sx, ax);
+            ay = fma(w2[kk], sw, ay);
+            az = fma(d2[kk], sw, az);
           }
-          ax = fma(w2[kk], sx, ax);
-          ay = fma(w2[kk], sw, ay);
-          az = fma(d2[kk], sw, az);
+          const R w1 = Wa[PS + jj];
+          ax *= w1;
+          ay *= Wa[4 * PS + jj];
+          az *= w1;
         }
-        smem_add(&Fa[3 * a + 0], Wa[P + jj] * ax);
-        smem_add(&Fa[3 * a + 1], Wa[4 * P + jj] * ay);
-        smem_add(&Fa[3 * a + 2], Wa[P + jj] * az);
-      }
-      __syncthreads();
-      for (int a = threadIdx.x; a < cnt; a += blockDim.x) {
-        // dU/ds = -(q / (V Mtot^2)) (gx, gy, gz);  F = -h^{-T} dU/ds
-        const int j = c0 + a;
-        const int idx = sorted_idx[j];
-        const R gx = Fa[3 * a], gy = Fa[3 * a + 1], gz = Fa[3 * a + 2];
-        const R qa = sorted_tq[j].w;
-        if constexpr (std::is_same<R, float>::value) {
-          const float f = qa * (float)gg.fscale;
+        // segmented sum: lane j of a group ends with rows j .. P-1 of its atom
 #pragma unroll
-          for (int c = 0; c < 3; ++c)
-            forces[3 * (int64_t)idx + c] =
-                (IO)(f * (g.hinvf[c] * gx + g.hinvf[3 + c] * gy + g.hinvf[6 + c] * gz));
-        } else {
-          const double f = qa * gg.fscale;
+        for (int s = 1; s < P; s <<= 1) {
+          const R tx = __shfl_down_sync(0xffffffffu, ax, s);
+          const R ty = __shfl_down_sync(0xffffffffu, ay, s);
+          const R tz = __shfl_down_sync(0xffffffffu, az, s);
+          if (jj + s < P) {
+            ax += tx;
+            ay += ty;
+            az += tz;
+          }
+        }
+        if (valid && jj == 0) {
+          // dU/ds = -(q / (V Mtot^2)) (gx, gy, gz);  F = -h^{-T} dU/ds
+          const int j = c0 + a;
+          const int idx = sorted_idx[j];
+          const R qa = sorted_tq[j].w;
+          if constexpr (std::is_same<R, float>::value) {
+            const float f = qa * (float)gg.fscale;
 #pragma unroll
-          for (int c = 0; c < 3; ++c)
-            forces[3 * (int64_t)idx + c] =
-                (IO)(f * (g.hinv[c] * gx + g.hinv[3 + c] * gy + g.hinv[6 + c] * gz));
+            for (int c = 0; c < 3; ++c)
+              forces[3 * (int64_t)idx + c] =
+                  (IO)(f * (g.hinvf[c] * ax + g.hinvf[3 + c] * ay + g.hinvf[6 + c] * az));
+          } else {
+            const double f = qa * gg.fscale;
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+              forces[3 * (int64_t)idx + c] =
+                  (IO)(f * (g.hinv[c] * ax + g.hinv[3 + c] * ay + g.hinv[6 + c] * az));
+          }
         }
       }
       __syncthreads();

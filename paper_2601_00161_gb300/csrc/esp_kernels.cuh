@@ -37,6 +37,8 @@ struct TileGeom {
   float Ahi[9], Alo[9];
   // magic multipliers for division by E[1] and by ceil(E[2] / 4)
   unsigned int div_E1, div_E2v;
+  // (max |w|)^3 over the window, with a small margin: bounds |q w0 w1 w2| / |q|
+  float wmax3;
 };
 
 // Constants of the fused scaling + reduction pass over the half spectrum.
@@ -61,45 +63,60 @@ struct GatherGeom {
 
 // Tile block of spread / gather, fixed per stencil width P so that all shared-memory
 // strides are compile-time constants: a tile holds T0 x T1 x T2 stencil bases and its CTA
-// owns the padded block E = T + P - 1; rows are padded to the pitch E3p >= E2 with
-// E3p = -P (mod 32), which puts consecutive stencil rows of one atom on consecutive banks.
-constexpr int tile_pitch(int e2, int p) {
+// owns the padded block E = T + P - 1.  Rows are padded to the pitch E3p = -P (mod 32)
+// (E3p = 32 - P for these tiles) and planes to the stride S1 = P^2 (mod 32).  The point
+// (i, j, k) of one atom's stencil then lies in bank (b + i P^2 + (P - 1 - j) P + k) mod 32,
+// b fixed per atom: the P^3 points in the order (i, reversed j, k) fall on consecutive
+// banks, so any 32 consecutive ones never share a bank.
+__host__ __device__ constexpr int tile_pitch(int e2, int p) {
   int x = e2;
   while ((x + p) % 32 != 0) ++x;
   return x;
 }
+__host__ __device__ constexpr int plane_stride(int e1, int e3p, int p) {
+  int y = e1 * e3p;
+  while ((y - p * p) % 32 != 0) ++y;
+  return y;
+}
+__host__ __device__ constexpr int round_up4(int x) { return (x + 3) & ~3; }
 template <int P>
 struct TileC {
   static constexpr int T0 = 8, T1 = 8, T2 = (P <= 8) ? 16 : 8;
   static constexpr int E0 = T0 + P - 1, E1 = T1 + P - 1, E2 = T2 + P - 1;
   static constexpr int E3p = tile_pitch(E2, P);
-  static constexpr int S1 = E1 * E3p;
-  static constexpr int VOL = E0 * S1;
+  static constexpr int S1 = plane_stride(E1, E3p, P);
+  static constexpr int VOL = round_up4(E0 * S1);  // a multiple of 4 for vector clears
 };
 inline void tile_shape(int P, int T[3], int* E3p, int* vol) {
   T[0] = 8;
   T[1] = 8;
   T[2] = P <= 8 ? 16 : 8;
   *E3p = tile_pitch(T[2] + P - 1, P);
-  *vol = (T[0] + P - 1) * (T[1] + P - 1) * *E3p;
+  *vol = round_up4((T[0] + P - 1) * plane_stride(T[1] + P - 1, *E3p, P));
 }
 
 // Atoms a CTA takes from its tile per chunk in spread / gather: all warps compute the
-// window values of a chunk, then share out its (atom, stencil row) items.
+// window values of a chunk, then share out its atoms.
 constexpr int kChunk = 128;
 
+// Per-atom record of window values in shared memory, starting on a 16-byte boundary:
+// spread [w0 | q w1 | w2] (3P values, padded to a multiple of 4); gather
+// [w0 | w1 | w2 | w0' | w1' | w2'], each vector in a slot of round_up4(P) values.
+__host__ __device__ constexpr int record_stride(bool gather, int P) {
+  return gather ? 6 * round_up4(P) : round_up4(3 * P);
+}
+
 // Shared-memory layout of spread / gather, byte offsets aligned to 32 bytes: the padded
-// tile block, then the chunk's window values, force sums (gather) and local bases.
-// es = element size of the compute type.
+// tile block, then the chunk's window records and local bases.  es = element size of the
+// compute type (the FP32 spread accumulates 32-bit integers of the same size).
 struct SmemLayout {
-  size_t w, f, b, total;
+  size_t w, b, total;
 };
 __host__ __device__ inline size_t align32(size_t x) { return (x + 31) & ~(size_t)31; }
 __host__ __device__ inline SmemLayout smem_layout(bool gather, size_t es, size_t vol, int P) {
   SmemLayout L;
   L.w = align32(vol * es);
-  L.f = align32(L.w + (size_t)kChunk * (gather ? 6 : 3) * P * es);
-  L.b = align32(L.f + (gather ? (size_t)kChunk * 3 * es : 0));
+  L.b = align32(L.w + (size_t)kChunk * record_stride(gather, P) * es);
   L.total = align32(L.b + (size_t)kChunk * sizeof(int));
   return L;
 }
@@ -111,7 +128,6 @@ cudaError_t launch_bin(bool io_double, bool fp64, const void* pos, const void* q
                        const TileGeom& g, int* tile_count, int* ptile, int* prank, int* plb,
                        void* tq, void* bin_part, cudaStream_t st);
 int bin_blocks(int64_t n);
-// count: zero on entry (bin adds into it), zero again on exit; work[0..1] zeroed too
 // count: zero on entry (bin adds into it), zero again on exit; work[0..1] zeroed too.
 // bin_part: per binning block 3 compensated sums (float pairs); bsum: scan_blocks() ints.
 cudaError_t launch_scan(int* count, int* suboff, int* toff, int* bsum, int ntiles, int ksub,
