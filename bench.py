@@ -180,6 +180,19 @@ def recorded_traffic(kernel: str):
         return None
 
 
+def accuracy_record():
+    """The workload's measured pressure / force errors (FP64 oracle study, committed)."""
+    path = os.path.join(ROOT, "tests", "golden", "membrane_slab_accuracy.json")
+    try:
+        with open(path) as f:
+            e = json.load(f)["workload_vs_reference_a"]
+    except (OSError, KeyError, ValueError):
+        return None
+    return {"pressure_diag_rel_err": e["pressure_diag"], "pressure_frobenius_rel_err": e["pressure_frobenius"],
+            "pressure_offdiag_rel_err": e["pressure_offdiag"], "forces_rms_rel_err": e["forces_rms"],
+            "source": "tests/golden/membrane_slab_accuracy.json (FP64 oracle vs Delta=1e-11 reference)"}
+
+
 def single_thread():
     """Limit BLAS / OpenMP pools to one thread (the oracle's own work is single-threaded
     numpy either way); a no-op where threadpoolctl is not installed."""
@@ -380,7 +393,8 @@ def esp_arm(args):
                        "grid": list(S.grid), "P": S.P, "delta": S.delta, "c": round(c, 6),
                        "r_c_A": S.rc, "step": "energy + 3x3 virial + forces",
                        "l2": "flushed between timed steps (512 MB write)",
-                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "accuracy": accuracy_record()},
             "stage_ms": {k: round(v, 5) for k, v in avg.items()},
             "roofline": roofline,
             "other_bounds": other,
