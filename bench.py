@@ -252,8 +252,6 @@ def esp_arm(args):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    esp.esp_profile(plan.handle, True)
-    stage_tot = {k: 0.0 for k in esp.STAGES}
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     clocks = ClockSampler(local)
@@ -262,6 +260,23 @@ def esp_arm(args):
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
+    # timed region: K steps, the L2 flushed before each, one CUDA event pair per step
+    for i in range(args.steps):
+        flush.zero_()
+        ev0[i].record(stream)
+        step()
+        ev1[i].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    # second timed region of K steps with an event before and after every stage (the
+    # library records them as nodes of its graph): per-kernel durations for the roofline
+    esp.esp_profile(plan.handle, True)
+    for _ in range(2):
+        step()
+    stage_tot = {k: 0.0 for k in esp.STAGES}
+    prof_ms = 0.0
     for i in range(args.steps):
         flush.zero_()
         ev0[i].record(stream)
@@ -269,12 +284,10 @@ def esp_arm(args):
         ev1[i].record(stream)
         for k, v in esp.esp_profile_read(plan.handle).items():  # synchronises the stream
             stage_tot[k] += v
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+        prof_ms += ev0[i].elapsed_time(ev1[i])
     clk = clocks.stop()
     esp.esp_profile(plan.handle, False)
-    step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
+    step_ms_prof = prof_ms / args.steps
     my_seconds = sum(step_ms) / 1e3
     if world > 1:
         tt = torch.tensor([my_seconds], dtype=torch.float64, device="cuda")
@@ -396,6 +409,8 @@ def esp_arm(args):
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
                        "accuracy": accuracy_record()},
             "stage_ms": {k: round(v, 5) for k, v in avg.items()},
+            "stage_timing": ("second timed region of the same K steps with a CUDA event before and "
+                             f"after every stage; its steps took {step_ms_prof:.5f} ms each"),
             "roofline": roofline,
             "other_bounds": other,
             "energy_pressure_only": energy_pressure,

@@ -155,7 +155,8 @@ int esp_plan_info(esp_plan_t plan, double* info, int len);
 /* Per-stage timing with CUDA events on the plan's stream.  esp_profile(plan, 1) creates
  * the events and records one before and after every stage of each later step;
  * esp_profile_read synchronises the stream and writes the last step's stage durations
- * in ms, in the order: [0] memsets, [1] bin, [2] scan, [3] scatter, [4] grid zeroing,
+ * in ms, in the order: [0] set-up, [1] bin (which also clears the spread grid), [2] scan,
+ * [3] scatter, [4] separate grid clearing (0 when the bin kernel clears the grid),
  * [5] spread, [6] forward FFT, [7] scale + reduce, [8] inverse FFT, [9] gather
  * (stages that did not run read 0).  Writes min(len, 10) values. */
 int esp_profile(esp_plan_t plan, int enable);

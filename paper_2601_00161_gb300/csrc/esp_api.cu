@@ -368,7 +368,8 @@ int run_step(esp_plan_t p, const void* pos, const void* q, void* forces, double*
   // kernel of every step.  acc[0..6] is written by the scale kernel, acc[7..9] by scan.
   mark(p, kBin);
   ESP_CUDA(p, esp::launch_bin(p->io_double, fp64, pos, q, p->n, p->tg, p->d_count, p->d_ptile,
-                              p->d_prank, p->d_plb, p->d_tq, p->d_binpart, st));
+                              p->d_prank, p->d_plb, p->d_tq, p->d_binpart, p->d_grid,
+                              es * Mtot, st));
   mark(p, kScan);
   ESP_CUDA(p, esp::launch_scan(p->d_count, p->d_suboff, p->d_offset, p->d_bsum, p->ntiles,
                                p->tg.ksub, p->d_binpart, p->n > 0 ? p->bin_blocks : 0, acc,
@@ -377,8 +378,6 @@ int run_step(esp_plan_t p, const void* pos, const void* q, void* forces, double*
   ESP_CUDA(p, esp::launch_scatter(fp64, p->n, p->tg.ksub, p->d_ptile, p->d_prank, p->d_plb, p->d_tq,
                                   p->d_suboff, p->d_sorted_tq, p->d_sorted_lb,
                                   p->d_sorted_idx, st));
-  mark(p, kZero);
-  ESP_CUDA(p, cudaMemsetAsync(p->d_grid, 0, es * Mtot, st));
   mark(p, kSpread);
   ESP_CUDA(p, esp::launch_spread(fp64, p->tg, p->ntiles, p->spread_blocks, p->d_sorted_tq,
                                  p->d_sorted_lb, p->d_offset, work, p->d_wtab, p->d_grid, st));
@@ -1019,7 +1018,7 @@ extern "C" int esp_spread_noalloc(const double cell[9], int64_t n, const int gri
   // the array keeps the last call's contents: the counters must start at zero
   ESP_CUDA(nullptr, cudaMemsetAsync(count, 0, sizeof(int) * ((size_t)p->ntiles * esp::kSub + 2), st));
   ESP_CUDA(nullptr, esp::launch_bin(p->io_double, p->fp64, pos, q, n, g, count, ptile, prank, plb,
-                                    tq, binpart, st));
+                                    tq, binpart, nullptr, 0, st));
   ESP_CUDA(nullptr, esp::launch_scan(count, suboff, toff, bsum, p->ntiles, g.ksub, binpart,
                                      n > 0 ? esp::bin_blocks(n) : 0, acc, work, st));
   ESP_CUDA(nullptr, esp::launch_scatter(p->fp64, n, g.ksub, ptile, prank, plb, tq, suboff, stq,

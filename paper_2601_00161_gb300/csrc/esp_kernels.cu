@@ -180,10 +180,15 @@ __global__ void __launch_bounds__(kThreads) k_bin(const IO* __restrict__ pos,
                                                   int* __restrict__ prank,
                                                   int* __restrict__ plb,
                                                   typename Vec4<R>::T* __restrict__ tq,
-                                                  float2* __restrict__ bin_part) {
+                                                  float2* __restrict__ bin_part,
+                                                  int4* __restrict__ zero, int64_t nzero) {
   // FP32 inputs on the FP32 path use the compensated FP32 transform (FP64 only for the
   // rare coordinate next to a stencil switch); everything else uses FP64.
   constexpr bool kDF = std::is_same<IO, float>::value && std::is_same<R, float>::value;
+  // the spread target grid is cleared here too (nzero 16-byte words), saving a memset
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nzero;
+       i += (int64_t)gridDim.x * blockDim.x)
+    zero[i] = make_int4(0, 0, 0, 0);
   DF sq, sq2, bad;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -499,6 +504,23 @@ struct LaneCols {
   int j[Cols<P>::MP > 0 ? Cols<P>::MP : 1];
   int k[Cols<P>::MP > 0 ? Cols<P>::MP : 1];
   unsigned tail[Cols<P>::NG > 0 ? Cols<P>::NG : 1];
+  // the same tail points unpacked for the spread: byte offset of a 4- or 8-byte element,
+  // record indices of w0[i], q w1[j] and w2[k], and whether the lane has a point
+  int tail_off[Cols<P>::NG > 0 ? Cols<P>::NG : 1];
+  int tail_i[Cols<P>::NG > 0 ? Cols<P>::NG : 1], tail_j[Cols<P>::NG > 0 ? Cols<P>::NG : 1],
+      tail_k[Cols<P>::NG > 0 ? Cols<P>::NG : 1];
+  bool tail_ok[Cols<P>::NG > 0 ? Cols<P>::NG : 1];
+  __device__ __forceinline__ LaneCols(int lane, int elem_bytes) : LaneCols(lane) {
+#pragma unroll
+    for (int g = 0; g < (Cols<P>::NG > 0 ? Cols<P>::NG : 1); ++g) {
+      const unsigned tp = tail[g];
+      tail_ok[g] = (tp >> 31) != 0u;
+      tail_off[g] = (int)(tp & 0xffffu) * elem_bytes;
+      tail_i[g] = (tp >> 16) & 15;
+      tail_j[g] = P + ((tp >> 20) & 15);
+      tail_k[g] = 2 * P + ((tp >> 24) & 15);
+    }
+  }
   __device__ __forceinline__ explicit LaneCols(int lane) {
     using C = Cols<P>;
 #pragma unroll
@@ -573,6 +595,7 @@ __global__ void __launch_bounds__(kThreads) k_spread(
   const int E0 = g.E[0], E2 = g.E[2];  // this plan's tiles (<= TC)
   const SmemLayout L = smem_layout(false, sizeof(R), (size_t)vol, P);
   R* W = reinterpret_cast<R*>(smem_raw + L.w);  // per atom [w0 | q w1 | w2]
+  V4* TQ = reinterpret_cast<V4*>(smem_raw + L.t);  // per atom (t0, t1, t2, q)
   int* B = reinterpret_cast<int*>(smem_raw + L.b);
   __shared__ int s_tile;
   __shared__ float s_qsum[kThreads / 32];
@@ -582,11 +605,8 @@ __global__ void __launch_bounds__(kThreads) k_spread(
   constexpr int NP = kThreads / P;  // pairs per sweep
   const int p_t = threadIdx.x % P, pair0 = threadIdx.x / P;
   const bool evaluator = pair0 < NP;
-  R cw[D + 1];
-#pragma unroll
-  for (int k = 0; k <= D; ++k) cw[k] = evaluator ? wtab[k * P + p_t] : R(0);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const LaneCols<P, S1, E3p> lc(lane);
+  const LaneCols<P, S1, E3p> lc(lane, (int)sizeof(A));
 
   if (threadIdx.x == 0) s_tile = atomicAdd(&work[0], 1);
   {
@@ -626,16 +646,26 @@ __global__ void __launch_bounds__(kThreads) k_spread(
       }
       for (int c0 = start; c0 < end; c0 += kChunk) {
         const int cnt = min(kChunk, end - c0);
+        // the chunk's atoms into shared memory with one coalesced load each
+        for (int a = threadIdx.x; a < cnt; a += blockDim.x) {
+          TQ[a] = sorted_tq[c0 + a];
+          B[a] = local_base<S1, E3p>(sorted_lb[c0 + a]);
+        }
+        __syncthreads();
         if (evaluator) {
+          // coefficients of stencil point p_t (a small table, L1-resident): loaded here so
+          // the registers are free in the other phases
+          R cw[D + 1];
+#pragma unroll
+          for (int k = 0; k <= D; ++k) cw[k] = __ldg(wtab + k * P + p_t);
           for (int pr = pair0; pr < 3 * cnt; pr += NP) {
             const int a = pr / 3, d = pr - 3 * a;
-            const V4 v = sorted_tq[c0 + a];
+            const V4 v = TQ[a];
             R w = horner_reg<R, D>(cw, tq_comp<R>(v, d));
             if (d == 1) w *= v.w * scale;
             W[a * RS + d * P + p_t] = w;
           }
         }
-        for (int a = threadIdx.x; a < cnt; a += blockDim.x) B[a] = local_base<S1, E3p>(sorted_lb[c0 + a]);
         __syncthreads();
         for (int a = warp; a < cnt; a += kThreads / 32) {
           const R* Wa = W + a * RS;
@@ -650,12 +680,9 @@ __global__ void __launch_bounds__(kThreads) k_spread(
           }
 #pragma unroll
           for (int t = 0; t < CM::NG; ++t) {
-            const unsigned tp = lc.tail[t];
-            if (tp >> 31) {
-              const int i = (tp >> 16) & 15, jj = (tp >> 20) & 15, kk = (tp >> 24) & 15;
-              red_fixed<0>(base + (tp & 0xffffu) * (unsigned)sizeof(A),
-                           Wa[i] * (Wa[P + jj] * Wa[2 * P + kk]));
-            }
+            if (lc.tail_ok[t])
+              red_fixed<0>(base + (unsigned)lc.tail_off[t],
+                           Wa[lc.tail_i[t]] * (Wa[lc.tail_j[t]] * Wa[lc.tail_k[t]]));
           }
         }
         __syncthreads();
@@ -994,7 +1021,10 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 4 : 
   const int E0 = g.E[0], E2 = g.E[2];  // this plan's tiles (<= TC)
   const SmemLayout L = smem_layout(true, sizeof(R), (size_t)vol, P);
   R* W = reinterpret_cast<R*>(smem_raw + L.w);  // per atom [w0|w1|w2|w0'|w1'|w2'], slots of PS
+  using V4 = typename Vec4<R>::T;
+  V4* TQ = reinterpret_cast<V4*>(smem_raw + L.t);  // per atom (t0, t1, t2, q)
   int* B = reinterpret_cast<int*>(smem_raw + L.b);
+  int* X = reinterpret_cast<int*>(smem_raw + L.x);  // per atom its index in the input
   __shared__ int s_tile;
 
   constexpr int D = WinDeg<R>::value;
@@ -1004,12 +1034,6 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 4 : 
   const int slot = lane / P, jj = lane - slot * P;
   const int p_t = threadIdx.x % P, pair0 = threadIdx.x / P;
   const bool evaluator = pair0 < NP;
-  R cw[D + 1], cd[D + 1];
-#pragma unroll
-  for (int k = 0; k <= D; ++k) {
-    cw[k] = evaluator ? wtab[k * P + p_t] : R(0);
-    cd[k] = evaluator ? wtab[(D + 1) * P + k * P + p_t] : R(0);
-  }
 
   for (;;) {
     __syncthreads();  // the previous tile is done and s_tile consumed
@@ -1027,24 +1051,42 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 4 : 
     bool loaded = false;
     if constexpr (std::is_same<R, float>::value) {
       if (g.vec4) {
+        // rounds of kU float4 per thread: all loads issued before the first store
+        constexpr int kU = P <= 11 ? 4 : 2;
         const int E2v = (E2 + 3) >> 2;
         const int nload = E0 * E1 * E2v;
-        for (int e = threadIdx.x; e < nload; e += blockDim.x) {
-          const int ab = fast_div(e, g.div_E2v);
-          const int c4 = e - ab * E2v;
-          const int a = ab / E1;
-          const int b = ab - a * E1;
-          if (b >= g.E[1]) continue;
-          const int gi = wrap3(o0 + a, g.M[0]);
-          const int gj = wrap3(o1 + b, g.M[1]);
-          const int gk = wrap3(o2 + 4 * c4, g.M[2]);
-          const float4 v =
-              *reinterpret_cast<const float4*>(grid + ((int64_t)gi * g.M[1] + gj) * g.M[2] + gk);
-          float* dst = phi + a * S1 + b * E3p + 4 * c4;
-          dst[0] = v.x;
-          dst[1] = v.y;
-          dst[2] = v.z;
-          dst[3] = v.w;
+        for (int e0 = threadIdx.x; e0 < nload; e0 += kU * blockDim.x) {
+          float4 v[kU];
+          int dst[kU];
+#pragma unroll
+          for (int u = 0; u < kU; ++u) {
+            const int e = e0 + u * blockDim.x;
+            dst[u] = -1;
+            if (e < nload) {
+              const int ab = fast_div(e, g.div_E2v);
+              const int c4 = e - ab * E2v;
+              const int a = ab / E1;
+              const int b = ab - a * E1;
+              if (b < g.E[1]) {
+                const int gi = wrap3(o0 + a, g.M[0]);
+                const int gj = wrap3(o1 + b, g.M[1]);
+                const int gk = wrap3(o2 + 4 * c4, g.M[2]);
+                v[u] = __ldcg(reinterpret_cast<const float4*>(
+                    grid + ((int64_t)gi * g.M[1] + gj) * g.M[2] + gk));
+                dst[u] = a * S1 + b * E3p + 4 * c4;
+              }
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < kU; ++u) {
+            if (dst[u] >= 0) {
+              float* d = phi + dst[u];
+              d[0] = v[u].x;
+              d[1] = v[u].y;
+              d[2] = v[u].z;
+              d[3] = v[u].w;
+            }
+          }
         }
         loaded = true;
       }
@@ -1066,16 +1108,29 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 4 : 
 
     for (int c0 = start; c0 < end; c0 += kChunk) {
       const int cnt = min(kChunk, end - c0);
+      // the chunk's atoms into shared memory with one coalesced load each
+      for (int a = threadIdx.x; a < cnt; a += blockDim.x) {
+        TQ[a] = sorted_tq[c0 + a];
+        B[a] = local_base<S1, E3p>(sorted_lb[c0 + a]);
+        X[a] = sorted_idx[c0 + a];
+      }
+      __syncthreads();  // also covers the staging of phi for the first chunk
       if (evaluator) {
+        // coefficients of stencil point p_t, window and derivative (L1-resident table)
+        R cw[D + 1], cd[D + 1];
+#pragma unroll
+        for (int k = 0; k <= D; ++k) {
+          cw[k] = __ldg(wtab + k * P + p_t);
+          cd[k] = __ldg(wtab + (D + 1) * P + k * P + p_t);
+        }
         for (int pr = pair0; pr < 3 * cnt; pr += NP) {
           const int a = pr / 3, d = pr - 3 * a;
-          const R t = tq_comp<R>(sorted_tq[c0 + a], d);
+          const R t = tq_comp<R>(TQ[a], d);
           W[a * RS + d * PS + p_t] = horner_reg<R, D>(cw, t);
           W[a * RS + (3 + d) * PS + p_t] = horner_reg<R, D>(cd, t) * dscale_of<R>(g, d);
         }
       }
-      for (int a = threadIdx.x; a < cnt; a += blockDim.x) B[a] = local_base<S1, E3p>(sorted_lb[c0 + a]);
-      __syncthreads();  // also covers the staging of phi for the first chunk
+      __syncthreads();
       // lane j of an atom's group: the P x P points (i, k) of row j, contracted in registers
       //   gx = w1[j] sum_k w2[k] sum_i phi w0'[i],  gy = w1'[j] sum_k w2[k] sum_i phi w0[i],
       //   gz = w1[j] sum_k w2'[k] sum_i phi w0[i]
@@ -1123,9 +1178,8 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 4 : 
         }
         if (valid && jj == 0) {
           // dU/ds = -(q / (V Mtot^2)) (gx, gy, gz);  F = -h^{-T} dU/ds
-          const int j = c0 + a;
-          const int idx = sorted_idx[j];
-          const R qa = sorted_tq[j].w;
+          const int idx = X[a];
+          const R qa = TQ[a].w;
           if constexpr (std::is_same<R, float>::value) {
             const float f = qa * (float)gg.fscale;
 #pragma unroll
@@ -1176,26 +1230,35 @@ cudaError_t with_P(int P, F&& f) {
 // ---- host launchers --------------------------------------------------------------------
 cudaError_t launch_bin(bool io_double, bool fp64, const void* pos, const void* q, int64_t n,
                        const TileGeom& g, int* tile_count, int* ptile, int* prank, int* plb,
-                       void* tq, void* bin_part_v, cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
+                       void* tq, void* bin_part_v, void* zero_buf, size_t zero_bytes,
+                       cudaStream_t st) {
+  if (n <= 0 || zero_bytes % 16 != 0) {
+    if (zero_bytes) {
+      const cudaError_t e = cudaMemsetAsync(zero_buf, 0, zero_bytes, st);
+      if (e != cudaSuccess || n <= 0) return e;
+    }
+    zero_bytes = 0;
+  }
   float2* bin_part = (float2*)bin_part_v;
   const int nb = grid_blocks(n);
+  int4* zero = (int4*)zero_buf;
+  const int64_t nzero = (int64_t)(zero_bytes / 16);
   if (io_double && fp64)
     k_bin<double, double><<<nb, kThreads, 0, st>>>((const double*)pos, (const double*)q, n, g,
                                                     tile_count, ptile, prank, plb,
-                                                    (double4*)tq, bin_part);
+                                                    (double4*)tq, bin_part, zero, nzero);
   else if (io_double)
     k_bin<double, float><<<nb, kThreads, 0, st>>>((const double*)pos, (const double*)q, n, g,
                                                    tile_count, ptile, prank, plb, (float4*)tq,
-                                                   bin_part);
+                                                   bin_part, zero, nzero);
   else if (fp64)
     k_bin<float, double><<<nb, kThreads, 0, st>>>((const float*)pos, (const float*)q, n, g,
                                                    tile_count, ptile, prank, plb, (double4*)tq,
-                                                   bin_part);
+                                                   bin_part, zero, nzero);
   else
     k_bin<float, float><<<nb, kThreads, 0, st>>>((const float*)pos, (const float*)q, n, g,
                                                   tile_count, ptile, prank, plb, (float4*)tq,
-                                                  bin_part);
+                                                  bin_part, zero, nzero);
   return cudaGetLastError();
 }
 

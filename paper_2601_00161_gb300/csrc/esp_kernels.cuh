@@ -107,26 +107,31 @@ __host__ __device__ constexpr int record_stride(bool gather, int P) {
 }
 
 // Shared-memory layout of spread / gather, byte offsets aligned to 32 bytes: the padded
-// tile block, then the chunk's window records and local bases.  es = element size of the
-// compute type (the FP32 spread accumulates 32-bit integers of the same size).
+// tile block, the chunk's window records, its (t, q) vectors, local bases and (gather)
+// atom indices.  es = element size of the compute type (the FP32 spread accumulates 32-bit
+// integers of the same size).
 struct SmemLayout {
-  size_t w, b, total;
+  size_t w, t, b, x, total;
 };
 __host__ __device__ inline size_t align32(size_t x) { return (x + 31) & ~(size_t)31; }
 __host__ __device__ inline SmemLayout smem_layout(bool gather, size_t es, size_t vol, int P) {
   SmemLayout L;
   L.w = align32(vol * es);
-  L.b = align32(L.w + (size_t)kChunk * record_stride(gather, P) * es);
-  L.total = align32(L.b + (size_t)kChunk * sizeof(int));
+  L.t = align32(L.w + (size_t)kChunk * record_stride(gather, P) * es);
+  L.b = align32(L.t + (size_t)kChunk * 4 * es);
+  L.x = align32(L.b + (size_t)kChunk * sizeof(int));
+  L.total = align32(L.x + (gather ? (size_t)kChunk * sizeof(int) : 0));
   return L;
 }
 
 // ---- launchers (return cudaGetLastError() of the launch) -----------------------------
 // io_double: pos/q/F are double (else float).  fp64: compute type double (else float).
 
+// Also clears zero_bytes of zero_buf (the spread target grid), by a memset when n <= 0.
 cudaError_t launch_bin(bool io_double, bool fp64, const void* pos, const void* q, int64_t n,
                        const TileGeom& g, int* tile_count, int* ptile, int* prank, int* plb,
-                       void* tq, void* bin_part, cudaStream_t st);
+                       void* tq, void* bin_part, void* zero_buf, size_t zero_bytes,
+                       cudaStream_t st);
 int bin_blocks(int64_t n);
 // count: zero on entry (bin adds into it), zero again on exit; work[0..1] zeroed too.
 // bin_part: per binning block 3 compensated sums (float pairs); bsum: scan_blocks() ints.
