@@ -113,6 +113,24 @@ int esp_set_stream(esp_plan_t plan, void* stream);
  */
 int esp_step(esp_plan_t plan, const void* pos, const void* q, void* forces, double* d_accum);
 
+/*
+ * esp_cell_gradient - derivative of the long-range energy U = U_F + U_self + U_bg with
+ * respect to the cell matrix at fixed Cartesian positions, for automatic differentiation
+ * through NPT cell changes (Sec. 2.2, eq. (instheta), with r = h s):
+ *     dU/dh = -W h^{-T} + sum_i F_i s_i^T,   s_i = h^{-1} r_i (as given, not wrapped),
+ * W = W_F + U_bg I the virial and F the forces of an esp_step that wrote forces.  At
+ * fixed reduced coordinates the second term is absent: dU/dh|_s = -W h^{-T}.
+ *   pos, forces  device arrays N x 3 of the I/O type: the positions of that esp_step and
+ *                the forces it wrote (atoms with non-finite positions are left out).
+ *   d_accum      that step's accumulator (NULL: the plan's own).
+ *   d_grad       device array of 9 doubles, row-major (d_grad[3 a + b] = dU/dh_ab),
+ *                overwritten.
+ * Asynchronous on the plan's stream; uses the plan's current cell.
+ * Errors: ESP_ERR_ARG, ESP_ERR_CUDA.
+ */
+int esp_cell_gradient(esp_plan_t plan, const void* pos, const void* forces,
+                      const double* d_accum, double* d_grad);
+
 /* Energy and pressure only (Algorithm 1: no inverse FFT, Sec. 4.1).  Synchronises the
  * plan's stream and fills *out.  Keeps the spectrum so that an immediately following
  * esp_forces_from_spectrum needs no second spread / forward FFT.

@@ -39,6 +39,7 @@ EXPORTS = (
     "esp_forces", "esp_forces_from_spectrum", "esp_compute_host", "esp_result_from_accum",
     "esp_copy_grid", "esp_copy_spectrum", "esp_plan_info", "esp_destroy", "esp_last_error",
     "esp_c_from_tolerance", "esp_profile", "esp_profile_read", "esp_spread_noalloc",
+    "esp_cell_gradient",
 )
 
 ESP_NOALLOC_MAX_ATOMS = 65536
@@ -108,6 +109,7 @@ def _load():
         "esp_profile": (ci, [vp, ci]),
         "esp_profile_read": (ci, [vp, dptr, ci]),
         "esp_spread_noalloc": (ci, [dptr, i64, ctypes.POINTER(ci), ci, cd, ci, vp, vp, vp, vp]),
+        "esp_cell_gradient": (ci, [vp, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -168,6 +170,10 @@ def esp_forces(plan, pos, q, forces):
 
 def esp_forces_from_spectrum(plan, forces):
     _check(_lib.esp_forces_from_spectrum(plan, _ptr(forces)), plan)
+
+
+def esp_cell_gradient(plan, pos, forces, accum, grad):
+    _check(_lib.esp_cell_gradient(plan, _ptr(pos), _ptr(forces), _ptr(accum), _ptr(grad)), plan)
 
 
 def esp_compute_host(plan, pos: np.ndarray, q: np.ndarray, forces: np.ndarray | None):
@@ -255,6 +261,7 @@ class Plan:
         self.P, self.c, self.rc = int(P), float(c), float(rc)
         st = stream if stream is not None else torch.cuda.current_stream().cuda_stream
         self.handle = esp_plan(cell, n, grid, P, c, rc, flags, st)
+        self.cell = np.array(cell, dtype=np.float64).reshape(3, 3)
 
     def close(self):
         if getattr(self, "handle", None):
@@ -277,6 +284,7 @@ class Plan:
 
     def set_cell(self, cell):
         esp_set_cell(self.handle, cell)
+        self.cell = np.array(cell, dtype=np.float64).reshape(3, 3)
 
     def energy_pressure(self, pos, q) -> dict:
         pos, q = self._in(pos, q)
@@ -314,3 +322,6 @@ class Plan:
         a = np.empty(shp, dtype=np.complex128 if self.fp64 else np.complex64)
         esp_copy_spectrum(self.handle, a)
         return a
+
+
+from .autograd import LongRangeEnergy, long_range_energy  # noqa: E402,F401

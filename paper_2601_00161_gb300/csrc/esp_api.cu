@@ -739,6 +739,20 @@ int esp_forces_from_spectrum(esp_plan_t p, void* forces) {
   return ESP_OK;
 }
 
+int esp_cell_gradient(esp_plan_t p, const void* pos, const void* forces, const double* d_accum,
+                      double* d_grad) {
+  if (!p) return fail(nullptr, ESP_ERR_ARG, "plan is NULL");
+  if (!d_grad || (p->n > 0 && (!pos || !forces)))
+    return fail(p, ESP_ERR_ARG, "pos, forces or d_grad is NULL");
+  DeviceGuard guard(p->device);
+  esp::CellGradArgs c;
+  for (int i = 0; i < 9; ++i) c.hinv[i] = p->hinv[i];
+  c.bg_coef = -2.0 * M_PI / p->V * p->Xbg;
+  ESP_CUDA(p, esp::launch_cell_grad(p->io_double, pos, forces, p->n, c,
+                                    d_accum ? d_accum : p->d_accum, d_grad, p->stream));
+  return ESP_OK;
+}
+
 int esp_compute_host(esp_plan_t p, const void* pos, const void* q, void* forces,
                      esp_result* out) {
   if (!p) return fail(nullptr, ESP_ERR_ARG, "plan is NULL");

@@ -1200,6 +1200,55 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 4 : 
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Cell gradient of the long-range energy at fixed Cartesian positions (Sec. 2.2, eq.
+// (instheta) with r = h s): dU/dh = -W h^{-T} + sum_i F_i s_i^T, s_i = h^{-1} r_i as given
+// (unwrapped), W = W_F + U_bg I.  grad (row-major, zeroed by the host) receives each
+// block's part of the moment sum; block 0 adds -W h^{-T} from the step's accumulator.
+template <typename IO>
+__global__ void __launch_bounds__(kThreads) k_cell_grad(const IO* __restrict__ pos,
+                                                        const IO* __restrict__ F, int64_t n,
+                                                        CellGradArgs c,
+                                                        const double* __restrict__ acc,
+                                                        double* __restrict__ grad) {
+  double m[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) m[e] = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double r[3] = {(double)pos[3 * i], (double)pos[3 * i + 1], (double)pos[3 * i + 2]};
+    if (!(isfinite(r[0]) && isfinite(r[1]) && isfinite(r[2]))) continue;  // skipped atoms
+    const double f[3] = {(double)F[3 * i], (double)F[3 * i + 1], (double)F[3 * i + 2]};
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const double sb = c.hinv[3 * b] * r[0] + c.hinv[3 * b + 1] * r[1] + c.hinv[3 * b + 2] * r[2];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) m[3 * a + b] += f[a] * sb;
+    }
+  }
+  __shared__ double part[kThreads / 32][9];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    const double v = warp_sum(m[e]);
+    if (lane == 0) part[warp][e] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 9) {
+    double v = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) v += part[w][threadIdx.x];
+    if (blockIdx.x == 0) {
+      // -(W h^{-T})_{ab} = -sum_c W_ac hinv_bc, W = W_F + U_bg I (accumulator: xx yy zz xy xz yz)
+      const double ubg = c.bg_coef * acc[7] * acc[7];
+      const double W[9] = {acc[1] + ubg, acc[4], acc[5], acc[4], acc[2] + ubg, acc[6],
+                           acc[5], acc[6], acc[3] + ubg};
+      const int a = threadIdx.x / 3, b = threadIdx.x % 3;
+      v -= W[3 * a] * c.hinv[3 * b] + W[3 * a + 1] * c.hinv[3 * b + 1] + W[3 * a + 2] * c.hinv[3 * b + 2];
+    }
+    atomicAdd(grad + threadIdx.x, v);
+  }
+}
+
 int grid_blocks(int64_t n) {
   int64_t b = (n + kThreads - 1) / kThreads;
   if (b < 1) b = 1;
@@ -1400,6 +1449,21 @@ cudaError_t launch_gather(bool fp64, bool io_double, const GatherGeom& gg, int n
           (const float*)wtab, (const float*)grid, (float*)forces);
     return cudaGetLastError();
   });
+}
+
+cudaError_t launch_cell_grad(bool io_double, const void* pos, const void* forces, int64_t n,
+                             const CellGradArgs& c, const double* accum, double* grad,
+                             cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(grad, 0, 9 * sizeof(double), st);
+  if (e != cudaSuccess) return e;
+  const int nb = grid_blocks(n > 0 ? n : 1);
+  if (io_double)
+    k_cell_grad<double><<<nb, kThreads, 0, st>>>((const double*)pos, (const double*)forces, n, c,
+                                                 accum, grad);
+  else
+    k_cell_grad<float><<<nb, kThreads, 0, st>>>((const float*)pos, (const float*)forces, n, c,
+                                                accum, grad);
+  return cudaGetLastError();
 }
 
 // resident CTAs per SM for the spread and gather kernels of this configuration

@@ -61,6 +61,12 @@ struct GatherGeom {
   double fscale;  // 1 / (V Mtot^2)
 };
 
+// Constants of the cell gradient: h^{-1} (row-major) and U_bg = bg_coef * (sum q)^2.
+struct CellGradArgs {
+  double hinv[9];
+  double bg_coef;
+};
+
 // Tile block of spread / gather, fixed per stencil width P so that all shared-memory
 // strides are compile-time constants: a tile holds T0 x T1 x T2 stencil bases and its CTA
 // owns the padded block E = T + P - 1.  Rows are padded to the pitch E3p = -P (mod 32)
@@ -155,6 +161,10 @@ cudaError_t launch_gather(bool fp64, bool io_double, const GatherGeom& gg, int n
                           int nblocks, const void* sorted_tq, const int* sorted_lb,
                           const int* sorted_idx, const int* toff, int* work, const void* wtab,
                           const void* grid, void* forces, cudaStream_t st);
+// dU/dh at fixed positions into grad[9] (row-major): -W h^{-T} + sum_i F_i (h^{-1} r_i)^T
+cudaError_t launch_cell_grad(bool io_double, const void* pos, const void* forces, int64_t n,
+                             const CellGradArgs& c, const double* accum, double* grad,
+                             cudaStream_t st);
 cudaError_t occupancy(bool fp64, bool io_double, int P, size_t spread_smem, size_t gather_smem,
                       int* spread_ctas, int* gather_ctas);
 
