@@ -87,6 +87,18 @@ def dist_env():
     return world, rank, local
 
 
+def max_over_ranks(my_seconds: float, world: int, device: str) -> float:
+    """The slowest rank's time, on every rank (an all-reduce MAX; one process: itself)."""
+    if world == 1:
+        return my_seconds
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([my_seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def aggregate(per_rank_seconds, per_rank_steps):
     """Whole-job throughput: units all ranks processed over the slowest rank's time."""
     t = max(per_rank_seconds)
@@ -289,13 +301,10 @@ def esp_arm(args):
     esp.esp_profile(plan.handle, False)
     step_ms_prof = prof_ms / args.steps
     my_seconds = sum(step_ms) / 1e3
-    if world > 1:
-        tt = torch.tensor([my_seconds], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-        value = world * args.steps / t_max
-    else:
-        value, t_max = aggregate([my_seconds], [args.steps])
+    # replicas: every rank ran K steps of its own workload; whole-job throughput is all
+    # ranks' steps over the slowest rank's time
+    t_max = max_over_ranks(my_seconds, world, "cuda")
+    value, _ = aggregate([t_max] * world, [args.steps] * world)
     res = esp.esp_result_from_accum(plan.handle, acc.cpu().numpy()).as_dict()
 
     # dominant kernel of ours and its roofline (algorithmic bytes / event-timed duration)
