@@ -114,6 +114,27 @@ int esp_set_stream(esp_plan_t plan, void* stream);
 int esp_step(esp_plan_t plan, const void* pos, const void* q, void* forces, double* d_accum);
 
 /*
+ * esp_near - the near (real-space) part of the PSWF split on the GPU (Sec. 3, eq. (UN);
+ * forces as in eq. (Fc); pressure as in eq. (PinsN)): every pair and periodic image with
+ * |r_i - r_j + h n| <= r_c, u = r / r_c,
+ *     N(r) = (1 - phi_0(u)) / r,   F_N(u) = 1 - phi_0(u) + u psi_0(u) / C_0,
+ *     U_N = 1/2 sum' q_i q_j N(r),   F_i = sum_j q_i q_j F_N r_ij / r^3,
+ *     W_N = 1/2 sum' q_i q_j F_N r_ij (x) r_ij / r^3,
+ * r_ij = r_i - r_j - h n.  W_N carries the sign that -(dU_N/dh) h^T gives; eq. (PinsN)
+ * prints the opposite one.  No exclusions.  A cell list of the plan's current cell is
+ * built on the device every call; with the long-range step it gives the total Coulomb
+ * energy U_N + U_F + U_self + U_bg.
+ *   pos, q    device arrays N x 3 and N of the I/O type.
+ *   forces    device array N x 3 of the I/O type: overwritten (add = 0) or added to
+ *             (add = 1, e.g. after an esp_step that wrote the long-range forces there).
+ *   d_out     device array of 7 doubles, overwritten: U_N, W_N xx yy zz xy xz yz.
+ * Asynchronous on the plan's stream; the first call allocates the cell-list buffers.
+ * Atoms with non-finite input are left out.  Errors: ESP_ERR_ARG, ESP_ERR_CUDA.
+ */
+int esp_near(esp_plan_t plan, const void* pos, const void* q, void* forces, int add,
+             double* d_out);
+
+/*
  * esp_cell_gradient - derivative of the long-range energy U = U_F + U_self + U_bg with
  * respect to the cell matrix at fixed Cartesian positions, for automatic differentiation
  * through NPT cell changes (Sec. 2.2, eq. (instheta), with r = h s):

@@ -39,7 +39,7 @@ EXPORTS = (
     "esp_forces", "esp_forces_from_spectrum", "esp_compute_host", "esp_result_from_accum",
     "esp_copy_grid", "esp_copy_spectrum", "esp_plan_info", "esp_destroy", "esp_last_error",
     "esp_c_from_tolerance", "esp_profile", "esp_profile_read", "esp_spread_noalloc",
-    "esp_cell_gradient",
+    "esp_cell_gradient", "esp_near",
 )
 
 ESP_NOALLOC_MAX_ATOMS = 65536
@@ -110,6 +110,7 @@ def _load():
         "esp_profile_read": (ci, [vp, dptr, ci]),
         "esp_spread_noalloc": (ci, [dptr, i64, ctypes.POINTER(ci), ci, cd, ci, vp, vp, vp, vp]),
         "esp_cell_gradient": (ci, [vp, vp, vp, vp, vp]),
+        "esp_near": (ci, [vp, vp, vp, vp, ci, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -174,6 +175,10 @@ def esp_forces_from_spectrum(plan, forces):
 
 def esp_cell_gradient(plan, pos, forces, accum, grad):
     _check(_lib.esp_cell_gradient(plan, _ptr(pos), _ptr(forces), _ptr(accum), _ptr(grad)), plan)
+
+
+def esp_near(plan, pos, q, forces, add, out):
+    _check(_lib.esp_near(plan, _ptr(pos), _ptr(q), _ptr(forces), int(add), _ptr(out)), plan)
 
 
 def esp_compute_host(plan, pos: np.ndarray, q: np.ndarray, forces: np.ndarray | None):
@@ -308,6 +313,18 @@ class Plan:
         esp_step(self.handle, pos, q, F, acc)
         res = esp_result_from_accum(self.handle, acc.cpu().numpy()).as_dict()
         return res, F
+
+    def near(self, pos, q, forces=None, add=False):
+        """Near part of the split: (U_N, W_N 3x3, forces).  ``forces`` is overwritten, or
+        added to when ``add``."""
+        pos, q = self._in(pos, q)
+        if forces is None:
+            forces = self.torch.zeros((self.n, 3), dtype=self.io_dtype, device="cuda")
+        out = self.torch.empty(7, dtype=self.torch.float64, device="cuda")
+        esp_near(self.handle, pos, q, forces, add, out)
+        o = out.cpu().numpy()
+        W = np.array([[o[1], o[4], o[5]], [o[4], o[2], o[6]], [o[5], o[6], o[3]]])
+        return float(o[0]), W, forces
 
     def info(self) -> dict:
         return esp_plan_info(self.handle)

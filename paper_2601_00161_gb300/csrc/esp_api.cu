@@ -96,6 +96,18 @@ struct esp_plan_s {
   void* g_f = nullptr;
   double* g_acc = nullptr;
   bool g_prof = false;
+  // near part (allocated by the first esp_near call; the cell list follows the cell)
+  esp::NearGeom ng{};
+  int near_cells_alloc = 0;
+  int near_ndeg = 0;
+  void* d_neartab = nullptr;
+  int* d_ncount = nullptr;  // atoms per cell (zero between calls)
+  int* d_ncoff = nullptr;   // exclusive offsets (cells + 1)
+  int* d_ncell = nullptr;
+  int* d_nrank = nullptr;
+  void* d_nxq_tmp = nullptr;
+  void* d_nxq = nullptr;
+  int* d_nidx = nullptr;
   // per-stage CUDA events (esp_profile)
   bool profiling = false;
   cudaEvent_t ev[16] = {};
@@ -255,6 +267,44 @@ int build_window_tables(esp_plan_t p, std::vector<double>& tab) {
   return ESP_OK;
 }
 
+// Near kernel on u = r / r_c in [0, 1], kRadialPieces pieces in (u - centre): 1 - phi_0(u)
+// and F_N(u) = 1 - phi_0(u) + u psi_0(u) / C_0, phi_0(u) = (1 / C_0) int_0^u psi_0 by
+// 40-point Gauss-Legendre (Sec. 3.1, eqs. (decomposition), (mathFN)).
+int build_near_tables(esp_plan_t p, std::vector<double>& tab) {
+  const esp::Prolate& pr = p->pswf;
+  const double tol = p->fp64 ? 3e-15 : 2e-8;
+  const int NR = esp::kRadialPieces;
+  std::vector<double> gx, gw;
+  esp::gauss_legendre(40, gx, gw);
+  auto phi0 = [&](double u) {
+    double s = 0.0;
+    for (size_t k = 0; k < gx.size(); ++k) s += gw[k] * pr.eval(0.5 * u * (gx[k] + 1.0));
+    return 0.5 * u * s / pr.C0;
+  };
+  auto g1 = [&](double u) { return 1.0 - phi0(u); };
+  auto g2 = [&](double u) { return 1.0 - phi0(u) + u * pr.eval(u) / pr.C0; };
+  for (int deg = 6; deg <= esp::kMaxDeg; ++deg) {
+    tab.assign(2 * NR * (deg + 1), 0.0);
+    std::vector<double> coef(deg + 1);
+    double err = 0.0;
+    for (int j = 0; j < NR; ++j) {
+      const double lo = (double)j / NR, hi = (double)(j + 1) / NR;
+      double e1 = esp::fit_piece(g1, lo, hi, deg, coef.data());
+      for (int k = 0; k <= deg; ++k) tab[j * (deg + 1) + k] = coef[k];
+      double e2 = esp::fit_piece(g2, lo, hi, deg, coef.data());
+      for (int k = 0; k <= deg; ++k) tab[(NR + j) * (deg + 1) + k] = coef[k];
+      err = std::max(err, std::max(e1, e2));  // both functions are 1 at u = 0
+    }
+    if (err <= tol || deg == esp::kMaxDeg) {
+      if (err > (p->fp64 ? 1e-14 : 5e-8))
+        return fail(p, ESP_ERR_ARG, "near-kernel polynomial fit did not converge");
+      p->near_ndeg = deg;
+      return ESP_OK;
+    }
+  }
+  return ESP_OK;
+}
+
 // Radial psi_0 and psi_0' on x in [0, 1] (the Fourier kernel of eq. (UF) and its
 // derivative in eq. (Far)), kRadialPieces pieces, coefficients of (x - centre)^k.
 int build_radial_tables(esp_plan_t p, std::vector<double>& tab) {
@@ -315,7 +365,9 @@ void release(esp_plan_t p) {
   void* bufs[] = {p->d_wtab,      p->d_radtab,    p->d_invw2,    p->d_grid,      p->d_spec,  p->d_tq,
                   p->d_count,     p->d_offset,    p->d_ptile,    p->d_prank,     p->d_plb,  p->d_suboff, p->d_binpart, p->d_bsum,
                   p->d_sorted_tq, p->d_sorted_lb, p->d_sorted_idx, p->d_accum,   p->d_partials,
-                  p->d_counter,   p->d_io_pos,    p->d_io_q,     p->d_io_f};
+                  p->d_counter,   p->d_io_pos,    p->d_io_q,     p->d_io_f,
+                  p->d_neartab,   p->d_ncount,    p->d_ncoff,    p->d_ncell,     p->d_nrank,
+                  p->d_nxq_tmp,   p->d_nxq,       p->d_nidx};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (p->h_accum) cudaFreeHost(p->h_accum);
@@ -736,6 +788,65 @@ int esp_forces_from_spectrum(esp_plan_t p, void* forces) {
                                  p->d_sorted_tq, p->d_sorted_lb, p->d_sorted_idx, p->d_offset,
                                  work, p->d_wtab, p->d_grid, forces, st));
   p->spectrum_kept = false;
+  return ESP_OK;
+}
+
+int esp_near(esp_plan_t p, const void* pos, const void* q, void* forces, int add,
+             double* d_out) {
+  if (!p) return fail(nullptr, ESP_ERR_ARG, "plan is NULL");
+  if (!d_out || (p->n > 0 && (!pos || !q || !forces)))
+    return fail(p, ESP_ERR_ARG, "pos, q, forces or d_out is NULL");
+  DeviceGuard guard(p->device);
+  // cell list of the current cell: nc bins of at least r_c per axis, R neighbours each side
+  esp::NearGeom& ng = p->ng;
+  int ncells = 1;
+  for (int d = 0; d < 3; ++d) {
+    // perpendicular width of the cell along reduced axis d: 1 / |row d of h^{-1}|
+    const double* r = p->hinv + 3 * d;
+    const double width = 1.0 / std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
+    ng.nc[d] = std::max(1, (int)std::min(1024.0, std::floor(width / p->rc)));
+    ng.R[d] = std::max(1, (int)std::ceil(p->rc * ng.nc[d] / width));
+    ncells *= ng.nc[d];
+  }
+  for (int i = 0; i < 9; ++i) {
+    ng.h[i] = p->h[i];
+    ng.hinv[i] = p->hinv[i];
+  }
+  ng.rc = p->rc;
+  ng.inv_rc = 1.0 / p->rc;
+  if (!p->d_neartab) {
+    std::vector<double> tab;
+    int rc = build_near_tables(p, tab);
+    if (rc != ESP_OK) return rc;
+    if ((rc = upload(p, &p->d_neartab, tab)) != ESP_OK) return rc;
+    const size_t es = p->fp64 ? 8 : 4;
+    const size_t nn = std::max<int64_t>(p->n, 1);
+    ESP_CUDA(p, cudaMalloc(&p->d_ncell, nn * sizeof(int)));
+    ESP_CUDA(p, cudaMalloc(&p->d_nrank, nn * sizeof(int)));
+    ESP_CUDA(p, cudaMalloc(&p->d_nidx, nn * sizeof(int)));
+    ESP_CUDA(p, cudaMalloc(&p->d_nxq_tmp, nn * 4 * es));
+    ESP_CUDA(p, cudaMalloc(&p->d_nxq, nn * 4 * es));
+  }
+  ng.ndeg = p->near_ndeg;
+  if (ncells > p->near_cells_alloc) {
+    if (p->d_ncount) cudaFree(p->d_ncount);
+    if (p->d_ncoff) cudaFree(p->d_ncoff);
+    p->d_ncount = nullptr;
+    p->d_ncoff = nullptr;
+    p->near_cells_alloc = 0;
+    ESP_CUDA(p, cudaMalloc(&p->d_ncount, (size_t)ncells * sizeof(int)));
+    ESP_CUDA(p, cudaMalloc(&p->d_ncoff, ((size_t)ncells + 1) * sizeof(int)));
+    ESP_CUDA(p, cudaMemset(p->d_ncount, 0, (size_t)ncells * sizeof(int)));
+    p->near_cells_alloc = ncells;
+  }
+  cudaStream_t st = p->stream;
+  ESP_CUDA(p, esp::launch_near_bin(p->io_double, p->fp64, pos, q, p->n, ng, p->d_ncount,
+                                   p->d_ncell, p->d_nrank, p->d_nxq_tmp, st));
+  ESP_CUDA(p, esp::launch_near_scan(p->d_ncount, p->d_ncoff, ncells, st));
+  ESP_CUDA(p, esp::launch_near_scatter(p->fp64, p->n, p->d_ncell, p->d_nrank, p->d_ncoff,
+                                       p->d_nxq_tmp, p->d_nxq, p->d_nidx, st));
+  ESP_CUDA(p, esp::launch_near_pairs(p->fp64, p->io_double, ng, ncells, p->d_ncoff, p->d_nxq,
+                                     p->d_nidx, p->d_neartab, forces, add, d_out, st));
   return ESP_OK;
 }
 

@@ -1249,6 +1249,208 @@ __global__ void __launch_bounds__(kThreads) k_cell_grad(const IO* __restrict__ p
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Near part of the split (Sec. 3, eqs. (UN), (Fc), (PinsN) with the sign of -dU/dh h^T):
+// U_N = 1/2 sum' q_i q_j N(r), N(r) = (1 - phi_0(r/r_c)) / r on r <= r_c; the force on i
+// sum_j q_i q_j F_N(r) r_ij / r^3 with F_N = 1 - phi_0 + u psi_0(u) / C_0; the virial
+// 1/2 sum' q_i q_j F_N(r) r_ij (x) r_ij / r^3.  Both functions of u = r / r_c come from
+// piecewise polynomials (the radial table layout).
+
+// FP32 sums compensated, FP64 sums plain
+template <typename R>
+struct Sum;
+template <>
+struct Sum<float> {
+  DF d;
+  __device__ __forceinline__ void add(float v) { d.add(v); }
+  __device__ __forceinline__ double value() const { return (double)d.hi + (double)d.lo; }
+};
+template <>
+struct Sum<double> {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ double value() const { return v; }
+};
+
+template <typename IO, typename R>
+__global__ void __launch_bounds__(kThreads) k_near_bin(const IO* __restrict__ pos,
+                                                       const IO* __restrict__ q, int64_t n,
+                                                       NearGeom ng, int* __restrict__ ccount,
+                                                       int* __restrict__ cell,
+                                                       int* __restrict__ rank,
+                                                       typename Vec4<R>::T* __restrict__ xq) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double r[3] = {(double)pos[3 * i], (double)pos[3 * i + 1], (double)pos[3 * i + 2]};
+    const double qi = (double)q[i];
+    if (!(isfinite(r[0]) && isfinite(r[1]) && isfinite(r[2]) && isfinite(qi))) {
+      cell[i] = -1;
+      continue;
+    }
+    int c[3];
+    double f[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      double sd = ng.hinv[3 * d] * r[0] + ng.hinv[3 * d + 1] * r[1] + ng.hinv[3 * d + 2] * r[2];
+      sd -= floor(sd);
+      if (sd >= 1.0) sd = 0.0;
+      c[d] = min((int)(sd * ng.nc[d]), ng.nc[d] - 1);
+      f[d] = sd - (double)c[d] / ng.nc[d];  // reduced offset from the cell corner
+    }
+    const int id = (c[0] * ng.nc[1] + c[1]) * ng.nc[2] + c[2];
+    cell[i] = id;
+    rank[i] = atomicAdd(&ccount[id], 1);
+    typename Vec4<R>::T v;
+    v.x = (R)(ng.h[0] * f[0] + ng.h[1] * f[1] + ng.h[2] * f[2]);
+    v.y = (R)(ng.h[3] * f[0] + ng.h[4] * f[1] + ng.h[5] * f[2]);
+    v.z = (R)(ng.h[6] * f[0] + ng.h[7] * f[1] + ng.h[8] * f[2]);
+    v.w = (R)qi;
+    xq[i] = v;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_near_scan(int* __restrict__ ccount,
+                                                        int* __restrict__ coff, int ncells) {
+  __shared__ int wsum[kThreads / 32];
+  int carry = 0;
+  for (int base = 0; base < ncells; base += 4 * kThreads) {
+    int v[4], s = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int i = base + 4 * threadIdx.x + k;
+      v[k] = i < ncells ? ccount[i] : 0;
+      if (i < ncells) ccount[i] = 0;
+      s += v[k];
+    }
+    int total;
+    int o = block_exclusive_scan(s, wsum, &total) + carry;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int i = base + 4 * threadIdx.x + k;
+      if (i < ncells) coff[i] = o;
+      o += v[k];
+    }
+    carry += total;
+    __syncthreads();  // wsum is reused
+  }
+  if (threadIdx.x == 0) coff[ncells] = carry;
+}
+
+template <typename V>
+__global__ void __launch_bounds__(kThreads) k_near_scatter(int64_t n, const int* __restrict__ cell,
+                                                           const int* __restrict__ rank,
+                                                           const int* __restrict__ coff,
+                                                           const V* __restrict__ xq_tmp,
+                                                           V* __restrict__ xq,
+                                                           int* __restrict__ idx) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = cell[i];
+    if (c < 0) continue;
+    const int dst = coff[c] + rank[i];
+    xq[dst] = xq_tmp[i];
+    idx[dst] = (int)i;
+  }
+}
+
+// One CTA per cell: its atoms (kThreads at a time, one per thread) against every atom of
+// the neighbour cells, which are staged in shared memory.  The pair vector of an atom in
+// cell c and an image in the unwrapped neighbour cell c + o is x_i - x_j - h o / nc, x the
+// positions relative to the cell corners, so FP32 differences stay small.  A full list:
+// every pair is met from both ends, the energy and virial take half of each.
+template <typename R, typename IO>
+__global__ void __launch_bounds__(kThreads) k_near_pairs(NearGeom ng, const int* __restrict__ coff,
+                                                         const typename Vec4<R>::T* __restrict__ xq,
+                                                         const int* __restrict__ idx,
+                                                         const R* __restrict__ tab,
+                                                         IO* __restrict__ forces, int add,
+                                                         double* __restrict__ out) {
+  using V4 = typename Vec4<R>::T;
+  __shared__ V4 S[kThreads];
+  __shared__ double part[kThreads / 32][7];
+  const int C = blockIdx.x;
+  const int c2 = C % ng.nc[2], c1 = (C / ng.nc[2]) % ng.nc[1], c0 = C / (ng.nc[2] * ng.nc[1]);
+  const int ib = coff[C], ie = coff[C + 1];
+  const R rc2 = (R)(ng.rc * ng.rc), inv_rc = (R)ng.inv_rc;
+  Sum<R> U, W[6];
+  for (int i0 = ib; i0 < ie; i0 += kThreads) {
+    const int i = i0 + threadIdx.x;
+    const bool valid = i < ie;
+    const V4 xi = valid ? xq[i] : V4{};
+    Sum<R> fx, fy, fz;
+    for (int o0 = -ng.R[0]; o0 <= ng.R[0]; ++o0)
+      for (int o1 = -ng.R[1]; o1 <= ng.R[1]; ++o1)
+        for (int o2 = -ng.R[2]; o2 <= ng.R[2]; ++o2) {
+          const int n0 = c0 + o0, n1 = c1 + o1, n2 = c2 + o2;
+          const int w0 = ((n0 % ng.nc[0]) + ng.nc[0]) % ng.nc[0];
+          const int w1 = ((n1 % ng.nc[1]) + ng.nc[1]) % ng.nc[1];
+          const int w2 = ((n2 % ng.nc[2]) + ng.nc[2]) % ng.nc[2];
+          const int Cn = (w0 * ng.nc[1] + w1) * ng.nc[2] + w2;
+          // h o / nc, the corner of the unwrapped neighbour relative to this cell's corner
+          const double f0 = (double)o0 / ng.nc[0], f1 = (double)o1 / ng.nc[1],
+                       f2 = (double)o2 / ng.nc[2];
+          const R dx = (R)(ng.h[0] * f0 + ng.h[1] * f1 + ng.h[2] * f2);
+          const R dy = (R)(ng.h[3] * f0 + ng.h[4] * f1 + ng.h[5] * f2);
+          const R dz = (R)(ng.h[6] * f0 + ng.h[7] * f1 + ng.h[8] * f2);
+          const int jb = coff[Cn], je = coff[Cn + 1];
+          for (int j0 = jb; j0 < je; j0 += kThreads) {
+            __syncthreads();  // the previous batch is consumed
+            if (j0 + (int)threadIdx.x < je) S[threadIdx.x] = xq[j0 + threadIdx.x];
+            __syncthreads();
+            const int cnt = min(kThreads, je - j0);
+            if (!valid) continue;
+            for (int jj = 0; jj < cnt; ++jj) {
+              const V4 xj = S[jj];
+              const R rx = (xi.x - xj.x) - dx, ry = (xi.y - xj.y) - dy, rz = (xi.z - xj.z) - dz;
+              const R r2 = rx * rx + ry * ry + rz * rz;
+              if (!(r2 > R(0) && r2 <= rc2)) continue;
+              const R r = sqrt(r2);
+              const R inv_r = R(1) / r;
+              R g1, g2;
+              radial_eval<R>(tab, ng.ndeg, r * inv_rc, &g1, &g2);
+              const R qq = xi.w * xj.w;
+              const R e = qq * g1 * inv_r;
+              const R f = qq * g2 * inv_r * inv_r * inv_r;
+              fx.add(f * rx);
+              fy.add(f * ry);
+              fz.add(f * rz);
+              const R hf = R(0.5) * f;
+              U.add(R(0.5) * e);
+              W[0].add(hf * rx * rx);
+              W[1].add(hf * ry * ry);
+              W[2].add(hf * rz * rz);
+              W[3].add(hf * rx * ry);
+              W[4].add(hf * rx * rz);
+              W[5].add(hf * ry * rz);
+            }
+          }
+        }
+    if (valid) {
+      const int a = idx[i];
+      const double F[3] = {fx.value(), fy.value(), fz.value()};
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const double base = add ? (double)forces[3 * (int64_t)a + d] : 0.0;
+        forces[3 * (int64_t)a + d] = (IO)(base + F[d]);
+      }
+    }
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double v[7] = {U.value(), W[0].value(), W[1].value(), W[2].value(),
+                 W[3].value(), W[4].value(), W[5].value()};
+#pragma unroll
+  for (int e = 0; e < 7; ++e) {
+    const double t = warp_sum(v[e]);
+    if (lane == 0) part[warp][e] = t;
+  }
+  __syncthreads();
+  if (threadIdx.x < 7) {
+    double t = 0.0;
+    for (int w = 0; w < kThreads / 32; ++w) t += part[w][threadIdx.x];
+    if (t != 0.0) atomicAdd(out + threadIdx.x, t);
+  }
+}
+
 int grid_blocks(int64_t n) {
   int64_t b = (n + kThreads - 1) / kThreads;
   if (b < 1) b = 1;
@@ -1463,6 +1665,62 @@ cudaError_t launch_cell_grad(bool io_double, const void* pos, const void* forces
   else
     k_cell_grad<float><<<nb, kThreads, 0, st>>>((const float*)pos, (const float*)forces, n, c,
                                                 accum, grad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_near_bin(bool io_double, bool fp64, const void* pos, const void* q,
+                            int64_t n, const NearGeom& ng, int* ccount, int* cell, int* rank,
+                            void* xq_tmp, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int nb = grid_blocks(n);
+  if (io_double && fp64)
+    k_near_bin<double, double><<<nb, kThreads, 0, st>>>((const double*)pos, (const double*)q, n,
+                                                        ng, ccount, cell, rank, (double4*)xq_tmp);
+  else if (io_double)
+    k_near_bin<double, float><<<nb, kThreads, 0, st>>>((const double*)pos, (const double*)q, n,
+                                                       ng, ccount, cell, rank, (float4*)xq_tmp);
+  else if (fp64)
+    k_near_bin<float, double><<<nb, kThreads, 0, st>>>((const float*)pos, (const float*)q, n, ng,
+                                                       ccount, cell, rank, (double4*)xq_tmp);
+  else
+    k_near_bin<float, float><<<nb, kThreads, 0, st>>>((const float*)pos, (const float*)q, n, ng,
+                                                      ccount, cell, rank, (float4*)xq_tmp);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_near_scan(int* ccount, int* coff, int ncells, cudaStream_t st) {
+  k_near_scan<<<1, kThreads, 0, st>>>(ccount, coff, ncells);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_near_scatter(bool fp64, int64_t n, const int* cell, const int* rank,
+                                const int* coff, const void* xq_tmp, void* xq, int* idx,
+                                cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int nb = grid_blocks(n);
+  if (fp64)
+    k_near_scatter<double4><<<nb, kThreads, 0, st>>>(n, cell, rank, coff, (const double4*)xq_tmp,
+                                                     (double4*)xq, idx);
+  else
+    k_near_scatter<float4><<<nb, kThreads, 0, st>>>(n, cell, rank, coff, (const float4*)xq_tmp,
+                                                    (float4*)xq, idx);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_near_pairs(bool fp64, bool io_double, const NearGeom& ng, int ncells,
+                             const int* coff, const void* xq, const int* idx, const void* tab,
+                             void* forces, int add, double* out, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out, 0, 7 * sizeof(double), st);
+  if (e != cudaSuccess || ncells <= 0) return e;
+  if (fp64)
+    k_near_pairs<double, double><<<ncells, kThreads, 0, st>>>(
+        ng, coff, (const double4*)xq, idx, (const double*)tab, (double*)forces, add, out);
+  else if (io_double)
+    k_near_pairs<float, double><<<ncells, kThreads, 0, st>>>(
+        ng, coff, (const float4*)xq, idx, (const float*)tab, (double*)forces, add, out);
+  else
+    k_near_pairs<float, float><<<ncells, kThreads, 0, st>>>(
+        ng, coff, (const float4*)xq, idx, (const float*)tab, (float*)forces, add, out);
   return cudaGetLastError();
 }
 

@@ -61,6 +61,18 @@ struct GatherGeom {
   double fscale;  // 1 / (V Mtot^2)
 };
 
+// Near (real-space) part of the split: a cell list with nc[d] >= 1 bins per reduced axis
+// (each bin at least r_c thick when nc[d] > 1) and R[d] neighbour bins on either side, so
+// every pair and periodic image within r_c is found exactly once.
+struct NearGeom {
+  int nc[3];
+  int R[3];
+  double h[9];     // row-major
+  double hinv[9];  // row-major
+  double rc, inv_rc;
+  int ndeg;        // degree of the near-kernel polynomials (kRadialPieces pieces in u)
+};
+
 // Constants of the cell gradient: h^{-1} (row-major) and U_bg = bg_coef * (sum q)^2.
 struct CellGradArgs {
   double hinv[9];
@@ -161,6 +173,22 @@ cudaError_t launch_gather(bool fp64, bool io_double, const GatherGeom& gg, int n
                           int nblocks, const void* sorted_tq, const int* sorted_lb,
                           const int* sorted_idx, const int* toff, int* work, const void* wtab,
                           const void* grid, void* forces, cudaStream_t st);
+// Near part.  bin: cell id, rank within the cell and the atom's position relative to its
+// cell corner (with q) in the input order; ccount (ncells ints) zero on entry.  scan:
+// coff[0..ncells] exclusive offsets, ccount zeroed again.  scatter: cell order.  pairs:
+// forces (overwritten, or added to when add != 0) and out[0..6] = U_N, W_N xx yy zz xy xz
+// yz (overwritten).
+cudaError_t launch_near_bin(bool io_double, bool fp64, const void* pos, const void* q,
+                            int64_t n, const NearGeom& ng, int* ccount, int* cell, int* rank,
+                            void* xq_tmp, cudaStream_t st);
+cudaError_t launch_near_scan(int* ccount, int* coff, int ncells, cudaStream_t st);
+cudaError_t launch_near_scatter(bool fp64, int64_t n, const int* cell, const int* rank,
+                                const int* coff, const void* xq_tmp, void* xq, int* idx,
+                                cudaStream_t st);
+cudaError_t launch_near_pairs(bool fp64, bool io_double, const NearGeom& ng, int ncells,
+                             const int* coff, const void* xq, const int* idx, const void* tab,
+                             void* forces, int add, double* out, cudaStream_t st);
+
 // dU/dh at fixed positions into grad[9] (row-major): -W h^{-T} + sum_i F_i (h^{-1} r_i)^T
 cudaError_t launch_cell_grad(bool io_double, const void* pos, const void* forces, int64_t n,
                              const CellGradArgs& c, const double* accum, double* grad,
