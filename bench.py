@@ -400,6 +400,25 @@ def esp_arm(args):
                        "ms_per_step": round(tot / args.steps, 5),
                        "step": "bin/sort, spread, forward FFT, scaling + energy/virial reduction"}
 
+    # the near part of the split on the same workload (esp_near; not part of the
+    # long-range metric): pair sums within r_c, forces added onto the long-range ones
+    near_out = torch.empty(7, dtype=torch.float64, device="cuda")
+    for _ in range(2):
+        esp.esp_near(plan.handle, pos, q, F, 1, near_out)
+    tot = 0.0
+    n_near = max(3, min(args.steps, 10))
+    for _ in range(n_near):
+        flush.zero_()
+        e0.record(stream)
+        esp.esp_near(plan.handle, pos, q, F, 1, near_out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tot += e0.elapsed_time(e1)
+    near_ms = tot / n_near
+    near_part = {"ms": round(near_ms, 4),
+                 "step": "near part of the split (esp_near): device cell list, pairs within r_c, "
+                         "energy, virial, forces added onto the long-range ones"}
+
     launches_per_step = 7  # bin, scan (2), scatter, spread, scale, gather
     out = None
     if rank == 0:
@@ -423,6 +442,7 @@ def esp_arm(args):
             "roofline": roofline,
             "other_bounds": other,
             "energy_pressure_only": energy_pressure,
+            "near_part": near_part,
             "e2e": e2e,
             "gpu_launches": launches_per_step * args.steps,
             "clocks": clk,

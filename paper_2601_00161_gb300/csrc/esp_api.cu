@@ -808,6 +808,13 @@ int esp_near(esp_plan_t p, const void* pos, const void* q, void* forces, int add
     ng.R[d] = std::max(1, (int)std::ceil(p->rc * ng.nc[d] / width));
     ncells *= ng.nc[d];
   }
+  {
+    // neighbour offsets (2R+1)^3: the kernel keeps their vectors in shared memory
+    const long noff = (long)(2 * ng.R[0] + 1) * (2 * ng.R[1] + 1) * (2 * ng.R[2] + 1);
+    if (noff > 512)
+      return fail(p, ESP_ERR_SUPPORT, "cell too narrow for the near-part cell list (more than "
+                                      "512 neighbour images): r_c is many cell widths");
+  }
   for (int i = 0; i < 9; ++i) {
     ng.h[i] = p->h[i];
     ng.hinv[i] = p->hinv[i];

@@ -1353,11 +1353,29 @@ __global__ void __launch_bounds__(kThreads) k_near_scatter(int64_t n, const int*
   }
 }
 
-// One CTA per cell: its atoms (kThreads at a time, one per thread) against every atom of
-// the neighbour cells, which are staged in shared memory.  The pair vector of an atom in
-// cell c and an image in the unwrapped neighbour cell c + o is x_i - x_j - h o / nc, x the
-// positions relative to the cell corners, so FP32 differences stay small.  A full list:
-// every pair is met from both ends, the energy and virial take half of each.
+// One CTA per cell, one warp per atom of the cell at a time.  The lanes stride over the
+// atoms of the neighbour cells (coalesced, shared through L1 by the CTA's warps); the
+// pair vector of an atom in cell c and an image in the unwrapped neighbour c + o is
+// x_i - x_j - h o / nc, x the positions relative to the cell corners, so FP32 differences
+// stay small.  Pairs within r_c go through a warp queue (ballot + population count) and
+// are worked 32 at a time, every lane busy.  A full list: each pair is met from both
+// ends, the energy and virial take half of each.
+// sum over the warp of a compensated FP32 value (or a double on the FP64 path)
+__device__ __forceinline__ double warp_total(const Sum<float>& s) {
+  DF v = s.d;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    DF w;
+    w.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    w.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    v.add(w);
+  }
+  return (double)v.hi + (double)v.lo;
+}
+__device__ __forceinline__ double warp_total(const Sum<double>& s) { return warp_sum(s.v); }
+
+// noff = (2 R0 + 1)(2 R1 + 1)(2 R2 + 1) neighbour offsets; dynamic shared memory holds
+// their displacement vectors h o / nc and wrapped cell ids for the CTA's cell.
 template <typename R, typename IO>
 __global__ void __launch_bounds__(kThreads) k_near_pairs(NearGeom ng, const int* __restrict__ coff,
                                                          const typename Vec4<R>::T* __restrict__ xq,
@@ -1366,76 +1384,114 @@ __global__ void __launch_bounds__(kThreads) k_near_pairs(NearGeom ng, const int*
                                                          IO* __restrict__ forces, int add,
                                                          double* __restrict__ out) {
   using V4 = typename Vec4<R>::T;
-  __shared__ V4 S[kThreads];
+  constexpr int kQ = 64;  // queue ring per warp
+  __shared__ V4 Q[kThreads / 32][kQ];  // (r_ij, q_j)
   __shared__ double part[kThreads / 32][7];
+  extern __shared__ __align__(16) unsigned char near_smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned lt = (1u << lane) - 1u;
+  V4* q_w = Q[warp];
   const int C = blockIdx.x;
   const int c2 = C % ng.nc[2], c1 = (C / ng.nc[2]) % ng.nc[1], c0 = C / (ng.nc[2] * ng.nc[1]);
   const int ib = coff[C], ie = coff[C + 1];
+  const int s0 = 2 * ng.R[0] + 1, s1 = 2 * ng.R[1] + 1, s2 = 2 * ng.R[2] + 1;
+  const int noff = s0 * s1 * s2;
+  V4* OFF = reinterpret_cast<V4*>(near_smem);
+  int* NC = reinterpret_cast<int*>(near_smem + (size_t)noff * sizeof(V4));
+  for (int t = threadIdx.x; t < noff; t += blockDim.x) {
+    const int o0 = t / (s1 * s2) - ng.R[0], o1 = (t / s2) % s1 - ng.R[1], o2 = t % s2 - ng.R[2];
+    const int w0 = (((c0 + o0) % ng.nc[0]) + ng.nc[0]) % ng.nc[0];
+    const int w1 = (((c1 + o1) % ng.nc[1]) + ng.nc[1]) % ng.nc[1];
+    const int w2 = (((c2 + o2) % ng.nc[2]) + ng.nc[2]) % ng.nc[2];
+    NC[t] = (w0 * ng.nc[1] + w1) * ng.nc[2] + w2;
+    // h o / nc: the corner of the unwrapped neighbour relative to this cell's corner
+    const double f0 = (double)o0 / ng.nc[0], f1 = (double)o1 / ng.nc[1], f2 = (double)o2 / ng.nc[2];
+    V4 d;
+    d.x = (R)(ng.h[0] * f0 + ng.h[1] * f1 + ng.h[2] * f2);
+    d.y = (R)(ng.h[3] * f0 + ng.h[4] * f1 + ng.h[5] * f2);
+    d.z = (R)(ng.h[6] * f0 + ng.h[7] * f1 + ng.h[8] * f2);
+    d.w = R(0);
+    OFF[t] = d;
+  }
+  __syncthreads();
   const R rc2 = (R)(ng.rc * ng.rc), inv_rc = (R)ng.inv_rc;
-  Sum<R> U, W[6];
-  for (int i0 = ib; i0 < ie; i0 += kThreads) {
-    const int i = i0 + threadIdx.x;
-    const bool valid = i < ie;
-    const V4 xi = valid ? xq[i] : V4{};
-    Sum<R> fx, fy, fz;
-    for (int o0 = -ng.R[0]; o0 <= ng.R[0]; ++o0)
-      for (int o1 = -ng.R[1]; o1 <= ng.R[1]; ++o1)
-        for (int o2 = -ng.R[2]; o2 <= ng.R[2]; ++o2) {
-          const int n0 = c0 + o0, n1 = c1 + o1, n2 = c2 + o2;
-          const int w0 = ((n0 % ng.nc[0]) + ng.nc[0]) % ng.nc[0];
-          const int w1 = ((n1 % ng.nc[1]) + ng.nc[1]) % ng.nc[1];
-          const int w2 = ((n2 % ng.nc[2]) + ng.nc[2]) % ng.nc[2];
-          const int Cn = (w0 * ng.nc[1] + w1) * ng.nc[2] + w2;
-          // h o / nc, the corner of the unwrapped neighbour relative to this cell's corner
-          const double f0 = (double)o0 / ng.nc[0], f1 = (double)o1 / ng.nc[1],
-                       f2 = (double)o2 / ng.nc[2];
-          const R dx = (R)(ng.h[0] * f0 + ng.h[1] * f1 + ng.h[2] * f2);
-          const R dy = (R)(ng.h[3] * f0 + ng.h[4] * f1 + ng.h[5] * f2);
-          const R dz = (R)(ng.h[6] * f0 + ng.h[7] * f1 + ng.h[8] * f2);
+  Sum<R> U, W[6];  // per lane over all of the warp's pairs
+
+  for (int i = ib + warp; i < ie; i += kThreads / 32) {
+    const V4 xi = xq[i];
+    Sum<R> fx, fy, fz;  // per lane, this atom
+    // the pair terms of queue entries [h, h + m), lane l taking entry h + l
+    auto work = [&](int h, int m) {
+      if (lane < m) {
+        const V4 e4 = q_w[(h + lane) & (kQ - 1)];
+        const R rx = e4.x, ry = e4.y, rz = e4.z;
+        const R r2 = rx * rx + ry * ry + rz * rz;
+        R inv_r, r;
+        if constexpr (std::is_same<R, float>::value) {
+          inv_r = rsqrtf(r2);
+          r = r2 * inv_r;
+        } else {
+          r = sqrt(r2);
+          inv_r = R(1) / r;
+        }
+        R g1, g2;
+        radial_eval<R>(tab, ng.ndeg, r * inv_rc, &g1, &g2);
+        const R qq = xi.w * e4.w;
+        const R e = qq * g1 * inv_r;
+        const R f = qq * g2 * inv_r * inv_r * inv_r;
+        fx.add(f * rx);
+        fy.add(f * ry);
+        fz.add(f * rz);
+        const R hf = R(0.5) * f;
+        U.add(R(0.5) * e);
+        W[0].add(hf * rx * rx);
+        W[1].add(hf * ry * ry);
+        W[2].add(hf * rz * rz);
+        W[3].add(hf * rx * ry);
+        W[4].add(hf * rx * rz);
+        W[5].add(hf * ry * rz);
+      }
+    };
+    int qh = 0, qn = 0;  // queue head and length (warp-uniform)
+    for (int t = 0; t < noff; ++t) {
+          const V4 d = OFF[t];
+          const R dx = d.x, dy = d.y, dz = d.z;
+          const int Cn = NC[t];
           const int jb = coff[Cn], je = coff[Cn + 1];
-          for (int j0 = jb; j0 < je; j0 += kThreads) {
-            __syncthreads();  // the previous batch is consumed
-            if (j0 + (int)threadIdx.x < je) S[threadIdx.x] = xq[j0 + threadIdx.x];
-            __syncthreads();
-            const int cnt = min(kThreads, je - j0);
-            if (!valid) continue;
-            for (int jj = 0; jj < cnt; ++jj) {
-              const V4 xj = S[jj];
-              const R rx = (xi.x - xj.x) - dx, ry = (xi.y - xj.y) - dy, rz = (xi.z - xj.z) - dz;
-              const R r2 = rx * rx + ry * ry + rz * rz;
-              if (!(r2 > R(0) && r2 <= rc2)) continue;
-              const R r = sqrt(r2);
-              const R inv_r = R(1) / r;
-              R g1, g2;
-              radial_eval<R>(tab, ng.ndeg, r * inv_rc, &g1, &g2);
-              const R qq = xi.w * xj.w;
-              const R e = qq * g1 * inv_r;
-              const R f = qq * g2 * inv_r * inv_r * inv_r;
-              fx.add(f * rx);
-              fy.add(f * ry);
-              fz.add(f * rz);
-              const R hf = R(0.5) * f;
-              U.add(R(0.5) * e);
-              W[0].add(hf * rx * rx);
-              W[1].add(hf * ry * ry);
-              W[2].add(hf * rz * rz);
-              W[3].add(hf * rx * ry);
-              W[4].add(hf * rx * rz);
-              W[5].add(hf * ry * rz);
+          for (int j0 = jb; j0 < je; j0 += 32) {
+            const int j = j0 + lane;
+            bool pass = false;
+            V4 ent{};
+            if (j < je) {
+              const V4 xj = xq[j];
+              ent.x = (xi.x - xj.x) - dx;
+              ent.y = (xi.y - xj.y) - dy;
+              ent.z = (xi.z - xj.z) - dz;
+              ent.w = xj.w;
+              const R r2 = ent.x * ent.x + ent.y * ent.y + ent.z * ent.z;
+              pass = r2 > R(0) && r2 <= rc2;
+            }
+            const unsigned m = __ballot_sync(0xffffffffu, pass);
+            if (pass) q_w[(qh + qn + __popc(m & lt)) & (kQ - 1)] = ent;
+            qn += __popc(m);
+            __syncwarp();
+            if (qn >= 32) {
+              work(qh, 32);
+              qh = (qh + 32) & (kQ - 1);
+              qn -= 32;
+              __syncwarp();  // the worked entries may be overwritten now
             }
           }
-        }
-    if (valid) {
+    }
+    work(qh, qn);
+    __syncwarp();
+    const double F[3] = {warp_total(fx), warp_total(fy), warp_total(fz)};
+    if (lane < 3) {
       const int a = idx[i];
-      const double F[3] = {fx.value(), fy.value(), fz.value()};
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        const double base = add ? (double)forces[3 * (int64_t)a + d] : 0.0;
-        forces[3 * (int64_t)a + d] = (IO)(base + F[d]);
-      }
+      const double base = add ? (double)forces[3 * (int64_t)a + lane] : 0.0;
+      forces[3 * (int64_t)a + lane] = (IO)(base + F[lane]);
     }
   }
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double v[7] = {U.value(), W[0].value(), W[1].value(), W[2].value(),
                  W[3].value(), W[4].value(), W[5].value()};
 #pragma unroll
@@ -1712,14 +1768,17 @@ cudaError_t launch_near_pairs(bool fp64, bool io_double, const NearGeom& ng, int
                              void* forces, int add, double* out, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(out, 0, 7 * sizeof(double), st);
   if (e != cudaSuccess || ncells <= 0) return e;
+  const size_t noff = (size_t)(2 * ng.R[0] + 1) * (2 * ng.R[1] + 1) * (2 * ng.R[2] + 1);
+  const size_t smem = noff * ((fp64 ? sizeof(double4) : sizeof(float4)) + sizeof(int));
+  if (smem > 24 * 1024) return cudaErrorInvalidValue;  // the host rejects such cells first
   if (fp64)
-    k_near_pairs<double, double><<<ncells, kThreads, 0, st>>>(
+    k_near_pairs<double, double><<<ncells, kThreads, smem, st>>>(
         ng, coff, (const double4*)xq, idx, (const double*)tab, (double*)forces, add, out);
   else if (io_double)
-    k_near_pairs<float, double><<<ncells, kThreads, 0, st>>>(
+    k_near_pairs<float, double><<<ncells, kThreads, smem, st>>>(
         ng, coff, (const float4*)xq, idx, (const float*)tab, (double*)forces, add, out);
   else
-    k_near_pairs<float, float><<<ncells, kThreads, 0, st>>>(
+    k_near_pairs<float, float><<<ncells, kThreads, smem, st>>>(
         ng, coff, (const float4*)xq, idx, (const float*)tab, (float*)forces, add, out);
   return cudaGetLastError();
 }
