@@ -36,12 +36,12 @@ def default_params(h, tol: float = 1e-16, rcut: float | None = None):
     return beta, rcut, kcut
 
 
-def ewald(pos, q, h, beta=None, rcut=None, kcut=None, forces=True):
+def ewald(pos, q, h, beta=None, rcut=None, kcut=None, forces=True, tol=1e-16, cell_list=False):
     h = lattice.check_cell(h)
     pos = np.asarray(pos, dtype=np.float64)
     q = np.asarray(q, dtype=np.float64)
     if beta is None:
-        beta, rcut, kcut = default_params(h, rcut=rcut)
+        beta, rcut, kcut = default_params(h, tol=tol, rcut=rcut)
     V = float(np.linalg.det(h))
     N = len(q)
     F = np.zeros((N, 3))
@@ -49,7 +49,8 @@ def ewald(pos, q, h, beta=None, rcut=None, kcut=None, forces=True):
 
     # real space: u(r) = q_i q_j erfc(beta r) / r,  f(r) = -u'(r) / (r q_i q_j)
     U_real = 0.0
-    for i, j, rv, r in lattice.pair_images(pos, h, rcut):
+    pairs = lattice.pair_cells if cell_list else lattice.pair_images
+    for i, j, rv, r in pairs(pos, h, rcut):
         qq = q[i] * q[j]
         e = erfc(beta * r) / r
         U_real += 0.5 * float(np.sum(qq * e))

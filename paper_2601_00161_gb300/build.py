@@ -23,7 +23,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libesp.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-SOURCES = ["esp_kernels.cu", "esp_api.cu", "esp_pswf.cpp"]
+SOURCES = ["esp_kernels.cu", "esp_api.cu", "esp_pswf.cpp", "esp_mlp.cu"]
 
 
 def nvcc() -> str:

@@ -185,6 +185,39 @@ def small_random(n: int, cell, seed: int, grid=(16, 18, 20), P=6, delta=1e-6, rc
     return System(f"random{n}", pos, q, cell, tuple(grid), P, delta, rc)
 
 
+def selector_system(i: int) -> System:
+    """System i (0..63) of the parameter selector's set.
+
+    N log-uniform in [500, 4000] (whole molecules or ion pairs), density 0.1 atoms/A^3,
+    triclinic cell: diagonal lengths with aspect ratios in [0.8, 1.25] and upper-triangle
+    tilts uniform in [0, 0.3] of the lengths; even i water, odd i the LiTFSI-like ionic
+    composition.  Grid, P, Delta and r_c are placeholders: the selector chooses them.
+    """
+    rng = _rng(2000 + i)
+    n_target = math.exp(rng.uniform(math.log(500.0), math.log(4000.0)))
+    ionic = i % 2 == 1
+    per = 16 if ionic else 3
+    units = max(2, int(round(n_target / per)))
+    n = units * per
+    vol = n / 0.1
+    aspect = np.exp(rng.uniform(np.log(0.8), np.log(1.25), size=3))
+    L = aspect * (vol / np.prod(aspect)) ** (1.0 / 3.0)
+    cell = np.diag(L)
+    cell[0, 1], cell[0, 2], cell[1, 2] = rng.uniform(0.0, 0.3, size=3) * np.array([L[0], L[0], L[1]])
+    if ionic:
+        axyz, aq = anion_template(rng)
+        li = rng.random((units, 3)) @ cell.T
+        apos, aqq = place(rng, axyz, aq, rng.random((units, 3)) @ cell.T)
+        pos = np.concatenate([li, apos])
+        q = np.concatenate([np.ones(units), aqq])
+    else:
+        pos, q = water(units, cell, rng)
+    return System(f"selector{i:02d}", pos, neutralise(q), cell, (32, 32, 32), 6, 1e-5, 9.0,
+                  {"composition": "ionic" if ionic else "water"})
+
+
+N_SELECTOR_SYSTEMS = 64
+
 WORKLOADS = {
     "water648_cubic": water_cubic,
     "water30k_triclinic": water_triclinic,

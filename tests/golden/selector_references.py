@@ -1,0 +1,58 @@
+"""Classical Ewald references for the parameter selector's 64 systems (FP64 oracle only).
+
+Writes ``selector_references.json`` beside this file: for each ``synthetic.selector_system(i)``
+its Coulomb energy and virial tensor W = -(dU/dh) h^T (so the pressure tensor of eq.
+(instheta) without the kinetic term is W / V), from ``oracle.ewald`` at splitting
+tolerance 1e-12 (tin-foil boundary, Sec. 3.2).  The selector's GPU tests run the method
+at many parameter choices against these values.
+
+    python tests/golden/selector_references.py     # a few minutes on 8 cores
+"""
+
+from __future__ import annotations
+
+import json
+import multiprocessing as mp
+import os
+import sys
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+TOL = 1e-12
+
+
+def reference(i: int):
+    import synthetic
+    from oracle import lattice
+    from oracle.ewald import ewald
+
+    S = synthetic.selector_system(i)
+    w = float(np.min(lattice.widths(S.cell)))
+    # real-space cut-off: at most half the narrowest width, three cell-list bins when possible
+    rcut = min(0.5 * w, max(8.0, w / 3.0))
+    E = ewald(S.pos, S.q, S.cell, forces=False, tol=TOL, rcut=rcut, cell_list=True)
+    return {"i": i, "n": S.n, "composition": S.meta["composition"], "energy": E["energy"],
+            "virial": E["virial"].tolist(), "ewald_rcut": rcut, "ewald_beta": E["params"][0]}
+
+
+def main():
+    import synthetic
+
+    with mp.get_context("spawn").Pool(min(8, os.cpu_count() or 1)) as pool:
+        refs = pool.map(reference, range(synthetic.N_SELECTOR_SYSTEMS))
+    out = {"what": "Ewald energy and virial of synthetic.selector_system(i), oracle.ewald at "
+                   f"splitting tolerance {TOL:g} (tin-foil)",
+           "script": "tests/golden/selector_references.py (FP64 oracle only)",
+           "systems": refs}
+    with open(os.path.join(HERE, "selector_references.json"), "w") as f:
+        json.dump(out, f, indent=1)
+    print(len(refs), "references")
+
+
+if __name__ == "__main__":
+    main()

@@ -1,9 +1,10 @@
-"""The C ABI library loads and exports every symbol include/esp.h declares (no GPU).
+"""The C ABI library loads and exports every symbol include/*.h declares (no GPU).
 
 Only host-side logic runs here: no kernel launch and no device allocation.
 """
 
 import ctypes
+import glob
 import os
 import re
 
@@ -11,13 +12,14 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "esp.h")
+MLP_HEADER = os.path.join(ROOT, "include", "esp_mlp.h")
 LIB = os.path.join(ROOT, "paper_2601_00161_gb300", "libesp.so")
 
 
-def declared_functions():
-    text = open(HEADER).read()
+def declared_functions(header=HEADER):
+    text = open(header).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(esp_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(esp_[a-z0-9_]+)\s*\(", text)))
 
 
 @pytest.fixture(scope="module")
@@ -30,18 +32,32 @@ def lib():
 
 
 def test_every_declared_symbol_is_exported(lib):
-    names = declared_functions()
-    assert len(names) >= 15
+    headers = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
+    assert HEADER in headers and MLP_HEADER in headers
+    names = [n for h in headers for n in declared_functions(h)]
+    assert len(names) >= 25
     for n in names:
         assert hasattr(lib, n), n
 
 
 def test_binding_names_match_header():
     import paper_2601_00161_gb300 as esp
+    from paper_2601_00161_gb300 import mlp
 
     assert sorted(esp.EXPORTS) == declared_functions()
     for n in esp.EXPORTS:
         assert callable(getattr(esp, n))
+    assert sorted(mlp.EXPORTS) == declared_functions(MLP_HEADER)
+    for n in mlp.EXPORTS:
+        assert callable(getattr(mlp, n))
+
+
+def test_mlp_rejects_bad_sizes_without_a_device():
+    from paper_2601_00161_gb300 import mlp
+
+    assert mlp.esp_mlp_n_params(7, 64, 4) == 64 * 7 + 64 + 64 * 64 + 64 + 4 * 64 + 4
+    with pytest.raises(mlp.MLPError):
+        mlp.MLP(0, 64, 4, 16)
 
 
 def test_c_from_tolerance_host_logic(lib):

@@ -78,3 +78,4 @@ def test_near_field_same_with_cell_list():
     assert abs(a["energy_near"] - b["energy_near"]) < 1e-12 * abs(a["energy_near"])
     assert np.max(np.abs(a["virial_near"] - b["virial_near"])) < 1e-12 * np.max(np.abs(a["virial_near"]))
     assert np.max(np.abs(a["forces_near"] - b["forces_near"])) < 1e-12 * np.max(np.abs(a["forces_near"]))
+
