@@ -176,3 +176,68 @@ def self_and_background(q, h, c, rc):
     Q = float(np.sum(q))
     U_bg = -2.0 * math.pi * Q * Q / V * X
     return dict(energy_self=U_self, energy_bg=U_bg, pressure_bg=U_bg / V)
+
+
+def interpolate(pos, h, M, P, c, field, rows=None, chunk=2048):
+    """sum_g field(g) w(g/M - s_i): a field on the grid read at the atoms with the window."""
+    p = split_constants(c, 1.0)[0]
+    s = lattice.reduced(pos, h)
+    rows = np.arange(len(pos)) if rows is None else np.asarray(rows)
+    out = np.zeros(len(rows))
+    flat = field.ravel()
+    for a in range(0, len(rows), chunk):
+        ii = rows[a:a + chunk]
+        g, w = [], []
+        for d in range(3):
+            gd, wd = window_1d(p, M[d] * s[ii, d], P, M[d])
+            g.append(np.mod(gd, M[d]))
+            w.append(wd)
+        idx = (g[0][:, :, None, None] * M[1] + g[1][:, None, :, None]) * M[2] + g[2][:, None, None, :]
+        out[a:a + chunk] = np.einsum("nijk,ni,nj,nk->n", flat[idx], w[0], w[1], w[2])
+    return out
+
+
+def esp_grid_fields(pos, q, h, M, P, c, rc, kind):
+    """Per-atom quantities from fields on the grid (Sec. 4.4 and Appendix C).
+
+    kind "ik":     forces by ik-differentiation, F_i = -(q_i / (V Mtot^2)) sum_g
+                   E_d(g) w(g/M - s_i), E_d the inverse transform of i k_d G X (eq.
+                   (rhodiagforce)); [N, 3].
+    kind "virial": per-atom virial W^i_ab = (q_i / (2 V Mtot^2)) sum_g Pi_ab(g) w, Pi_ab the
+                   inverse transform of K_ab X / w^2 with K the pressure kernel of eq.
+                   (PFfinal) times V (eqs. (rhodiag), (PinsFind)); [N, 6] as xx yy zz xy xz yz.
+    kind "energy": per-atom energy U^i = (q_i / (2 V Mtot^2)) sum_g phi(g) w, phi the inverse
+                   transform of G X; [N].
+    """
+    h = lattice.check_cell(h)
+    pos = np.asarray(pos, dtype=np.float64)
+    q = np.asarray(q, dtype=np.float64)
+    M = tuple(int(v) for v in M)
+    V = float(np.linalg.det(h))
+    Mtot = float(np.prod(M))
+    X = np.fft.rfftn(spread(pos, q, h, M, P, c))
+    md = modes(h, M, P, c, rc)
+    ins = md["inside"]
+    G = np.where(ins, md["Fhat"] * md["inv_w2"], 0.0)
+    k = md["k"]
+
+    def back(spec):
+        return np.fft.irfftn(spec, s=M, axes=(0, 1, 2)) * Mtot
+
+    if kind == "ik":
+        out = np.empty((len(q), 3))
+        for d in range(3):
+            out[:, d] = -q / (V * Mtot * Mtot) * interpolate(pos, h, M, P, c, back(1j * k[..., d] * G * X))
+        return out
+    if kind == "energy":
+        return q / (2.0 * V * Mtot * Mtot) * interpolate(pos, h, M, P, c, back(G * X))
+    if kind == "virial":
+        k2 = np.where(ins, md["k2"], 1.0)
+        coef = np.where(ins, md["dterm"] - 2.0 * md["Fhat"] / k2, 0.0) * md["inv_w2"]
+        Fw = np.where(ins, md["Fhat"] * md["inv_w2"], 0.0)
+        out = np.empty((len(q), 6))
+        for n, (a, b) in enumerate(((0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2))):
+            K = coef * k[..., a] * k[..., b] + (Fw if a == b else 0.0)
+            out[:, n] = q / (2.0 * V * Mtot * Mtot) * interpolate(pos, h, M, P, c, back(K * X))
+        return out
+    raise ValueError(kind)
