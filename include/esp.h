@@ -114,6 +114,32 @@ int esp_set_stream(esp_plan_t plan, void* stream);
 int esp_step(esp_plan_t plan, const void* pos, const void* q, void* forces, double* d_accum);
 
 /*
+ * Per-atom variants of the long-range step.  Each runs the step without forces (so the
+ * energy and virial of esp_step land in the plan's own accumulator), builds fields from
+ * the spectrum, takes their inverse FFTs and reads them at the atoms with the window
+ * (not its gradient).  Outputs are device arrays of the I/O type in the input order;
+ * atoms with non-finite input are left untouched.  Asynchronous on the plan's stream;
+ * the first call allocates 6 spectra and 6 grids and the batched transforms.
+ * Errors: ESP_ERR_ARG, ESP_ERR_CUDA, ESP_ERR_CUFFT.
+ *
+ * esp_forces_ik - forces by ik-differentiation (Appendix C, eq. (rhodiagforce)):
+ *     F_i = -(q_i / (V Mtot^2)) sum_g E(g) w(g / M - s_i),  E = inverse FFT of i k G X,
+ *     G = F^c / w^2; three inverse FFTs.  Momentum is conserved exactly (sum_i F_i = 0 up
+ *     to rounding), energy only to the discretisation error; esp_forces is the analytical
+ *     differentiation the paper uses.   forces: N x 3.
+ * esp_local_virial - per-atom long-range virial for local pressure profiles (Sec. 4.4,
+ *     eqs. (rhodiag), (PinsFind)): W^i = (q_i / (2 V Mtot^2)) sum_g Pi(g) w(g / M - s_i),
+ *     Pi = inverse FFT of K X / w^2, K the pressure kernel of eq. (PFfinal) times V;
+ *     sum_i W^i = W_F, P^i = W^i / V.   virial: N x 6 as xx yy zz xy xz yz.
+ * esp_atom_energy - per-atom Fourier energy U^i = (q_i / (2 V Mtot^2)) sum_g phi(g) w,
+ *     phi = inverse FFT of G X; sum_i U^i = U_F (self and background terms not included).
+ *     energy: N.
+ */
+int esp_forces_ik(esp_plan_t plan, const void* pos, const void* q, void* forces);
+int esp_local_virial(esp_plan_t plan, const void* pos, const void* q, void* virial);
+int esp_atom_energy(esp_plan_t plan, const void* pos, const void* q, void* energy);
+
+/*
  * esp_near - the near (real-space) part of the PSWF split on the GPU (Sec. 3, eq. (UN);
  * forces as in eq. (Fc); pressure as in eq. (PinsN)): every pair and periodic image with
  * |r_i - r_j + h n| <= r_c, u = r / r_c,

@@ -39,7 +39,7 @@ EXPORTS = (
     "esp_forces", "esp_forces_from_spectrum", "esp_compute_host", "esp_result_from_accum",
     "esp_copy_grid", "esp_copy_spectrum", "esp_plan_info", "esp_destroy", "esp_last_error",
     "esp_c_from_tolerance", "esp_profile", "esp_profile_read", "esp_spread_noalloc",
-    "esp_cell_gradient", "esp_near",
+    "esp_cell_gradient", "esp_near", "esp_forces_ik", "esp_local_virial", "esp_atom_energy",
 )
 
 ESP_NOALLOC_MAX_ATOMS = 65536
@@ -111,6 +111,9 @@ def _load():
         "esp_spread_noalloc": (ci, [dptr, i64, ctypes.POINTER(ci), ci, cd, ci, vp, vp, vp, vp]),
         "esp_cell_gradient": (ci, [vp, vp, vp, vp, vp]),
         "esp_near": (ci, [vp, vp, vp, vp, ci, vp]),
+        "esp_forces_ik": (ci, [vp, vp, vp, vp]),
+        "esp_local_virial": (ci, [vp, vp, vp, vp]),
+        "esp_atom_energy": (ci, [vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -175,6 +178,18 @@ def esp_forces_from_spectrum(plan, forces):
 
 def esp_cell_gradient(plan, pos, forces, accum, grad):
     _check(_lib.esp_cell_gradient(plan, _ptr(pos), _ptr(forces), _ptr(accum), _ptr(grad)), plan)
+
+
+def esp_forces_ik(plan, pos, q, forces):
+    _check(_lib.esp_forces_ik(plan, _ptr(pos), _ptr(q), _ptr(forces)), plan)
+
+
+def esp_local_virial(plan, pos, q, virial):
+    _check(_lib.esp_local_virial(plan, _ptr(pos), _ptr(q), _ptr(virial)), plan)
+
+
+def esp_atom_energy(plan, pos, q, energy):
+    _check(_lib.esp_atom_energy(plan, _ptr(pos), _ptr(q), _ptr(energy)), plan)
 
 
 def esp_near(plan, pos, q, forces, add, out):
@@ -325,6 +340,27 @@ class Plan:
         o = out.cpu().numpy()
         W = np.array([[o[1], o[4], o[5]], [o[4], o[2], o[6]], [o[5], o[6], o[3]]])
         return float(o[0]), W, forces
+
+    def forces_ik(self, pos, q):
+        """Forces by ik-differentiation (momentum-conserving variant)."""
+        pos, q = self._in(pos, q)
+        out = self.torch.empty((self.n, 3), dtype=self.io_dtype, device="cuda")
+        esp_forces_ik(self.handle, pos, q, out)
+        return out
+
+    def local_virial(self, pos, q):
+        """Per-atom long-range virial [n, 6] (xx yy zz xy xz yz); divide by V for pressure."""
+        pos, q = self._in(pos, q)
+        out = self.torch.empty((self.n, 6), dtype=self.io_dtype, device="cuda")
+        esp_local_virial(self.handle, pos, q, out)
+        return out
+
+    def atom_energy(self, pos, q):
+        """Per-atom Fourier energy [n]; sums to the reciprocal energy."""
+        pos, q = self._in(pos, q)
+        out = self.torch.empty(self.n, dtype=self.io_dtype, device="cuda")
+        esp_atom_energy(self.handle, pos, q, out)
+        return out
 
     def info(self) -> dict:
         return esp_plan_info(self.handle)

@@ -108,6 +108,12 @@ struct esp_plan_s {
   void* d_nxq_tmp = nullptr;
   void* d_nxq = nullptr;
   int* d_nidx = nullptr;
+  // field variants (allocated on first use): up to 6 half spectra and 6 real grids, batched
+  // inverse transforms for 3 and 6 fields
+  void* d_fspec = nullptr;
+  void* d_fgrid = nullptr;
+  cufftHandle finv3 = 0, finv6 = 0;
+  bool have_finv3 = false, have_finv6 = false;
   // per-stage CUDA events (esp_profile)
   bool profiling = false;
   cudaEvent_t ev[16] = {};
@@ -367,7 +373,7 @@ void release(esp_plan_t p) {
                   p->d_sorted_tq, p->d_sorted_lb, p->d_sorted_idx, p->d_accum,   p->d_partials,
                   p->d_counter,   p->d_io_pos,    p->d_io_q,     p->d_io_f,
                   p->d_neartab,   p->d_ncount,    p->d_ncoff,    p->d_ncell,     p->d_nrank,
-                  p->d_nxq_tmp,   p->d_nxq,       p->d_nidx};
+                  p->d_nxq_tmp,   p->d_nxq,       p->d_nidx,     p->d_fspec,     p->d_fgrid};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (p->h_accum) cudaFreeHost(p->h_accum);
@@ -376,6 +382,8 @@ void release(esp_plan_t p) {
     if (e) cudaEventDestroy(e);
   if (p->have_fwd) cufftDestroy(p->fwd);
   if (p->have_inv) cufftDestroy(p->inv);
+  if (p->have_finv3) cufftDestroy(p->finv3);
+  if (p->have_finv6) cufftDestroy(p->finv6);
   delete p;
 }
 
@@ -789,6 +797,80 @@ int esp_forces_from_spectrum(esp_plan_t p, void* forces) {
                                  work, p->d_wtab, p->d_grid, forces, st));
   p->spectrum_kept = false;
   return ESP_OK;
+}
+
+// Field variants: the step without forces (the spectrum X stays), fields built from X,
+// their inverse transforms (batched), and window interpolation at the atoms.
+// kind 0: per-atom energy (1 field), 1: ik-differentiation forces (3), 2: per-atom virial (6).
+int run_fields(esp_plan_t p, const void* pos, const void* q, int kind, void* out, double coef) {
+  const int nf = kind == 0 ? 1 : (kind == 1 ? 3 : 6);
+  const size_t es = p->fp64 ? 8 : 4;
+  const size_t ns = (size_t)p->M[0] * p->M[1] * p->H2;
+  const size_t Mtot = (size_t)p->M[0] * p->M[1] * p->M[2];
+  if (!p->d_fspec) {
+    ESP_CUDA(p, cudaMalloc(&p->d_fspec, 6 * ns * 2 * es));
+    ESP_CUDA(p, cudaMalloc(&p->d_fgrid, 6 * Mtot * es));
+  }
+  auto batched = [&](cufftHandle* h, bool* have, int batch) -> int {
+    if (*have) return ESP_OK;
+    int n[3] = {p->M[0], p->M[1], p->M[2]};
+    if (cufftPlanMany(h, 3, n, nullptr, 1, (int)ns, nullptr, 1, (int)Mtot,
+                      p->fp64 ? CUFFT_Z2D : CUFFT_C2R, batch) != CUFFT_SUCCESS)
+      return fail(p, ESP_ERR_CUFFT, "cufftPlanMany (field transforms) failed");
+    *have = true;
+    if (cufftSetStream(*h, p->stream) != CUFFT_SUCCESS)
+      return fail(p, ESP_ERR_CUFFT, "cufftSetStream failed");
+    return ESP_OK;
+  };
+  int rc = ESP_OK;
+  cufftHandle plan = p->inv;
+  if (nf == 3 && (rc = batched(&p->finv3, &p->have_finv3, 3)) != ESP_OK) return rc;
+  if (nf == 6 && (rc = batched(&p->finv6, &p->have_finv6, 6)) != ESP_OK) return rc;
+  if (nf == 3) plan = p->finv3;
+  if (nf == 6) plan = p->finv6;
+  if ((rc = run_step(p, pos, q, nullptr, p->d_accum)) != ESP_OK) return rc;
+  cudaStream_t st = p->stream;
+  ESP_CUDA(p, esp::launch_fields(p->fp64, kind, p->sg, p->d_spec, p->d_invw2, p->d_radtab,
+                                 p->d_fspec, st));
+  if (p->fp64)
+    ESP_CUFFT(p, cufftExecZ2D(plan, (cufftDoubleComplex*)p->d_fspec, (cufftDoubleReal*)p->d_fgrid));
+  else
+    ESP_CUFFT(p, cufftExecC2R(plan, (cufftComplex*)p->d_fspec, (cufftReal*)p->d_fgrid));
+  // gathers of up to 3 fields at a time (one at a time when 3 tiles do not fit)
+  const int per = esp::fields_smem_bytes(p->fp64, p->P, 3) <= 227 * 1024 ? 3 : 1;
+  int* work = p->d_count + (size_t)p->ntiles * esp::kSub;
+  for (int f0 = 0; f0 < nf; f0 += per) {
+    ESP_CUDA(p, cudaMemsetAsync(work + 1, 0, sizeof(int), st));
+    const int k = std::min(per, nf - f0);
+    ESP_CUDA(p, esp::launch_gather_fields(p->fp64, p->io_double, p->tg, p->ntiles, p->gather_blocks, k,
+                                          p->d_sorted_tq, p->d_sorted_lb, p->d_sorted_idx,
+                                          p->d_offset, work, p->d_wtab,
+                                          (const unsigned char*)p->d_fgrid + (size_t)f0 * Mtot * es,
+                                          (int64_t)Mtot, coef, out, nf, f0, st));
+  }
+  p->spectrum_kept = true;
+  return ESP_OK;
+}
+
+int esp_forces_ik(esp_plan_t p, const void* pos, const void* q, void* forces) {
+  if (!p) return fail(nullptr, ESP_ERR_ARG, "plan is NULL");
+  if (p->n > 0 && (!pos || !q || !forces)) return fail(p, ESP_ERR_ARG, "NULL argument");
+  DeviceGuard guard(p->device);
+  return run_fields(p, pos, q, 1, forces, -p->gg.fscale);
+}
+
+int esp_local_virial(esp_plan_t p, const void* pos, const void* q, void* virial) {
+  if (!p) return fail(nullptr, ESP_ERR_ARG, "plan is NULL");
+  if (p->n > 0 && (!pos || !q || !virial)) return fail(p, ESP_ERR_ARG, "NULL argument");
+  DeviceGuard guard(p->device);
+  return run_fields(p, pos, q, 2, virial, 0.5 * p->gg.fscale);
+}
+
+int esp_atom_energy(esp_plan_t p, const void* pos, const void* q, void* energy) {
+  if (!p) return fail(nullptr, ESP_ERR_ARG, "plan is NULL");
+  if (p->n > 0 && (!pos || !q || !energy)) return fail(p, ESP_ERR_ARG, "NULL argument");
+  DeviceGuard guard(p->device);
+  return run_fields(p, pos, q, 0, energy, 0.5 * p->gg.fscale);
 }
 
 int esp_near(esp_plan_t p, const void* pos, const void* q, void* forces, int add,

@@ -22,6 +22,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
 #include <type_traits>
 #include <utility>
 
@@ -1507,6 +1508,233 @@ __global__ void __launch_bounds__(kThreads) k_near_pairs(NearGeom ng, const int*
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Fields on the grid from the kept spectrum X (Sec. 4.4 and Appendix C), one warp per
+// spectrum row, lanes along i2, the same in-sphere decision as k_scale:
+//   KIND 0: G X                         (potential; per-atom energy)
+//   KIND 1: i k_d G X, d = x, y, z      (eq. (rhodiagforce): ik-differentiation)
+//   KIND 2: K_ab X / w^2, ab = xx yy zz xy xz yz, K = F I + (A x psi_0' / k^4 - 2 F / k^2) k k
+//                                       (eq. (rhodiag): local pressure)
+// G = F / w^2 with F = A psi_0(x) / k^2.  Modes outside the sphere are zero.  Field f of
+// the output starts at out + f * M0 M1 H2.
+template <typename R, int KIND>
+__global__ void __launch_bounds__(kThreads) k_fields(const typename Cplx<R>::T* __restrict__ spec,
+                                                     ScaleGeom s, const R* __restrict__ invw2,
+                                                     const R* __restrict__ radtab,
+                                                     typename Cplx<R>::T* __restrict__ out) {
+  constexpr int NF = KIND == 0 ? 1 : (KIND == 1 ? 3 : 6);
+  using C = typename Cplx<R>::T;
+  const int lane = threadIdx.x & 31;
+  const int nrows = s.M[0] * s.M[1];
+  const int64_t Sz = (int64_t)nrows * s.H2;
+  const ScaleConst<R> sc(s);
+  const R* iw0 = invw2;
+  const R* iw1 = invw2 + s.M[0];
+  const R* iw2 = invw2 + s.M[0] + s.M[1];
+  const int warps = (int)((gridDim.x * blockDim.x) >> 5);
+  for (int row = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5); row < nrows; row += warps) {
+    const int i0 = row / s.M[1];
+    const int i1 = row - i0 * s.M[1];
+    const int m0 = (2 * i0 <= s.M[0]) ? i0 : i0 - s.M[0];
+    const int m1 = (2 * i1 <= s.M[1]) ? i1 : i1 - s.M[1];
+    const bool rowin = abs(m0) <= s.mmax[0] && abs(m1) <= s.mmax[1];
+    const R f0 = R(m0), f1 = R(m1);
+    const R kx0 = f0 * bvec<R>(s, 0) + f1 * bvec<R>(s, 3);
+    const R ky0 = f0 * bvec<R>(s, 1) + f1 * bvec<R>(s, 4);
+    const R kz0 = f0 * bvec<R>(s, 2) + f1 * bvec<R>(s, 5);
+    const R iw01 = iw0[i0] * iw1[i1];
+    for (int i2 = lane; i2 < s.H2; i2 += 32) {
+      const int m2 = i2;
+      bool inside = rowin && m2 <= s.mmax[2] && (m0 | m1 | m2) != 0;
+      R kx = R(0), ky = R(0), kz = R(0), k2 = R(0);
+      if (inside) {
+        const R f2 = R(m2);
+        kx = kx0 + f2 * bvec<R>(s, 6);
+        ky = ky0 + f2 * bvec<R>(s, 7);
+        kz = kz0 + f2 * bvec<R>(s, 8);
+        k2 = kx * kx + ky * ky + kz * kz;
+        const R K2r = sc.K2;
+        if (sizeof(R) == 8 || fabs(k2 - K2r) <= R(1e-5) * K2r) {
+          const double dx = m0 * s.b[0] + m1 * s.b[3] + m2 * s.b[6];
+          const double dy = m0 * s.b[1] + m1 * s.b[4] + m2 * s.b[7];
+          const double dz = m0 * s.b[2] + m1 * s.b[5] + m2 * s.b[8];
+          inside = dx * dx + dy * dy + dz * dz <= s.K2;
+        } else {
+          inside = k2 <= K2r;
+        }
+      }
+      C o[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) o[f].x = o[f].y = R(0);
+      if (inside) {
+        const C X = spec[(int64_t)row * s.H2 + i2];
+        const R iw = iw01 * iw2[i2];
+        const R x = sqrt(k2) * sc.x_per_k;
+        R psi, dpsi;
+        radial_eval(radtab, s.rdeg, x, &psi, &dpsi);
+        const R Fhat = sc.A * psi / k2;
+        if constexpr (KIND == 0) {
+          const R G = Fhat * iw;
+          o[0].x = G * X.x;
+          o[0].y = G * X.y;
+        } else if constexpr (KIND == 1) {
+          const R G = Fhat * iw;
+          const R kk[3] = {kx, ky, kz};
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {  // i t X = (-t X.y, t X.x)
+            const R t = kk[d] * G;
+            o[d].x = -t * X.y;
+            o[d].y = t * X.x;
+          }
+        } else {
+          const R dterm = sc.A * x * dpsi / (k2 * k2);
+          const R cf = (dterm - R(2) * Fhat / k2) * iw;
+          const R Fw = Fhat * iw;
+          const R K[6] = {Fw + cf * kx * kx, Fw + cf * ky * ky, Fw + cf * kz * kz,
+                          cf * kx * ky,      cf * kx * kz,      cf * ky * kz};
+#pragma unroll
+          for (int f = 0; f < 6; ++f) {
+            o[f].x = K[f] * X.x;
+            o[f].y = K[f] * X.y;
+          }
+        }
+      }
+#pragma unroll
+      for (int f = 0; f < NF; ++f) out[f * Sz + (int64_t)row * s.H2 + i2] = o[f];
+    }
+  }
+}
+
+// Window interpolation of NF (<= 3) real fields at the atoms: as k_gather (staged tile
+// blocks, P lanes per atom, segmented shuffle), contracting with w0 w1 w2 only;
+// out[idx * stride + off + f] = coef q_i sum_g field_f(g) w(g / M - s_i).
+template <typename R, typename IO, int P, int NF>
+__global__ void __launch_bounds__(kThreads, 2) k_gather_fields(
+    const typename Vec4<R>::T* __restrict__ sorted_tq, const int* __restrict__ sorted_lb,
+    const int* __restrict__ sorted_idx, const int* __restrict__ toff, TileGeom g, int ntiles,
+    int* __restrict__ work, const R* __restrict__ wtab, const R* __restrict__ fields,
+    int64_t field_stride, double coef, IO* __restrict__ out, int stride, int off) {
+  using TC = TileC<P>;
+  using V4 = typename Vec4<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int E1 = TC::E1, E3p = TC::E3p, vol = TC::VOL, S1 = TC::S1;
+  constexpr int PS = round_up4(P), RS = 3 * PS;
+  R* phi = reinterpret_cast<R*>(smem_raw);  // NF blocks of vol
+  const size_t wo = align32((size_t)NF * vol * sizeof(R));
+  R* W = reinterpret_cast<R*>(smem_raw + wo);
+  V4* TQ = reinterpret_cast<V4*>(smem_raw + wo + align32((size_t)kChunk * RS * sizeof(R)));
+  int* B = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(TQ) + align32((size_t)kChunk * sizeof(V4)));
+  int* X = B + kChunk;
+  __shared__ int s_tile;
+  const int E0 = g.E[0], E2 = g.E[2];
+  constexpr int D = WinDeg<R>::value;
+  constexpr int NP = kThreads / P;
+  constexpr int G = 32 / P;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int slot = lane / P, jj = lane - slot * P;
+  const int p_t = threadIdx.x % P, pair0 = threadIdx.x / P;
+  const bool evaluator = pair0 < NP;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_tile = atomicAdd(&work[1], 1);
+    __syncthreads();
+    const int tile = s_tile;
+    if (tile >= ntiles) break;
+    const int start = toff[tile], end = toff[tile + 1];
+    if (start == end) continue;
+    const int t2 = tile % g.nt[2];
+    const int t1 = (tile / g.nt[2]) % g.nt[1];
+    const int t0 = tile / (g.nt[2] * g.nt[1]);
+    const int o0 = t0 * g.T[0], o1 = t1 * g.T[1], o2 = t2 * g.T[2];
+    {
+      const int E1r = g.E[1];
+      const int nload = E0 * E1r * E2;
+      for (int e = threadIdx.x; e < NF * nload; e += blockDim.x) {
+        const int f = e / nload, r = e - f * nload;
+        const int c = r % E2;
+        const int ab = r / E2;
+        const int b = ab % E1r;
+        const int a = ab / E1r;
+        const int gi = wrap_index(o0 + a, g.M[0]);
+        const int gj = wrap_index(o1 + b, g.M[1]);
+        const int gk = wrap_index(o2 + c, g.M[2]);
+        phi[f * vol + a * S1 + b * E3p + c] =
+            fields[f * field_stride + ((int64_t)gi * g.M[1] + gj) * g.M[2] + gk];
+      }
+    }
+    for (int c0 = start; c0 < end; c0 += kChunk) {
+      const int cnt = min(kChunk, end - c0);
+      for (int a = threadIdx.x; a < cnt; a += blockDim.x) {
+        TQ[a] = sorted_tq[c0 + a];
+        B[a] = local_base<S1, E3p>(sorted_lb[c0 + a]);
+        X[a] = sorted_idx[c0 + a];
+      }
+      __syncthreads();
+      if (evaluator) {
+        R cw[D + 1];
+#pragma unroll
+        for (int k = 0; k <= D; ++k) cw[k] = __ldg(wtab + k * P + p_t);
+        for (int pr = pair0; pr < 3 * cnt; pr += NP) {
+          const int a = pr / 3, d = pr - 3 * a;
+          W[a * RS + d * PS + p_t] = horner_reg<R, D>(cw, tq_comp<R>(TQ[a], d));
+        }
+      }
+      __syncthreads();
+      for (int a0 = warp * G; a0 < cnt; a0 += (kThreads / 32) * G) {
+        const int a = a0 + slot;
+        const bool valid = slot < G && a < cnt;
+        R acc[NF];
+#pragma unroll
+        for (int f = 0; f < NF; ++f) acc[f] = R(0);
+        if (valid) {
+          const R* Wa = W + a * RS;
+          R w0[P], w2[P];
+          load_record<R, P>(Wa, w0);
+          load_record<R, P>(Wa + 2 * PS, w2);
+          const R w1 = Wa[PS + jj];
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            const R* src = phi + f * vol + B[a] + jj * E3p;
+            R sum = R(0);
+#pragma unroll
+            for (int kk = 0; kk < P; ++kk) {
+              R sw = R(0);
+#pragma unroll
+              for (int i = 0; i < P; ++i) sw = fma(src[i * S1 + kk], w0[i], sw);
+              sum = fma(w2[kk], sw, sum);
+            }
+            acc[f] = w1 * sum;
+          }
+        }
+#pragma unroll
+        for (int sft = 1; sft < P; sft <<= 1) {
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            const R t = __shfl_down_sync(0xffffffffu, acc[f], sft);
+            if (jj + sft < P) acc[f] += t;
+          }
+        }
+        if (valid && jj == 0) {
+          const double qa = (double)TQ[a].w;
+#pragma unroll
+          for (int f = 0; f < NF; ++f)
+            out[(int64_t)X[a] * stride + off + f] = (IO)(coef * qa * (double)acc[f]);
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+size_t fields_smem(bool fp64, int P, int NF) {
+  int T[3], E3p, vol;
+  tile_shape(P, T, &E3p, &vol);
+  const size_t es = fp64 ? 8 : 4;
+  const size_t rs = 3 * (size_t)round_up4(P);
+  return align32((size_t)NF * vol * es) + align32(kChunk * rs * es) + align32(kChunk * 4 * es) +
+         2 * kChunk * sizeof(int);
+}
+
 int grid_blocks(int64_t n) {
   int64_t b = (n + kThreads - 1) / kThreads;
   if (b < 1) b = 1;
@@ -1781,6 +2009,60 @@ cudaError_t launch_near_pairs(bool fp64, bool io_double, const NearGeom& ng, int
     k_near_pairs<float, float><<<ncells, kThreads, smem, st>>>(
         ng, coff, (const float4*)xq, idx, (const float*)tab, (float*)forces, add, out);
   return cudaGetLastError();
+}
+
+size_t fields_smem_bytes(bool fp64, int P, int NF) { return fields_smem(fp64, P, NF); }
+
+cudaError_t launch_fields(bool fp64, int kind, const ScaleGeom& s, const void* spec,
+                          const void* invw2, const void* radtab, void* out, cudaStream_t st) {
+  const int rows = s.M[0] * s.M[1];
+  const int nb = std::max(1, std::min((rows + kThreads / 32 - 1) / (kThreads / 32), 152 * 8));
+  if (fp64) {
+    using C = double2;
+    if (kind == 0) k_fields<double, 0><<<nb, kThreads, 0, st>>>((const C*)spec, s, (const double*)invw2, (const double*)radtab, (C*)out);
+    else if (kind == 1) k_fields<double, 1><<<nb, kThreads, 0, st>>>((const C*)spec, s, (const double*)invw2, (const double*)radtab, (C*)out);
+    else k_fields<double, 2><<<nb, kThreads, 0, st>>>((const C*)spec, s, (const double*)invw2, (const double*)radtab, (C*)out);
+  } else {
+    using C = float2;
+    if (kind == 0) k_fields<float, 0><<<nb, kThreads, 0, st>>>((const C*)spec, s, (const float*)invw2, (const float*)radtab, (C*)out);
+    else if (kind == 1) k_fields<float, 1><<<nb, kThreads, 0, st>>>((const C*)spec, s, (const float*)invw2, (const float*)radtab, (C*)out);
+    else k_fields<float, 2><<<nb, kThreads, 0, st>>>((const C*)spec, s, (const float*)invw2, (const float*)radtab, (C*)out);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_fields(bool fp64, bool io_double, const TileGeom& g, int ntiles,
+                                 int nblocks, int nf, const void* sorted_tq, const int* sorted_lb,
+                                 const int* sorted_idx, const int* toff, int* work,
+                                 const void* wtab, const void* fields, int64_t field_stride,
+                                 double coef, void* out, int stride, int off, cudaStream_t st) {
+  if (nf != 1 && nf != 3) return cudaErrorInvalidValue;
+  const size_t smem = fields_smem(fp64, g.P, nf);
+  return with_P(g.P, [&](auto pc) -> cudaError_t {
+    constexpr int PP = decltype(pc)::value;
+    auto go = [&](auto kernel, auto tq, auto wt, auto fl, auto o) -> cudaError_t {
+      cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      kernel<<<nblocks, kThreads, smem, st>>>(tq, sorted_lb, sorted_idx, toff, g, ntiles, work, wt,
+                                              fl, field_stride, coef, o, stride, off);
+      return cudaGetLastError();
+    };
+    if (fp64) {
+      auto tq = (const double4*)sorted_tq;
+      auto wt = (const double*)wtab;
+      auto fl = (const double*)fields;
+      return nf == 1 ? go(k_gather_fields<double, double, PP, 1>, tq, wt, fl, (double*)out)
+                     : go(k_gather_fields<double, double, PP, 3>, tq, wt, fl, (double*)out);
+    }
+    auto tq = (const float4*)sorted_tq;
+    auto wt = (const float*)wtab;
+    auto fl = (const float*)fields;
+    if (io_double)
+      return nf == 1 ? go(k_gather_fields<float, double, PP, 1>, tq, wt, fl, (double*)out)
+                     : go(k_gather_fields<float, double, PP, 3>, tq, wt, fl, (double*)out);
+    return nf == 1 ? go(k_gather_fields<float, float, PP, 1>, tq, wt, fl, (float*)out)
+                   : go(k_gather_fields<float, float, PP, 3>, tq, wt, fl, (float*)out);
+  });
 }
 
 // resident CTAs per SM for the spread and gather kernels of this configuration

@@ -189,6 +189,20 @@ cudaError_t launch_near_pairs(bool fp64, bool io_double, const NearGeom& ng, int
                              const int* coff, const void* xq, const int* idx, const void* tab,
                              void* forces, int add, double* out, cudaStream_t st);
 
+// Fields from the kept spectrum (kind 0: G X; 1: i k_d G X; 2: K_ab X / w^2), written as
+// 1, 3 or 6 half spectra one after the other.
+cudaError_t launch_fields(bool fp64, int kind, const ScaleGeom& s, const void* spec,
+                          const void* invw2, const void* radtab, void* out, cudaStream_t st);
+// Window interpolation of nf (1 or 3) real grids at the atoms (grids field_stride apart):
+// out[idx * stride + off + f] = coef q_i sum_g field_f(g) w(g / M - s_i); work[1] zero on
+// entry (it is the gather's tile counter).
+cudaError_t launch_gather_fields(bool fp64, bool io_double, const TileGeom& g, int ntiles,
+                                 int nblocks, int nf, const void* sorted_tq, const int* sorted_lb,
+                                 const int* sorted_idx, const int* toff, int* work,
+                                 const void* wtab, const void* fields, int64_t field_stride,
+                                 double coef, void* out, int stride, int off, cudaStream_t st);
+size_t fields_smem_bytes(bool fp64, int P, int NF);
+
 // dU/dh at fixed positions into grad[9] (row-major): -W h^{-T} + sum_i F_i (h^{-1} r_i)^T
 cudaError_t launch_cell_grad(bool io_double, const void* pos, const void* forces, int64_t n,
                              const CellGradArgs& c, const double* accum, double* grad,
