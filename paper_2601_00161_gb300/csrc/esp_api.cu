@@ -274,19 +274,13 @@ int build_window_tables(esp_plan_t p, std::vector<double>& tab) {
 }
 
 // Near kernel on u = r / r_c in [0, 1], kRadialPieces pieces in (u - centre): 1 - phi_0(u)
-// and F_N(u) = 1 - phi_0(u) + u psi_0(u) / C_0, phi_0(u) = (1 / C_0) int_0^u psi_0 by
-// 40-point Gauss-Legendre (Sec. 3.1, eqs. (decomposition), (mathFN)).
+// and F_N(u) = 1 - phi_0(u) + u psi_0(u) / C_0, phi_0(u) = (1 / C_0) int_0^u psi_0 from the
+// Legendre series term by term (Sec. 3.1, eqs. (decomposition), (mathFN)).
 int build_near_tables(esp_plan_t p, std::vector<double>& tab) {
   const esp::Prolate& pr = p->pswf;
   const double tol = p->fp64 ? 3e-15 : 2e-8;
   const int NR = esp::kRadialPieces;
-  std::vector<double> gx, gw;
-  esp::gauss_legendre(40, gx, gw);
-  auto phi0 = [&](double u) {
-    double s = 0.0;
-    for (size_t k = 0; k < gx.size(); ++k) s += gw[k] * pr.eval(0.5 * u * (gx[k] + 1.0));
-    return 0.5 * u * s / pr.C0;
-  };
+  auto phi0 = [&](double u) { return pr.integral(u) / pr.C0; };
   auto g1 = [&](double u) { return 1.0 - phi0(u); };
   auto g2 = [&](double u) { return 1.0 - phi0(u) + u * pr.eval(u) / pr.C0; };
   for (int deg = 6; deg <= esp::kMaxDeg; ++deg) {

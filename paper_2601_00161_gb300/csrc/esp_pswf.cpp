@@ -131,6 +131,23 @@ double Prolate::deriv(double x) const {
   return s;
 }
 
+double Prolate::integral(double u) const {
+  // Legendre values P_0..P_{deg+1} at u and at 0
+  std::vector<double> pu(deg + 2), pz(deg + 2);
+  pu[0] = 1.0;
+  pz[0] = 1.0;
+  pu[1] = u;
+  pz[1] = 0.0;
+  for (int k = 1; k <= deg; ++k) {
+    pu[k + 1] = ((2.0 * k + 1.0) * u * pu[k] - k * pu[k - 1]) / (k + 1.0);
+    pz[k + 1] = (-k * pz[k - 1]) / (k + 1.0);
+  }
+  double s = a[0] * u;
+  for (int k = 1; k <= deg; ++k)
+    s += a[k] * ((pu[k + 1] - pu[k - 1]) - (pz[k + 1] - pz[k - 1])) / (2.0 * k + 1.0);
+  return s;
+}
+
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
   x.assign(n, 0.0);
   w.assign(n, 0.0);

@@ -19,6 +19,8 @@ struct Prolate {
   bool solve(double c);
   double eval(double x) const;   // psi_0(x), |x| <= 1
   double deriv(double x) const;  // psi_0'(x), |x| <= 1
+  // int_0^u psi_0, |u| <= 1, term by term: int P_k = (P_{k+1} - P_{k-1}) / (2k + 1), k >= 1
+  double integral(double u) const;
 };
 
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);
