@@ -231,6 +231,21 @@ def cpu_baseline_oracle(S, c):
                       f"{WORKLOAD}, {S.n} atoms, FP64, numpy/pocketfft, 1 thread: {dt:.2f} s"}
 
 
+def cpu_openmp_baseline(S, c, steps=2):
+    """The plain OpenMP FP64 ESP (oracle/esp_omp.c) on all host cores, the full workload."""
+    from oracle.esp_omp import esp_omp
+
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    esp_omp(S.pos, S.q, S.cell, S.grid, S.P, c, S.rc, threads=cores)  # warm-up (page-in)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        esp_omp(S.pos, S.q, S.cell, S.grid, S.P, c, S.rc, threads=cores)
+    dt = (time.perf_counter() - t0) / steps
+    return {"value": round(1.0 / dt, 4), "unit": "steps/s", "cores": cores,
+            "kind": "plain OpenMP FP64 ESP (oracle/esp_omp.c: spread with atomics, own mixed-radix FFT)",
+            "sample": f"{steps} full steps of {WORKLOAD} ({S.n} atoms, energy, virial, forces): {dt:.3f} s each"}
+
+
 def esp_arm(args):
     import torch
 
@@ -451,6 +466,7 @@ def esp_arm(args):
         }
         if not args.no_cpu_baseline and world == 1:
             out["cpu_baseline"] = cpu_baseline_oracle(S, c)
+            out["cpu_openmp_baseline"] = cpu_openmp_baseline(S, c)
     plan.close()
     if world > 1:
         dist.destroy_process_group()
