@@ -964,7 +964,9 @@ int esp_compute_host(esp_plan_t p, const void* pos, const void* q, void* forces,
     ESP_CUDA(p, cudaMemcpyAsync(p->d_io_pos, pos, 3 * io_es * p->n, cudaMemcpyHostToDevice, st));
     ESP_CUDA(p, cudaMemcpyAsync(p->d_io_q, q, io_es * p->n, cudaMemcpyHostToDevice, st));
   }
-  int rc = run_step(p, p->d_io_pos, p->d_io_q, forces ? p->d_io_f : nullptr, p->d_accum);
+  // the step through the captured graph: its device buffers are fixed, so one capture
+  // serves every call (plain launches on the legacy default stream)
+  int rc = run_step_graph(p, p->d_io_pos, p->d_io_q, forces ? p->d_io_f : nullptr, p->d_accum);
   if (rc != ESP_OK) return rc;
   ESP_CUDA(p, cudaMemcpyAsync(p->h_accum, p->d_accum, sizeof(double) * ESP_ACCUM_LEN,
                               cudaMemcpyDeviceToHost, st));
