@@ -323,7 +323,7 @@ def esp_arm(args):
     res = esp.esp_result_from_accum(plan.handle, acc.cpu().numpy()).as_dict()
 
     # dominant kernel of ours and its roofline (algorithmic bytes / event-timed duration)
-    ours = ["bin", "scan", "scatter", "spread", "scale", "gather"]
+    ours = ["bin", "scan", "scatter", "spread", "xfft_scale", "gather"]
     avg = {k: stage_tot[k] / args.steps for k in esp.STAGES}
     dom = max(ours, key=lambda k: avg[k])
     Mtot = S.grid[0] * S.grid[1] * S.grid[2]

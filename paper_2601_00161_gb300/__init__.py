@@ -45,7 +45,7 @@ EXPORTS = (
 ESP_NOALLOC_MAX_ATOMS = 65536
 ESP_NOALLOC_MAX_TILES = 4096
 
-STAGES = ("memset", "bin", "scan", "scatter", "zero_grid", "spread", "fft_fwd", "scale",
+STAGES = ("memset", "bin", "scan", "scatter", "zero_grid", "spread", "fft_fwd", "xfft_scale",
           "fft_inv", "gather")
 
 

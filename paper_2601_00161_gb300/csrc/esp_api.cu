@@ -56,8 +56,16 @@ struct esp_plan_s {
   esp::ScaleGeom sg{};
   esp::GatherGeom gg{};
   int ntiles = 0;
-  int scale_blocks = 0;  // sizes the partials: one block per 8 spectrum rows at most
-  int zero_blocks = 0;
+  esp::XGeom xg{};       // the transform along axis 0 fused with the scaling
+  int xblocks = 0;       // its CTAs: column groups
+  int xactive = 0;       // groups whose lines may meet the sphere (ordered first)
+  int* d_xorder = nullptr;           // group order, active first
+  unsigned char* d_xcol = nullptr;   // per column: line may meet the sphere
+  int* h_xorder = nullptr;           // pinned staging of the two
+  unsigned char* h_xcol = nullptr;
+  // the final sum of the transform's per-CTA partials runs on a branch of its own
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_start = nullptr, ev_zero = nullptr;
   int bin_blocks = 0;
   int spread_blocks = 0, gather_blocks = 0;
   // device buffers
@@ -66,6 +74,8 @@ struct esp_plan_s {
   void* d_invw2 = nullptr;
   void* d_grid = nullptr;
   void* d_spec = nullptr;
+  void* d_spec2 = nullptr;  // scaled half spectrum, input of the plane C2R (cleared per step)
+  void* d_xtw = nullptr;  // M0 roots e^{-2 pi i m / M0} (compute type)
   int* d_count = nullptr;   // kSub counters per tile, then 2 work counters (spread, gather)
   int* d_suboff = nullptr;  // exclusive scan of d_count (tile-major)
   int* d_offset = nullptr;  // first sorted atom of each tile (ntiles + 1)
@@ -80,13 +90,15 @@ struct esp_plan_s {
   int* d_sorted_idx = nullptr;
   double* d_accum = nullptr;
   double* d_partials = nullptr;
-  unsigned int* d_counter = nullptr;
   void* d_io_pos = nullptr;
   void* d_io_q = nullptr;
   void* d_io_f = nullptr;
   double* h_accum = nullptr;  // pinned
-  cufftHandle fwd = 0, inv = 0;
-  bool have_fwd = false, have_inv = false;
+  // plane transforms over (i1, i2) for every i0 (R2C / C2R, batched) of the force step,
+  // whose transform along i0 is k_xfft; fwd3: the full 3D R2C of the energy and pressure
+  // step (the spectrum is kept); inv3: the full 3D C2R of one field (on first use)
+  cufftHandle fwd = 0, inv = 0, fwd3 = 0, inv3 = 0;
+  bool have_fwd = false, have_inv = false, have_fwd3 = false, have_inv3 = false;
   bool spectrum_kept = false;
   // CUDA graph of the last esp_step (re-captured when its arguments or the cell change)
   bool use_graph = true;
@@ -215,6 +227,51 @@ void update_cell_constants(esp_plan_t p) {
   p->sg.scalef = (float)p->sg.scale;
   p->gg.g = p->tg;
   p->gg.fscale = 1.0 / (p->V * Mtot * Mtot);
+}
+
+// Column groups of the transform along axis 0 for the current cell: a column (m1, m2) is
+// active when its line k = m0 b_0 + v (v = m1 b_1 + m2 b_2) may enter the sphere |k| <= K:
+// |m1| <= mmax1, m2 <= mmax2 and the squared distance |v|^2 - (v.b_0)^2 / |b_0|^2 of the
+// line from the origin at most K^2 (1 + 1e-6).  Groups with an active column come first.
+// The staging copy waits for the stream, so a step still reading the old order is done.
+int update_xfft_tasks(esp_plan_t p) {
+  const esp::ScaleGeom& s = p->sg;
+  const esp::XGeom& x = p->xg;
+  const double* b = s.b;
+  const double bb = b[0] * b[0] + b[1] * b[1] + b[2] * b[2];
+  ESP_CUDA(p, cudaStreamSynchronize(p->stream));
+  const int NC = 1 << x.lognc;
+  int na = 0, ni = p->xblocks - 1;
+  for (int gi = 0; gi < p->xblocks; ++gi) {
+    bool any = false;
+    for (int c = 0; c < NC; ++c) {
+      const int f = gi * NC + c;
+      if (f >= x.ncol) break;
+      const int i1 = f / s.H2, m2 = f % s.H2;
+      const int m1 = (2 * i1 <= s.M[1]) ? i1 : i1 - s.M[1];
+      bool act = false;
+      if (std::abs(m1) <= s.mmax[1] && m2 <= s.mmax[2]) {
+        const double vx = m1 * b[3] + m2 * b[6], vy = m1 * b[4] + m2 * b[7], vz = m1 * b[5] + m2 * b[8];
+        const double vb = vx * b[0] + vy * b[1] + vz * b[2];
+        act = vx * vx + vy * vy + vz * vz - vb * vb / bb <= s.K2 * (1.0 + 1e-6) + 1e-300;
+      }
+      p->h_xcol[f] = act ? 1 : 0;
+      any = any || act;
+    }
+    // active groups from the front, the others from the back
+    if (any)
+      p->h_xorder[na++] = gi;
+    else
+      p->h_xorder[ni--] = gi;
+  }
+  // no active group (no mode inside the sphere): one group still writes the zero sums
+  p->xactive = std::max(na, 1);
+  if (na == 0) std::reverse(p->h_xorder, p->h_xorder + p->xblocks);
+  ESP_CUDA(p, cudaMemcpyAsync(p->d_xorder, p->h_xorder, sizeof(int) * p->xblocks,
+                              cudaMemcpyHostToDevice, p->stream));
+  ESP_CUDA(p, cudaMemcpyAsync(p->d_xcol, p->h_xcol, (size_t)x.ncol, cudaMemcpyHostToDevice,
+                              p->stream));
+  return ESP_OK;
 }
 
 template <typename R>
@@ -362,20 +419,29 @@ void build_invw2(esp_plan_t p, std::vector<double>& out) {
 void release(esp_plan_t p) {
   if (!p) return;
   if (p->stream) cudaStreamSynchronize(p->stream);
-  void* bufs[] = {p->d_wtab,      p->d_radtab,    p->d_invw2,    p->d_grid,      p->d_spec,  p->d_tq,
+  void* bufs[] = {p->d_wtab,      p->d_radtab,    p->d_invw2,    p->d_grid,      p->d_spec,  p->d_spec2, p->d_xtw, p->d_xorder, p->d_xcol, p->d_tq,
                   p->d_count,     p->d_offset,    p->d_ptile,    p->d_prank,     p->d_plb,  p->d_suboff, p->d_binpart, p->d_bsum,
                   p->d_sorted_tq, p->d_sorted_lb, p->d_sorted_idx, p->d_accum,   p->d_partials,
-                  p->d_counter,   p->d_io_pos,    p->d_io_q,     p->d_io_f,
+                  p->d_io_pos,    p->d_io_q,     p->d_io_f,
                   p->d_neartab,   p->d_ncount,    p->d_ncoff,    p->d_ncell,     p->d_nrank,
                   p->d_nxq_tmp,   p->d_nxq,       p->d_nidx,     p->d_fspec,     p->d_fgrid};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (p->h_accum) cudaFreeHost(p->h_accum);
+  if (p->h_xorder) cudaFreeHost(p->h_xorder);
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  if (p->ev_join) cudaEventDestroy(p->ev_join);
+  if (p->ev_start) cudaEventDestroy(p->ev_start);
+  if (p->ev_zero) cudaEventDestroy(p->ev_zero);
+  if (p->side) cudaStreamDestroy(p->side);
+  if (p->h_xcol) cudaFreeHost(p->h_xcol);
   if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
   for (cudaEvent_t e : p->ev)
     if (e) cudaEventDestroy(e);
   if (p->have_fwd) cufftDestroy(p->fwd);
   if (p->have_inv) cufftDestroy(p->inv);
+  if (p->have_inv3) cufftDestroy(p->inv3);
+  if (p->have_fwd3) cufftDestroy(p->fwd3);
   if (p->have_finv3) cufftDestroy(p->finv3);
   if (p->have_finv6) cufftDestroy(p->finv6);
   delete p;
@@ -420,6 +486,15 @@ int run_step(esp_plan_t p, const void* pos, const void* q, void* forces, double*
   int* work = p->d_count + (size_t)p->ntiles * esp::kSub;
   // d_count and the work counters are zero here: set at plan time, re-zeroed by the scan
   // kernel of every step.  acc[0..6] is written by the scale kernel, acc[7..9] by scan.
+  const bool want_f = forces != nullptr;
+  if (want_f) {
+    // the scaled spectrum's buffer is cleared on the side branch while the atoms are
+    // binned and spread: k_xfft writes only the columns that meet the sphere
+    ESP_CUDA(p, cudaEventRecord(p->ev_start, st));
+    ESP_CUDA(p, cudaStreamWaitEvent(p->side, p->ev_start, 0));
+    ESP_CUDA(p, cudaMemsetAsync(p->d_spec2, 0, 2 * es * (size_t)p->M[0] * p->M[1] * p->H2, p->side));
+    ESP_CUDA(p, cudaEventRecord(p->ev_zero, p->side));
+  }
   mark(p, kBin);
   ESP_CUDA(p, esp::launch_bin(p->io_double, fp64, pos, q, p->n, p->tg, p->d_count, p->d_ptile,
                               p->d_prank, p->d_plb, p->d_tq, p->d_binpart, p->d_grid,
@@ -436,25 +511,35 @@ int run_step(esp_plan_t p, const void* pos, const void* q, void* forces, double*
   ESP_CUDA(p, esp::launch_spread(fp64, p->tg, p->ntiles, p->spread_blocks, p->d_sorted_tq,
                                  p->d_sorted_lb, p->d_offset, work, p->d_wtab, p->d_grid, st));
   mark(p, kFftFwd);
+  // forces: plane transforms (the transform along axis 0 is fused into k_xfft); energy and
+  // pressure only: the full 3D transform, whose spectrum is kept
+  const cufftHandle fplan = want_f ? p->fwd : p->fwd3;
   if (fp64)
-    ESP_CUFFT(p, cufftExecD2Z(p->fwd, (cufftDoubleReal*)p->d_grid, (cufftDoubleComplex*)p->d_spec));
+    ESP_CUFFT(p, cufftExecD2Z(fplan, (cufftDoubleReal*)p->d_grid, (cufftDoubleComplex*)p->d_spec));
   else
-    ESP_CUFFT(p, cufftExecR2C(p->fwd, (cufftReal*)p->d_grid, (cufftComplex*)p->d_spec));
-  const bool want_f = forces != nullptr;
+    ESP_CUFFT(p, cufftExecR2C(fplan, (cufftReal*)p->d_grid, (cufftComplex*)p->d_spec));
   mark(p, kScale);
-  ESP_CUDA(p, esp::launch_scale(fp64, want_f, p->sg, p->d_spec, p->d_invw2, p->d_radtab,
-                                p->d_partials, p->d_counter, acc, p->zero_blocks, st));
+  if (want_f) ESP_CUDA(p, cudaStreamWaitEvent(st, p->ev_zero, 0));
+  ESP_CUDA(p, esp::launch_xfft(fp64, want_f, want_f, p->xg, p->sg, p->d_spec, p->d_spec2, p->d_xtw, p->d_invw2,
+                               p->d_radtab, p->d_partials, p->d_xorder, p->d_xcol, p->xactive,
+                               st));
+  // the energy and virial sums finish on the side branch while the forces go on
+  ESP_CUDA(p, cudaEventRecord(p->ev_fork, st));
+  ESP_CUDA(p, cudaStreamWaitEvent(p->side, p->ev_fork, 0));
+  ESP_CUDA(p, esp::launch_xsum(fp64, p->d_partials, p->xactive, acc, p->side));
+  ESP_CUDA(p, cudaEventRecord(p->ev_join, p->side));
   mark(p, kFftInv);
   if (want_f) {
     if (fp64)
-      ESP_CUFFT(p, cufftExecZ2D(p->inv, (cufftDoubleComplex*)p->d_spec, (cufftDoubleReal*)p->d_grid));
+      ESP_CUFFT(p, cufftExecZ2D(p->inv, (cufftDoubleComplex*)p->d_spec2, (cufftDoubleReal*)p->d_grid));
     else
-      ESP_CUFFT(p, cufftExecC2R(p->inv, (cufftComplex*)p->d_spec, (cufftReal*)p->d_grid));
+      ESP_CUFFT(p, cufftExecC2R(p->inv, (cufftComplex*)p->d_spec2, (cufftReal*)p->d_grid));
     mark(p, kGather);
     ESP_CUDA(p, esp::launch_gather(fp64, p->io_double, p->gg, p->ntiles, p->gather_blocks,
                                    p->d_sorted_tq, p->d_sorted_lb, p->d_sorted_idx,
                                    p->d_offset, work, p->d_wtab, p->d_grid, forces, st));
   }
+  ESP_CUDA(p, cudaStreamWaitEvent(st, p->ev_join, 0));
   mark(p, kNStage);
   p->spectrum_kept = !want_f;
   return ESP_OK;
@@ -641,8 +726,38 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
   int dev = 0;
   cudaGetDevice(&dev);
   p->device = dev;
-  p->scale_blocks = (p->M[0] * p->M[1] + esp::kThreads / 32 - 1) / (esp::kThreads / 32) + 1;
-  p->zero_blocks = 2 * sms;
+  // the transform along axis 0: radices 8, 4, 2, 3, 5, 7, then the other prime factors;
+  // 2^lognc columns per CTA, as many as keep two CTAs' shared memory within an SM
+  {
+    esp::XGeom& x = p->xg;
+    x.M0 = p->M[0];
+    x.ncol = p->M[1] * p->H2;
+    int n = x.M0, np = 0;
+    auto push = [&](int r) {
+      if (np < esp::kMaxPass) x.radix[np] = r;
+      ++np;
+      n /= r;
+    };
+    while (n % 8 == 0) push(8);
+    if (n % 4 == 0) push(4);
+    if (n % 2 == 0) push(2);
+    for (int r : {3, 5, 7})
+      while (n % r == 0) push(r);
+    for (int r = 11; (int64_t)r * r <= n; r += 2)
+      while (n % r == 0) push(r);
+    if (n > 1) push(n);
+    if (np > esp::kMaxPass) return bail(fail(p, ESP_ERR_ARG, "grid size M1 has too many prime factors"));
+    x.npass = np;
+    if (x.M0 >= (1 << 16)) return bail(fail(p, ESP_ERR_ARG, "grid size M1 too large"));
+    for (int k = 0, ns = 1; k < np; ns *= x.radix[k], ++k)
+      x.ns_magic[k] = (unsigned int)((((unsigned long long)1 << 32) + ns - 1) / ns);
+    x.lognc = 3;
+    while (x.lognc > 0 && esp::xfft_smem_bytes(p->fp64, x.M0, x.lognc, p->rdeg) > 100 * 1024)
+      --x.lognc;
+    if (esp::xfft_smem_bytes(p->fp64, x.M0, x.lognc, p->rdeg) > 227 * 1024)
+      return bail(fail(p, ESP_ERR_ARG, "grid size M1 too large for the transform along axis 1"));
+    p->xblocks = esp::xfft_blocks(x);
+  }
 
   const size_t es = p->fp64 ? 8 : 4;
   const size_t io_es = p->io_double ? 8 : 4;
@@ -659,6 +774,7 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
   } while (0)
   ALLOC(p->d_grid, es * Mtot);
   ALLOC(p->d_spec, 2 * es * nspec);
+  ALLOC(p->d_spec2, 2 * es * nspec);
   p->bin_blocks = esp::bin_blocks(n);
   ALLOC(p->d_count, sizeof(int) * ((size_t)p->ntiles * esp::kSub + 2));
   ALLOC(p->d_suboff, sizeof(int) * ((size_t)p->ntiles * esp::kSub + 1));
@@ -673,27 +789,62 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
   ALLOC(p->d_sorted_lb, sizeof(int) * nn);
   ALLOC(p->d_sorted_idx, sizeof(int) * nn);
   ALLOC(p->d_accum, sizeof(double) * ESP_ACCUM_LEN);
-  ALLOC(p->d_partials, sizeof(double) * 8 * p->scale_blocks);
-  ALLOC(p->d_counter, sizeof(unsigned int));
+  ALLOC(p->d_partials, sizeof(double) * 7 * (size_t)p->xblocks);
+  ALLOC(p->d_xtw, 2 * es * (size_t)p->M[0]);
+  ALLOC(p->d_xorder, sizeof(int) * (size_t)p->xblocks);
+  ALLOC(p->d_xcol, (size_t)p->xg.ncol);
 #undef ALLOC
   (void)io_es;
   {
-    cudaError_t e = cudaMemset(p->d_counter, 0, sizeof(unsigned int));
-    if (e == cudaSuccess)
-      e = cudaMemset(p->d_count, 0, sizeof(int) * ((size_t)p->ntiles * esp::kSub + 2));
+    cudaError_t e = cudaMemset(p->d_count, 0, sizeof(int) * ((size_t)p->ntiles * esp::kSub + 2));
     if (e == cudaSuccess) e = cudaMemset(p->d_accum, 0, sizeof(double) * ESP_ACCUM_LEN);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_accum, sizeof(double) * ESP_ACCUM_LEN);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_xorder, sizeof(int) * (size_t)p->xblocks);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_xcol, (size_t)p->xg.ncol);
     if (e != cudaSuccess) return bail(cuda_fail(p, e, "plan workspace set-up"));
   }
   {
-    cufftResult r1 = cufftPlan3d(&p->fwd, p->M[0], p->M[1], p->M[2], p->fp64 ? CUFFT_D2Z : CUFFT_R2C);
-    if (r1 != CUFFT_SUCCESS) return bail(fail(p, ESP_ERR_CUFFT, "cufftPlan3d (forward) failed"));
+    // roots of unity for the transform along axis 0, FP64 on the host
+    std::vector<double> tw(2 * (size_t)p->M[0]);
+    for (int m = 0; m < p->M[0]; ++m) {
+      tw[2 * m] = std::cos(2.0 * M_PI * m / p->M[0]);
+      tw[2 * m + 1] = -std::sin(2.0 * M_PI * m / p->M[0]);
+    }
+    cudaError_t e;
+    if (p->fp64) {
+      e = cudaMemcpy(p->d_xtw, tw.data(), sizeof(double) * tw.size(), cudaMemcpyHostToDevice);
+    } else {
+      std::vector<float> twf(tw.begin(), tw.end());
+      e = cudaMemcpy(p->d_xtw, twf.data(), sizeof(float) * twf.size(), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess)
+      e = esp::configure_xfft(p->fp64, esp::xfft_smem_bytes(p->fp64, p->xg.M0, p->xg.lognc, p->rdeg));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_zero, cudaEventDisableTiming);
+    if (e != cudaSuccess) return bail(cuda_fail(p, e, "transform set-up"));
+    if ((rc = update_xfft_tasks(p)) != ESP_OK) return bail(rc);
+  }
+  {
+    // plane transforms: every i0 plane over (i1, i2), batched
+    int n2[2] = {p->M[1], p->M[2]};
+    const int nr = p->M[1] * p->M[2], nc = p->M[1] * p->H2;
+    cufftResult r1 = cufftPlanMany(&p->fwd, 2, n2, nullptr, 1, nr, nullptr, 1, nc,
+                                   p->fp64 ? CUFFT_D2Z : CUFFT_R2C, p->M[0]);
+    if (r1 != CUFFT_SUCCESS) return bail(fail(p, ESP_ERR_CUFFT, "cufftPlanMany (forward) failed"));
     p->have_fwd = true;
-    cufftResult r2 = cufftPlan3d(&p->inv, p->M[0], p->M[1], p->M[2], p->fp64 ? CUFFT_Z2D : CUFFT_C2R);
-    if (r2 != CUFFT_SUCCESS) return bail(fail(p, ESP_ERR_CUFFT, "cufftPlan3d (inverse) failed"));
+    cufftResult r2 = cufftPlanMany(&p->inv, 2, n2, nullptr, 1, nc, nullptr, 1, nr,
+                                   p->fp64 ? CUFFT_Z2D : CUFFT_C2R, p->M[0]);
+    if (r2 != CUFFT_SUCCESS) return bail(fail(p, ESP_ERR_CUFFT, "cufftPlanMany (inverse) failed"));
     p->have_inv = true;
+    cufftResult r3 = cufftPlan3d(&p->fwd3, p->M[0], p->M[1], p->M[2], p->fp64 ? CUFFT_D2Z : CUFFT_R2C);
+    if (r3 != CUFFT_SUCCESS) return bail(fail(p, ESP_ERR_CUFFT, "cufftPlan3d (forward) failed"));
+    p->have_fwd3 = true;
     if (cufftSetStream(p->fwd, p->stream) != CUFFT_SUCCESS ||
-        cufftSetStream(p->inv, p->stream) != CUFFT_SUCCESS)
+        cufftSetStream(p->inv, p->stream) != CUFFT_SUCCESS ||
+        cufftSetStream(p->fwd3, p->stream) != CUFFT_SUCCESS)
       return bail(fail(p, ESP_ERR_CUFFT, "cufftSetStream failed"));
   }
   {
@@ -726,7 +877,7 @@ int esp_set_cell(esp_plan_t p, const double cell[9]) {
   update_cell_constants(p);
   p->spectrum_kept = false;
   drop_graph(p);
-  return ESP_OK;
+  return update_xfft_tasks(p);
 }
 
 int esp_set_stream(esp_plan_t p, void* stream) {
@@ -734,7 +885,8 @@ int esp_set_stream(esp_plan_t p, void* stream) {
   p->stream = (cudaStream_t)stream;
   drop_graph(p);
   if (cufftSetStream(p->fwd, p->stream) != CUFFT_SUCCESS ||
-      cufftSetStream(p->inv, p->stream) != CUFFT_SUCCESS)
+      cufftSetStream(p->inv, p->stream) != CUFFT_SUCCESS ||
+      cufftSetStream(p->fwd3, p->stream) != CUFFT_SUCCESS)
     return fail(p, ESP_ERR_CUFFT, "cufftSetStream failed");
   return ESP_OK;
 }
@@ -778,12 +930,16 @@ int esp_forces_from_spectrum(esp_plan_t p, void* forces) {
   DeviceGuard guard(p->device);
   cudaStream_t st = p->stream;
   const bool fp64 = p->fp64;
-  ESP_CUDA(p, esp::launch_scale(fp64, true, p->sg, p->d_spec, p->d_invw2, p->d_radtab,
-                                p->d_partials, p->d_counter, p->d_accum, p->zero_blocks, st));
+  ESP_CUDA(p, cudaMemsetAsync(p->d_spec2, 0,
+                              2 * (fp64 ? 8 : 4) * (size_t)p->M[0] * p->M[1] * p->H2, st));
+  ESP_CUDA(p, esp::launch_xfft(fp64, false, true, p->xg, p->sg, p->d_spec, p->d_spec2, p->d_xtw,
+                               p->d_invw2, p->d_radtab, p->d_partials, p->d_xorder, p->d_xcol,
+                               p->xactive, st));
+  ESP_CUDA(p, esp::launch_xsum(fp64, p->d_partials, p->xactive, p->d_accum, st));
   if (fp64)
-    ESP_CUFFT(p, cufftExecZ2D(p->inv, (cufftDoubleComplex*)p->d_spec, (cufftDoubleReal*)p->d_grid));
+    ESP_CUFFT(p, cufftExecZ2D(p->inv, (cufftDoubleComplex*)p->d_spec2, (cufftDoubleReal*)p->d_grid));
   else
-    ESP_CUFFT(p, cufftExecC2R(p->inv, (cufftComplex*)p->d_spec, (cufftReal*)p->d_grid));
+    ESP_CUFFT(p, cufftExecC2R(p->inv, (cufftComplex*)p->d_spec2, (cufftReal*)p->d_grid));
   int* work = p->d_count + (size_t)p->ntiles * esp::kSub;
   ESP_CUDA(p, cudaMemsetAsync(work + 1, 0, sizeof(int), st));
   ESP_CUDA(p, esp::launch_gather(fp64, p->io_double, p->gg, p->ntiles, p->gather_blocks,
@@ -817,11 +973,12 @@ int run_fields(esp_plan_t p, const void* pos, const void* q, int kind, void* out
     return ESP_OK;
   };
   int rc = ESP_OK;
-  cufftHandle plan = p->inv;
+  if (nf == 1 && (rc = batched(&p->inv3, &p->have_inv3, 1)) != ESP_OK) return rc;
   if (nf == 3 && (rc = batched(&p->finv3, &p->have_finv3, 3)) != ESP_OK) return rc;
   if (nf == 6 && (rc = batched(&p->finv6, &p->have_finv6, 6)) != ESP_OK) return rc;
-  if (nf == 3) plan = p->finv3;
-  if (nf == 6) plan = p->finv6;
+  const cufftHandle plan = nf == 1 ? p->inv3 : (nf == 3 ? p->finv3 : p->finv6);
+  if (cufftSetStream(plan, p->stream) != CUFFT_SUCCESS)
+    return fail(p, ESP_ERR_CUFFT, "cufftSetStream failed");
   if ((rc = run_step(p, pos, q, nullptr, p->d_accum)) != ESP_OK) return rc;
   cudaStream_t st = p->stream;
   ESP_CUDA(p, esp::launch_fields(p->fp64, kind, p->sg, p->d_spec, p->d_invw2, p->d_radtab,

@@ -798,205 +798,491 @@ struct ScaleConst {
   }
 };
 
-template <typename R, bool WRITE>
-__global__ void __launch_bounds__(kThreads) k_scale(typename Cplx<R>::T* __restrict__ spec,
-                                                    ScaleGeom s, const R* __restrict__ invw2,
-                                                    const R* __restrict__ radtab,
-                                                    double* __restrict__ partials,
-                                                    unsigned int* __restrict__ counter,
-                                                    double* __restrict__ accum, int nred) {
-  // Blocks [0, nred): one warp per row (m0, m1) of the bounding box of the sphere
-  // |k| <= K, lanes along i2; they scale (force path) and reduce.  Blocks from nred on
-  // (force path only) zero the rows outside the box, which hold no in-sphere mode.
-  // FP64 path: plain FP64 sums.  FP32 path: compensated FP32 sums per lane and across
-  // the warp (about 48 significant bits), FP64 from the block totals on.
-  using Acc = typename std::conditional<std::is_same<R, double>::value, double, DF>::type;
+// ---------------------------------------------------------------------------------------
+// The transform along the first grid axis, fused with the scaling and the reduction
+// (eqs. (UF) and (WF)).  cuFFT transforms the planes i0 = const over (i1, i2) (R2C along
+// i2, then along i1); what is left of the 3D transform is an FFT of length M0 along every
+// column (i1, i2) of the [M0][M1][H2] half spectrum.  A CTA takes NC consecutive columns
+// (consecutive in memory, so each row i0 is one contiguous segment), keeps them in shared
+// memory as buf[i0][c] and runs
+//   FWD: the forward transform along i0 (mixed-radix Stockham passes);
+//   the sums of eqs. (UF) / (WF) over the sphere |k| <= K, and with INV the scaling of
+//        every mode by G(k) = F^(k) / w^(k)^2;
+//   INV: the inverse transform along i0 of the scaled modes.
+// Without FWD the columns hold the full 3D spectrum X already (the energy and pressure
+// path and the kept spectrum); without INV nothing is written.  Column groups come in the
+// order order[blockIdx]: the first nactive hold every column whose line through k may
+// enter the sphere (colact = 1, decided on the host from the cell).  The grid is those
+// nactive CTAs; with INV they write their columns to out, whose other columns (all of
+// whose modes scale to zero) the caller has cleared.  FP32: compensated FP32 sums (about 48 significant bits);
+// FP64: plain FP64.  Per-CTA sums go to partials; k_xsum adds them up.
+
+// DIT Stockham pass over buf[i0][c] (Govindaraju et al., SC'08, restated for mixed radix):
+// butterfly j < M0 / RAD, k = j mod Ns, reads in[j + t M0 / RAD], multiplies by
+// w^(t k M0 / (Ns RAD)) (w = e^{-2 pi i / M0}; conjugate for the inverse), takes the
+// RAD-point DFT and writes out[(j - k) RAD + k + t Ns]; Ns is the product of the radices
+// of the passes before.
+template <typename R>
+__device__ __forceinline__ typename Cplx<R>::T cmk(R x, R y) {
+  typename Cplx<R>::T z;
+  z.x = x;
+  z.y = y;
+  return z;
+}
+template <typename C>
+__device__ __forceinline__ C cadd(C a, C b) {
+  a.x += b.x;
+  a.y += b.y;
+  return a;
+}
+template <typename C>
+__device__ __forceinline__ C csub(C a, C b) {
+  a.x -= b.x;
+  a.y -= b.y;
+  return a;
+}
+// a * w (SIGN < 0) or a * conj(w) (SIGN > 0)
+template <int SIGN, typename C>
+__device__ __forceinline__ C ctw(C a, C w) {
+  C z;
+  if constexpr (SIGN < 0) {
+    z.x = a.x * w.x - a.y * w.y;
+    z.y = a.x * w.y + a.y * w.x;
+  } else {
+    z.x = a.x * w.x + a.y * w.y;
+    z.y = a.y * w.x - a.x * w.y;
+  }
+  return z;
+}
+// a * (SIGN i)
+template <int SIGN, typename C>
+__device__ __forceinline__ C crot(C a) {
+  C z;
+  if constexpr (SIGN < 0) {
+    z.x = a.y;
+    z.y = -a.x;
+  } else {
+    z.x = -a.y;
+    z.y = a.x;
+  }
+  return z;
+}
+
+template <int SIGN, typename C>
+__device__ __forceinline__ void dft4(C& a, C& b, C& c, C& d) {
+  const C s0 = cadd(a, c), d0 = csub(a, c), s1 = cadd(b, d), d1 = crot<SIGN>(csub(b, d));
+  a = cadd(s0, s1);
+  c = csub(s0, s1);
+  b = cadd(d0, d1);
+  d = csub(d0, d1);
+}
+
+// RAD-point DFT in registers, y_u = sum_t v_t e^{SIGN 2 pi i u t / RAD}.  RAD = 3, 5, 7 take
+// their roots from the table (root m at index m M0 / RAD).
+template <typename R, int RAD, int SIGN>
+__device__ __forceinline__ void dft_reg(typename Cplx<R>::T (&v)[RAD],
+                                        const typename Cplx<R>::T* tw, int M0) {
+  using C = typename Cplx<R>::T;
+  if constexpr (RAD == 2) {
+    const C a = v[0];
+    v[0] = cadd(a, v[1]);
+    v[1] = csub(a, v[1]);
+  } else if constexpr (RAD == 4) {
+    dft4<SIGN>(v[0], v[1], v[2], v[3]);
+  } else if constexpr (RAD == 8) {
+    C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    C o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+    dft4<SIGN>(e0, e1, e2, e3);
+    dft4<SIGN>(o0, o1, o2, o3);
+    const R h = R(0.70710678118654752440);  // 1 / sqrt(2)
+    // o_u *= e^{SIGN 2 pi i u / 8}
+    o1 = cmk<R>(h * (o1.x - SIGN * o1.y), h * (o1.y + SIGN * o1.x));
+    o2 = crot<SIGN>(o2);
+    o3 = cmk<R>(h * (-o3.x - SIGN * o3.y), h * (-o3.y + SIGN * o3.x));
+    v[0] = cadd(e0, o0);
+    v[4] = csub(e0, o0);
+    v[1] = cadd(e1, o1);
+    v[5] = csub(e1, o1);
+    v[2] = cadd(e2, o2);
+    v[6] = csub(e2, o2);
+    v[3] = cadd(e3, o3);
+    v[7] = csub(e3, o3);
+  } else {
+    C w[RAD];
+    const int step = M0 / RAD;
+#pragma unroll
+    for (int m = 0; m < RAD; ++m) w[m] = tw[m * step];
+    C y[RAD];
+#pragma unroll
+    for (int u = 0; u < RAD; ++u) {
+      C a = v[0];
+#pragma unroll
+      for (int t = 1; t < RAD; ++t) {
+        const C z = ctw<SIGN>(v[t], w[(u * t) % RAD]);
+        a.x += z.x;
+        a.y += z.y;
+      }
+      y[u] = a;
+    }
+#pragma unroll
+    for (int u = 0; u < RAD; ++u) v[u] = y[u];
+  }
+}
+
+template <typename R, int RAD, int SIGN>
+__device__ __forceinline__ void xpass(const typename Cplx<R>::T* in, typename Cplx<R>::T* out,
+                                      const typename Cplx<R>::T* tw, int M0, int lognc,
+                                      int Ns, unsigned int ns_magic) {
+  using C = typename Cplx<R>::T;
+  const int L = M0 / RAD;
+  const int stride = L / Ns;  // M0 / (Ns RAD)
+  const int ncm = (1 << lognc) - 1;
+  const int nb = L << lognc;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    const int c = b & ncm, j = b >> lognc;
+    const int k = Ns == 1 ? 0 : j - fast_div(j, ns_magic) * Ns;
+    C v[RAD];
+#pragma unroll
+    for (int t = 0; t < RAD; ++t) v[t] = in[((j + t * L) << lognc) + c];
+    if (k > 0) {
+#pragma unroll
+      for (int t = 1; t < RAD; ++t) v[t] = ctw<SIGN>(v[t], tw[t * k * stride]);
+    }
+    dft_reg<R, RAD, SIGN>(v, tw, M0);
+    const int d = (j - k) * RAD + k;
+#pragma unroll
+    for (int t = 0; t < RAD; ++t) out[((d + t * Ns) << lognc) + c] = v[t];
+  }
+}
+
+// A pass of a prime radix p > 7: one output per thread, p products each.
+template <typename R, int SIGN>
+__device__ __forceinline__ void xpass_any(const typename Cplx<R>::T* in,
+                                          typename Cplx<R>::T* out,
+                                          const typename Cplx<R>::T* tw, int M0, int lognc,
+                                          int Ns, unsigned int ns_magic, int p) {
+  using C = typename Cplx<R>::T;
+  const int L = M0 / p;
+  const int stride = L / Ns;
+  const int ncm = (1 << lognc) - 1;
+  const int n = M0 << lognc;
+  for (int o = threadIdx.x; o < n; o += blockDim.x) {
+    const int c = o & ncm, r = o >> lognc;
+    const int u = r / L, j = r - u * L;
+    const int k = Ns == 1 ? 0 : j - fast_div(j, ns_magic) * Ns;
+    C a = cmk<R>(R(0), R(0));
+    for (int t = 0; t < p; ++t) {
+      int idx = t * k * stride + ((u * t) % p) * L;
+      if (idx >= M0) idx -= M0;
+      const C z = ctw<SIGN>(in[((j + t * L) << lognc) + c], tw[idx]);
+      a.x += z.x;
+      a.y += z.y;
+    }
+    out[(((j - k) * p + k + u * Ns) << lognc) + c] = a;
+  }
+}
+
+// All passes of one direction; returns the buffer that holds the result.
+template <typename R, int SIGN>
+__device__ __forceinline__ typename Cplx<R>::T* xfft_lines(typename Cplx<R>::T* a,
+                                                           typename Cplx<R>::T* b,
+                                                           const typename Cplx<R>::T* tw,
+                                                           const XGeom& x) {
+  int Ns = 1;
+  for (int s = 0; s < x.npass; ++s) {
+    const int rad = x.radix[s];
+    const unsigned int mg = x.ns_magic[s];
+    switch (rad) {
+      case 8: xpass<R, 8, SIGN>(a, b, tw, x.M0, x.lognc, Ns, mg); break;
+      case 4: xpass<R, 4, SIGN>(a, b, tw, x.M0, x.lognc, Ns, mg); break;
+      case 2: xpass<R, 2, SIGN>(a, b, tw, x.M0, x.lognc, Ns, mg); break;
+      case 3: xpass<R, 3, SIGN>(a, b, tw, x.M0, x.lognc, Ns, mg); break;
+      case 5: xpass<R, 5, SIGN>(a, b, tw, x.M0, x.lognc, Ns, mg); break;
+      case 7: xpass<R, 7, SIGN>(a, b, tw, x.M0, x.lognc, Ns, mg); break;
+      default: xpass_any<R, SIGN>(a, b, tw, x.M0, x.lognc, Ns, mg, rad); break;
+    }
+    Ns *= rad;
+    __syncthreads();
+    typename Cplx<R>::T* t = a;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
+// Sums of 8 values over the 32 lanes of a warp in a fixed order.  Each of the first three
+// levels halves the values a lane keeps and sends the other half to its partner, so lane l
+// ends with the warp total of value c(l) = 4 ((l >> 4) & 1) + 2 ((l >> 3) & 1) + ((l >> 2)
+// & 1): 9 shuffle-and-add steps instead of 8 x 5.
+__device__ __forceinline__ DF shfl_xor(const DF& a, int o) {
+  DF r;
+  r.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
+  r.lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
+  return r;
+}
+__device__ __forceinline__ double shfl_xor(double a, int o) {
+  return __shfl_xor_sync(0xffffffffu, a, o);
+}
+__device__ __forceinline__ void acc_add(DF& a, const DF& b) { a.add(b); }
+__device__ __forceinline__ void acc_add(double& a, double b) { a += b; }
+__device__ __forceinline__ int sum8_slot(int lane) {
+  return 4 * ((lane >> 4) & 1) + 2 * ((lane >> 3) & 1) + ((lane >> 2) & 1);
+}
+template <typename A>
+__device__ __forceinline__ A warp_sum8(const A (&v)[8]) {
   const int lane = threadIdx.x & 31;
-  typename Cplx<R>::T zero;
-  zero.x = R(0);
-  zero.y = R(0);
-  const int w0box = 2 * s.mmax[0] + 1, w1box = 2 * s.mmax[1] + 1;
-  if ((int)blockIdx.x >= nred) {
-    if (WRITE) {
-      const int nrows = s.M[0] * s.M[1];
-      const int warps = ((gridDim.x - nred) * blockDim.x) >> 5;
-      for (int row = (((int)blockIdx.x - nred) * blockDim.x + threadIdx.x) >> 5; row < nrows;
-           row += warps) {
-        const int i0 = row / s.M[1];
-        const int i1 = row - i0 * s.M[1];
-        const int m0 = (2 * i0 <= s.M[0]) ? i0 : i0 - s.M[0];
-        const int m1 = (2 * i1 <= s.M[1]) ? i1 : i1 - s.M[1];
-        if (abs(m0) <= s.mmax[0] && abs(m1) <= s.mmax[1]) continue;
-        typename Cplx<R>::T* rowp = spec + (int64_t)row * s.H2;
-        for (int i2 = lane; i2 < s.H2; i2 += 32) rowp[i2] = zero;
+  A w4[4], w2[2], w1;
+  {
+    const bool up = (lane & 16) != 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      w4[i] = up ? v[4 + i] : v[i];
+      acc_add(w4[i], shfl_xor(up ? v[i] : v[4 + i], 16));
+    }
+  }
+  {
+    const bool up = (lane & 8) != 0;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      w2[i] = up ? w4[2 + i] : w4[i];
+      acc_add(w2[i], shfl_xor(up ? w4[i] : w4[2 + i], 8));
+    }
+  }
+  {
+    const bool up = (lane & 4) != 0;
+    w1 = up ? w2[1] : w2[0];
+    acc_add(w1, shfl_xor(up ? w2[0] : w2[1], 4));
+  }
+  acc_add(w1, shfl_xor(w1, 2));
+  acc_add(w1, shfl_xor(w1, 1));
+  return w1;
+}
+
+// The 7 reduction components (U_F and W_F xx yy zz xy xz yz) of a CTA in a fixed order:
+// warp_sum8, then threads j < 7 add the NW warp totals of component j in warp order.
+template <typename A, int NW>
+__device__ __forceinline__ A cta_sum7(const A (&acc)[7], A (*red)[NW]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  A v[8];
+#pragma unroll
+  for (int j = 0; j < 7; ++j) v[j] = acc[j];
+  v[7] = A{};
+  const A t = warp_sum8(v);
+  const int c = sum8_slot(lane);
+  if ((lane & 3) == 0 && c < 7) red[c][wid] = t;
+  __syncthreads();
+  A r{};
+  if (threadIdx.x < 7)
+    for (int w = 0; w < NW; ++w) acc_add(r, red[threadIdx.x][w]);
+  return r;
+}
+
+// Final sum of the per-CTA partials of k_xfft (component j at partials[j * nblk + b]) in a
+// fixed order: one CTA, launched after k_xfft (on a branch of its own in the step graph).
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_xsum(const double* __restrict__ partials, int nblk,
+                                                   double* __restrict__ accum) {
+  using A = typename std::conditional<std::is_same<R, double>::value, double, DF>::type;
+  __shared__ A red[7][kThreads / 32];
+  A s[7];
+#pragma unroll
+  for (int j = 0; j < 7; ++j) s[j] = A{};
+#pragma unroll 4
+  for (int b = threadIdx.x; b < nblk; b += blockDim.x) {
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+      if constexpr (std::is_same<R, double>::value) {
+        s[j] += partials[(size_t)j * nblk + b];
+      } else {
+        const float2 v = reinterpret_cast<const float2*>(partials)[(size_t)j * nblk + b];
+        DF y;
+        y.hi = v.x;
+        y.lo = v.y;
+        s[j].add(y);
       }
     }
-    return;
   }
-  Acc acc[7];
-  if constexpr (std::is_same<R, double>::value)
-    for (int j = 0; j < 7; ++j) acc[j] = 0.0;
-  const R* iw0 = invw2;
-  const R* iw1 = invw2 + s.M[0];
-  const R* iw2 = invw2 + s.M[0] + s.M[1];
+  const A t = cta_sum7<A, kThreads / 32>(s, red);
+  if (threadIdx.x < 7) {
+    if constexpr (std::is_same<R, double>::value)
+      accum[threadIdx.x] = t;
+    else
+      accum[threadIdx.x] = (double)t.hi + (double)t.lo;
+  }
+}
+
+template <typename R, bool FWD, bool INV>
+__global__ void __launch_bounds__(kXThreads, std::is_same<R, float>::value ? 2 : 1) k_xfft(const typename Cplx<R>::T* __restrict__ spec,
+                                                   typename Cplx<R>::T* __restrict__ out,
+                                                   XGeom x, ScaleGeom s,
+                                                   const typename Cplx<R>::T* __restrict__ twg,
+                                                   const R* __restrict__ invw2,
+                                                   const R* __restrict__ radtab,
+                                                   double* __restrict__ partials,
+                                                   const int* __restrict__ order,
+                                                   const unsigned char* __restrict__ colact,
+                                                   int nactive) {
+  using C = typename Cplx<R>::T;
+  constexpr bool kD = std::is_same<R, double>::value;
+  using Acc = typename std::conditional<kD, double, DF>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int M0 = x.M0, lognc = x.lognc, NC = 1 << lognc;
+  const int nrt = 2 * kRadialPieces * (s.rdeg + 1);
+  C* tw = reinterpret_cast<C*>(smem_raw);
+  C* buf0 = tw + M0;
+  C* buf1 = buf0 + (M0 << lognc);
+  R* iw0 = reinterpret_cast<R*>(buf1 + (M0 << lognc));  // 1 / w0^2 along the column
+  R* rt = iw0 + M0;                                    // radial polynomials
+  // per column: k of (0, m1, m2), 1 / (w1^2 w2^2) times the Hermitian weight, m1, m2, flags
+  __shared__ R ck[3][32], cw[32], cg[32];
+  __shared__ int cm1[32], cm2[32], cflag[32];
+  static_assert(INV || !FWD, "the forward transform is only fused with the inverse one");
+  const int f0 = order[blockIdx.x] * NC;
+  const int total = M0 << lognc;
+  const int64_t rowst = x.ncol;  // elements between rows i0 and i0 + 1
   const ScaleConst<R> sc(s);
-  const int r = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  if (r < w0box * w1box) {
-    const int u0 = r / w1box;
-    const int m0 = u0 - s.mmax[0], m1 = r - u0 * w1box - s.mmax[1];
-    const int i0 = m0 >= 0 ? m0 : m0 + s.M[0];
-    const int i1 = m1 >= 0 ? m1 : m1 + s.M[1];
-    typename Cplx<R>::T* rowp = spec + ((int64_t)i0 * s.M[1] + i1) * s.H2;
-    const R f0 = R(m0), f1 = R(m1);
-    const R kx0 = f0 * bvec<R>(s, 0) + f1 * bvec<R>(s, 3);
-    const R ky0 = f0 * bvec<R>(s, 1) + f1 * bvec<R>(s, 4);
-    const R kz0 = f0 * bvec<R>(s, 2) + f1 * bvec<R>(s, 5);
-    const R iw01 = iw0[i0] * iw1[i1];
-    for (int i2 = lane; i2 < s.H2; i2 += 32) {
+
+  if (threadIdx.x < NC) {
+    const int c = threadIdx.x, f = f0 + c;
+    int flag = 0;
+    if (f < x.ncol) {
+      const int i1 = f / s.H2, i2 = f - (f / s.H2) * s.H2;
+      const int m1 = (2 * i1 <= s.M[1]) ? i1 : i1 - s.M[1];
       const int m2 = i2;
-      bool inside = m2 <= s.mmax[2] && (m0 | m1 | m2) != 0;
+      flag = colact[f] ? 3 : 1;  // a column of the spectrum; 3: its line may meet the sphere
+      const R f1 = R(m1), f2 = R(m2);
+      ck[0][c] = f1 * bvec<R>(s, 3) + f2 * bvec<R>(s, 6);
+      ck[1][c] = f1 * bvec<R>(s, 4) + f2 * bvec<R>(s, 7);
+      ck[2][c] = f1 * bvec<R>(s, 5) + f2 * bvec<R>(s, 8);
+      const bool single = (i2 == 0) || ((s.M[2] & 1) == 0 && 2 * i2 == s.M[2]);
+      cg[c] = invw2[s.M[0] + i1] * invw2[s.M[0] + s.M[1] + i2];
+      cw[c] = (single ? R(1) : R(2)) * cg[c];
+      cm1[c] = m1;
+      cm2[c] = m2;
+    }
+    cflag[c] = flag;
+  }
+  for (int e = threadIdx.x; e < M0; e += blockDim.x) {
+    tw[e] = twg[e];
+    iw0[e] = invw2[e];
+  }
+  for (int e = threadIdx.x; e < nrt; e += blockDim.x) rt[e] = radtab[e];
+  Acc acc[7];
+  if constexpr (kD)
+    for (int j = 0; j < 7; ++j) acc[j] = 0.0;
+  {
+    // the columns into shared memory, kU loads in flight per thread
+    constexpr int kU = 4;
+    for (int e0 = threadIdx.x; e0 < total; e0 += kU * blockDim.x) {
+      C v[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int e = e0 + u * blockDim.x;
+        const int f = f0 + (e & (NC - 1));
+        v[u] = (e < total && f < x.ncol) ? spec[(int64_t)(e >> lognc) * rowst + f]
+                                         : cmk<R>(R(0), R(0));
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e < total) buf0[e] = v[u];
+      }
+    }
+    __syncthreads();
+    C* cur = buf0;
+    C* oth = buf1;
+    if (FWD) {
+      cur = xfft_lines<R, -1>(buf0, buf1, tw, x);
+      oth = cur == buf0 ? buf1 : buf0;
+    }
+    // scaling and sums; uniform trip count per warp (the FP64 boundary test is voted)
+    for (int e0 = 0; e0 < total; e0 += blockDim.x) {
+      const int e = e0 + threadIdx.x;
+      const bool ok = e < total;
+      const int c = e & (NC - 1), i0 = e >> lognc;
+      const int m0 = (2 * i0 <= M0) ? i0 : i0 - M0;
+      bool inside = ok && cflag[c] == 3 && abs(m0) <= s.mmax[0] && (m0 | cm1[c] | cm2[c]) != 0;
       R kx = R(0), ky = R(0), kz = R(0), k2 = R(0);
       if (inside) {
-        const R f2 = R(m2);
-        kx = kx0 + f2 * bvec<R>(s, 6);
-        ky = ky0 + f2 * bvec<R>(s, 7);
-        kz = kz0 + f2 * bvec<R>(s, 8);
+        const R f0r = R(m0);
+        kx = f0r * bvec<R>(s, 0) + ck[0][c];
+        ky = f0r * bvec<R>(s, 1) + ck[1][c];
+        kz = f0r * bvec<R>(s, 2) + ck[2][c];
         k2 = kx * kx + ky * ky + kz * kz;
-        // The in-sphere decision is an FP64 one (as in the FP64 oracle): FP32 decides
-        // only when it is far from the boundary.
-        const R K2r = sc.K2;
-        if (sizeof(R) == 8 || fabs(k2 - K2r) <= R(1e-5) * K2r) {
+      }
+      // the in-sphere decision is an FP64 one (as in the FP64 oracle); FP32 decides only
+      // away from the boundary
+      const bool near = inside && (kD || fabs(k2 - sc.K2) <= R(1e-5) * sc.K2);
+      if (__any_sync(0xffffffffu, near)) {
+        if (near) {
+          const int m1 = cm1[c], m2 = cm2[c];
           const double dx = m0 * s.b[0] + m1 * s.b[3] + m2 * s.b[6];
           const double dy = m0 * s.b[1] + m1 * s.b[4] + m2 * s.b[7];
           const double dz = m0 * s.b[2] + m1 * s.b[5] + m2 * s.b[8];
           inside = dx * dx + dy * dy + dz * dz <= s.K2;
-        } else {
-          inside = k2 <= K2r;
         }
       }
+      if (!kD && !near && inside) inside = k2 <= sc.K2;
+      if (!ok) continue;
       if (!inside) {
-        if (WRITE) rowp[i2] = zero;
+        if (INV) cur[e] = cmk<R>(R(0), R(0));
         continue;
       }
-      const typename Cplx<R>::T X = rowp[i2];
-      const R iw = iw01 * iw2[i2];
+      const C X = cur[e];
+      const R iw = iw0[i0] * cw[c];
       const R kmag = sqrt(k2);
-      const R x = kmag * sc.x_per_k;
+      const R xa = kmag * sc.x_per_k;
       R psi, dpsi;
-      radial_eval(radtab, s.rdeg, x, &psi, &dpsi);
+      radial_eval(rt, s.rdeg, xa, &psi, &dpsi);
       const R Fhat = sc.A * psi / k2;
-      const R dterm = sc.A * x * dpsi / (k2 * k2);
-      const bool single = (i2 == 0) || ((s.M[2] & 1) == 0 && 2 * i2 == s.M[2]);
-      const R a = (single ? R(1) : R(2)) * (X.x * X.x + X.y * X.y) * iw * sc.scale;
+      const R dterm = sc.A * xa * dpsi / (k2 * k2);
+      const R a = (X.x * X.x + X.y * X.y) * iw * sc.scale;
       const R aF = a * Fhat;
-      const R ck = a * (dterm - R(2) * Fhat / k2);
+      const R ckk = a * (dterm - R(2) * Fhat / k2);
       const R contrib[7] = {aF,
-                            aF + ck * kx * kx,
-                            aF + ck * ky * ky,
-                            aF + ck * kz * kz,
-                            ck * kx * ky,
-                            ck * kx * kz,
-                            ck * ky * kz};
+                            aF + ckk * kx * kx,
+                            aF + ckk * ky * ky,
+                            aF + ckk * kz * kz,
+                            ckk * kx * ky,
+                            ckk * kx * kz,
+                            ckk * ky * kz};
 #pragma unroll
       for (int j = 0; j < 7; ++j) {
-        if constexpr (std::is_same<R, double>::value)
+        if constexpr (kD)
           acc[j] += contrib[j];
         else
           acc[j].add(contrib[j]);
       }
-      if (WRITE) {
-        const R G = Fhat * iw;
-        typename Cplx<R>::T y;
-        y.x = X.x * G;
-        y.y = X.y * G;
-        rowp[i2] = y;
+      if (INV) {
+        // conjugated: the inverse transform is the forward one between two conjugations
+        const R G = Fhat * iw0[i0] * cg[c];
+        cur[e] = cmk<R>(X.x * G, -X.y * G);
+      }
+    }
+    if (INV) {
+      __syncthreads();
+      cur = xfft_lines<R, -1>(cur, oth, tw, x);
+      for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int c = e & (NC - 1), f = f0 + c;
+        if (f < x.ncol) {
+          C v = cur[e];
+          v.y = -v.y;
+          out[(int64_t)(e >> lognc) * rowst + f] = v;
+        }
       }
     }
   }
-  // block reduction, then the last block folds the per-block partials in a fixed order
-  __shared__ bool last;
-  const int wid = threadIdx.x >> 5;
-  if constexpr (std::is_same<R, double>::value) {
-    __shared__ double red[7][kThreads / 32];
-#pragma unroll
-    for (int j = 0; j < 7; ++j) {
-      const double v = warp_sum(acc[j]);
-      if (lane == 0) red[j][wid] = v;
-    }
-    __syncthreads();
+  {
+    // the CTA's sums in a fixed order (FP32: compensated pairs); k_xsum adds them up
+    __shared__ Acc red[7][kXThreads / 32];
+    const Acc t = cta_sum7<Acc, kXThreads / 32>(acc, red);
     if (threadIdx.x < 7) {
-      double v = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[threadIdx.x][w];
-      partials[threadIdx.x * nred + blockIdx.x] = v;
+      if constexpr (kD)
+        partials[(size_t)threadIdx.x * nactive + blockIdx.x] = t;
+      else
+        reinterpret_cast<float2*>(partials)[(size_t)threadIdx.x * nactive + blockIdx.x] =
+            make_float2(t.hi, t.lo);
     }
-  } else {
-    // compensated sums across the warp and the block; one FP64 conversion per block
-    __shared__ float red[7][kThreads / 32][2];
-#pragma unroll
-    for (int j = 0; j < 7; ++j) {
-      DF x = acc[j];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        DF y;
-        y.hi = __shfl_xor_sync(0xffffffffu, x.hi, o);
-        y.lo = __shfl_xor_sync(0xffffffffu, x.lo, o);
-        x.add(y);
-      }
-      if (lane == 0) {
-        red[j][wid][0] = x.hi;
-        red[j][wid][1] = x.lo;
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x < 7) {
-      DF x;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-        DF y;
-        y.hi = red[threadIdx.x][w][0];
-        y.lo = red[threadIdx.x][w][1];
-        x.add(y);
-      }
-      reinterpret_cast<float2*>(partials)[threadIdx.x * nred + blockIdx.x] = make_float2(x.hi, x.lo);
-    }
-  }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(counter, 1u) == (unsigned)nred - 1);
-  __syncthreads();
-  if (last) {
-    // warp j sums component j: coalesced L2 loads (ld.cg: written by other blocks before
-    // their fence), then a fixed-order warp reduction
-    __threadfence();
-    const int j = threadIdx.x >> 5;
-    if (j < 7) {
-      if constexpr (std::is_same<R, double>::value) {
-        double v = 0.0;
-        const double* pj = partials + (size_t)j * nred;
-        for (int b = lane; b < nred; b += 32) v += __ldcg(pj + b);
-        v = warp_sum(v);
-        if (lane == 0) accum[j] = v;
-      } else {
-        // compensated FP32 to the end, one FP64 conversion
-        DF x;
-        const float2* pj = reinterpret_cast<const float2*>(partials) + (size_t)j * nred;
-        for (int b = lane; b < nred; b += 32) {
-          const float2 v = __ldcg(pj + b);
-          DF y;
-          y.hi = v.x;
-          y.lo = v.y;
-          x.add(y);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          DF y;
-          y.hi = __shfl_xor_sync(0xffffffffu, x.hi, o);
-          y.lo = __shfl_xor_sync(0xffffffffu, x.lo, o);
-          x.add(y);
-        }
-        if (lane == 0) accum[j] = (double)x.hi + (double)x.lo;
-      }
-    }
-    if (threadIdx.x == 0) *counter = 0u;
   }
 }
 
@@ -1885,32 +2171,69 @@ cudaError_t launch_spread(bool fp64, const TileGeom& g, int ntiles, int nblocks,
   });
 }
 
-cudaError_t launch_scale(bool fp64, bool write, const ScaleGeom& s, void* spec,
-                         const void* invw2, const void* radtab, double* partials,
-                         unsigned int* counter, double* accum, int zero_blocks,
-                         cudaStream_t st) {
-  const int nbox = (2 * s.mmax[0] + 1) * (2 * s.mmax[1] + 1);
-  const int nred = (nbox + kThreads / 32 - 1) / (kThreads / 32);
-  const int nb = nred + (write ? zero_blocks : 0);
-  if (fp64) {
-    if (write)
-      k_scale<double, true><<<nb, kThreads, 0, st>>>((double2*)spec, s, (const double*)invw2,
-                                                    (const double*)radtab, partials, counter,
-                                                    accum, nred);
-    else
-      k_scale<double, false><<<nb, kThreads, 0, st>>>((double2*)spec, s, (const double*)invw2,
-                                                     (const double*)radtab, partials, counter,
-                                                     accum, nred);
-  } else {
-    if (write)
-      k_scale<float, true><<<nb, kThreads, 0, st>>>((float2*)spec, s, (const float*)invw2,
-                                                   (const float*)radtab, partials, counter,
-                                                   accum, nred);
-    else
-      k_scale<float, false><<<nb, kThreads, 0, st>>>((float2*)spec, s, (const float*)invw2,
-                                                    (const float*)radtab, partials, counter,
-                                                    accum, nred);
-  }
+int xfft_blocks(const XGeom& x) { return (x.ncol + (1 << x.lognc) - 1) >> x.lognc; }
+
+size_t xfft_smem_bytes(bool fp64, int M0, int lognc, int rdeg) {
+  const size_t es = fp64 ? 8 : 4;
+  return 2 * es * ((size_t)M0 + 2 * ((size_t)M0 << lognc)) +
+         es * ((size_t)M0 + 2 * (size_t)kRadialPieces * (rdeg + 1));
+}
+
+namespace {
+template <typename R>
+cudaError_t set_xfft_smem(size_t smem) {
+  cudaError_t e;
+  const int b = (int)smem;
+  if ((e = cudaFuncSetAttribute(k_xfft<R, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)))
+    return e;
+  if ((e = cudaFuncSetAttribute(k_xfft<R, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)))
+    return e;
+  return cudaFuncSetAttribute(k_xfft<R, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+}
+template <typename R>
+void run_xfft(bool fwd, bool inv, const XGeom& x, const ScaleGeom& s, const void* spec, void* out,
+              const void* tw,
+              const void* invw2, const void* radtab, double* partials, const int* order,
+              const unsigned char* colact, int nactive, cudaStream_t st) {
+  using C = typename Cplx<R>::T;
+  const int nb = nactive;
+  const size_t smem = xfft_smem_bytes(std::is_same<R, double>::value, x.M0, x.lognc, s.rdeg);
+  auto go = [&](auto kern) {
+    kern<<<nb, kXThreads, smem, st>>>((const C*)spec, (C*)out, x, s, (const C*)tw, (const R*)invw2,
+                                      (const R*)radtab, partials, order, colact, nactive);
+  };
+  if (fwd)
+    go(k_xfft<R, true, true>);
+  else if (inv)
+    go(k_xfft<R, false, true>);
+  else
+    go(k_xfft<R, false, false>);
+}
+}  // namespace
+
+cudaError_t configure_xfft(bool fp64, size_t smem) {
+  return fp64 ? set_xfft_smem<double>(smem) : set_xfft_smem<float>(smem);
+}
+
+cudaError_t launch_xfft(bool fp64, bool fwd, bool inv, const XGeom& x, const ScaleGeom& s,
+                        const void* spec, void* out, const void* tw, const void* invw2,
+                        const void* radtab,
+                        double* partials, const int* order, const unsigned char* colact,
+                        int nactive, cudaStream_t st) {
+  if ((fwd && !inv) || nactive < 1) return cudaErrorInvalidValue;
+  if (fp64)
+    run_xfft<double>(fwd, inv, x, s, spec, out, tw, invw2, radtab, partials, order, colact, nactive, st);
+  else
+    run_xfft<float>(fwd, inv, x, s, spec, out, tw, invw2, radtab, partials, order, colact, nactive, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_xsum(bool fp64, const double* partials, int nblk, double* accum,
+                        cudaStream_t st) {
+  if (fp64)
+    k_xsum<double><<<1, kThreads, 0, st>>>(partials, nblk, accum);
+  else
+    k_xsum<float><<<1, kThreads, 0, st>>>(partials, nblk, accum);
   return cudaGetLastError();
 }
 

@@ -56,6 +56,19 @@ struct ScaleGeom {
   float K2f, x_per_kf, Af, scalef;  // FP32 copies
 };
 
+// The FFT along the first grid axis (fused with the scaling): length M0 = product of the
+// pass radices (8, 4, 2, 3, 5, 7, then primes), over ncol = M1 * H2 columns taken
+// 2^lognc at a time per CTA.
+constexpr int kMaxPass = 32;
+struct XGeom {
+  int M0;
+  int ncol;
+  int lognc;
+  int npass;
+  int radix[kMaxPass];
+  unsigned int ns_magic[kMaxPass];  // ceil(2^32 / Ns) (unused for Ns = 1), Ns = product of the radices before
+};
+
 struct GatherGeom {
   TileGeom g;
   double fscale;  // 1 / (V Mtot^2)
@@ -163,12 +176,27 @@ cudaError_t launch_scatter(bool fp64, int64_t n, int ksub, const int* ptile, con
 cudaError_t launch_spread(bool fp64, const TileGeom& g, int ntiles, int nblocks,
                           const void* sorted_tq, const int* sorted_lb, const int* toff,
                           int* work, const void* wtab, void* grid, cudaStream_t st);
-// Blocks: one warp per spectrum row of the sphere's bounding box, plus zero_blocks that
-// clear the other rows on the force path.  partials needs 7 x (rows / 8 + 1) doubles.
-cudaError_t launch_scale(bool fp64, bool write, const ScaleGeom& s, void* spec,
-                         const void* invw2, const void* radtab, double* partials,
-                         unsigned int* counter, double* accum, int zero_blocks,
-                         cudaStream_t st);
+// The transform along axis 0 fused with the scaling (k_xfft, kXThreads per CTA): the
+// sums of U_F and W_F over the sphere; fwd: the columns first take the forward transform
+// along axis 0 (the planes are transformed), else they hold the full 3D spectrum; inv: the
+// scaled modes take the inverse transform along axis 0 and go to out, of which only the
+// active columns are written (the caller clears out first); fwd needs inv.  tw: M0 roots e^{-2 pi i m / M0}
+// of the compute type.  order: the xfft_blocks(x) column groups, the nactive (>= 1)
+// groups holding every column with colact[f] = 1 first.  colact: per column, 1 if its line
+// k = m0 b_0 + m1 b_1 + m2 b_2 may enter the sphere |k| <= K.  partials: 7 x nactive
+// doubles (per-CTA sums of U_F and W_F xx yy zz xy xz yz); launch_xsum(partials, nactive)
+// adds them into accum[0..6].
+constexpr int kXThreads = 512;
+int xfft_blocks(const XGeom& x);
+size_t xfft_smem_bytes(bool fp64, int M0, int lognc, int rdeg);
+cudaError_t configure_xfft(bool fp64, size_t smem);
+cudaError_t launch_xfft(bool fp64, bool fwd, bool inv, const XGeom& x, const ScaleGeom& s,
+                        const void* spec, void* out, const void* tw, const void* invw2,
+                        const void* radtab,
+                        double* partials, const int* order, const unsigned char* colact,
+                        int nactive, cudaStream_t st);
+cudaError_t launch_xsum(bool fp64, const double* partials, int nblk, double* accum,
+                        cudaStream_t st);
 cudaError_t launch_gather(bool fp64, bool io_double, const GatherGeom& gg, int ntiles,
                           int nblocks, const void* sorted_tq, const int* sorted_lb,
                           const int* sorted_idx, const int* toff, int* work, const void* wtab,
