@@ -74,7 +74,9 @@ typedef struct {
 
 /*
  * esp_plan - build a plan for N atoms in cell h on an M1 x M2 x M3 grid.
- *   grid[3]  M_d >= 2; the real grid is row-major with the third index fastest.
+ *   grid[3]  M_d >= 2; the real grid is row-major with the third index fastest.  M1 at
+ *            most about 8000 (FP32) or 4000 (FP64): the transform along the first axis
+ *            keeps a column group in shared memory (ESP_ERR_ARG beyond).
  *   w        stencil width P (grid points per dimension, Sec. 4.3), 3 <= P <= 12, P < M_d.
  *   c        PSWF shape parameter c > 0 (Sec. 3.1; see esp_c_from_tolerance).
  *   alpha    the split radius r_c in Angstrom (Sec. 3.1, eq. (decomposition)); ESP has
@@ -222,8 +224,10 @@ int esp_plan_info(esp_plan_t plan, double* info, int len);
  * esp_profile_read synchronises the stream and writes the last step's stage durations
  * in ms, in the order: [0] set-up, [1] bin (which also clears the spread grid), [2] scan,
  * [3] scatter, [4] separate grid clearing (0 when the bin kernel clears the grid),
- * [5] spread, [6] forward FFT, [7] scale + reduce, [8] inverse FFT, [9] gather
- * (stages that did not run read 0).  Writes min(len, 10) values. */
+ * [5] spread, [6] forward FFT (the plane transforms on the force path, the full 3D
+ * transform on the energy and pressure path), [7] transform along the first axis fused
+ * with the scaling and the sums, [8] inverse plane transforms, [9] gather (stages that
+ * did not run read 0).  Writes min(len, 10) values. */
 int esp_profile(esp_plan_t plan, int enable);
 int esp_profile_read(esp_plan_t plan, double* stage_ms, int len);
 

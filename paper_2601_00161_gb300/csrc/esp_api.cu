@@ -227,6 +227,7 @@ void update_cell_constants(esp_plan_t p) {
   p->sg.scalef = (float)p->sg.scale;
   p->gg.g = p->tg;
   p->gg.fscale = 1.0 / (p->V * Mtot * Mtot);
+  p->gg.fscalef = (float)p->gg.fscale;
 }
 
 // Column groups of the transform along axis 0 for the current cell: a column (m1, m2) is

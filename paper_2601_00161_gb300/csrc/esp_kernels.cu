@@ -1468,7 +1468,7 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 4 : 
           const int idx = X[a];
           const R qa = TQ[a].w;
           if constexpr (std::is_same<R, float>::value) {
-            const float f = qa * (float)gg.fscale;
+            const float f = qa * gg.fscalef;
 #pragma unroll
             for (int c = 0; c < 3; ++c)
               forces[3 * (int64_t)idx + c] =

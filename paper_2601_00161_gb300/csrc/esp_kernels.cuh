@@ -72,6 +72,7 @@ struct XGeom {
 struct GatherGeom {
   TileGeom g;
   double fscale;  // 1 / (V Mtot^2)
+  float fscalef;  // the same in FP32 (an FP64 conversion per atom is slow on this part)
 };
 
 // Near (real-space) part of the split: a cell list with nc[d] >= 1 bins per reduced axis
