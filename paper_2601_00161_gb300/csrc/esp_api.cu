@@ -502,8 +502,7 @@ int run_step(esp_plan_t p, const void* pos, const void* q, void* forces, double*
                               es * Mtot, st));
   mark(p, kScan);
   ESP_CUDA(p, esp::launch_scan(p->d_count, p->d_suboff, p->d_offset, p->d_bsum, p->ntiles,
-                               p->tg.ksub, p->d_binpart, p->n > 0 ? p->bin_blocks : 0, acc,
-                               work, st));
+                               p->tg.ksub, work, st));
   mark(p, kScatter);
   ESP_CUDA(p, esp::launch_scatter(fp64, p->n, p->tg.ksub, p->d_ptile, p->d_prank, p->d_plb, p->d_tq,
                                   p->d_suboff, p->d_sorted_tq, p->d_sorted_lb,
@@ -527,7 +526,8 @@ int run_step(esp_plan_t p, const void* pos, const void* q, void* forces, double*
   // the energy and virial sums finish on the side branch while the forces go on
   ESP_CUDA(p, cudaEventRecord(p->ev_fork, st));
   ESP_CUDA(p, cudaStreamWaitEvent(p->side, p->ev_fork, 0));
-  ESP_CUDA(p, esp::launch_xsum(fp64, p->d_partials, p->xactive, acc, p->side));
+  ESP_CUDA(p, esp::launch_xsum(fp64, p->d_partials, p->xactive, p->d_binpart,
+                               p->n > 0 ? p->bin_blocks : 0, acc, p->side));
   ESP_CUDA(p, cudaEventRecord(p->ev_join, p->side));
   mark(p, kFftInv);
   if (want_f) {
@@ -936,7 +936,8 @@ int esp_forces_from_spectrum(esp_plan_t p, void* forces) {
   ESP_CUDA(p, esp::launch_xfft(fp64, false, true, p->xg, p->sg, p->d_spec, p->d_spec2, p->d_xtw,
                                p->d_invw2, p->d_radtab, p->d_partials, p->d_xorder, p->d_xcol,
                                p->xactive, st));
-  ESP_CUDA(p, esp::launch_xsum(fp64, p->d_partials, p->xactive, p->d_accum, st));
+  ESP_CUDA(p, esp::launch_xsum(fp64, p->d_partials, p->xactive, p->d_binpart,
+                               p->n > 0 ? p->bin_blocks : 0, p->d_accum, st));
   if (fp64)
     ESP_CUFFT(p, cufftExecZ2D(p->inv, (cufftDoubleComplex*)p->d_spec2, (cufftDoubleReal*)p->d_grid));
   else
@@ -1387,8 +1388,7 @@ extern "C" int esp_spread_noalloc(const double cell[9], int64_t n, const int gri
   ESP_CUDA(nullptr, cudaMemsetAsync(count, 0, sizeof(int) * ((size_t)p->ntiles * esp::kSub + 2), st));
   ESP_CUDA(nullptr, esp::launch_bin(p->io_double, p->fp64, pos, q, n, g, count, ptile, prank, plb,
                                     tq, binpart, nullptr, 0, st));
-  ESP_CUDA(nullptr, esp::launch_scan(count, suboff, toff, bsum, p->ntiles, g.ksub, binpart,
-                                     n > 0 ? esp::bin_blocks(n) : 0, acc, work, st));
+  ESP_CUDA(nullptr, esp::launch_scan(count, suboff, toff, bsum, p->ntiles, g.ksub, work, st));
   ESP_CUDA(nullptr, esp::launch_scatter(p->fp64, n, g.ksub, ptile, prank, plb, tq, suboff, stq,
                                         slb, sidx, st));
   ESP_CUDA(nullptr, cudaMemsetAsync(grid_out, 0, es * Mtot, st));

@@ -63,6 +63,13 @@ __device__ __forceinline__ int fast_div(int x, unsigned int m) {
 }
 
 // x in [0, 3 m) -> x mod m
+// Programmatic dependent launch: a kernel launched with programmatic stream serialization
+// may start while the kernel before it finishes; it waits here before touching that
+// kernel's results (a no-op for a plain launch).  The trigger lets the next kernel's CTAs
+// be scheduled early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;"); }
+
 __device__ __forceinline__ int wrap3(int x, int m) {
   x = x >= m ? x - m : x;
   return x >= m ? x - m : x;
@@ -183,6 +190,7 @@ __global__ void __launch_bounds__(kThreads) k_bin(const IO* __restrict__ pos,
                                                   typename Vec4<R>::T* __restrict__ tq,
                                                   float2* __restrict__ bin_part,
                                                   int4* __restrict__ zero, int64_t nzero) {
+  pdl_trigger();
   // FP32 inputs on the FP32 path use the compensated FP32 transform (FP64 only for the
   // rare coordinate next to a stencil switch); everything else uses FP64.
   constexpr bool kDF = std::is_same<IO, float>::value && std::is_same<R, float>::value;
@@ -283,9 +291,9 @@ __global__ void __launch_bounds__(kThreads) k_bin(const IO* __restrict__ pos,
 //                 exclusive prefix to suboff and its total to bsum, and zeroes the counts
 //                 for the next step;
 //   k_scan_fix    each block adds the sum of the totals of the blocks before it and
-//                 writes the tile offsets toff[t] = suboff[t * ksub]; block 0 also adds
-//                 up the binning partials (sum q, sum q^2, skipped atoms) into accum[7..9]
-//                 and resets the work counters of spread and gather.
+//                 writes the tile offsets toff[t] = suboff[t * ksub]; block 0 also resets
+//                 the work counters of spread and gather.  (The binning partials are
+//                 added up by k_xsum, off the critical path.)
 constexpr int kScanBlock = 4 * kThreads;
 
 __device__ __forceinline__ int block_exclusive_scan(int v, int* wsum, int* total) {
@@ -315,6 +323,8 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* wsum, int* total
 __global__ void __launch_bounds__(kThreads) k_scan_local(int* __restrict__ count,
                                                          int* __restrict__ suboff,
                                                          int* __restrict__ bsum, int n) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ int wsum[kThreads / 32];
   const int i = blockIdx.x * kScanBlock + 4 * threadIdx.x;
   int v[4] = {0, 0, 0, 0};
@@ -351,9 +361,9 @@ __global__ void __launch_bounds__(kThreads) k_scan_fix(int* __restrict__ suboff,
                                                        int* __restrict__ toff,
                                                        const int* __restrict__ bsum,
                                                        int ntiles, int ksub,
-                                                       const float2* __restrict__ bin_part,
-                                                       int nbin, double* __restrict__ accum,
                                                        int* __restrict__ work) {
+  pdl_wait();
+  pdl_trigger();
   __shared__ int red[kThreads / 32];
   const int n = ntiles * ksub;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -380,29 +390,7 @@ __global__ void __launch_bounds__(kThreads) k_scan_fix(int* __restrict__ suboff,
     suboff[n] = tot;
     toff[ntiles] = tot;
   }
-  if (blockIdx.x == 0) {
-    if (threadIdx.x < 2) work[threadIdx.x] = 0;
-    // binning partials: warp j adds component j in compensated FP32 (fixed order); one
-    // FP64 conversion at the end (dependent FP64 chains are slow on this part)
-    if (wid < 3) {
-      DF a;
-      for (int b = lane; b < nbin; b += 32) {
-        const float2 v = bin_part[3 * b + wid];
-        DF y;
-        y.hi = v.x;
-        y.lo = v.y;
-        a.add(y);
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        DF y;
-        y.hi = __shfl_xor_sync(0xffffffffu, a.hi, o);
-        y.lo = __shfl_xor_sync(0xffffffffu, a.lo, o);
-        a.add(y);
-      }
-      if (lane == 0) accum[7 + wid] = (double)a.hi + (double)a.lo;
-    }
-  }
+  if (blockIdx.x == 0 && threadIdx.x < 2) work[threadIdx.x] = 0;
 }
 
 template <typename V>
@@ -410,6 +398,8 @@ __global__ void __launch_bounds__(kThreads) k_scatter(
     int64_t n, int ksub, const int* __restrict__ ptile, const int* __restrict__ prank,
     const int* __restrict__ plb, const V* __restrict__ tq, const int* __restrict__ offset,
     V* __restrict__ sorted_tq, int* __restrict__ sorted_lb, int* __restrict__ sorted_idx) {
+  pdl_wait();
+  pdl_trigger();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int tile = ptile[i];
@@ -584,6 +574,7 @@ __global__ void __launch_bounds__(kThreads) k_spread(
     const typename Vec4<R>::T* __restrict__ sorted_tq, const int* __restrict__ sorted_lb,
     const int* __restrict__ toff, TileGeom g, int ntiles, int* __restrict__ work,
     const R* __restrict__ wtab, R* __restrict__ grid) {
+  pdl_wait();
   using V4 = typename Vec4<R>::T;
   using TC = TileC<P>;
   using CM = Cols<P>;
@@ -1077,13 +1068,33 @@ __device__ __forceinline__ A cta_sum7(const A (&acc)[7], A (*red)[NW]) {
   return r;
 }
 
-// Final sum of the per-CTA partials of k_xfft (component j at partials[j * nblk + b]) in a
-// fixed order: one CTA, launched after k_xfft (on a branch of its own in the step graph).
+// Final sums in a fixed order, one CTA launched after k_xfft (on a branch of its own in the
+// step graph): accum[0..6] from the per-CTA partials of k_xfft (component j at
+// partials[j * nblk + b]); accum[7..9] (sum q, sum q^2, skipped atoms) from the binning
+// partials (3 compensated pairs per k_bin block).
 template <typename R>
 __global__ void __launch_bounds__(kThreads) k_xsum(const double* __restrict__ partials, int nblk,
+                                                   const float2* __restrict__ bin_part, int nbin,
                                                    double* __restrict__ accum) {
   using A = typename std::conditional<std::is_same<R, double>::value, double, DF>::type;
   __shared__ A red[7][kThreads / 32];
+  __shared__ DF redb[7][kThreads / 32];
+  {
+    DF sb[7];
+#pragma unroll 4
+    for (int b = threadIdx.x; b < nbin; b += blockDim.x) {
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const float2 v = bin_part[3 * b + j];
+        DF y;
+        y.hi = v.x;
+        y.lo = v.y;
+        sb[j].add(y);
+      }
+    }
+    const DF t = cta_sum7<DF, kThreads / 32>(sb, redb);
+    if (threadIdx.x < 3) accum[7 + threadIdx.x] = (double)t.hi + (double)t.lo;
+  }
   A s[7];
 #pragma unroll
   for (int j = 0; j < 7; ++j) s[j] = A{};
@@ -1299,6 +1310,7 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 4 : 
     const int* __restrict__ sorted_idx, const int* __restrict__ toff, GatherGeom gg,
     int ntiles, int* __restrict__ work, const R* __restrict__ wtab,
     const R* __restrict__ grid, IO* __restrict__ forces) {
+  pdl_wait();
   const TileGeom& g = gg.g;
   using TC = TileC<P>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -2049,6 +2061,28 @@ cudaError_t with_P(int P, F&& f) {
 }  // namespace
 
 // ---- host launchers --------------------------------------------------------------------
+// A launch with programmatic stream serialization (the kernel begins with pdl_wait), so
+// its launch overlaps the end of the kernel before it; plain on the legacy default stream.
+template <typename... KArgs, typename... Args>
+cudaError_t pdl_launch(void (*kern)(KArgs...), int grid, int block, size_t smem,
+                       cudaStream_t st, Args... args) {
+  if (st == nullptr) {
+    kern<<<grid, block, smem, st>>>(args...);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, static_cast<KArgs>(args)...);
+}
+
 cudaError_t launch_bin(bool io_double, bool fp64, const void* pos, const void* q, int64_t n,
                        const TileGeom& g, int* tile_count, int* ptile, int* prank, int* plb,
                        void* tq, void* bin_part_v, void* zero_buf, size_t zero_bytes,
@@ -2084,16 +2118,13 @@ cudaError_t launch_bin(bool io_double, bool fp64, const void* pos, const void* q
 }
 
 cudaError_t launch_scan(int* count, int* suboff, int* toff, int* bsum, int ntiles, int ksub,
-                        const void* bin_part, int nbin, double* accum, int* work,
-                        cudaStream_t st) {
+                        int* work, cudaStream_t st) {
   const int n = ntiles * ksub;
   const int nb = (n + kScanBlock - 1) / kScanBlock;
-  k_scan_local<<<nb, kThreads, 0, st>>>(count, suboff, bsum, n);
-  cudaError_t e = cudaGetLastError();
+  cudaError_t e = pdl_launch(k_scan_local, nb, kThreads, 0, st, count, suboff, bsum, n);
   if (e != cudaSuccess) return e;
-  k_scan_fix<<<nb, kThreads, 0, st>>>(suboff, toff, bsum, ntiles, ksub, (const float2*)bin_part,
-                                      nbin, accum, work);
-  return cudaGetLastError();
+  return pdl_launch(k_scan_fix, nb, kThreads, 0, st, suboff, toff, (const int*)bsum, ntiles, ksub,
+                    work);
 }
 
 int scan_blocks(int ntiles, int ksub) { return (ntiles * ksub + kScanBlock - 1) / kScanBlock; }
@@ -2106,13 +2137,10 @@ cudaError_t launch_scatter(bool fp64, int64_t n, int ksub, const int* ptile, con
   if (n <= 0) return cudaSuccess;
   const int nb = grid_blocks(n);
   if (fp64)
-    k_scatter<double4><<<nb, kThreads, 0, st>>>(n, ksub, ptile, prank, plb, (const double4*)tq,
-                                                offset, (double4*)sorted_tq, sorted_lb,
-                                                sorted_idx);
-  else
-    k_scatter<float4><<<nb, kThreads, 0, st>>>(n, ksub, ptile, prank, plb, (const float4*)tq, offset,
-                                               (float4*)sorted_tq, sorted_lb, sorted_idx);
-  return cudaGetLastError();
+    return pdl_launch(k_scatter<double4>, nb, kThreads, 0, st, n, ksub, ptile, prank, plb,
+                      (const double4*)tq, offset, (double4*)sorted_tq, sorted_lb, sorted_idx);
+  return pdl_launch(k_scatter<float4>, nb, kThreads, 0, st, n, ksub, ptile, prank, plb,
+                    (const float4*)tq, offset, (float4*)sorted_tq, sorted_lb, sorted_idx);
 }
 
 size_t spread_smem_bytes(bool fp64, const TileGeom& g) {
@@ -2160,14 +2188,11 @@ cudaError_t launch_spread(bool fp64, const TileGeom& g, int ntiles, int nblocks,
   return with_P(g.P, [&](auto pc) -> cudaError_t {
     constexpr int PP = decltype(pc)::value;
     if (fp64)
-      k_spread<double, PP><<<nblocks, kThreads, smem, st>>>(
-          (const double4*)sorted_tq, sorted_lb, toff, g, ntiles, work, (const double*)wtab,
-          (double*)grid);
-    else
-      k_spread<float, PP><<<nblocks, kThreads, smem, st>>>(
-          (const float4*)sorted_tq, sorted_lb, toff, g, ntiles, work, (const float*)wtab,
-          (float*)grid);
-    return cudaGetLastError();
+      return pdl_launch(k_spread<double, PP>, nblocks, kThreads, smem, st,
+                        (const double4*)sorted_tq, sorted_lb, toff, g, ntiles, work,
+                        (const double*)wtab, (double*)grid);
+    return pdl_launch(k_spread<float, PP>, nblocks, kThreads, smem, st, (const float4*)sorted_tq,
+                      sorted_lb, toff, g, ntiles, work, (const float*)wtab, (float*)grid);
   });
 }
 
@@ -2191,23 +2216,23 @@ cudaError_t set_xfft_smem(size_t smem) {
   return cudaFuncSetAttribute(k_xfft<R, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
 }
 template <typename R>
-void run_xfft(bool fwd, bool inv, const XGeom& x, const ScaleGeom& s, const void* spec, void* out,
+cudaError_t run_xfft(bool fwd, bool inv, const XGeom& x, const ScaleGeom& s, const void* spec, void* out,
               const void* tw,
               const void* invw2, const void* radtab, double* partials, const int* order,
               const unsigned char* colact, int nactive, cudaStream_t st) {
   using C = typename Cplx<R>::T;
   const int nb = nactive;
   const size_t smem = xfft_smem_bytes(std::is_same<R, double>::value, x.M0, x.lognc, s.rdeg);
+  // a plain launch: on the force path the kernel also waits for the side branch's clear
   auto go = [&](auto kern) {
-    kern<<<nb, kXThreads, smem, st>>>((const C*)spec, (C*)out, x, s, (const C*)tw, (const R*)invw2,
-                                      (const R*)radtab, partials, order, colact, nactive);
+    kern<<<nb, kXThreads, smem, st>>>((const C*)spec, (C*)out, x, s, (const C*)tw,
+                                      (const R*)invw2, (const R*)radtab, partials, order, colact,
+                                      nactive);
+    return cudaGetLastError();
   };
-  if (fwd)
-    go(k_xfft<R, true, true>);
-  else if (inv)
-    go(k_xfft<R, false, true>);
-  else
-    go(k_xfft<R, false, false>);
+  if (fwd) return go(k_xfft<R, true, true>);
+  if (inv) return go(k_xfft<R, false, true>);
+  return go(k_xfft<R, false, false>);
 }
 }  // namespace
 
@@ -2222,18 +2247,19 @@ cudaError_t launch_xfft(bool fp64, bool fwd, bool inv, const XGeom& x, const Sca
                         int nactive, cudaStream_t st) {
   if ((fwd && !inv) || nactive < 1) return cudaErrorInvalidValue;
   if (fp64)
-    run_xfft<double>(fwd, inv, x, s, spec, out, tw, invw2, radtab, partials, order, colact, nactive, st);
-  else
-    run_xfft<float>(fwd, inv, x, s, spec, out, tw, invw2, radtab, partials, order, colact, nactive, st);
-  return cudaGetLastError();
+    return run_xfft<double>(fwd, inv, x, s, spec, out, tw, invw2, radtab, partials, order, colact,
+                            nactive, st);
+  return run_xfft<float>(fwd, inv, x, s, spec, out, tw, invw2, radtab, partials, order, colact,
+                         nactive, st);
 }
 
-cudaError_t launch_xsum(bool fp64, const double* partials, int nblk, double* accum,
-                        cudaStream_t st) {
+cudaError_t launch_xsum(bool fp64, const double* partials, int nblk, const void* bin_part,
+                        int nbin, double* accum, cudaStream_t st) {
+  const float2* bp = (const float2*)bin_part;
   if (fp64)
-    k_xsum<double><<<1, kThreads, 0, st>>>(partials, nblk, accum);
+    k_xsum<double><<<1, kThreads, 0, st>>>(partials, nblk, bp, nbin, accum);
   else
-    k_xsum<float><<<1, kThreads, 0, st>>>(partials, nblk, accum);
+    k_xsum<float><<<1, kThreads, 0, st>>>(partials, nblk, bp, nbin, accum);
   return cudaGetLastError();
 }
 
@@ -2245,18 +2271,16 @@ cudaError_t launch_gather(bool fp64, bool io_double, const GatherGeom& gg, int n
   return with_P(gg.g.P, [&](auto pc) -> cudaError_t {
     constexpr int PP = decltype(pc)::value;
     if (fp64)
-      k_gather<double, double, PP><<<nblocks, kThreads, smem, st>>>(
-          (const double4*)sorted_tq, sorted_lb, sorted_idx, toff, gg, ntiles, work,
-          (const double*)wtab, (const double*)grid, (double*)forces);
-    else if (io_double)
-      k_gather<float, double, PP><<<nblocks, kThreads, smem, st>>>(
-          (const float4*)sorted_tq, sorted_lb, sorted_idx, toff, gg, ntiles, work,
-          (const float*)wtab, (const float*)grid, (double*)forces);
-    else
-      k_gather<float, float, PP><<<nblocks, kThreads, smem, st>>>(
-          (const float4*)sorted_tq, sorted_lb, sorted_idx, toff, gg, ntiles, work,
-          (const float*)wtab, (const float*)grid, (float*)forces);
-    return cudaGetLastError();
+      return pdl_launch(k_gather<double, double, PP>, nblocks, kThreads, smem, st,
+                        (const double4*)sorted_tq, sorted_lb, sorted_idx, toff, gg, ntiles, work,
+                        (const double*)wtab, (const double*)grid, (double*)forces);
+    if (io_double)
+      return pdl_launch(k_gather<float, double, PP>, nblocks, kThreads, smem, st,
+                        (const float4*)sorted_tq, sorted_lb, sorted_idx, toff, gg, ntiles, work,
+                        (const float*)wtab, (const float*)grid, (double*)forces);
+    return pdl_launch(k_gather<float, float, PP>, nblocks, kThreads, smem, st,
+                      (const float4*)sorted_tq, sorted_lb, sorted_idx, toff, gg, ntiles, work,
+                      (const float*)wtab, (const float*)grid, (float*)forces);
   });
 }
 

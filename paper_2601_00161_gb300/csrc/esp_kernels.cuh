@@ -166,10 +166,9 @@ cudaError_t launch_bin(bool io_double, bool fp64, const void* pos, const void* q
                        cudaStream_t st);
 int bin_blocks(int64_t n);
 // count: zero on entry (bin adds into it), zero again on exit; work[0..1] zeroed too.
-// bin_part: per binning block 3 compensated sums (float pairs); bsum: scan_blocks() ints.
+// bsum: scan_blocks() ints.
 cudaError_t launch_scan(int* count, int* suboff, int* toff, int* bsum, int ntiles, int ksub,
-                        const void* bin_part, int nbin, double* accum, int* work,
-                        cudaStream_t st);
+                        int* work, cudaStream_t st);
 int scan_blocks(int ntiles, int ksub);
 cudaError_t launch_scatter(bool fp64, int64_t n, int ksub, const int* ptile, const int* prank,
                            const int* plb, const void* tq, const int* offset, void* sorted_tq,
@@ -186,7 +185,8 @@ cudaError_t launch_spread(bool fp64, const TileGeom& g, int ntiles, int nblocks,
 // groups holding every column with colact[f] = 1 first.  colact: per column, 1 if its line
 // k = m0 b_0 + m1 b_1 + m2 b_2 may enter the sphere |k| <= K.  partials: 7 x nactive
 // doubles (per-CTA sums of U_F and W_F xx yy zz xy xz yz); launch_xsum(partials, nactive)
-// adds them into accum[0..6].
+// adds them into accum[0..6], and the binning partials (bin_part: per binning block 3
+// compensated sums as float pairs; nbin blocks, 0 for no atoms) into accum[7..9].
 constexpr int kXThreads = 512;
 int xfft_blocks(const XGeom& x);
 size_t xfft_smem_bytes(bool fp64, int M0, int lognc, int rdeg);
@@ -196,8 +196,8 @@ cudaError_t launch_xfft(bool fp64, bool fwd, bool inv, const XGeom& x, const Sca
                         const void* radtab,
                         double* partials, const int* order, const unsigned char* colact,
                         int nactive, cudaStream_t st);
-cudaError_t launch_xsum(bool fp64, const double* partials, int nblk, double* accum,
-                        cudaStream_t st);
+cudaError_t launch_xsum(bool fp64, const double* partials, int nblk, const void* bin_part,
+                        int nbin, double* accum, cudaStream_t st);
 cudaError_t launch_gather(bool fp64, bool io_double, const GatherGeom& gg, int ntiles,
                           int nblocks, const void* sorted_tq, const int* sorted_lb,
                           const int* sorted_idx, const int* toff, int* work, const void* wtab,
