@@ -434,7 +434,7 @@ def esp_arm(args):
                  "step": "near part of the split (esp_near): device cell list, pairs within r_c, "
                          "energy, virial, forces added onto the long-range ones"}
 
-    launches_per_step = 7  # bin, scan (2), scatter, spread, scale, gather
+    launches_per_step = 8  # bin, scan (2), scatter, spread, xfft, xsum, gather
     out = None
     if rank == 0:
         ms = 1e3 * t_max / args.steps
