@@ -54,7 +54,7 @@ def run_gpu(S, c, precision, forces=True):
     return plan, res, F, pos.double().cpu().numpy(), q.double().cpu().numpy()
 
 
-def check(S, precision, c=None, forces=True, force_rows=None):
+def check(S, precision, c=None, forces=True, force_rows=None, ftol=None):
     c = c_from_tolerance(S.delta) if c is None else c
     plan, res, F, pos, q = run_gpu(S, c, precision, forces)
     # the oracle sees exactly the inputs the GPU saw (FP32 rounding included)
@@ -65,8 +65,9 @@ def check(S, precision, c=None, forces=True, force_rows=None):
     assert rel(res["pressure_recip"], ref["virial"] / np.linalg.det(S.cell)) < tol
     if forces:
         Fg = F if force_rows is None else F[force_rows]
-        assert rel(Fg, ref["forces"]) < tol
-        assert np.max(np.abs(Fg - ref["forces"])) < 10 * tol * np.max(np.abs(ref["forces"]))
+        ft = tol if ftol is None else ftol
+        assert rel(Fg, ref["forces"]) < ft
+        assert np.max(np.abs(Fg - ref["forces"])) < 10 * ft * np.max(np.abs(ref["forces"]))
     plan.close()
     return res, F
 
@@ -79,6 +80,29 @@ ORTHO = np.diag([11.0, 13.0, 17.0])
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_water648(precision):
     check(sy.water_cubic(), precision)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("grid,cell,n", [
+    # 1001 = 7 * 11 * 13: passes of radix 7 and of two larger primes, and a first axis long
+    # enough that fewer columns share a CTA (4 in FP32, 2 in FP64).  The cross-section is
+    # kept several r_c wide: a cell a few angstrom thin has transverse forces a hundred
+    # times below the longitudinal ones, which FP32 cannot resolve to 2e-6 normwise.
+    ((1001, 28, 30), np.diag([300.0, 12.0, 13.0]), 1200),
+    # a prime first axis: one direct pass of length 127
+    ((127, 16, 18), np.diag([60.0, 5.0, 5.5]), 150),
+])
+def test_first_axis_transform_sizes(precision, grid, cell, n):
+    """The transform along the first axis (in shared memory, fused with the scaling) for
+    lengths that the common grid sizes do not reach.  FP64 holds the 1e-12 bar.  FP32
+    forces on the 1001-point axis come out 7.6e-6 from the oracle normwise, exactly as
+    the full cuFFT 3D transform plus a separate scaling gave (measured on the same
+    inputs), against 1.1e-6 on a 250-point axis at the same spacing: the loss is FP32
+    arithmetic on the long axis, not this transform.  Those forces are held to the
+    1e-5 accuracy bar of the method's target instead of 2e-6; energy and virial keep 2e-6."""
+    rc = fitting_rc(cell, grid, 1e-5)
+    S = sy.small_random(n, cell, seed=31, grid=grid, P=6, delta=1e-5, rc=rc)
+    check(S, precision, ftol=1e-5 if (precision == "fp32" and grid[0] > 512) else None)
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
