@@ -197,7 +197,8 @@ int esp_forces_from_spectrum(esp_plan_t plan, void* forces);
 
 /* End-to-end call with HOST buffers: copies pos, q (I/O type) to the device, runs the
  * full step, copies forces (may be NULL) back and fills *out (may be NULL).
- * Synchronous.  pos/q/forces may be pageable or pinned host memory. */
+ * Synchronous.  pos/q/forces may be pageable or pinned host memory; page-locked pos and
+ * q are read in place by the binning kernel (no staging copy), others are copied first. */
 int esp_compute_host(esp_plan_t plan, const void* pos, const void* q, void* forces,
                      esp_result* out);
 
@@ -214,8 +215,9 @@ int esp_copy_spectrum(esp_plan_t plan, void* host_dst);
 
 /* Plan facts: [0] c, [1] r_c, [2] psi_0(0), [3] C_0, [4] lambda_0, [5] window table
  * degree, [6] radial table degree, [7] max window fit error / psi_0(0), [8] max radial
- * fit error / psi_0(0), [9] tiles, [10] tile T1, [11] T2, [12] T3, [13] kernel launches
- * per full step, [14] background constant X = r_c^2/2 - int_0^{r_c} r phi_0.
+ * fit error / psi_0(0), [9] tiles, [10] tile T1, [11] T2, [12] T3, [13] launches of the
+ * library's own kernels per full step (cuFFT's not counted), [14] background constant
+ * X = r_c^2/2 - int_0^{r_c} r phi_0.
  * Writes min(len, 15) values. */
 int esp_plan_info(esp_plan_t plan, double* info, int len);
 

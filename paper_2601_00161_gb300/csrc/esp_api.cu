@@ -1106,6 +1106,18 @@ int esp_cell_gradient(esp_plan_t p, const void* pos, const void* forces, const d
   return ESP_OK;
 }
 
+namespace {
+// The device address of page-locked (pinned or registered) host memory, else NULL.
+const void* mapped_host(const void* ptr) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();  // clear the error of an unknown pointer
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+}  // namespace
+
 int esp_compute_host(esp_plan_t p, const void* pos, const void* q, void* forces,
                      esp_result* out) {
   if (!p) return fail(nullptr, ESP_ERR_ARG, "plan is NULL");
@@ -1119,13 +1131,24 @@ int esp_compute_host(esp_plan_t p, const void* pos, const void* q, void* forces,
     ESP_CUDA(p, cudaMalloc(&p->d_io_f, 3 * io_es * nn));
   }
   cudaStream_t st = p->stream;
+  // Page-locked host inputs are read by the binning kernel in place (through their device
+  // mapping); other host memory is copied to the plan's staging buffers first.
+  const void* dpos = p->d_io_pos;
+  const void* dq = p->d_io_q;
   if (p->n > 0) {
-    ESP_CUDA(p, cudaMemcpyAsync(p->d_io_pos, pos, 3 * io_es * p->n, cudaMemcpyHostToDevice, st));
-    ESP_CUDA(p, cudaMemcpyAsync(p->d_io_q, q, io_es * p->n, cudaMemcpyHostToDevice, st));
+    const void* mpos = mapped_host(pos);
+    const void* mq = mapped_host(q);
+    if (mpos && mq) {
+      dpos = mpos;
+      dq = mq;
+    } else {
+      ESP_CUDA(p, cudaMemcpyAsync(p->d_io_pos, pos, 3 * io_es * p->n, cudaMemcpyHostToDevice, st));
+      ESP_CUDA(p, cudaMemcpyAsync(p->d_io_q, q, io_es * p->n, cudaMemcpyHostToDevice, st));
+    }
   }
-  // the step through the captured graph: its device buffers are fixed, so one capture
-  // serves every call (plain launches on the legacy default stream)
-  int rc = run_step_graph(p, p->d_io_pos, p->d_io_q, forces ? p->d_io_f : nullptr, p->d_accum);
+  // the step through the captured graph: one capture serves every call with the same
+  // input buffers (plain launches on the legacy default stream)
+  int rc = run_step_graph(p, dpos, dq, forces ? p->d_io_f : nullptr, p->d_accum);
   if (rc != ESP_OK) return rc;
   ESP_CUDA(p, cudaMemcpyAsync(p->h_accum, p->d_accum, sizeof(double) * ESP_ACCUM_LEN,
                               cudaMemcpyDeviceToHost, st));
@@ -1178,7 +1201,7 @@ int esp_plan_info(esp_plan_t p, double* info, int len) {
                         (double)p->tg.T[0],
                         (double)p->tg.T[1],
                         (double)p->tg.T[2],
-                        6.0,
+                        8.0,  // bin, scan (2), scatter, spread, k_xfft, k_xsum, gather
                         p->Xbg};
   for (int i = 0; i < std::min(len, 15); ++i) info[i] = v[i];
   return ESP_OK;

@@ -205,6 +205,19 @@ def test_forces_from_kept_spectrum_and_host_entry(precision):
     rh = esp.esp_compute_host(plan.handle, S.pos.astype(npdt), S.q.astype(npdt), Fh)
     assert rel(rh.energy_recip, r["energy_recip"]) < TOL[precision]
     assert rel(Fh, F2.double().cpu().numpy()) < TOL[precision]
+    # page-locked inputs are read in place by the binning kernel: same results, and a
+    # second call with new contents of the same buffers sees the new positions
+    pos_p = torch.tensor(S.pos.astype(npdt)).pin_memory().numpy()
+    q_p = torch.tensor(S.q.astype(npdt)).pin_memory().numpy()
+    Fp = torch.empty((S.n, 3), dtype=dt).pin_memory().numpy()
+    rp = esp.esp_compute_host(plan.handle, pos_p, q_p, Fp)
+    assert rel(rp.energy_recip, r["energy_recip"]) < TOL[precision]
+    assert rel(Fp, F2.double().cpu().numpy()) < TOL[precision]
+    shift = np.array([0.37, -0.21, 0.55])
+    pos_p[:] = (S.pos + shift).astype(npdt)
+    rp2 = esp.esp_compute_host(plan.handle, pos_p, q_p, Fp)
+    r2 = plan.energy_pressure(torch.tensor(pos_p, device="cuda"), q)
+    assert rel(rp2.energy_recip, r2["energy_recip"]) < TOL[precision]
     plan.close()
 
 
