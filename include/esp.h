@@ -94,7 +94,10 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
              double c, double alpha, int precision, void* stream);
 
 /* NPT: change the cell (same N, grid, P, c, r_c); no allocation.  The spectrum kept for
- * esp_forces_from_spectrum becomes stale.  Errors: ESP_ERR_CELL, ESP_ERR_GRID. */
+ * esp_forces_from_spectrum becomes stale.  The host rebuilds the schedule of the transform
+ * along the first axis (which columns meet the cutoff sphere) and copies it on the plan's
+ * stream after waiting for that stream, so the call must not happen while the stream is
+ * being captured.  Errors: ESP_ERR_CELL, ESP_ERR_GRID. */
 int esp_set_cell(esp_plan_t plan, const double cell[9]);
 
 /* Change the stream subsequent calls run on. */
