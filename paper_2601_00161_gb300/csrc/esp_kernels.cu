@@ -432,6 +432,26 @@ __device__ __forceinline__ R horner_reg(const R (&c)[D + 1], R t) {
   return v;
 }
 
+// Two FP32 Horner evaluations in step, as packed pairs (fma.rn.f32x2: each half rounds as
+// a separate fma.rn, so the values equal those of two horner_reg calls).
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void unpack2(unsigned long long r, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(r));
+}
+// tau holds the packed argument t - 1/2 of both polynomials
+template <int D>
+__device__ __forceinline__ unsigned long long horner2(const unsigned long long (&c)[D + 1],
+                                                      unsigned long long tau) {
+  unsigned long long v = c[D];
+#pragma unroll
+  for (int k = D - 1; k >= 0; --k) asm("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(v) : "l"(tau), "l"(c[k]));
+  return v;
+}
+
 template <typename R>
 __device__ __forceinline__ R tq_comp(const typename Vec4<R>::T& v, int d) {
   return d == 0 ? v.x : (d == 1 ? v.y : v.z);
@@ -557,6 +577,24 @@ __device__ __forceinline__ void spread_column(unsigned addr, const R (&w0)[sizeo
                                               std::integer_sequence<int, I...>) {
   (red_fixed<I * S1 * (int)sizeof(R)>(addr, w0[I] * pw), ...);
 }
+// FP32: the same with the products taken as packed pairs (mul.rn.f32x2 rounds each half
+// as mul.rn): w0p[m] holds (w0[2m], w0[2m + 1]), pw2 holds (pw, pw)
+template <int S1, int P, int... M>
+__device__ __forceinline__ void spread_column2(unsigned addr,
+                                               const unsigned long long (&w0p)[(P + 1) / 2],
+                                               unsigned long long pw2,
+                                               std::integer_sequence<int, M...>) {
+  auto one = [&](auto mc) {
+    constexpr int m = decltype(mc)::value;
+    unsigned long long pr;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(pr) : "l"(w0p[m]), "l"(pw2));
+    float lo, hi;
+    unpack2(pr, lo, hi);
+    red_fixed<2 * m * S1 * 4>(addr, lo);
+    if constexpr (2 * m + 1 < P) red_fixed<(2 * m + 1) * S1 * 4>(addr, hi);
+  };
+  (one(std::integral_constant<int, M>{}), ...);
+}
 
 // ---------------------------------------------------------------------------------------
 // Persistent CTAs take tiles from a global work counter (work[0], zeroed every step).
@@ -661,14 +699,29 @@ __global__ void __launch_bounds__(kThreads) k_spread(
         __syncthreads();
         for (int a = warp; a < cnt; a += kThreads / 32) {
           const R* Wa = W + a * RS;
-          R w0[P];
-          load_record<R, P>(Wa, w0);
           const unsigned base = acc_s + (unsigned)(B[a] * (int)sizeof(A));
+          if constexpr (kFixed) {
+            // the record's w0 as packed pairs straight from the 16-byte aligned record
+            unsigned long long w0p[(P + 1) / 2];
+            const unsigned long long* Wp = reinterpret_cast<const unsigned long long*>(Wa);
 #pragma unroll
-          for (int m = 0; m < CM::MP; ++m) {
-            const R pw = Wa[P + lc.j[m]] * Wa[2 * P + lc.k[m]];
-            spread_column<R, S1>(base + (unsigned)(lc.off[m] * (int)sizeof(A)), w0, pw,
-                                 std::make_integer_sequence<int, P>{});
+            for (int m = 0; m < (P + 1) / 2; ++m) w0p[m] = Wp[m];
+#pragma unroll
+            for (int m = 0; m < CM::MP; ++m) {
+              const float pw = Wa[P + lc.j[m]] * Wa[2 * P + lc.k[m]];
+              spread_column2<S1, P>(base + (unsigned)(lc.off[m] * (int)sizeof(A)), w0p,
+                                    pack2(pw, pw),
+                                    std::make_integer_sequence<int, (P + 1) / 2>{});
+            }
+          } else {
+            R w0[P];
+            load_record<R, P>(Wa, w0);
+#pragma unroll
+            for (int m = 0; m < CM::MP; ++m) {
+              const R pw = Wa[P + lc.j[m]] * Wa[2 * P + lc.k[m]];
+              spread_column<R, S1>(base + (unsigned)(lc.off[m] * (int)sizeof(A)), w0, pw,
+                                   std::make_integer_sequence<int, P>{});
+            }
           }
 #pragma unroll
           for (int t = 0; t < CM::NG; ++t) {
@@ -1416,17 +1469,33 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 4 : 
       __syncthreads();  // also covers the staging of phi for the first chunk
       if (evaluator) {
         // coefficients of stencil point p_t, window and derivative (L1-resident table)
-        R cw[D + 1], cd[D + 1];
+        if constexpr (std::is_same<R, float>::value) {
+          // window and derivative together as packed pairs
+          unsigned long long cwd[D + 1];
 #pragma unroll
-        for (int k = 0; k <= D; ++k) {
-          cw[k] = __ldg(wtab + k * P + p_t);
-          cd[k] = __ldg(wtab + (D + 1) * P + k * P + p_t);
-        }
-        for (int pr = pair0; pr < 3 * cnt; pr += NP) {
-          const int a = pr / 3, d = pr - 3 * a;
-          const R t = tq_comp<R>(TQ[a], d);
-          W[a * RS + d * PS + p_t] = horner_reg<R, D>(cw, t);
-          W[a * RS + (3 + d) * PS + p_t] = horner_reg<R, D>(cd, t) * dscale_of<R>(g, d);
+          for (int k = 0; k <= D; ++k)
+            cwd[k] = pack2(__ldg(wtab + k * P + p_t), __ldg(wtab + (D + 1) * P + k * P + p_t));
+          for (int pr = pair0; pr < 3 * cnt; pr += NP) {
+            const int a = pr / 3, d = pr - 3 * a;
+            const float tau = tq_comp<R>(TQ[a], d) - 0.5f;  // the polynomials are in t - 1/2
+            float w, dw;
+            unpack2(horner2<D>(cwd, pack2(tau, tau)), w, dw);
+            W[a * RS + d * PS + p_t] = w;
+            W[a * RS + (3 + d) * PS + p_t] = dw * dscale_of<R>(g, d);
+          }
+        } else {
+          R cw[D + 1], cd[D + 1];
+#pragma unroll
+          for (int k = 0; k <= D; ++k) {
+            cw[k] = __ldg(wtab + k * P + p_t);
+            cd[k] = __ldg(wtab + (D + 1) * P + k * P + p_t);
+          }
+          for (int pr = pair0; pr < 3 * cnt; pr += NP) {
+            const int a = pr / 3, d = pr - 3 * a;
+            const R t = tq_comp<R>(TQ[a], d);
+            W[a * RS + d * PS + p_t] = horner_reg<R, D>(cw, t);
+            W[a * RS + (3 + d) * PS + p_t] = horner_reg<R, D>(cd, t) * dscale_of<R>(g, d);
+          }
         }
       }
       __syncthreads();
