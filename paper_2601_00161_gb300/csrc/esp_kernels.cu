@@ -2,21 +2,27 @@
 //   k_bin      wrap s = h^{-1} r into [0,1), stencil base and fractional offset
 //              (Sec. 4.3), tile id and rank within the tile; the integer stencil
 //              decision is taken in FP64 near a switch so it matches the FP64 oracle
-//   k_scan_*   multi-block exclusive scan of the tile counters, charge sums
+//   k_scan_*   multi-block exclusive scan of the tile counters
 //   k_scatter  counting-sort permutation of (offset t, q), local base and atom index
-//   k_spread   eq. (gridding): one warp owns one tile's padded block in shared memory
-//              and adds each atom's P^3 footprint with plain loads and stores; the block
-//              is then added to the periodic grid
-//   k_scale    eqs. (diag)/(PFfinal): per half-spectrum mode the deconvolved weight, the
-//              Fourier kernel and the 3x3 pressure kernel, reduced in FP64 (compensated
-//              FP32 on the FP32 path); optionally writes G X for the force path
+//   k_spread   eq. (gridding): persistent CTAs stage a tile's padded block in shared
+//              memory; a warp adds one atom's P^3 footprint at a time along lane-fixed
+//              stencil columns (32 distinct banks per add), as 32-bit fixed point with
+//              the native shared-memory integer add; the block then goes to the periodic
+//              grid with float4 global reductions
+//   k_xfft     the transform along the first grid axis of the column groups whose lines
+//              meet the sphere |k| <= c / r_c (mixed-radix Stockham passes in shared
+//              memory), fused with eqs. (diag)/(PFfinal): per mode the deconvolved weight,
+//              the Fourier kernel and the 3x3 pressure kernel, summed per CTA (compensated
+//              FP32 on the FP32 path), and for forces G X and the inverse transform
+//   k_xsum     the fixed-order final sums of k_xfft's partials and of the charge sums
 //   k_gather   eq. (AD): the CTA stages its tile's padded block of the potential grid in
 //              shared memory; P lanes per atom contract its P^3 points with the window
 //              and its gradient, a segmented shuffle sums them
 //
-// Shared-memory layout of a tile block: row pitch E3p = P (mod 32) and plane stride
+// Shared-memory layout of a tile block: row pitch E3p = -P (mod 32) and plane stride
 // S1 = P^2 (mod 32), so the stencil point (i, j, k) of an atom lies in bank
-// (b + i P^2 + j P + k) mod 32 and 32 consecutive flat stencil indices never share a bank.
+// (b + i P^2 + (P - 1 - j) P + k) mod 32 and 32 consecutive points in the order
+// (i, reversed j, k) never share a bank.
 #include "esp_kernels.cuh"
 
 #include <cuda_runtime.h>
@@ -1877,7 +1883,7 @@ __global__ void __launch_bounds__(kThreads) k_near_pairs(NearGeom ng, const int*
 
 // ---------------------------------------------------------------------------------------
 // Fields on the grid from the kept spectrum X (Sec. 4.4 and Appendix C), one warp per
-// spectrum row, lanes along i2, the same in-sphere decision as k_scale:
+// spectrum row, lanes along i2, the same in-sphere decision as k_xfft:
 //   KIND 0: G X                         (potential; per-atom energy)
 //   KIND 1: i k_d G X, d = x, y, z      (eq. (rhodiagforce): ik-differentiation)
 //   KIND 2: K_ab X / w^2, ab = xx yy zz xy xz yz, K = F I + (A x psi_0' / k^4 - 2 F / k^2) k k
