@@ -128,19 +128,53 @@ def prolate(c: float) -> Prolate0:
     return Prolate0(c)
 
 
+def edge_ratio(p: Prolate0) -> float:
+    """psi_0^c(1) / psi_0^c(0) from the prolate differential equation at its end point.
+
+    At x = 1 the Legendre series sums terms of order one to a value of order Delta, so it
+    keeps only about 16 + log10(Delta) digits.  Instead: psi_0 solves
+        (1 - x^2) u'' - 2 x u' + (chi_0 - c^2 x^2) u = 0,
+    chi_0 the eigenvalue of L_c found above, and is the solution regular at the singular
+    point x = 1.  With y = 1 - x that solution is the power series u = sum_j b_j y^j,
+    b_0 = 1, whose coefficients follow from collecting powers of y in
+        y (2 - y) u_yy + 2 (1 - y) u_y + (chi_0 - c^2 (1 - y)^2) u = 0:
+        2 (j + 1)^2 b_{j+1} = (j (j + 1) + c^2 - chi_0) b_j - 2 c^2 b_{j-1} + c^2 b_{j-2}.
+    The series converges for |y| < 2 (the other singular point is x = -1), so at x = 0
+    (y = 1) psi_0(0) / psi_0(1) = sum_j b_j; the terms are positive for the most part and
+    no cancellation to the size of Delta occurs.
+    """
+    c2 = p.c * p.c
+    b = [1.0]
+    total = 1.0
+    j = 0
+    while True:
+        bj = b[j]
+        bj1 = b[j - 1] if j >= 1 else 0.0
+        bj2 = b[j - 2] if j >= 2 else 0.0
+        nxt = ((j * (j + 1) + c2 - p.chi0) * bj - 2.0 * c2 * bj1 + c2 * bj2) / (2.0 * (j + 1) ** 2)
+        b.append(nxt)
+        total += nxt
+        j += 1
+        if j > 20 and abs(nxt) < 1e-18 * abs(total):
+            break
+        if j > 100000:
+            raise RuntimeError("edge series did not converge")
+    return 1.0 / total
+
+
 def c_from_tolerance(delta: float) -> float:
     """Shape parameter c with psi_0^c(1) / psi_0^c(0) = delta (Sec. 5.1 tuning rule).
 
     The paper writes psi_0^c(1) = Delta without fixing the scale of psi_0 in that rule;
     the ratio to psi_0(0) is the reading used here (parity unpinned: the paper prints no
-    value of c).  The ratio decreases monotonically in c, so plain bisection works.
+    value of c).  The ratio decreases monotonically in c, so plain bisection works; it is
+    evaluated by ``edge_ratio`` (no cancellation at x = 1).
     """
     if not (0.0 < delta < 1.0):
         raise ValueError("delta must be in (0, 1)")
 
     def ratio(c):
-        p = Prolate0(c)
-        return p.psi(1.0) / p.psi_at_0
+        return edge_ratio(Prolate0(c))
 
     lo, hi = 1e-3, 4.0
     while ratio(hi) > delta:

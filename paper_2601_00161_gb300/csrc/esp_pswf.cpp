@@ -179,12 +179,33 @@ void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w) {
   }
 }
 
+// psi_0(1) / psi_0(0) without summing the Legendre series at x = 1 (that sum cancels
+// down to the size of the ratio).  psi_0 is the solution of the prolate equation
+// (1 - x^2) u'' - 2 x u' + (chi_0 - c^2 x^2) u = 0 that stays regular at the singular
+// point x = 1: in y = 1 - x a power series sum_j b_j y^j with b_0 = 1 and
+//   2 (j+1)^2 b_{j+1} = (j (j+1) + c^2 - chi_0) b_j - 2 c^2 b_{j-1} + c^2 b_{j-2},
+// convergent for |y| < 2.  At x = 0 (y = 1) it sums to psi_0(0) / psi_0(1).
+double Prolate::edge_ratio() const {
+  const double c2 = c * c;
+  double b0 = 1.0, bm1 = 0.0, bm2 = 0.0, sum = 1.0;
+  for (int j = 0; j < 100000; ++j) {
+    const double b1 = ((j * (j + 1.0) + c2 - chi0) * b0 - 2.0 * c2 * bm1 + c2 * bm2) /
+                      (2.0 * (j + 1.0) * (j + 1.0));
+    sum += b1;
+    bm2 = bm1;
+    bm1 = b0;
+    b0 = b1;
+    if (j >= 20 && std::fabs(b1) < 1e-18 * std::fabs(sum)) break;
+  }
+  return 1.0 / sum;
+}
+
 double c_from_tolerance(double delta) {
   if (!(delta > 0.0 && delta < 1.0)) return -1.0;
   auto ratio = [](double c) {
     Prolate p;
     if (!p.solve(c)) return -1.0;
-    return p.eval(1.0) / p.psi_at_0;
+    return p.edge_ratio();
   };
   double lo = 1e-3, hi = 4.0;
   while (ratio(hi) > delta) {

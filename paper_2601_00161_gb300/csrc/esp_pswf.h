@@ -21,6 +21,9 @@ struct Prolate {
   double deriv(double x) const;  // psi_0'(x), |x| <= 1
   // int_0^u psi_0, |u| <= 1, term by term: int P_k = (P_{k+1} - P_{k-1}) / (2k + 1), k >= 1
   double integral(double u) const;
+  // psi_0(1) / psi_0(0) from the regular series of the prolate equation at x = 1 (no
+  // cancellation, unlike eval(1.0) for small ratios)
+  double edge_ratio() const;
 };
 
 void gauss_legendre(int n, std::vector<double>& x, std::vector<double>& w);

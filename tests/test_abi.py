@@ -65,6 +65,13 @@ def test_c_from_tolerance_host_logic(lib):
 
     c = esp.esp_c_from_tolerance(1e-5)
     assert 13.5 < c < 14.5
+    # the library's tuning rule (Sturm bisection + its own series at x = 1) against the
+    # oracle's (library eigensolver + its series)
+    from oracle.pswf import c_from_tolerance
+
+    for k in range(3, 12):
+        ref = c_from_tolerance(10.0 ** -k)
+        assert abs(esp.esp_c_from_tolerance(10.0 ** -k) / ref - 1.0) < 1e-12, k
     assert esp.esp_c_from_tolerance(1e-7) > c
     with pytest.raises(esp.ESPError):
         esp.esp_c_from_tolerance(2.0)

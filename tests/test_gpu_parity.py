@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import synthetic as sy
-from oracle.esp_grid import esp_grid, spread
+from oracle.esp_grid import esp_grid, self_and_background, spread
 from oracle.pswf import c_from_tolerance
 
 pytestmark = pytest.mark.gpu
@@ -143,6 +143,46 @@ def test_empty_and_single_atom(precision):
     assert np.max(np.abs(F - ref["forces"])) < tol / rc ** 2
     assert res["energy_bg"] < 0.0
     plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("net", [1.0, -2.5])
+def test_charged_cell_self_and_background(precision, net):
+    """Host scalars of a non-neutral cell against the oracle: the self energy of eq.
+    (selfen) from the device sum of q^2, and the background energy and pressure of eq.
+    (Corr) from the device sum of q (FP64 sums on both paths)."""
+    rc = fitting_rc(TRI, (24, 26, 30), 1e-6)
+    S = sy.small_random(300, TRI, seed=13, grid=(24, 26, 30), P=6, delta=1e-6, rc=rc)
+    S.q[:5] += net / 5.0
+    c = c_from_tolerance(S.delta)
+    for forces in (True, False):
+        plan, res, F, pos, q = run_gpu(S, c, precision, forces)
+        ref = self_and_background(q, S.cell, c, rc)
+        assert abs(res["qsum"] - q.sum()) < 1e-12 * np.abs(q).sum()
+        assert rel(res["q2sum"], (q * q).sum()) < 1e-12
+        for key in ("energy_self", "energy_bg", "pressure_bg"):
+            assert rel(res[key], ref[key]) < 1e-12, (key, res[key], ref[key])
+        assert res["energy_bg"] < 0.0
+        plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", ["water648", "odd_triclinic", "membrane_slab"])
+def test_energy_pressure_only_path(precision, case):
+    """esp_energy_pressure: the step without forces (Algorithm 1, Sec. 4.1; no inverse
+    transform, no gather) runs its own transform sequence.  Energy, virial and pressure
+    against the oracle, and the host scalars too."""
+    if case == "water648":
+        S = sy.water_cubic()
+    elif case == "odd_triclinic":
+        S = sy.small_random(411, TRI, seed=17, grid=(21, 25, 27), P=7, delta=1e-5,
+                            rc=fitting_rc(TRI, (21, 25, 27), 1e-5))
+    else:
+        S = sy.membrane_slab()
+    res, _ = check(S, precision, forces=False)
+    q = torch.tensor(S.q, dtype=torch.float64 if precision == "fp64" else torch.float32).double().numpy()
+    ref = self_and_background(q, S.cell, c_from_tolerance(S.delta), S.rc)
+    assert rel(res["energy_self"], ref["energy_self"]) < 1e-12
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])

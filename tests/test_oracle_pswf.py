@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 from numpy.polynomial import legendre as npleg
 
-from oracle.pswf import Prolate0, c_from_tolerance, prolate
+from oracle.pswf import Prolate0, c_from_tolerance, edge_ratio, prolate
 
 CS = [0.5, 2.0, 7.0, 13.36, 21.2, 30.0]
 
@@ -128,3 +128,43 @@ def test_tuning_rule_trend():
         assert 0.0 < c - math.log(1 / d) < 4.0
         assert c > prev
         prev = c
+
+
+@pytest.mark.parametrize("c", [0.5, 2.0, 7.0])
+def test_edge_ratio_matches_legendre_series(c):
+    # where psi_0(1) is not small the Legendre series at x = 1 loses nothing to
+    # cancellation, and the regular series of the differential equation must agree
+    p = Prolate0(c)
+    assert abs(edge_ratio(p) / (p.psi(1.0) / p.psi_at_0) - 1.0) < 1e-13
+
+
+def test_edge_ratio_small_c_limit():
+    # c -> 0: psi_0 -> 1/sqrt(2), a constant, so the ratio tends to 1
+    assert abs(edge_ratio(Prolate0(1e-4)) - 1.0) < 1e-8
+
+
+@pytest.mark.parametrize("c", [14.08, 30.0])
+def test_edge_ratio_against_extended_precision(c):
+    # An independent 40-digit evaluation of the same ratio by the Legendre route (the
+    # tridiagonal eigenproblem of L_c and the series at x = 1 and x = 0, with
+    # P_k(1) = 1 and P_{2i}(0) = (-1)^i (2i-1)!!/(2i)!!), where FP64 would cancel.
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    n = int(math.ceil(c)) + 40
+    c2 = mp.mpf(c) ** 2
+    A = mp.matrix(n, n)
+    for i in range(n):
+        k = mp.mpf(2 * i)
+        A[i, i] = k * (k + 1) + c2 * (2 * k * k + 2 * k - 1) / ((2 * k - 1) * (2 * k + 3))
+        if i + 1 < n:
+            A[i, i + 1] = A[i + 1, i] = c2 * (k + 1) * (k + 2) / ((2 * k + 3) * mp.sqrt((2 * k + 1) * (2 * k + 5)))
+    E, Q = mp.eigsy(A)
+    j = min(range(n), key=lambda i: E[i])
+    at1 = mp.fsum(Q[i, j] * mp.sqrt(2 * i + mp.mpf(1) / 2) for i in range(n))
+    at0, p0 = mp.mpf(0), mp.mpf(1)
+    for i in range(n):
+        if i > 0:
+            p0 = -p0 * (2 * i - 1) / (2 * i)
+        at0 += Q[i, j] * mp.sqrt(2 * i + mp.mpf(1) / 2) * p0
+    ref = float(at1 / at0)
+    assert abs(edge_ratio(Prolate0(c)) / ref - 1.0) < 1e-12
