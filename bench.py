@@ -47,9 +47,10 @@ BYTES_PER_ATOM = {"spread": 16, "gather": 28, "bin": 16, "scatter": 16 + 24}
 BYTES_PER_POINT = {"spread": 4, "gather": 4}
 # FP32 window polynomial degree of the library (Horner, Sec. 4.3)
 WINDOW_DEG_F32 = 13
-# GB300: 152 SMs, 128 FP32 lanes per SM (one FMA = 2 FLOP per lane and clock); one shared
-# memory wavefront (32 lanes of 4 B) per SM and clock
-SMS, FP32_LANES = 152, 128
+# GB300 unit counts: 128 FP32 lanes per SM (one FMA = 2 FLOP per lane and clock), one
+# shared-memory wavefront (32 lanes of 4 B) per SM and clock, SM clock at most 2070 MHz.
+# The SM count is read from the device.
+FP32_LANES, SM_MAX_MHZ = 128, 2070.0
 
 
 def algorithmic_ops(kernel: str, P: int):
@@ -57,15 +58,23 @@ def algorithmic_ops(kernel: str, P: int):
 
     spread: 3P window values by Horner (2 FLOP per degree), the P^2 products q w1 w2, and
     P^3 products w0 (q w1 w2) accumulated into the tile (P^3 adds).
-    gather: 3P values and 3P derivatives by Horner, then for each of the P^3 points the
-    potential times three products (w0' w1 w2, w0 w1' w2, w0 w1 w2'), about 8 FLOP.
+    gather: 3P window values and 3P derivatives by Horner (2 FLOP per degree each), then
+    the separable contraction of the P^3 potential values: sum_i phi w0'_i and
+    sum_i phi w0_i per point (2 P^3 multiply-adds), three multiply-adds per (j, k) pair
+    and three products per row j.
     """
     d = WINDOW_DEG_F32
     if kernel == "spread":
         return 3 * P * 2 * d + 2 * P * P + 2 * P ** 3, P ** 3
     if kernel == "gather":
-        return 6 * P * 2 * d + 8 * P ** 3, 0
+        return 6 * P * 2 * d + 2 * (2 * P ** 3 + 3 * P * P + 3 * P), 0
     return None, None
+
+
+def sm_count(device=0) -> int:
+    import torch
+
+    return int(torch.cuda.get_device_properties(device).multi_processor_count)
 
 
 def parse_args(argv=None):
@@ -77,6 +86,8 @@ def parse_args(argv=None):
     ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     ap.add_argument("--no-fp64-compare", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=sorted(synthetic.WORKLOADS), default=WORKLOAD,
+                    help="workload to time (the headline metric is quoted on the default)")
     return ap.parse_args(argv)
 
 
@@ -168,11 +179,11 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def recorded_traffic(kernel: str):
+def recorded_traffic(kernel: str, workload: str = WORKLOAD):
     """dram bytes per launch from the committed ncu summary, if it matches this source."""
     import hashlib
 
-    path = os.path.join(ROOT, "profiles", f"{kernel}_{WORKLOAD}.md")
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     src = os.path.join(ROOT, "paper_2601_00161_gb300", "csrc", "esp_kernels.cu")
     try:
         text = open(path).read()
@@ -192,8 +203,10 @@ def recorded_traffic(kernel: str):
         return None
 
 
-def accuracy_record():
+def accuracy_record(workload: str = WORKLOAD):
     """The workload's measured pressure / force errors (FP64 oracle study, committed)."""
+    if workload != WORKLOAD:
+        return None
     path = os.path.join(ROOT, "tests", "golden", "membrane_slab_accuracy.json")
     try:
         with open(path) as f:
@@ -228,7 +241,7 @@ def cpu_baseline_oracle(S, c):
         dt = time.perf_counter() - t0
     return {"value": 1.0 / dt, "unit": "steps/s", "cores": 1, "kind": "oracle",
             "sample": f"one full oracle step (spread, FFT, scaling, inverse FFT, gather) of "
-                      f"{WORKLOAD}, {S.n} atoms, FP64, numpy/pocketfft, 1 thread: {dt:.2f} s"}
+                      f"{S.name}, {S.n} atoms, FP64, numpy/pocketfft, 1 thread: {dt:.2f} s"}
 
 
 def cpu_openmp_baseline(S, c, steps=2):
@@ -243,7 +256,7 @@ def cpu_openmp_baseline(S, c, steps=2):
     dt = (time.perf_counter() - t0) / steps
     return {"value": round(1.0 / dt, 4), "unit": "steps/s", "cores": cores,
             "kind": "plain OpenMP FP64 ESP (oracle/esp_omp.c: spread with atomics, own mixed-radix FFT)",
-            "sample": f"{steps} full steps of {WORKLOAD} ({S.n} atoms, energy, virial, forces): {dt:.3f} s each"}
+            "sample": f"{steps} full steps of {S.name} ({S.n} atoms, energy, virial, forces): {dt:.3f} s each"}
 
 
 def esp_arm(args):
@@ -257,7 +270,7 @@ def esp_arm(args):
         import torch.distributed as dist
 
         dist.init_process_group("nccl")
-    S = synthetic.membrane_slab()
+    S = synthetic.WORKLOADS[args.workload]()
     c = esp.esp_c_from_tolerance(S.delta)
     fp64 = args.precision == "fp64"
     dt = torch.float64 if fp64 else torch.float32
@@ -322,33 +335,57 @@ def esp_arm(args):
     value, _ = aggregate([t_max] * world, [args.steps] * world)
     res = esp.esp_result_from_accum(plan.handle, acc.cpu().numpy()).as_dict()
 
-    # dominant kernel of ours and its roofline (algorithmic bytes / event-timed duration)
+    # dominant kernel of ours and its roofline.  Spread and gather do 30-40 FLOP per
+    # algorithmic byte (per atom: ~2 kFLOP against 16-28 B plus 4 B per grid point), above
+    # the FP32 ridge of ~12 FLOP/B, so the FP32 path reports them against the FP32 FMA
+    # ceiling (unit counts x the maximum SM clock); the FP64 path against HBM.
     ours = ["bin", "scan", "scatter", "spread", "xfft_scale", "gather"]
     avg = {k: stage_tot[k] / args.steps for k in esp.STAGES}
     dom = max(ours, key=lambda k: avg[k])
     Mtot = S.grid[0] * S.grid[1] * S.grid[2]
-    alg = BYTES_PER_ATOM.get(dom, 16) * S.n + BYTES_PER_POINT.get(dom, 0) * Mtot
-    if fp64:
-        alg *= 2
+    sms = sm_count(local)
     peak, peak_kind = measured_peaks()
-    achieved = alg / (avg[dom] * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(achieved / peak, 4), "traffic": recorded_traffic(dom),
-                "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.8 TB/s",
-                "algorithmic_bytes": alg, "avg_ms": round(avg[dom], 5)}
-    # the same kernels against the FP32 FMA and shared-memory accumulation ceilings (nominal
-    # unit counts at the sampled SM clock), and cuFFT against the HBM copy bandwidth
-    sm_hz = 1e6 * (clk.get("sm_mhz") or 2070.0)
+
+    def hbm_of(kern):
+        b = BYTES_PER_ATOM.get(kern, 16) * S.n + BYTES_PER_POINT.get(kern, 0) * Mtot
+        return b * (2 if fp64 else 1)
+
+    fp32_peak_tflops = sms * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    flop_dom, _ = algorithmic_ops(dom, S.P)
+    if not fp64 and flop_dom:
+        ach = flop_dom * S.n / (avg[dom] * 1e-3) / 1e12
+        roofline = {"bound": "alu", "kernel": dom, "achieved": round(ach, 3),
+                    "peak": round(fp32_peak_tflops, 2), "unit": "TFLOP/s",
+                    "frac": round(ach / fp32_peak_tflops, 4),
+                    "traffic": recorded_traffic(dom, args.workload),
+                    "peak_kind": (f"derived: {sms} SMs x {FP32_LANES} FP32 lanes x 2 FLOP x "
+                                  f"{SM_MAX_MHZ:.0f} MHz (maximum SM clock)"),
+                    "algorithmic_flop": flop_dom * S.n, "algorithmic_bytes": hbm_of(dom),
+                    "avg_ms": round(avg[dom], 5)}
+    else:
+        alg = hbm_of(dom)
+        achieved = alg / (avg[dom] * 1e-3) / 1e9
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                    "unit": "GB/s", "frac": round(achieved / peak, 4),
+                    "traffic": recorded_traffic(dom, args.workload),
+                    "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured" else "fallback 6.8 TB/s",
+                    "algorithmic_bytes": alg, "avg_ms": round(avg[dom], 5)}
+    # spread and gather against every ceiling: HBM (measured copy bandwidth), FP32 FMA and
+    # shared-memory accumulation (unit counts at the sampled SM clock), and the transforms
+    # against the HBM copy bandwidth
+    sm_hz = 1e6 * (clk.get("sm_mhz") or SM_MAX_MHZ)
     other = {}
     for kern in ("spread", "gather"):
         flop, red = algorithmic_ops(kern, S.P)
         t = avg[kern] * 1e-3
-        fp32_peak = SMS * FP32_LANES * 2 * sm_hz
+        fp32_peak = sms * FP32_LANES * 2 * sm_hz
+        gbs = hbm_of(kern) / t / 1e9
         other[kern] = {"ms": round(avg[kern], 5),
                        "fp32_tflops": round(flop * S.n / t / 1e12, 3),
-                       "fp32_frac": round(flop * S.n / t / fp32_peak, 4)}
+                       "fp32_frac_at_sampled_clock": round(flop * S.n / t / fp32_peak, 4),
+                       "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / peak, 4)}
         if red:
-            red_peak = SMS * 32 * sm_hz
+            red_peak = sms * 32 * sm_hz
             other[kern]["smem_red_per_s"] = round(red * S.n / t, 1)
             other[kern]["smem_red_frac"] = round(red * S.n / t / red_peak, 4)
     H = S.grid[0] * S.grid[1] * (S.grid[2] // 2 + 1)
@@ -434,7 +471,7 @@ def esp_arm(args):
                  "step": "near part of the split (esp_near): device cell list, pairs within r_c, "
                          "energy, virial, forces added onto the long-range ones"}
 
-    launches_per_step = 8  # bin, scan (2), scatter, spread, xfft, xsum, gather
+    launches_per_step = int(plan.info()["launches"])  # the library's own kernels per full step
     out = None
     if rank == 0:
         ms = 1e3 * t_max / args.steps
@@ -445,12 +482,13 @@ def esp_arm(args):
             "dtype": "f32" if not fp64 else "f64", "data": "synthetic",
             "atoms_per_s": round(value * S.n, 1),
             "ns_per_day_equiv_2fs": round(value * 0.1728, 2),
-            "config": {"workload": WORKLOAD, "atoms": S.n, "cell_A": [120, 120, 150],
+            "config": {"workload": S.name, "atoms": S.n,
+                       "cell_A": np.round(S.cell, 4).tolist(),
                        "grid": list(S.grid), "P": S.P, "delta": S.delta, "c": round(c, 6),
                        "r_c_A": S.rc, "step": "energy + 3x3 virial + forces",
                        "l2": "flushed between timed steps (512 MB write)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-                       "accuracy": accuracy_record()},
+                       "accuracy": accuracy_record(S.name)},
             "stage_ms": {k: round(v, 5) for k, v in avg.items()},
             "stage_timing": ("second timed region of the same K steps with a CUDA event before and "
                              f"after every stage; its steps took {step_ms_prof:.5f} ms each"),
@@ -474,48 +512,34 @@ def esp_arm(args):
 
 
 def reference_arm(args):
-    """FP64 CPU oracle on host cores; each step a bounded sample of the workload.
-
-    The sample of one step is a periodic sub-cell of the slab: the atoms whose reduced
-    x and y coordinates lie in [0, 1/4) (a 30 x 30 x 150 A column through both water
-    layers and the slab, ~13k atoms), on the matching 32 x 32 x 160 grid with the same
-    P, c and r_c; one full oracle step on it (spread, FFT, scaling, inverse FFT,
-    gather).  The reported steps/s of the full workload is the sample's atoms/s divided
-    by the workload's atom count (the oracle's cost is linear in the atoms apart from the
-    FFT's log factor).
-    """
+    """FP64 CPU oracle on the host, one thread: each step is one full oracle step of the
+    workload (spread, FFT, scaling, inverse FFT, gather of every atom), about 3 s for the
+    210,240-atom slab, so W + K steps of the driver's default run finish in minutes."""
     from oracle.esp_grid import esp_grid
     from oracle.pswf import c_from_tolerance
 
     world, rank, _ = dist_env()
     if rank != 0:
         return None
-    S = synthetic.membrane_slab()
+    S = synthetic.WORKLOADS[args.workload]()
     c = c_from_tolerance(S.delta)
-    s = S.pos @ np.linalg.inv(S.cell).T
-    s -= np.floor(s)
-    sel = (s[:, 0] < 0.25) & (s[:, 1] < 0.25)
-    sub_cell = S.cell @ np.diag([0.25, 0.25, 1.0])
-    pos, q = S.pos[sel] - 0.0, S.q[sel]
-    grid = (S.grid[0] // 4, S.grid[1] // 4, S.grid[2])
     with single_thread():
         for _ in range(args.warmup):
-            esp_grid(pos, q, sub_cell, grid, S.P, c, S.rc)
+            esp_grid(S.pos, S.q, S.cell, S.grid, S.P, c, S.rc)
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            esp_grid(pos, q, sub_cell, grid, S.P, c, S.rc)
+            esp_grid(S.pos, S.q, S.cell, S.grid, S.P, c, S.rc)
         dt = time.perf_counter() - t0
-    atoms_per_s = args.steps * len(q) / dt
-    value = atoms_per_s / S.n
-    sample = (f"per step one full FP64 oracle step on a periodic 1/16 sub-cell column of "
-              f"{WORKLOAD} ({len(q)} atoms, 30x30x150 A, grid {grid[0]}x{grid[1]}x{grid[2]}, same P, c, r_c), "
-              f"1 host thread; value = sample atoms/s / {S.n}")
+    value = args.steps / dt
+    sample = (f"per step one full FP64 oracle step of {S.name} ({S.n} atoms, grid "
+              f"{S.grid[0]}x{S.grid[1]}x{S.grid[2]}, P = {S.P}; energy, virial, forces), "
+              f"numpy/pocketfft, 1 host thread")
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "atoms_per_s": atoms_per_s,
-        "config": {"workload": WORKLOAD, "atoms": S.n, "grid": list(S.grid), "P": S.P,
+        "data": "synthetic", "atoms_per_s": value * S.n,
+        "config": {"workload": S.name, "atoms": S.n, "grid": list(S.grid), "P": S.P,
                    "delta": S.delta, "r_c_A": S.rc},
         "cpu_baseline": {"value": value, "unit": "steps/s", "cores": 1, "kind": "oracle",
                          "sample": sample},

@@ -244,22 +244,27 @@ int esp_destroy(esp_plan_t plan);
 const char* esp_last_error(esp_plan_t plan);
 
 /*
- * esp_spread_noalloc - the spreading of eq. (gridding) without any device allocation, for
- * callers that cannot allocate device memory at this point (code running while a CUDA
- * graph is being captured by someone else, allocators that forbid cudaMalloc, embedded
- * runtimes with a fixed memory budget).  There is no counterpart in the paper: it is the
- * bin/sort and spread kernels of the plan path with their scratch (binning counters,
- * sorted atoms, the window table) in one static device array of the library, about 5.8 MB
- * that every GPU which loads the library keeps until the process exits.
+ * esp_spread_noalloc - spreading onto the grid as the plan path does it, without any
+ * device allocation.  The paper has no counterpart: this entry point exists for callers
+ * that cannot call cudaMalloc when they need a spread grid, for instance code that runs
+ * under an allocator or memory pool which forbids further device allocations, a runtime
+ * with a device-memory budget fixed at start-up, or a loop that must not pay the implicit
+ * device synchronisation a cudaMalloc or cudaFree may cost.  It runs the plan path's
+ * bin/sort and spread kernels with their scratch (binning counters, sorted atoms, the
+ * window table) in one static device array of the library, about 5.8 MB, which every GPU
+ * that loads the library holds until the process exits.
  *   cell, grid, w, c, precision: as for esp_plan (no split radius is needed here).
  *   n <= ESP_NOALLOC_MAX_ATOMS, and the grid at most ESP_NOALLOC_MAX_TILES tiles of
  *        8 x 8 x 16 points (8 x 8 x 8 for w > 8); larger inputs return ESP_ERR_ARG.
  *   pos, q     device arrays (N x 3 and N) of the I/O type; grid_out the caller's device
  *              array of M1*M2*M3 values of the compute type, overwritten with rho_s.
  *   stream     cudaStream_t to run on.  Asynchronous; non-finite atoms are skipped.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture.  All calls share the one array, so
- * calls that overlap on the GPU (other streams, other host threads) race: serialise them.
+ * The window table is rebuilt on the host only when (c, w, precision) changes, and reaches
+ * the array as a kernel argument, so no host buffer has to outlive the call.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current); make that first call before any stream capture.  All calls
+ * share the one array and every call starts by clearing the counters it needs, but calls
+ * that overlap on the GPU (other streams, other host threads) race on it: serialise them.
  * Errors: ESP_ERR_ARG, ESP_ERR_CELL, ESP_ERR_SUPPORT, ESP_ERR_CUDA (esp_last_error(NULL)).
  */
 #define ESP_NOALLOC_MAX_ATOMS 65536

@@ -448,6 +448,44 @@ void release(esp_plan_t p) {
   delete p;
 }
 
+// Tile geometry of spread and gather (p->M, p->P, p->fp64, p->deg and p->pswf set).  A
+// tile holds T0 x T1 x T2 stencil bases; the CTA working on it owns the padded block
+// (T + P - 1)^3.  T2 is a multiple of 4 so padded rows move as aligned float4 when M2 is
+// too.  Many small tiles keep the persistent CTAs of spread and gather busy to the end.
+int setup_tile_geom(esp_plan_t p) {
+  esp::TileGeom& g = p->tg;
+  const int w = p->P;
+  for (int d = 0; d < 3; ++d) g.M[d] = p->M[d];
+  g.P = w;
+  {
+    int Tc[3], E3p, vol;
+    esp::tile_shape(w, Tc, &E3p, &vol);
+    for (int d = 0; d < 3; ++d) g.T[d] = std::min(Tc[d], p->M[d]);
+    g.E3p = E3p;
+  }
+  p->ntiles = 1;
+  for (int d = 0; d < 3; ++d) {
+    g.nt[d] = (p->M[d] + g.T[d] - 1) / g.T[d];
+    g.E[d] = g.T[d] + w - 1;
+    g.dscale[d] = 2.0 * p->M[d] / w;
+    g.dscalef[d] = (float)g.dscale[d];
+    p->ntiles *= g.nt[d];
+  }
+  g.ksub = (int64_t)p->ntiles * esp::kSub <= esp::kMaxScan ? esp::kSub : 1;
+  if ((int64_t)p->ntiles * g.ksub > esp::kMaxScan)
+    return fail(p, ESP_ERR_ARG, "grid too large: more tiles than the binning scan handles");
+  g.vec4 = (!p->fp64 && g.T[2] % 4 == 0 && p->M[2] % 4 == 0 && (g.E[2] + 3) / 4 * 4 <= g.E3p) ? 1 : 0;
+  auto magic = [](unsigned int d) {
+    return (unsigned int)((((unsigned long long)1 << 32) + d - 1) / d);
+  };
+  g.div_E1 = magic((unsigned)g.E[1]);
+  g.div_E2v = magic((unsigned)((g.E[2] + 3) / 4));
+  g.deg = p->deg;
+  // psi_0 is even and largest at 0 on [-1, 1]; the margin covers the polynomial fit
+  g.wmax3 = (float)std::pow(p->pswf.psi_at_0 * (1.0 + 1e-6), 3.0);
+  return ESP_OK;
+}
+
 int fill_result(esp_plan_t p, const double* acc, esp_result* out) {
   if (!out) return ESP_OK;
   std::memset(out, 0, sizeof *out);
@@ -670,47 +708,14 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
   if ((rc = build_radial_tables(p, rtab)) != ESP_OK) return bail(rc);
   build_invw2(p, invw2);
 
-  // Tile geometry.  A tile holds T0 x T1 x T2 stencil bases; the CTA working on it owns
-  // the padded block (T + P - 1)^3.  T2 is a multiple of 4 so padded rows move as
-  // aligned float4 when M2 is too.  Many small tiles keep the persistent CTAs of spread
-  // and gather busy to the end.
   int sms = 152;
   {
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   }
+  if ((rc = setup_tile_geom(p)) != ESP_OK) return bail(rc);
   esp::TileGeom& g = p->tg;
-  for (int d = 0; d < 3; ++d) g.M[d] = p->M[d];
-  g.P = w;
-  {
-    int Tc[3], E3p, vol;
-    esp::tile_shape(w, Tc, &E3p, &vol);
-    for (int d = 0; d < 3; ++d) g.T[d] = std::min(Tc[d], p->M[d]);
-    g.E3p = E3p;
-  }
-  p->ntiles = 1;
-  for (int d = 0; d < 3; ++d) {
-    g.nt[d] = (p->M[d] + g.T[d] - 1) / g.T[d];
-    g.E[d] = g.T[d] + w - 1;
-    g.dscale[d] = 2.0 * p->M[d] / w;
-    g.dscalef[d] = (float)g.dscale[d];
-    p->ntiles *= g.nt[d];
-  }
-  g.ksub = (int64_t)p->ntiles * esp::kSub <= esp::kMaxScan ? esp::kSub : 1;
-  if ((int64_t)p->ntiles * g.ksub > esp::kMaxScan)
-    return bail(fail(p, ESP_ERR_ARG, "grid too large: more tiles than the binning scan handles"));
-  g.vec4 = (!p->fp64 && g.T[2] % 4 == 0 && p->M[2] % 4 == 0 && (g.E[2] + 3) / 4 * 4 <= g.E3p) ? 1 : 0;
-  {
-    auto magic = [](unsigned int d) {
-      return (unsigned int)((((unsigned long long)1 << 32) + d - 1) / d);
-    };
-    g.div_E1 = magic((unsigned)g.E[1]);
-    g.div_E2v = magic((unsigned)((g.E[2] + 3) / 4));
-  }
-  g.deg = p->deg;
-  // psi_0 is even and largest at 0 on [-1, 1]; the margin covers the polynomial fit
-  g.wmax3 = (float)std::pow(p->pswf.psi_at_0 * (1.0 + 1e-6), 3.0);
 
   esp::ScaleGeom& s = p->sg;
   for (int d = 0; d < 3; ++d) s.M[d] = p->M[d];
@@ -1313,6 +1318,37 @@ int noalloc_scratch(unsigned char** out) {
   return ESP_OK;
 }
 
+
+// The window table reaches the scratch array as a kernel argument (by value), so no
+// host buffer has to outlive the call.  At most 2 (kMaxDeg + 1) kMaxP values.
+struct WindowTableArg {
+  double v[2 * (esp::kMaxDeg + 1) * esp::kMaxP];
+  int n;
+};
+
+__global__ void k_put_window_table(WindowTableArg t, void* dst, int fp64) {
+  for (int i = threadIdx.x; i < t.n; i += blockDim.x) {
+    if (fp64)
+      static_cast<double*>(dst)[i] = t.v[i];
+    else
+      static_cast<float*>(dst)[i] = (float)t.v[i];
+  }
+}
+
+// The last window table built, so that repeated calls with the same (c, P, precision)
+// skip the eigen-solve and the polynomial fits.
+struct NoAllocTableCache {
+  bool valid = false;
+  double c = 0.0;
+  int P = 0;
+  bool fp64 = false;
+  int deg = 0;
+  double psi_at_0 = 0.0;
+  std::vector<double> tab;
+};
+std::mutex g_table_mu;
+NoAllocTableCache g_table_cache;
+
 }  // namespace
 
 extern "C" int esp_spread_noalloc(const double cell[9], int64_t n, const int grid[3], int w,
@@ -1342,52 +1378,49 @@ extern "C" int esp_spread_noalloc(const double cell[9], int64_t n, const int gri
   p->P = w;
   p->c = c;
   p->stream = (cudaStream_t)stream;
+  // errors after this point are reported through esp_last_error(NULL)
   auto report = [&](int code) {
-    g_plan_error = p->err;
+    if (code != ESP_OK) g_plan_error = p->err;
     return code;
   };
   int rc;
   if ((rc = set_cell_matrix(p, cell, p->h, p->hinv, &p->V)) != ESP_OK) return report(rc);
-  if (!p->pswf.solve(c)) return report(fail(p, ESP_ERR_ARG, "PSWF eigen-solve failed"));
-  std::vector<double> wtab;
-  if ((rc = build_window_tables(p, wtab)) != ESP_OK) return report(rc);
-  esp::TileGeom& g = p->tg;
-  for (int d = 0; d < 3; ++d) g.M[d] = p->M[d];
-  g.P = w;
+  WindowTableArg targ;
   {
-    int Tc[3], E3p, vol;
-    esp::tile_shape(w, Tc, &E3p, &vol);
-    for (int d = 0; d < 3; ++d) g.T[d] = std::min(Tc[d], p->M[d]);
-    g.E3p = E3p;
+    std::lock_guard<std::mutex> lock(g_table_mu);
+    NoAllocTableCache& tc = g_table_cache;
+    if (!(tc.valid && tc.c == c && tc.P == w && tc.fp64 == p->fp64)) {
+      tc.valid = false;
+      if (!p->pswf.solve(c)) return report(fail(p, ESP_ERR_ARG, "PSWF eigen-solve failed"));
+      if ((rc = build_window_tables(p, tc.tab)) != ESP_OK) return report(rc);
+      tc.c = c;
+      tc.P = w;
+      tc.fp64 = p->fp64;
+      tc.deg = p->deg;
+      tc.psi_at_0 = p->pswf.psi_at_0;
+      tc.valid = true;
+    }
+    p->deg = tc.deg;
+    p->pswf.psi_at_0 = tc.psi_at_0;  // the one PSWF constant the tile set-up reads
+    if (tc.tab.size() > sizeof targ.v / sizeof targ.v[0])
+      return report(fail(p, ESP_ERR_ARG, "window table too large"));
+    targ.n = (int)tc.tab.size();
+    std::copy(tc.tab.begin(), tc.tab.end(), targ.v);
   }
-  p->ntiles = 1;
-  for (int d = 0; d < 3; ++d) {
-    g.nt[d] = (p->M[d] + g.T[d] - 1) / g.T[d];
-    g.E[d] = g.T[d] + w - 1;
-    g.dscale[d] = 2.0 * p->M[d] / w;
-    g.dscalef[d] = (float)g.dscale[d];
-    p->ntiles *= g.nt[d];
-  }
+  if ((rc = setup_tile_geom(p)) != ESP_OK) return report(rc);
   if (p->ntiles > ESP_NOALLOC_MAX_TILES)
     return report(fail(p, ESP_ERR_ARG, "grid exceeds ESP_NOALLOC_MAX_TILES tiles for esp_spread_noalloc"));
-  g.ksub = esp::kSub;
-  g.vec4 = (!p->fp64 && g.T[2] % 4 == 0 && p->M[2] % 4 == 0 && (g.E[2] + 3) / 4 * 4 <= g.E3p) ? 1 : 0;
-  g.div_E1 = (unsigned int)((((unsigned long long)1 << 32) + g.E[1] - 1) / g.E[1]);
-  g.div_E2v = (unsigned int)((((unsigned long long)1 << 32) + (g.E[2] + 3) / 4 - 1) / ((g.E[2] + 3) / 4));
-  g.deg = p->deg;
-  // psi_0 is even and largest at 0 on [-1, 1]; the margin covers the polynomial fit
-  g.wmax3 = (float)std::pow(p->pswf.psi_at_0 * (1.0 + 1e-6), 3.0);
+  esp::TileGeom& g = p->tg;
   update_cell_constants(p);
 
   unsigned char* S = nullptr;
-  if ((rc = noalloc_scratch(&S)) != ESP_OK) return rc;
+  if ((rc = noalloc_scratch(&S)) != ESP_OK) return rc;  // reports through g_plan_error
   int* count = reinterpret_cast<int*>(S + kNoAlloc.count);
   int* work = count + (size_t)p->ntiles * esp::kSub;
   int* suboff = reinterpret_cast<int*>(S + kNoAlloc.suboff);
   int* toff = reinterpret_cast<int*>(S + kNoAlloc.toff);
   int* bsum = reinterpret_cast<int*>(S + kNoAlloc.bsum);
   void* binpart = S + kNoAlloc.binpart;
-  double* acc = reinterpret_cast<double*>(S + kNoAlloc.acc);
   int* ptile = reinterpret_cast<int*>(S + kNoAlloc.ptile);
   int* prank = reinterpret_cast<int*>(S + kNoAlloc.prank);
   int* plb = reinterpret_cast<int*>(S + kNoAlloc.plb);
@@ -1400,13 +1433,18 @@ extern "C" int esp_spread_noalloc(const double cell[9], int64_t n, const int gri
   cudaStream_t st = p->stream;
   const size_t es = p->fp64 ? 8 : 4;
   const size_t Mtot = (size_t)p->M[0] * p->M[1] * p->M[2];
-  // the window table (a pageable source: the copy is staged before the call returns)
-  if (p->fp64) {
-    ESP_CUDA(nullptr, cudaMemcpyAsync(dwtab, wtab.data(), es * wtab.size(), cudaMemcpyHostToDevice, st));
-  } else {
-    std::vector<float> f(wtab.begin(), wtab.end());
-    ESP_CUDA(nullptr, cudaMemcpyAsync(dwtab, f.data(), es * f.size(), cudaMemcpyHostToDevice, st));
-  }
+  const size_t ss = esp::spread_smem_bytes(p->fp64, g), gs = esp::gather_smem_bytes(p->fp64, g);
+  if (ss > 227 * 1024 || gs > 227 * 1024)
+    return report(fail(p, ESP_ERR_ARG, "tile does not fit in shared memory"));
+  ESP_CUDA(nullptr, esp::configure_kernels(p->fp64, w, ss, gs));
+  int dev = 0, sms = 152, occ_s = 1, occ_g = 1;
+  ESP_CUDA(nullptr, cudaGetDevice(&dev));
+  ESP_CUDA(nullptr, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  ESP_CUDA(nullptr, esp::occupancy(p->fp64, p->io_double, w, ss, gs, &occ_s, &occ_g));
+  const int nblocks = std::max(1, std::min(p->ntiles, sms * std::max(occ_s, 1)));
+
+  k_put_window_table<<<1, 256, 0, st>>>(targ, dwtab, p->fp64 ? 1 : 0);
+  ESP_CUDA(nullptr, cudaGetLastError());
   // the array keeps the last call's contents: the counters must start at zero
   ESP_CUDA(nullptr, cudaMemsetAsync(count, 0, sizeof(int) * ((size_t)p->ntiles * esp::kSub + 2), st));
   ESP_CUDA(nullptr, esp::launch_bin(p->io_double, p->fp64, pos, q, n, g, count, ptile, prank, plb,
@@ -1415,15 +1453,6 @@ extern "C" int esp_spread_noalloc(const double cell[9], int64_t n, const int gri
   ESP_CUDA(nullptr, esp::launch_scatter(p->fp64, n, g.ksub, ptile, prank, plb, tq, suboff, stq,
                                         slb, sidx, st));
   ESP_CUDA(nullptr, cudaMemsetAsync(grid_out, 0, es * Mtot, st));
-  const size_t ss = esp::spread_smem_bytes(p->fp64, g), gs = esp::gather_smem_bytes(p->fp64, g);
-  if (ss > 227 * 1024 || gs > 227 * 1024)
-    return fail(nullptr, ESP_ERR_ARG, "tile does not fit in shared memory");
-  ESP_CUDA(nullptr, esp::configure_kernels(p->fp64, w, ss, gs));
-  int dev = 0, sms = 152, occ_s = 1, occ_g = 1;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  ESP_CUDA(nullptr, esp::occupancy(p->fp64, p->io_double, w, ss, gs, &occ_s, &occ_g));
-  const int nblocks = std::max(1, std::min(p->ntiles, sms * std::max(occ_s, 1)));
   ESP_CUDA(nullptr, esp::launch_spread(p->fp64, g, p->ntiles, nblocks, stq, slb, toff, work,
                                        dwtab, grid_out, st));
   return ESP_OK;

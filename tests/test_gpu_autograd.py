@@ -9,7 +9,10 @@ backward: the step's forces and ``esp_cell_gradient``):
   the two evaluations, so the discrete energy is smooth there);
 * the chain rule through r = h s against the virial relation dU/dh|_s = -W h^{-T},
   W = W_F + U_bg I (Sec. 2.2 eq. (instheta)), for a charged cell too;
-* the FP32 path against the FP64 one.
+* the FP32 path against the FP64 one;
+* the 16,000-atom LiTFSI-like box (60 x 64 x 72 grid, P = 8): energy, position gradient
+  and cell gradient against the oracle's energy, forces and virial, and the position
+  gradient against central finite differences at h = 1e-4 A.
 """
 
 import math
@@ -19,7 +22,7 @@ import pytest
 
 import synthetic as sy
 from oracle import lattice
-from oracle.esp_grid import modes, stencil
+from oracle.esp_grid import esp_grid, modes, self_and_background, stencil
 from oracle.pswf import c_from_tolerance
 
 pytestmark = pytest.mark.gpu
@@ -166,3 +169,67 @@ def test_fp32_gradients_follow_fp64():
     assert abs(U32 - U64) < 2e-6 * scale
     assert np.linalg.norm(g32 - g64) < 2e-5 * np.linalg.norm(g64)
     assert np.max(np.abs(G32 - G64)) < 2e-5 * np.max(np.abs(G64))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_litfsi16k_gradients_against_the_oracle(precision):
+    """The LiTFSI-like workload (16,000 atoms, orthorhombic 50 x 56 x 62 A).
+
+    Forward: U = U_F + U_self + U_bg against the oracle.  Backward: -dU/dr against the
+    oracle's forces (eq. (AD)) and dU/dh against -W h^{-T} + sum_i F_i s_i^T built from the
+    oracle's virial W = W_F + U_bg I and forces (Sec. 2.2 eq. (instheta) with r = h s).
+    Each side is held to the parity bar (1e-12 FP64, 2e-6 FP32) relative to the size of
+    the terms it is made of: U against |U_F| + |U_self| + |U_bg|, the cell gradient
+    against |W h^{-T}| + |F|^T |s|.  In FP64 the position gradient also meets central
+    finite differences of the GPU energy at h = 1e-4 A, on coordinates whose +-h moves
+    change no stencil base (the discrete energy jumps at a switch).
+    """
+    S = sy.litfsi()
+    c = c_from_tolerance(S.delta)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    tol = 1e-12 if precision == "fp64" else 2e-6
+    plan = esp.Plan(S.cell, S.n, S.grid, S.P, c, S.rc, precision=precision)
+    pos = torch.tensor(S.pos, dtype=dt, device="cuda", requires_grad=True)
+    h = torch.tensor(S.cell, dtype=torch.float64, device="cuda", requires_grad=True)
+    q = torch.tensor(S.q, dtype=dt, device="cuda")
+    U = esp.long_range_energy(plan, pos, h, q)
+    U.backward()
+    posd = pos.detach().double().cpu().numpy()
+    qd = q.double().cpu().numpy()
+    ref = esp_grid(posd, qd, S.cell, S.grid, S.P, c, S.rc)
+    sb = self_and_background(qd, S.cell, c, S.rc)
+    U_ref = ref["energy"] + sb["energy_self"] + sb["energy_bg"]
+    scale = abs(ref["energy"]) + abs(sb["energy_self"]) + abs(sb["energy_bg"])
+    assert abs(float(U.detach()) - U_ref) < tol * scale
+    g = pos.grad.double().cpu().numpy()
+    F = ref["forces"]
+    assert np.linalg.norm(g + F) < tol * np.linalg.norm(F)
+    hinv = np.linalg.inv(S.cell)
+    s = posd @ hinv.T  # as given, not wrapped (the cell gradient's moment uses r = h s)
+    W = ref["virial"] + sb["energy_bg"] * np.eye(3)
+    G_ref = -W @ hinv.T + F.T @ s
+    G = h.grad.double().cpu().numpy()
+    size = np.linalg.norm(W @ hinv.T) + np.linalg.norm(np.abs(F).T @ np.abs(s))
+    assert np.linalg.norm(G - G_ref) < tol * size, (np.linalg.norm(G - G_ref) / size)
+    if precision == "fp64":
+        d = 1e-4
+        rng = np.random.default_rng(3)
+        checked = 0
+        hq = torch.tensor(S.cell, dtype=torch.float64, device="cuda")
+        for i in rng.choice(S.n, 10, replace=False):
+            for a in range(3):
+                p1, p2 = S.pos.copy(), S.pos.copy()
+                p1[i, a] += d
+                p2[i, a] -= d
+                s1 = lattice.reduced(p1[i:i + 1], S.cell)[0]
+                s2 = lattice.reduced(p2[i:i + 1], S.cell)[0]
+                if not all(np.array_equal(stencil(S.grid[e] * s1[e:e + 1], S.P)[0],
+                                          stencil(S.grid[e] * s2[e:e + 1], S.P)[0]) for e in range(3)):
+                    continue
+                e1 = energy(plan, torch.tensor(p1, device="cuda"), hq, q)
+                e2 = energy(plan, torch.tensor(p2, device="cuda"), hq, q)
+                fd = (e1 - e2) / (2 * d)
+                assert abs(fd - g[i, a]) < 1e-6 * np.max(np.abs(g)), (i, a, fd, g[i, a])
+                checked += 1
+        assert checked >= 20
+    plan.close()

@@ -1,8 +1,9 @@
 """The allocation-free spreading entry point against the plan path (GPU).
 
-esp_spread_noalloc serves callers that cannot allocate device memory when they spread
-(for example while another component is capturing a CUDA graph, or under an allocator
-that forbids cudaMalloc): its scratch lives in a static device array of the library.
+esp_spread_noalloc serves callers that cannot call cudaMalloc when they spread (code
+under an allocator or memory pool that forbids further device allocations, or a runtime
+with a device-memory budget fixed at start-up): its scratch lives in a static device
+array of the library.
 Here its output must match the spread grid of the ordinary plan path (esp_plan,
 esp_energy_pressure, esp_copy_grid) to the parity tolerances of the other GPU tests, on
 two calls in a row (the second reuses the array the first one left behind).  This file
@@ -56,6 +57,15 @@ def test_noalloc_spread_matches_plan_path(precision, case):
         got = out.double().cpu().numpy()
         assert np.all(np.isfinite(got))
         assert np.max(np.abs(got - ref)) < TOL[precision] * np.max(np.abs(ref))
+    # a call with another c (the library rebuilds its window table), then this c again
+    c2 = c_from_tolerance(S.delta * 10.0)
+    ref2 = plan_grid(S, c2, precision, pos, q)
+    for cc, rr in ((c2, ref2), (c, ref)):
+        out = torch.full(S.grid, float("nan"), dtype=dt, device="cuda")
+        esp.esp_spread_noalloc(S.cell, S.n, S.grid, S.P, cc, flag, pos, q, out)
+        torch.cuda.synchronize()
+        got = out.double().cpu().numpy()
+        assert np.max(np.abs(got - rr)) < TOL[precision] * np.max(np.abs(rr))
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
