@@ -339,7 +339,7 @@ def esp_arm(args):
     # algorithmic byte (per atom: ~2 kFLOP against 16-28 B plus 4 B per grid point), above
     # the FP32 ridge of ~12 FLOP/B, so the FP32 path reports them against the FP32 FMA
     # ceiling (unit counts x the maximum SM clock); the FP64 path against HBM.
-    ours = ["bin", "scan", "scatter", "spread", "xfft_scale", "gather"]
+    ours = ["bin", "spread", "fft_fwd", "xfft_scale", "fft_inv", "gather"]
     avg = {k: stage_tot[k] / args.steps for k in esp.STAGES}
     dom = max(ours, key=lambda k: avg[k])
     Mtot = S.grid[0] * S.grid[1] * S.grid[2]
@@ -388,11 +388,15 @@ def esp_arm(args):
             red_peak = sms * 32 * sm_hz
             other[kern]["smem_red_per_s"] = round(red * S.n / t, 1)
             other[kern]["smem_red_frac"] = round(red * S.n / t / red_peak, 4)
-    H = S.grid[0] * S.grid[1] * (S.grid[2] // 2 + 1)
+    # plane transforms: the real grid and the spectrum layout k_xfft works on (the box of
+    # the sphere with the library's plane kernels, else cuFFT's full half spectrum)
+    info = plan.info()
+    H = S.grid[0] * int(info["nb1"]) * int(info["nb2"])
     fft_bytes = (4 if not fp64 else 8) * Mtot + (8 if not fp64 else 16) * H
     for kern in ("fft_fwd", "fft_inv"):
         gbs = fft_bytes / (avg[kern] * 1e-3) / 1e9
         other[kern] = {"ms": round(avg[kern], 5), "bytes": fft_bytes,
+                       "kernel": "k_fplane / k_iplane" if info["box_mode"] else "cuFFT plane R2C / C2R",
                        "achieved_gbs": round(gbs, 1), "hbm_frac": round(gbs / peak, 4)}
 
     # end to end through the public C ABI with host buffers (H2D + step + D2H every step)

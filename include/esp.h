@@ -211,8 +211,9 @@ int esp_result_from_accum(esp_plan_t plan, const double accum_host[ESP_ACCUM_LEN
                           esp_result* out);
 
 /* Copy the plan's real grid (M1*M2*M3 values of the compute type; after esp_energy_pressure
- * the spread charge rho_s, after a step with forces the potential phi) or its half
- * spectrum (M1*M2*(M3/2+1) complex values) into a host buffer.  For tests. */
+ * the spread charge rho_s, after a step with forces the potential phi) or the half
+ * spectrum of that grid (M1*M2*(M3/2+1) complex values, the forward 3D transform of the
+ * grid's current content, taken by this call) into a host buffer.  For tests. */
 int esp_copy_grid(esp_plan_t plan, void* host_dst);
 int esp_copy_spectrum(esp_plan_t plan, void* host_dst);
 
@@ -220,15 +221,17 @@ int esp_copy_spectrum(esp_plan_t plan, void* host_dst);
  * degree, [6] radial table degree, [7] max window fit error / psi_0(0), [8] max radial
  * fit error / psi_0(0), [9] tiles, [10] tile T1, [11] T2, [12] T3, [13] launches of the
  * library's own kernels per full step (cuFFT's not counted), [14] background constant
- * X = r_c^2/2 - int_0^{r_c} r phi_0.
- * Writes min(len, 15) values. */
+ * X = r_c^2/2 - int_0^{r_c} r phi_0, [15] 1 if the library's plane transforms keep only the
+ * box of the sphere (0: cuFFT transforms the planes into the full half spectrum), [16], [17]
+ * the box (or full) extent in m1 and m2 of the layout k_xfft works on.
+ * Writes min(len, 18) values. */
 int esp_plan_info(esp_plan_t plan, double* info, int len);
 
 /* Per-stage timing with CUDA events on the plan's stream.  esp_profile(plan, 1) creates
  * the events and records one before and after every stage of each later step;
  * esp_profile_read synchronises the stream and writes the last step's stage durations
- * in ms, in the order: [0] set-up, [1] bin (which also clears the spread grid), [2] scan,
- * [3] scatter, [4] separate grid clearing (0 when the bin kernel clears the grid),
+ * in ms, in the order: [0] set-up, [1] bin (which also clears the spread grid and writes
+ * the atoms straight into their tiles' slots), [2], [3] unused (0), [4] unused (0),
  * [5] spread, [6] forward FFT (the plane transforms on the force path, the full 3D
  * transform on the energy and pressure path), [7] transform along the first axis fused
  * with the scaling and the sums, [8] inverse plane transforms, [9] gather (stages that
@@ -250,8 +253,8 @@ const char* esp_last_error(esp_plan_t plan);
  * under an allocator or memory pool which forbids further device allocations, a runtime
  * with a device-memory budget fixed at start-up, or a loop that must not pay the implicit
  * device synchronisation a cudaMalloc or cudaFree may cost.  It runs the plan path's
- * bin/sort and spread kernels with their scratch (binning counters, sorted atoms, the
- * window table) in one static device array of the library, about 5.8 MB, which every GPU
+ * bin/sort and spread kernels with their scratch (binning counters, binned atoms, the
+ * window table) in one static device array of the library, about 8.4 MB, which every GPU
  * that loads the library holds until the process exits.
  *   cell, grid, w, c, precision: as for esp_plan (no split radius is needed here).
  *   n <= ESP_NOALLOC_MAX_ATOMS, and the grid at most ESP_NOALLOC_MAX_TILES tiles of

@@ -221,10 +221,10 @@ def esp_copy_spectrum(plan, dst: np.ndarray):
 
 
 def esp_plan_info(plan) -> dict:
-    v = (ctypes.c_double * 15)()
-    _check(_lib.esp_plan_info(plan, v, 15), plan)
+    v = (ctypes.c_double * 18)()
+    _check(_lib.esp_plan_info(plan, v, 18), plan)
     keys = ["c", "rc", "psi0_at_0", "C0", "lambda0", "deg", "rdeg", "fit_err", "rfit_err",
-            "ntiles", "T1", "T2", "T3", "launches", "Xbg"]
+            "ntiles", "T1", "T2", "T3", "launches", "Xbg", "box_mode", "nb1", "nb2"]
     return dict(zip(keys, list(v)))
 
 

@@ -58,6 +58,12 @@ struct esp_plan_s {
   int ntiles = 0;
   esp::XGeom xg{};       // the transform along axis 0 fused with the scaling
   int xblocks = 0;       // its CTAs: column groups
+  // plane transforms over (i1, i2): the library's pruned kernels into the box of the
+  // sphere (box_mode), else cuFFT into the full half spectrum
+  esp::PlaneGeom pg{};
+  bool box_mode = false;
+  void* d_pbox = nullptr;  // planes transformed, the input of k_xfft (kept for forces)
+  void* d_ptw = nullptr;   // M1 then M2 roots (compute type)
   int xactive = 0;       // groups whose lines may meet the sphere (ordered first)
   int* d_xorder = nullptr;           // group order, active first
   unsigned char* d_xcol = nullptr;   // per column: line may meet the sphere
@@ -76,18 +82,9 @@ struct esp_plan_s {
   void* d_spec = nullptr;
   void* d_spec2 = nullptr;  // scaled half spectrum, input of the plane C2R (cleared per step)
   void* d_xtw = nullptr;  // M0 roots e^{-2 pi i m / M0} (compute type)
-  int* d_count = nullptr;   // kSub counters per tile, then 2 work counters (spread, gather)
-  int* d_suboff = nullptr;  // exclusive scan of d_count (tile-major)
-  int* d_offset = nullptr;  // first sorted atom of each tile (ntiles + 1)
-  int* d_bsum = nullptr;    // per scan block totals
+  // atoms binned by tile (esp::Bins): slot arrays, counters, overflow list, control words
+  esp::Bins bins{};
   double* d_binpart = nullptr;  // per binning block: sum q, sum q^2, skipped atoms
-  int* d_ptile = nullptr;
-  int* d_prank = nullptr;
-  int* d_plb = nullptr;
-  void* d_tq = nullptr;
-  void* d_sorted_tq = nullptr;
-  int* d_sorted_lb = nullptr;
-  int* d_sorted_idx = nullptr;
   double* d_accum = nullptr;
   double* d_partials = nullptr;
   void* d_io_pos = nullptr;
@@ -248,8 +245,8 @@ int update_xfft_tasks(esp_plan_t p) {
     for (int c = 0; c < NC; ++c) {
       const int f = gi * NC + c;
       if (f >= x.ncol) break;
-      const int i1 = f / s.H2, m2 = f % s.H2;
-      const int m1 = (2 * i1 <= s.M[1]) ? i1 : i1 - s.M[1];
+      const int b1 = f / x.nb2, m2 = f % x.nb2;
+      const int m1 = (2 * b1 <= x.nb1) ? b1 : b1 - x.nb1;
       bool act = false;
       if (std::abs(m1) <= s.mmax[1] && m2 <= s.mmax[2]) {
         const double vx = m1 * b[3] + m2 * b[6], vy = m1 * b[4] + m2 * b[7], vz = m1 * b[5] + m2 * b[8];
@@ -420,9 +417,10 @@ void build_invw2(esp_plan_t p, std::vector<double>& out) {
 void release(esp_plan_t p) {
   if (!p) return;
   if (p->stream) cudaStreamSynchronize(p->stream);
-  void* bufs[] = {p->d_wtab,      p->d_radtab,    p->d_invw2,    p->d_grid,      p->d_spec,  p->d_spec2, p->d_xtw, p->d_xorder, p->d_xcol, p->d_tq,
-                  p->d_count,     p->d_offset,    p->d_ptile,    p->d_prank,     p->d_plb,  p->d_suboff, p->d_binpart, p->d_bsum,
-                  p->d_sorted_tq, p->d_sorted_lb, p->d_sorted_idx, p->d_accum,   p->d_partials,
+  void* bufs[] = {p->d_wtab,      p->d_radtab,    p->d_invw2,    p->d_grid,      p->d_spec,  p->d_spec2, p->d_xtw, p->d_xorder, p->d_xcol,
+                  p->d_pbox,      p->d_ptw,
+                  p->bins.count,  p->bins.tcount, p->bins.tq,    p->bins.lb,     p->bins.idx, p->bins.otq, p->bins.ob, p->bins.oidx,
+                  p->bins.ctrl,   p->d_binpart,   p->d_accum,   p->d_partials,
                   p->d_io_pos,    p->d_io_q,     p->d_io_f,
                   p->d_neartab,   p->d_ncount,    p->d_ncoff,    p->d_ncell,     p->d_nrank,
                   p->d_nxq_tmp,   p->d_nxq,       p->d_nidx,     p->d_fspec,     p->d_fgrid};
@@ -448,6 +446,91 @@ void release(esp_plan_t p) {
   delete p;
 }
 
+unsigned int magic_of(unsigned int d) {
+  return (unsigned int)((((unsigned long long)1 << 32) + d - 1) / d);
+}
+
+// Passes of a mixed-radix transform of length n: radices 8, 4, 2, 3, 5, 7, then the other
+// prime factors; ns_magic[k] = ceil(2^32 / Ns), Ns the product of the radices before pass k.
+bool radix_plan(int n, int* radix, unsigned int* ns_magic, int* npass) {
+  int np = 0;
+  auto push = [&](int r) {
+    if (np < esp::kMaxPass) radix[np] = r;
+    ++np;
+    n /= r;
+  };
+  while (n % 8 == 0) push(8);
+  if (n % 4 == 0) push(4);
+  if (n % 2 == 0) push(2);
+  for (int r : {3, 5, 7})
+    while (n % r == 0) push(r);
+  for (int r = 11; (int64_t)r * r <= n; r += 2)
+    while (n % r == 0) push(r);
+  if (n > 1) push(n);
+  if (np > esp::kMaxPass) return false;
+  *npass = np;
+  for (int k = 0, ns = 1; k < np; ns *= radix[k], ++k) ns_magic[k] = magic_of((unsigned)ns);
+  return true;
+}
+
+// Layout of the transform along the first axis and the plane transforms for the current
+// cell.  The plane kernels keep only the box of the sphere (|m1| <= mmax1, m2 <= mmax2);
+// when their shared memory would exceed the budget, cuFFT transforms the planes into the
+// full half spectrum instead.  Either way the sizes stay within the buffers allocated
+// for the full layout.
+int setup_planes(esp_plan_t p) {
+  esp::PlaneGeom& pg = p->pg;
+  const int M1 = p->M[1], M2 = p->M[2];
+  pg.M0 = p->M[0];
+  pg.M1 = M1;
+  pg.M2 = M2;
+  pg.mmax1 = p->sg.mmax[1];
+  pg.nb1 = 2 * p->sg.mmax[1] + 1;
+  pg.nb2 = p->sg.mmax[2] + 1;
+  pg.npairs = (M1 + 1) / 2;
+  pg.m2_magic = magic_of((unsigned)M2);
+  pg.nb2_magic = magic_of((unsigned)pg.nb2);
+  bool ok = radix_plan(M2, pg.a.radix, pg.a.ns_magic, &pg.a.npass) &&
+            radix_plan(M1, pg.b.radix, pg.b.ns_magic, &pg.b.npass);
+  pg.a.n = M2;
+  pg.b.n = M1;
+  pg.b.nc = pg.nb2 | 1;
+  pg.b.nc_magic = magic_of((unsigned)pg.b.nc);
+  const size_t ce = p->fp64 ? 16 : 8;
+  const size_t budget = 200 * 1024;
+  int pb = std::min(32, pg.npairs + (pg.npairs & 1));
+  pb += pb & 1;
+  for (; pb >= 2; pb -= 2) {
+    pg.pairs_b = pb;
+    pg.a.nc = pb | 1;
+    if (esp::plane_smem_bytes(p->fp64, pg) <= budget) break;
+  }
+  ok = ok && pb >= 2;
+  if (ok) {
+    pg.a.nc_magic = magic_of((unsigned)pg.a.nc);
+    // every magic division stays exact: x d < 2^32 for the largest dividend x
+    const uint64_t lim = (uint64_t)1 << 32;
+    ok = (uint64_t)M2 * pg.a.nc * pg.a.nc < lim && (uint64_t)M1 * pg.b.nc * pg.b.nc < lim &&
+         (uint64_t)M2 * pg.a.nc * M2 < lim && (uint64_t)pg.nb2 * pg.a.nc * pg.nb2 < lim &&
+         (uint64_t)pg.nb1 * pg.nb2 * pg.nb2 < lim;
+  }
+  (void)ce;
+  esp::XGeom& x = p->xg;
+  p->box_mode = ok;
+  if (ok) {
+    x.nb1 = pg.nb1;
+    x.nb2 = pg.nb2;
+    const cudaError_t e = esp::configure_planes(p->fp64, esp::plane_smem_bytes(p->fp64, pg));
+    if (e != cudaSuccess) return cuda_fail(p, e, "cudaFuncSetAttribute (plane transforms)");
+  } else {
+    x.nb1 = M1;
+    x.nb2 = p->H2;
+  }
+  x.ncol = x.nb1 * x.nb2;
+  p->xblocks = esp::xfft_blocks(x);
+  return ESP_OK;
+}
+
 // Tile geometry of spread and gather (p->M, p->P, p->fp64, p->deg and p->pswf set).  A
 // tile holds T0 x T1 x T2 stencil bases; the CTA working on it owns the padded block
 // (T + P - 1)^3.  T2 is a multiple of 4 so padded rows move as aligned float4 when M2 is
@@ -471,9 +554,6 @@ int setup_tile_geom(esp_plan_t p) {
     g.dscalef[d] = (float)g.dscale[d];
     p->ntiles *= g.nt[d];
   }
-  g.ksub = (int64_t)p->ntiles * esp::kSub <= esp::kMaxScan ? esp::kSub : 1;
-  if ((int64_t)p->ntiles * g.ksub > esp::kMaxScan)
-    return fail(p, ESP_ERR_ARG, "grid too large: more tiles than the binning scan handles");
   g.vec4 = (!p->fp64 && g.T[2] % 4 == 0 && p->M[2] % 4 == 0 && (g.E[2] + 3) / 4 * 4 <= g.E3p) ? 1 : 0;
   auto magic = [](unsigned int d) {
     return (unsigned int)((((unsigned long long)1 << 32) + d - 1) / d);
@@ -515,6 +595,43 @@ inline void mark(esp_plan_t p, int i) {
   }
 }
 
+// Forward plane transforms: the grid into d_pbox (the box of the sphere, or the full half
+// spectrum through cuFFT).
+int planes_forward(esp_plan_t p) {
+  if (p->box_mode) {
+    ESP_CUDA(p, esp::launch_fplane(p->fp64, p->pg, p->d_grid, p->d_pbox, p->d_ptw, p->stream));
+    return ESP_OK;
+  }
+  if (p->fp64)
+    ESP_CUFFT(p, cufftExecD2Z(p->fwd, (cufftDoubleReal*)p->d_grid, (cufftDoubleComplex*)p->d_pbox));
+  else
+    ESP_CUFFT(p, cufftExecR2C(p->fwd, (cufftReal*)p->d_grid, (cufftComplex*)p->d_pbox));
+  return ESP_OK;
+}
+
+// Inverse plane transforms: the scaled columns of d_spec2 into the grid (the potential).
+int planes_inverse(esp_plan_t p) {
+  if (p->box_mode) {
+    ESP_CUDA(p, esp::launch_iplane(p->fp64, p->pg, p->d_spec2, p->d_xcol, p->d_grid, p->d_ptw,
+                                   p->stream));
+    return ESP_OK;
+  }
+  if (p->fp64)
+    ESP_CUFFT(p, cufftExecZ2D(p->inv, (cufftDoubleComplex*)p->d_spec2, (cufftDoubleReal*)p->d_grid));
+  else
+    ESP_CUFFT(p, cufftExecC2R(p->inv, (cufftComplex*)p->d_spec2, (cufftReal*)p->d_grid));
+  return ESP_OK;
+}
+
+// The full half spectrum of the real grid's current content into d_spec (cuFFT 3D R2C).
+int full_spectrum(esp_plan_t p) {
+  if (p->fp64)
+    ESP_CUFFT(p, cufftExecD2Z(p->fwd3, (cufftDoubleReal*)p->d_grid, (cufftDoubleComplex*)p->d_spec));
+  else
+    ESP_CUFFT(p, cufftExecR2C(p->fwd3, (cufftReal*)p->d_grid, (cufftComplex*)p->d_spec));
+  return ESP_OK;
+}
+
 int run_step(esp_plan_t p, const void* pos, const void* q, void* forces, double* acc) {
   cudaStream_t st = p->stream;
   const bool fp64 = p->fp64;
@@ -522,45 +639,34 @@ int run_step(esp_plan_t p, const void* pos, const void* q, void* forces, double*
   const size_t Mtot = (size_t)p->M[0] * p->M[1] * p->M[2];
   for (int i = 0; i <= kNStage; ++i) p->ev_used[i] = false;
   mark(p, kPrep);
-  int* work = p->d_count + (size_t)p->ntiles * esp::kSub;
-  // d_count and the work counters are zero here: set at plan time, re-zeroed by the scan
-  // kernel of every step.  acc[0..6] is written by the scale kernel, acc[7..9] by scan.
+  // the binning counters and control words are zero here: set at plan time, re-zeroed by
+  // the spread and gather kernels of every step.  acc[0..6] is written by the sums of the
+  // scaling, acc[7..9] by the sums of the binning partials.
   const bool want_f = forces != nullptr;
-  if (want_f) {
-    // the scaled spectrum's buffer is cleared on the side branch while the atoms are
-    // binned and spread: k_xfft writes only the columns that meet the sphere
+  const bool clear = want_f && !p->box_mode;
+  if (clear) {
+    // cuFFT's inverse reads the whole half spectrum: its buffer is cleared on the side
+    // branch while the atoms are binned and spread (k_xfft writes only the columns that
+    // meet the sphere; the library's inverse plane kernel reads the others as zero)
     ESP_CUDA(p, cudaEventRecord(p->ev_start, st));
     ESP_CUDA(p, cudaStreamWaitEvent(p->side, p->ev_start, 0));
     ESP_CUDA(p, cudaMemsetAsync(p->d_spec2, 0, 2 * es * (size_t)p->M[0] * p->M[1] * p->H2, p->side));
     ESP_CUDA(p, cudaEventRecord(p->ev_zero, p->side));
   }
   mark(p, kBin);
-  ESP_CUDA(p, esp::launch_bin(p->io_double, fp64, pos, q, p->n, p->tg, p->d_count, p->d_ptile,
-                              p->d_prank, p->d_plb, p->d_tq, p->d_binpart, p->d_grid,
-                              es * Mtot, st));
-  mark(p, kScan);
-  ESP_CUDA(p, esp::launch_scan(p->d_count, p->d_suboff, p->d_offset, p->d_bsum, p->ntiles,
-                               p->tg.ksub, work, st));
-  mark(p, kScatter);
-  ESP_CUDA(p, esp::launch_scatter(fp64, p->n, p->tg.ksub, p->d_ptile, p->d_prank, p->d_plb, p->d_tq,
-                                  p->d_suboff, p->d_sorted_tq, p->d_sorted_lb,
-                                  p->d_sorted_idx, st));
+  ESP_CUDA(p, esp::launch_bin(p->io_double, fp64, pos, q, p->n, p->tg, p->bins, p->d_binpart,
+                              p->d_grid, es * Mtot, st));
   mark(p, kSpread);
-  ESP_CUDA(p, esp::launch_spread(fp64, p->tg, p->ntiles, p->spread_blocks, p->d_sorted_tq,
-                                 p->d_sorted_lb, p->d_offset, work, p->d_wtab, p->d_grid, st));
+  ESP_CUDA(p, esp::launch_spread(fp64, p->tg, p->ntiles, p->spread_blocks, p->bins, p->d_wtab,
+                                 p->d_grid, st));
   mark(p, kFftFwd);
-  // forces: plane transforms (the transform along axis 0 is fused into k_xfft); energy and
-  // pressure only: the full 3D transform, whose spectrum is kept
-  const cufftHandle fplan = want_f ? p->fwd : p->fwd3;
-  if (fp64)
-    ESP_CUFFT(p, cufftExecD2Z(fplan, (cufftDoubleReal*)p->d_grid, (cufftDoubleComplex*)p->d_spec));
-  else
-    ESP_CUFFT(p, cufftExecR2C(fplan, (cufftReal*)p->d_grid, (cufftComplex*)p->d_spec));
+  int rc;
+  if ((rc = planes_forward(p)) != ESP_OK) return rc;
   mark(p, kScale);
-  if (want_f) ESP_CUDA(p, cudaStreamWaitEvent(st, p->ev_zero, 0));
-  ESP_CUDA(p, esp::launch_xfft(fp64, want_f, want_f, p->xg, p->sg, p->d_spec, p->d_spec2, p->d_xtw, p->d_invw2,
-                               p->d_radtab, p->d_partials, p->d_xorder, p->d_xcol, p->xactive,
-                               st));
+  if (clear) ESP_CUDA(p, cudaStreamWaitEvent(st, p->ev_zero, 0));
+  ESP_CUDA(p, esp::launch_xfft(fp64, true, want_f, p->xg, p->sg, p->d_pbox, p->d_spec2, p->d_xtw,
+                               p->d_invw2, p->d_radtab, p->d_partials, p->d_xorder, p->d_xcol,
+                               p->xactive, st));
   // the energy and virial sums finish on the side branch while the forces go on
   ESP_CUDA(p, cudaEventRecord(p->ev_fork, st));
   ESP_CUDA(p, cudaStreamWaitEvent(p->side, p->ev_fork, 0));
@@ -569,14 +675,10 @@ int run_step(esp_plan_t p, const void* pos, const void* q, void* forces, double*
   ESP_CUDA(p, cudaEventRecord(p->ev_join, p->side));
   mark(p, kFftInv);
   if (want_f) {
-    if (fp64)
-      ESP_CUFFT(p, cufftExecZ2D(p->inv, (cufftDoubleComplex*)p->d_spec2, (cufftDoubleReal*)p->d_grid));
-    else
-      ESP_CUFFT(p, cufftExecC2R(p->inv, (cufftComplex*)p->d_spec2, (cufftReal*)p->d_grid));
+    if ((rc = planes_inverse(p)) != ESP_OK) return rc;
     mark(p, kGather);
     ESP_CUDA(p, esp::launch_gather(fp64, p->io_double, p->gg, p->ntiles, p->gather_blocks,
-                                   p->d_sorted_tq, p->d_sorted_lb, p->d_sorted_idx,
-                                   p->d_offset, work, p->d_wtab, p->d_grid, forces, st));
+                                   p->bins, p->d_wtab, p->d_grid, forces, st));
   }
   ESP_CUDA(p, cudaStreamWaitEvent(st, p->ev_join, 0));
   mark(p, kNStage);
@@ -737,26 +839,12 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
   {
     esp::XGeom& x = p->xg;
     x.M0 = p->M[0];
+    x.nb1 = p->M[1];  // the full layout until the plane transforms are set up
+    x.nb2 = p->H2;
     x.ncol = p->M[1] * p->H2;
-    int n = x.M0, np = 0;
-    auto push = [&](int r) {
-      if (np < esp::kMaxPass) x.radix[np] = r;
-      ++np;
-      n /= r;
-    };
-    while (n % 8 == 0) push(8);
-    if (n % 4 == 0) push(4);
-    if (n % 2 == 0) push(2);
-    for (int r : {3, 5, 7})
-      while (n % r == 0) push(r);
-    for (int r = 11; (int64_t)r * r <= n; r += 2)
-      while (n % r == 0) push(r);
-    if (n > 1) push(n);
-    if (np > esp::kMaxPass) return bail(fail(p, ESP_ERR_ARG, "grid size M1 has too many prime factors"));
-    x.npass = np;
+    if (!radix_plan(x.M0, x.radix, x.ns_magic, &x.npass))
+      return bail(fail(p, ESP_ERR_ARG, "grid size M1 has too many prime factors"));
     if (x.M0 >= (1 << 16)) return bail(fail(p, ESP_ERR_ARG, "grid size M1 too large"));
-    for (int k = 0, ns = 1; k < np; ns *= x.radix[k], ++k)
-      x.ns_magic[k] = (unsigned int)((((unsigned long long)1 << 32) + ns - 1) / ns);
     x.lognc = 3;
     while (x.lognc > 0 && esp::xfft_smem_bytes(p->fp64, x.M0, x.lognc, p->rdeg) > 100 * 1024)
       --x.lognc;
@@ -781,19 +869,24 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
   ALLOC(p->d_grid, es * Mtot);
   ALLOC(p->d_spec, 2 * es * nspec);
   ALLOC(p->d_spec2, 2 * es * nspec);
+  ALLOC(p->d_pbox, 2 * es * nspec);
+  ALLOC(p->d_ptw, 2 * es * (size_t)(p->M[1] + p->M[2]));
   p->bin_blocks = esp::bin_blocks(n);
-  ALLOC(p->d_count, sizeof(int) * ((size_t)p->ntiles * esp::kSub + 2));
-  ALLOC(p->d_suboff, sizeof(int) * ((size_t)p->ntiles * esp::kSub + 1));
-  ALLOC(p->d_offset, sizeof(int) * (p->ntiles + 1));
+  {
+    esp::Bins& b = p->bins;
+    b.cap = esp::bin_capacity(n, p->ntiles);
+    const size_t nslot = (size_t)p->ntiles * b.cap;
+    ALLOC(b.count, sizeof(int) * (size_t)p->ntiles);
+    ALLOC(b.tcount, sizeof(int) * (size_t)p->ntiles);
+    ALLOC(b.tq, 4 * es * nslot);
+    ALLOC(b.lb, sizeof(int) * nslot);
+    ALLOC(b.idx, sizeof(int) * nslot);
+    ALLOC(b.otq, 4 * es * nn);
+    ALLOC(b.ob, 3 * sizeof(int) * nn);
+    ALLOC(b.oidx, sizeof(int) * nn);
+    ALLOC(b.ctrl, sizeof(int) * esp::kCtrl);
+  }
   ALLOC(p->d_binpart, sizeof(double) * 3 * p->bin_blocks);
-  ALLOC(p->d_bsum, sizeof(int) * esp::scan_blocks(p->ntiles, g.ksub));
-  ALLOC(p->d_ptile, sizeof(int) * nn);
-  ALLOC(p->d_prank, sizeof(int) * nn);
-  ALLOC(p->d_plb, sizeof(int) * nn);
-  ALLOC(p->d_tq, 4 * es * nn);
-  ALLOC(p->d_sorted_tq, 4 * es * nn);
-  ALLOC(p->d_sorted_lb, sizeof(int) * nn);
-  ALLOC(p->d_sorted_idx, sizeof(int) * nn);
   ALLOC(p->d_accum, sizeof(double) * ESP_ACCUM_LEN);
   ALLOC(p->d_partials, sizeof(double) * 7 * (size_t)p->xblocks);
   ALLOC(p->d_xtw, 2 * es * (size_t)p->M[0]);
@@ -802,7 +895,9 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
 #undef ALLOC
   (void)io_es;
   {
-    cudaError_t e = cudaMemset(p->d_count, 0, sizeof(int) * ((size_t)p->ntiles * esp::kSub + 2));
+    cudaError_t e = cudaMemset(p->bins.count, 0, sizeof(int) * (size_t)p->ntiles);
+    if (e == cudaSuccess) e = cudaMemset(p->bins.tcount, 0, sizeof(int) * (size_t)p->ntiles);
+    if (e == cudaSuccess) e = cudaMemset(p->bins.ctrl, 0, sizeof(int) * esp::kCtrl);
     if (e == cudaSuccess) e = cudaMemset(p->d_accum, 0, sizeof(double) * ESP_ACCUM_LEN);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_accum, sizeof(double) * ESP_ACCUM_LEN);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_xorder, sizeof(int) * (size_t)p->xblocks);
@@ -816,12 +911,24 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
       tw[2 * m] = std::cos(2.0 * M_PI * m / p->M[0]);
       tw[2 * m + 1] = -std::sin(2.0 * M_PI * m / p->M[0]);
     }
+    // and the M1 then M2 roots of the plane transforms
+    std::vector<double> ptw;
+    for (int d = 1; d <= 2; ++d)
+      for (int m = 0; m < p->M[d]; ++m) {
+        ptw.push_back(std::cos(2.0 * M_PI * m / p->M[d]));
+        ptw.push_back(-std::sin(2.0 * M_PI * m / p->M[d]));
+      }
     cudaError_t e;
     if (p->fp64) {
       e = cudaMemcpy(p->d_xtw, tw.data(), sizeof(double) * tw.size(), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(p->d_ptw, ptw.data(), sizeof(double) * ptw.size(), cudaMemcpyHostToDevice);
     } else {
       std::vector<float> twf(tw.begin(), tw.end());
       e = cudaMemcpy(p->d_xtw, twf.data(), sizeof(float) * twf.size(), cudaMemcpyHostToDevice);
+      std::vector<float> ptwf(ptw.begin(), ptw.end());
+      if (e == cudaSuccess)
+        e = cudaMemcpy(p->d_ptw, ptwf.data(), sizeof(float) * ptwf.size(), cudaMemcpyHostToDevice);
     }
     if (e == cudaSuccess)
       e = esp::configure_xfft(p->fp64, esp::xfft_smem_bytes(p->fp64, p->xg.M0, p->xg.lognc, p->rdeg));
@@ -831,6 +938,7 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_zero, cudaEventDisableTiming);
     if (e != cudaSuccess) return bail(cuda_fail(p, e, "transform set-up"));
+    if ((rc = setup_planes(p)) != ESP_OK) return bail(rc);
     if ((rc = update_xfft_tasks(p)) != ESP_OK) return bail(rc);
   }
   {
@@ -883,6 +991,7 @@ int esp_set_cell(esp_plan_t p, const double cell[9]) {
   update_cell_constants(p);
   p->spectrum_kept = false;
   drop_graph(p);
+  if ((rc = setup_planes(p)) != ESP_OK) return rc;
   return update_xfft_tasks(p);
 }
 
@@ -936,22 +1045,19 @@ int esp_forces_from_spectrum(esp_plan_t p, void* forces) {
   DeviceGuard guard(p->device);
   cudaStream_t st = p->stream;
   const bool fp64 = p->fp64;
-  ESP_CUDA(p, cudaMemsetAsync(p->d_spec2, 0,
-                              2 * (fp64 ? 8 : 4) * (size_t)p->M[0] * p->M[1] * p->H2, st));
-  ESP_CUDA(p, esp::launch_xfft(fp64, false, true, p->xg, p->sg, p->d_spec, p->d_spec2, p->d_xtw,
+  if (!p->box_mode)
+    ESP_CUDA(p, cudaMemsetAsync(p->d_spec2, 0,
+                                2 * (fp64 ? 8 : 4) * (size_t)p->M[0] * p->M[1] * p->H2, st));
+  // the kept plane transforms take the transform along i0, the scaling and its inverse
+  ESP_CUDA(p, esp::launch_xfft(fp64, true, true, p->xg, p->sg, p->d_pbox, p->d_spec2, p->d_xtw,
                                p->d_invw2, p->d_radtab, p->d_partials, p->d_xorder, p->d_xcol,
                                p->xactive, st));
   ESP_CUDA(p, esp::launch_xsum(fp64, p->d_partials, p->xactive, p->d_binpart,
                                p->n > 0 ? p->bin_blocks : 0, p->d_accum, st));
-  if (fp64)
-    ESP_CUFFT(p, cufftExecZ2D(p->inv, (cufftDoubleComplex*)p->d_spec2, (cufftDoubleReal*)p->d_grid));
-  else
-    ESP_CUFFT(p, cufftExecC2R(p->inv, (cufftComplex*)p->d_spec2, (cufftReal*)p->d_grid));
-  int* work = p->d_count + (size_t)p->ntiles * esp::kSub;
-  ESP_CUDA(p, cudaMemsetAsync(work + 1, 0, sizeof(int), st));
+  int rc;
+  if ((rc = planes_inverse(p)) != ESP_OK) return rc;
   ESP_CUDA(p, esp::launch_gather(fp64, p->io_double, p->gg, p->ntiles, p->gather_blocks,
-                                 p->d_sorted_tq, p->d_sorted_lb, p->d_sorted_idx, p->d_offset,
-                                 work, p->d_wtab, p->d_grid, forces, st));
+                                 p->bins, p->d_wtab, p->d_grid, forces, st));
   p->spectrum_kept = false;
   return ESP_OK;
 }
@@ -988,6 +1094,8 @@ int run_fields(esp_plan_t p, const void* pos, const void* q, int kind, void* out
     return fail(p, ESP_ERR_CUFFT, "cufftSetStream failed");
   if ((rc = run_step(p, pos, q, nullptr, p->d_accum)) != ESP_OK) return rc;
   cudaStream_t st = p->stream;
+  // the full 3D half spectrum of the spread grid (the step keeps only the box of the sphere)
+  if ((rc = full_spectrum(p)) != ESP_OK) return rc;
   ESP_CUDA(p, esp::launch_fields(p->fp64, kind, p->sg, p->d_spec, p->d_invw2, p->d_radtab,
                                  p->d_fspec, st));
   if (p->fp64)
@@ -996,13 +1104,10 @@ int run_fields(esp_plan_t p, const void* pos, const void* q, int kind, void* out
     ESP_CUFFT(p, cufftExecC2R(plan, (cufftComplex*)p->d_fspec, (cufftReal*)p->d_fgrid));
   // gathers of up to 3 fields at a time (one at a time when 3 tiles do not fit)
   const int per = esp::fields_smem_bytes(p->fp64, p->P, 3) <= 227 * 1024 ? 3 : 1;
-  int* work = p->d_count + (size_t)p->ntiles * esp::kSub;
   for (int f0 = 0; f0 < nf; f0 += per) {
-    ESP_CUDA(p, cudaMemsetAsync(work + 1, 0, sizeof(int), st));
     const int k = std::min(per, nf - f0);
     ESP_CUDA(p, esp::launch_gather_fields(p->fp64, p->io_double, p->tg, p->ntiles, p->gather_blocks, k,
-                                          p->d_sorted_tq, p->d_sorted_lb, p->d_sorted_idx,
-                                          p->d_offset, work, p->d_wtab,
+                                          p->bins, p->d_wtab,
                                           (const unsigned char*)p->d_fgrid + (size_t)f0 * Mtot * es,
                                           (int64_t)Mtot, coef, out, nf, f0, st));
   }
@@ -1186,6 +1291,8 @@ int esp_copy_spectrum(esp_plan_t p, void* host_dst) {
   DeviceGuard guard(p->device);
   const size_t es = p->fp64 ? 8 : 4;
   const size_t ns = (size_t)p->M[0] * p->M[1] * p->H2;
+  int rc;
+  if ((rc = full_spectrum(p)) != ESP_OK) return rc;
   ESP_CUDA(p, cudaStreamSynchronize(p->stream));
   ESP_CUDA(p, cudaMemcpy(host_dst, p->d_spec, 2 * es * ns, cudaMemcpyDeviceToHost));
   return ESP_OK;
@@ -1193,7 +1300,7 @@ int esp_copy_spectrum(esp_plan_t p, void* host_dst) {
 
 int esp_plan_info(esp_plan_t p, double* info, int len) {
   if (!p || !info || len < 0) return fail(p, ESP_ERR_ARG, "NULL argument");
-  const double v[15] = {p->c,
+  const double v[18] = {p->c,
                         p->rc,
                         p->pswf.psi_at_0,
                         p->pswf.C0,
@@ -1206,9 +1313,12 @@ int esp_plan_info(esp_plan_t p, double* info, int len) {
                         (double)p->tg.T[0],
                         (double)p->tg.T[1],
                         (double)p->tg.T[2],
-                        8.0,  // bin, scan (2), scatter, spread, k_xfft, k_xsum, gather
-                        p->Xbg};
-  for (int i = 0; i < std::min(len, 15); ++i) info[i] = v[i];
+                        p->box_mode ? 7.0 : 5.0,  // bin, spread, [k_fplane], k_xfft, k_xsum, [k_iplane], gather
+                        p->Xbg,
+                        p->box_mode ? 1.0 : 0.0,
+                        (double)p->xg.nb1,
+                        (double)p->xg.nb2};
+  for (int i = 0; i < std::min(len, 18); ++i) info[i] = v[i];
   return ESP_OK;
 }
 
@@ -1260,30 +1370,30 @@ namespace {
 
 constexpr size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// slots of the binned atoms: at least 32 per tile at the largest tile count
+constexpr size_t kNoAllocSlots = 2 * (size_t)ESP_NOALLOC_MAX_ATOMS > 32 * (size_t)ESP_NOALLOC_MAX_TILES
+                                     ? 2 * (size_t)ESP_NOALLOC_MAX_ATOMS
+                                     : 32 * (size_t)ESP_NOALLOC_MAX_TILES;
+
 struct NoAllocLayout {
-  size_t count, suboff, toff, bsum, binpart, acc, ptile, prank, plb, tq, stq, slb, sidx, wtab,
-      total;
+  size_t count, tcount, ctrl, binpart, tq, lb, idx, otq, ob, oidx, wtab, total;
 };
 
 constexpr NoAllocLayout noalloc_layout() {
-  const size_t N = ESP_NOALLOC_MAX_ATOMS, T = ESP_NOALLOC_MAX_TILES;
-  const size_t nsub = T * esp::kSub;
+  const size_t N = ESP_NOALLOC_MAX_ATOMS, T = ESP_NOALLOC_MAX_TILES, S = kNoAllocSlots;
   const size_t nbin = (N + esp::kThreads - 1) / esp::kThreads;
   NoAllocLayout L{};
   size_t o = 0;
-  L.count = o;   o = al256(o + sizeof(int) * (nsub + 2));
-  L.suboff = o;  o = al256(o + sizeof(int) * (nsub + 1));
-  L.toff = o;    o = al256(o + sizeof(int) * (T + 1));
-  L.bsum = o;    o = al256(o + sizeof(int) * (nsub / (4 * esp::kThreads) + 1));
+  L.count = o;   o = al256(o + sizeof(int) * T);
+  L.tcount = o;  o = al256(o + sizeof(int) * T);
+  L.ctrl = o;    o = al256(o + sizeof(int) * esp::kCtrl);
   L.binpart = o; o = al256(o + 3 * 8 * nbin);
-  L.acc = o;     o = al256(o + sizeof(double) * ESP_ACCUM_LEN);
-  L.ptile = o;   o = al256(o + sizeof(int) * N);
-  L.prank = o;   o = al256(o + sizeof(int) * N);
-  L.plb = o;     o = al256(o + sizeof(int) * N);
-  L.tq = o;      o = al256(o + 32 * N);
-  L.stq = o;     o = al256(o + 32 * N);
-  L.slb = o;     o = al256(o + sizeof(int) * N);
-  L.sidx = o;    o = al256(o + sizeof(int) * N);
+  L.tq = o;      o = al256(o + 32 * S);
+  L.lb = o;      o = al256(o + sizeof(int) * S);
+  L.idx = o;     o = al256(o + sizeof(int) * S);
+  L.otq = o;     o = al256(o + 32 * N);
+  L.ob = o;      o = al256(o + 3 * sizeof(int) * N);
+  L.oidx = o;    o = al256(o + sizeof(int) * N);
   L.wtab = o;    o = al256(o + sizeof(double) * 2 * (esp::kMaxDeg + 1) * esp::kMaxP);
   L.total = o;
   return L;
@@ -1415,19 +1525,19 @@ extern "C" int esp_spread_noalloc(const double cell[9], int64_t n, const int gri
 
   unsigned char* S = nullptr;
   if ((rc = noalloc_scratch(&S)) != ESP_OK) return rc;  // reports through g_plan_error
-  int* count = reinterpret_cast<int*>(S + kNoAlloc.count);
-  int* work = count + (size_t)p->ntiles * esp::kSub;
-  int* suboff = reinterpret_cast<int*>(S + kNoAlloc.suboff);
-  int* toff = reinterpret_cast<int*>(S + kNoAlloc.toff);
-  int* bsum = reinterpret_cast<int*>(S + kNoAlloc.bsum);
+  esp::Bins bins{};
+  bins.cap = std::max(32, std::min(esp::bin_capacity(n, p->ntiles),
+                                   (int)(kNoAllocSlots / (size_t)p->ntiles / 32 * 32)));
+  bins.count = reinterpret_cast<int*>(S + kNoAlloc.count);
+  bins.tcount = reinterpret_cast<int*>(S + kNoAlloc.tcount);
+  bins.ctrl = reinterpret_cast<int*>(S + kNoAlloc.ctrl);
+  bins.tq = S + kNoAlloc.tq;
+  bins.lb = reinterpret_cast<int*>(S + kNoAlloc.lb);
+  bins.idx = reinterpret_cast<int*>(S + kNoAlloc.idx);
+  bins.otq = S + kNoAlloc.otq;
+  bins.ob = reinterpret_cast<int*>(S + kNoAlloc.ob);
+  bins.oidx = reinterpret_cast<int*>(S + kNoAlloc.oidx);
   void* binpart = S + kNoAlloc.binpart;
-  int* ptile = reinterpret_cast<int*>(S + kNoAlloc.ptile);
-  int* prank = reinterpret_cast<int*>(S + kNoAlloc.prank);
-  int* plb = reinterpret_cast<int*>(S + kNoAlloc.plb);
-  void* tq = S + kNoAlloc.tq;
-  void* stq = S + kNoAlloc.stq;
-  int* slb = reinterpret_cast<int*>(S + kNoAlloc.slb);
-  int* sidx = reinterpret_cast<int*>(S + kNoAlloc.sidx);
   void* dwtab = S + kNoAlloc.wtab;
 
   cudaStream_t st = p->stream;
@@ -1445,15 +1555,13 @@ extern "C" int esp_spread_noalloc(const double cell[9], int64_t n, const int gri
 
   k_put_window_table<<<1, 256, 0, st>>>(targ, dwtab, p->fp64 ? 1 : 0);
   ESP_CUDA(nullptr, cudaGetLastError());
-  // the array keeps the last call's contents: the counters must start at zero
-  ESP_CUDA(nullptr, cudaMemsetAsync(count, 0, sizeof(int) * ((size_t)p->ntiles * esp::kSub + 2), st));
-  ESP_CUDA(nullptr, esp::launch_bin(p->io_double, p->fp64, pos, q, n, g, count, ptile, prank, plb,
-                                    tq, binpart, nullptr, 0, st));
-  ESP_CUDA(nullptr, esp::launch_scan(count, suboff, toff, bsum, p->ntiles, g.ksub, work, st));
-  ESP_CUDA(nullptr, esp::launch_scatter(p->fp64, n, g.ksub, ptile, prank, plb, tq, suboff, stq,
-                                        slb, sidx, st));
+  // the array keeps the last call's contents: the counters and control words must start
+  // at zero (a completed call leaves them zero, a failed one may not)
+  ESP_CUDA(nullptr, cudaMemsetAsync(bins.count, 0, sizeof(int) * (size_t)p->ntiles, st));
+  ESP_CUDA(nullptr, cudaMemsetAsync(bins.ctrl, 0, sizeof(int) * esp::kCtrl, st));
+  ESP_CUDA(nullptr, esp::launch_bin(p->io_double, p->fp64, pos, q, n, g, bins, binpart,
+                                    nullptr, 0, st));
   ESP_CUDA(nullptr, cudaMemsetAsync(grid_out, 0, es * Mtot, st));
-  ESP_CUDA(nullptr, esp::launch_spread(p->fp64, g, p->ntiles, nblocks, stq, slb, toff, work,
-                                       dwtab, grid_out, st));
+  ESP_CUDA(nullptr, esp::launch_spread(p->fp64, g, p->ntiles, nblocks, bins, dwtab, grid_out, st));
   return ESP_OK;
 }

@@ -1,9 +1,9 @@
 // sm_103a kernels of the ESP long-range step (Sec. 4.1 Algorithm 1 and Appendix C):
 //   k_bin      wrap s = h^{-1} r into [0,1), stencil base and fractional offset
-//              (Sec. 4.3), tile id and rank within the tile; the integer stencil
-//              decision is taken in FP64 near a switch so it matches the FP64 oracle
-//   k_scan_*   multi-block exclusive scan of the tile counters
-//   k_scatter  counting-sort permutation of (offset t, q), local base and atom index
+//              (Sec. 4.3), tile id; the atom goes straight to the next free slot of its
+//              tile (warp-aggregated atomics; past the tile's capacity, to an overflow
+//              list); the integer stencil decision is taken in FP64 near a switch so it
+//              matches the FP64 oracle
 //   k_spread   eq. (gridding): persistent CTAs stage a tile's padded block in shared
 //              memory; a warp adds one atom's P^3 footprint at a time along lane-fixed
 //              stencil columns (32 distinct banks per add), as 32-bit fixed point with
@@ -189,14 +189,11 @@ __device__ __forceinline__ double dscale_of<double>(const TileGeom& g, int d) {
 template <typename IO, typename R>
 __global__ void __launch_bounds__(kThreads) k_bin(const IO* __restrict__ pos,
                                                   const IO* __restrict__ q, int64_t n,
-                                                  TileGeom g, int* __restrict__ tile_count,
-                                                  int* __restrict__ ptile,
-                                                  int* __restrict__ prank,
-                                                  int* __restrict__ plb,
-                                                  typename Vec4<R>::T* __restrict__ tq,
+                                                  TileGeom g, Bins bins,
                                                   float2* __restrict__ bin_part,
                                                   int4* __restrict__ zero, int64_t nzero) {
   pdl_trigger();
+  using V4 = typename Vec4<R>::T;
   // FP32 inputs on the FP32 path use the compensated FP32 transform (FP64 only for the
   // rare coordinate next to a stencil switch); everything else uses FP64.
   constexpr bool kDF = std::is_same<IO, float>::value && std::is_same<R, float>::value;
@@ -204,60 +201,83 @@ __global__ void __launch_bounds__(kThreads) k_bin(const IO* __restrict__ pos,
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nzero;
        i += (int64_t)gridDim.x * blockDim.x)
     zero[i] = make_int4(0, 0, 0, 0);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const unsigned lanes_below = (1u << lane) - 1u;
+  V4* slot_tq = static_cast<V4*>(bins.tq);
   DF sq, sq2, bad;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const IO r0 = pos[3 * i], r1 = pos[3 * i + 1], r2 = pos[3 * i + 2], qi = q[i];
-    if (!(isfinite(r0) && isfinite(r1) && isfinite(r2) && isfinite(qi))) {
-      ptile[i] = -1;
-      bad.add(1.f);
-      continue;
-    }
-    int tc[3], lb[3];
-    R t[3];
+  // uniform trip count per warp: the slot ranks are handed out per warp
+  for (int64_t i0 = blockIdx.x * (int64_t)blockDim.x; i0 < n; i0 += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = i0 + threadIdx.x;
+    int tile = -1, lbp = 0, b[3] = {0, 0, 0};
+    V4 v{};
+    if (i < n) {
+      const IO r0 = pos[3 * i], r1 = pos[3 * i + 1], r2 = pos[3 * i + 2], qi = q[i];
+      if (!(isfinite(r0) && isfinite(r1) && isfinite(r2) && isfinite(qi))) {
+        bad.add(1.f);
+      } else {
+        int tc[3], lb[3];
+        R t[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      int b;
-      bool done = false;
-      if constexpr (kDF) {
-        const float rf[3] = {(float)r0, (float)r1, (float)r2};
-        done = stencil_base_df(g, d, rf, &b, &t[d]);
+        for (int d = 0; d < 3; ++d) {
+          bool done = false;
+          if constexpr (kDF) {
+            const float rf[3] = {(float)r0, (float)r1, (float)r2};
+            done = stencil_base_df(g, d, rf, &b[d], &t[d]);
+          }
+          if (!done) {
+            const double r[3] = {(double)r0, (double)r1, (double)r2};
+            double td;
+            stencil_base(reduced_coord(&g.hinv[3 * d], r), g.M[d], g.P, &b[d], &td);
+            t[d] = (R)td;
+          }
+          tc[d] = b[d] / g.T[d];
+          lb[d] = b[d] - tc[d] * g.T[d];
+        }
+        tile = (tc[0] * g.nt[1] + tc[1]) * g.nt[2] + tc[2];
+        v.x = t[0];
+        v.y = t[1];
+        v.z = t[2];
+        v.w = (R)qi;
+        lbp = lb[0] | (lb[1] << 10) | (lb[2] << 20);
+        if constexpr (std::is_same<IO, float>::value) {
+          sq.add(qi);
+          sq2.add(qi * qi);
+        } else {
+          // split the double into a float pair so the sums stay accurate to ~2^-48
+          const float qh = (float)qi, ql = (float)(qi - (double)qh);
+          const double q2 = qi * qi;
+          const float q2h = (float)q2, q2l = (float)(q2 - (double)q2h);
+          sq.add(qh);
+          sq.add(ql);
+          sq2.add(q2h);
+          sq2.add(q2l);
+        }
       }
-      if (!done) {
-        const double r[3] = {(double)r0, (double)r1, (double)r2};
-        double td;
-        stencil_base(reduced_coord(&g.hinv[3 * d], r), g.M[d], g.P, &b, &td);
-        t[d] = (R)td;
-      }
-      tc[d] = b / g.T[d];
-      lb[d] = b - tc[d] * g.T[d];
     }
-    const int tile = (tc[0] * g.nt[1] + tc[1]) * g.nt[2] + tc[2];
-    typename Vec4<R>::T v;
-    v.x = t[0];
-    v.y = t[1];
-    v.z = t[2];
-    v.w = (R)qi;
-    tq[i] = v;
-    ptile[i] = tile;
-    plb[i] = lb[0] | (lb[1] << 10) | (lb[2] << 20);
-    // kSub counters per tile, chosen by the atom's warp, spread the same-address atomics
-    prank[i] = atomicAdd(&tile_count[tile * g.ksub + (int)((i >> 5) & (g.ksub - 1))], 1);
-    if constexpr (std::is_same<IO, float>::value) {
-      sq.add(qi);
-      sq2.add(qi * qi);
-    } else {
-      // split the double into a float pair so the sums stay accurate to ~2^-48
-      const float qh = (float)qi, ql = (float)(qi - (double)qh);
-      const double q2 = qi * qi;
-      const float q2h = (float)q2, q2l = (float)(q2 - (double)q2h);
-      sq.add(qh);
-      sq.add(ql);
-      sq2.add(q2h);
-      sq2.add(q2l);
+    // lanes of one tile take consecutive slots with one atomic per tile and warp
+    const unsigned same = __match_any_sync(0xffffffffu, tile);
+    const int leader = __ffs(same) - 1;
+    int first = 0;
+    if (lane == leader && tile >= 0) first = atomicAdd(&bins.count[tile], __popc(same));
+    first = __shfl_sync(0xffffffffu, first, leader);
+    if (tile >= 0) {
+      const int r = first + __popc(same & lanes_below);
+      if (r < bins.cap) {
+        const int64_t sl = (int64_t)tile * bins.cap + r;
+        slot_tq[sl] = v;
+        bins.lb[sl] = lbp;
+        bins.idx[sl] = (int)i;
+      } else {
+        const int o = atomicAdd(&bins.ctrl[0], 1);
+        static_cast<V4*>(bins.otq)[o] = v;
+        bins.ob[3 * o] = b[0];
+        bins.ob[3 * o + 1] = b[1];
+        bins.ob[3 * o + 2] = b[2];
+        bins.oidx[o] = (int)i;
+      }
     }
   }
-  // compensated warp sums, then one FP64 value per warp and one FP64 atomic per block
+  // compensated warp sums, then one compensated pair per block (k_xsum adds them up)
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     DF a, b2, c;
@@ -272,14 +292,13 @@ __global__ void __launch_bounds__(kThreads) k_bin(const IO* __restrict__ pos,
     bad.add(c);
   }
   __shared__ float2 red[3][kThreads / 32];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (lane == 0) {
     red[0][wid] = make_float2(sq.hi, sq.lo);
     red[1][wid] = make_float2(sq2.hi, sq2.lo);
     red[2][wid] = make_float2(bad.hi, bad.lo);
   }
   __syncthreads();
-  if (threadIdx.x < 3) {  // compensated per-block partials; the scan kernel adds them up
+  if (threadIdx.x < 3) {
     DF a;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
       DF y;
@@ -291,129 +310,24 @@ __global__ void __launch_bounds__(kThreads) k_bin(const IO* __restrict__ pos,
   }
 }
 
-// Exclusive scan of the binning sub-counters (tile-major, ksub per tile) in two
-// multi-block kernels of kScanBlock counts per block:
-//   k_scan_local  each block scans its counts (int4 per thread), writes the local
-//                 exclusive prefix to suboff and its total to bsum, and zeroes the counts
-//                 for the next step;
-//   k_scan_fix    each block adds the sum of the totals of the blocks before it and
-//                 writes the tile offsets toff[t] = suboff[t * ksub]; block 0 also resets
-//                 the work counters of spread and gather.  (The binning partials are
-//                 added up by k_xsum, off the critical path.)
-constexpr int kScanBlock = 4 * kThreads;
-
-__device__ __forceinline__ int block_exclusive_scan(int v, int* wsum, int* total) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) wsum[wid] = x;
+// The CTA that finishes last resets the control words [first, first + cnt) of its kernel
+// (counters zero again for the next step).  Every CTA must reach this point.
+__device__ __forceinline__ void last_cta_resets(int* ctrl, int done_word, int first, int cnt,
+                                                int copy_from = -1, int copy_to = -1) {
   __syncthreads();
-  if (wid == 0) {
-    int t = lane < kThreads / 32 ? wsum[lane] : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, t, o);
-      if (lane >= o) t += y;
-    }
-    if (lane < kThreads / 32) wsum[lane] = t;
-  }
-  __syncthreads();
-  *total = wsum[kThreads / 32 - 1];
-  return (wid > 0 ? wsum[wid - 1] : 0) + x - v;
-}
-
-__global__ void __launch_bounds__(kThreads) k_scan_local(int* __restrict__ count,
-                                                         int* __restrict__ suboff,
-                                                         int* __restrict__ bsum, int n) {
-  pdl_wait();
-  pdl_trigger();
-  __shared__ int wsum[kThreads / 32];
-  const int i = blockIdx.x * kScanBlock + 4 * threadIdx.x;
-  int v[4] = {0, 0, 0, 0};
-  if (i + 3 < n) {
-    const int4 c = *reinterpret_cast<const int4*>(count + i);
-    v[0] = c.x;
-    v[1] = c.y;
-    v[2] = c.z;
-    v[3] = c.w;
-    *reinterpret_cast<int4*>(count + i) = make_int4(0, 0, 0, 0);
-  } else {
-    for (int f = 0; f < 4; ++f)
-      if (i + f < n) {
-        v[f] = count[i + f];
-        count[i + f] = 0;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const int done = atomicAdd(&ctrl[done_word], 1);
+    if (done == (int)gridDim.x - 1) {
+      __threadfence();
+      volatile int* vc = ctrl;
+      if (copy_from >= 0) {
+        vc[copy_to] = vc[copy_from];
+        vc[copy_from] = 0;
       }
-  }
-  int total;
-  int run = block_exclusive_scan(v[0] + v[1] + v[2] + v[3], wsum, &total);
-  int o[4];
-  for (int f = 0; f < 4; ++f) {
-    o[f] = run;
-    run += v[f];
-  }
-  if (i + 3 < n)
-    *reinterpret_cast<int4*>(suboff + i) = make_int4(o[0], o[1], o[2], o[3]);
-  else
-    for (int f = 0; f < 4; ++f)
-      if (i + f < n) suboff[i + f] = o[f];
-  if (threadIdx.x == 0) bsum[blockIdx.x] = total;
-}
-
-__global__ void __launch_bounds__(kThreads) k_scan_fix(int* __restrict__ suboff,
-                                                       int* __restrict__ toff,
-                                                       const int* __restrict__ bsum,
-                                                       int ntiles, int ksub,
-                                                       int* __restrict__ work) {
-  pdl_wait();
-  pdl_trigger();
-  __shared__ int red[kThreads / 32];
-  const int n = ntiles * ksub;
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  // sum of the totals of the blocks before this one
-  int pre = 0;
-  for (int b = threadIdx.x; b < (int)blockIdx.x; b += blockDim.x) pre += bsum[b];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) pre += __shfl_xor_sync(0xffffffffu, pre, o);
-  if (lane == 0) red[wid] = pre;
-  __syncthreads();
-  pre = 0;
-  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) pre += red[w];
-  const int i = blockIdx.x * kScanBlock + 4 * threadIdx.x;
-  for (int f = 0; f < 4; ++f) {
-    if (i + f < n) {
-      const int v = suboff[i + f] + pre;
-      suboff[i + f] = v;
-      if ((i + f) % ksub == 0) toff[(i + f) / ksub] = v;
+      for (int k = 0; k < cnt; ++k) vc[first + k] = 0;
+      __threadfence();
     }
-  }
-  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
-    const int last = blockIdx.x;
-    const int tot = pre + bsum[last];
-    suboff[n] = tot;
-    toff[ntiles] = tot;
-  }
-  if (blockIdx.x == 0 && threadIdx.x < 2) work[threadIdx.x] = 0;
-}
-
-template <typename V>
-__global__ void __launch_bounds__(kThreads) k_scatter(
-    int64_t n, int ksub, const int* __restrict__ ptile, const int* __restrict__ prank,
-    const int* __restrict__ plb, const V* __restrict__ tq, const int* __restrict__ offset,
-    V* __restrict__ sorted_tq, int* __restrict__ sorted_lb, int* __restrict__ sorted_idx) {
-  pdl_wait();
-  pdl_trigger();
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    const int tile = ptile[i];
-    if (tile < 0) continue;
-    const int dst = offset[tile * ksub + (int)((i >> 5) & (ksub - 1))] + prank[i];
-    sorted_tq[dst] = tq[i];
-    sorted_lb[dst] = plb[i];
-    sorted_idx[dst] = (int)i;
   }
 }
 
@@ -614,12 +528,13 @@ __device__ __forceinline__ void spread_column2(unsigned addr,
 // contribution is at most half a unit of 2^-30 times that bound.  The block then goes to
 // the periodic grid with global atomics, and is cleared as it is read.
 template <typename R, int P>
-__global__ void __launch_bounds__(kThreads) k_spread(
-    const typename Vec4<R>::T* __restrict__ sorted_tq, const int* __restrict__ sorted_lb,
-    const int* __restrict__ toff, TileGeom g, int ntiles, int* __restrict__ work,
-    const R* __restrict__ wtab, R* __restrict__ grid) {
+__global__ void __launch_bounds__(kThreads) k_spread(Bins bins, TileGeom g, int ntiles,
+                                                     const R* __restrict__ wtab,
+                                                     R* __restrict__ grid) {
   pdl_wait();
   using V4 = typename Vec4<R>::T;
+  const V4* __restrict__ sorted_tq = static_cast<const V4*>(bins.tq);
+  const int* __restrict__ sorted_lb = bins.lb;
   using TC = TileC<P>;
   using CM = Cols<P>;
   constexpr bool kFixed = std::is_same<R, float>::value;
@@ -633,9 +548,20 @@ __global__ void __launch_bounds__(kThreads) k_spread(
   R* W = reinterpret_cast<R*>(smem_raw + L.w);  // per atom [w0 | q w1 | w2]
   V4* TQ = reinterpret_cast<V4*>(smem_raw + L.t);  // per atom (t0, t1, t2, q)
   int* B = reinterpret_cast<int*>(smem_raw + L.b);
-  __shared__ int s_tile;
+  __shared__ int s_tile, s_cnt;
   __shared__ float s_qsum[kThreads / 32];
   const unsigned acc_s = (unsigned)__cvta_generic_to_shared(acc);
+  // thread 0 takes the next tile and moves its atom count out of the binning counter
+  auto next_tile = [&]() {
+    const int t = atomicAdd(&bins.ctrl[1], 1);
+    s_tile = t;
+    if (t < ntiles) {
+      const int c = min(bins.count[t], bins.cap);
+      bins.tcount[t] = c;
+      bins.count[t] = 0;
+      s_cnt = c;
+    }
+  };
 
   constexpr int D = WinDeg<R>::value;
   constexpr int NP = kThreads / P;  // pairs per sweep
@@ -644,7 +570,7 @@ __global__ void __launch_bounds__(kThreads) k_spread(
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const LaneCols<P, S1, E3p> lc(lane, (int)sizeof(A));
 
-  if (threadIdx.x == 0) s_tile = atomicAdd(&work[0], 1);
+  if (threadIdx.x == 0) next_tile();
   {
     // clear the block once; every flush clears what it reads
     using Z = typename std::conditional<kFixed, int4, double2>::type;
@@ -658,7 +584,7 @@ __global__ void __launch_bounds__(kThreads) k_spread(
   for (;;) {
     const int tile = s_tile;
     if (tile >= ntiles) break;
-    const int start = toff[tile], end = toff[tile + 1];
+    const int start = tile * bins.cap, end = start + s_cnt;
     if (start < end) {
       // fixed-point scale of this tile (FP32): a power of two, so scaling back is exact
       R scale = R(1), inv_scale = R(1);
@@ -795,9 +721,44 @@ __global__ void __launch_bounds__(kThreads) k_spread(
       }
     }
     __syncthreads();  // the block is read out and cleared; s_tile consumed
-    if (threadIdx.x == 0) s_tile = atomicAdd(&work[0], 1);
+    if (threadIdx.x == 0) next_tile();
     __syncthreads();
   }
+
+  // atoms past their tile's capacity: one warp per atom, window values in the warp's part
+  // of the record area, global atomics with periodic wrap
+  {
+    const int novf = bins.ctrl[0];
+    R* Ww = W + warp * (3 * kMaxP);
+    const V4* otq = static_cast<const V4*>(bins.otq);
+    for (;;) {
+      int o = 0;
+      if (lane == 0) o = atomicAdd(&bins.ctrl[2], 1);
+      o = __shfl_sync(0xffffffffu, o, 0);
+      if (o >= novf) break;
+      const V4 v = otq[o];
+      const int b0 = bins.ob[3 * o], b1 = bins.ob[3 * o + 1], b2 = bins.ob[3 * o + 2];
+      for (int e = lane; e < 3 * P; e += 32) {
+        const int d = e / P, pp = e - d * P;
+        const R tau = tq_comp<R>(v, d) - R(0.5);
+        R w = wtab[D * P + pp];
+        for (int k = D - 1; k >= 0; --k) w = fma(w, tau, wtab[k * P + pp]);
+        Ww[e] = w;
+      }
+      __syncwarp();
+      for (int l = lane; l < P * P * P; l += 32) {
+        const int i = l / (P * P), r = l - i * (P * P), j = r / P, k = r - j * P;
+        const R val = v.w * Ww[i] * Ww[P + j] * Ww[2 * P + k];
+        const int gi = wrap_index(b0 + i, g.M[0]);
+        const int gj = wrap_index(b1 + j, g.M[1]);
+        const int gk = wrap_index(b2 + k, g.M[2]);
+        atomicAdd(&grid[((int64_t)gi * g.M[1] + gj) * g.M[2] + gk], val);
+      }
+      __syncwarp();
+    }
+  }
+  // the overflow count passes to the gather; the spread's counters are zero again
+  last_cta_resets(bins.ctrl, 3, 1, 3, 0, 4);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1060,6 +1021,91 @@ __device__ __forceinline__ typename Cplx<R>::T* xfft_lines(typename Cplx<R>::T* 
   return a;
 }
 
+// ---------------------------------------------------------------------------------------
+// Line transforms of the plane kernels: the same Stockham passes as xpass, over nc (odd)
+// columns with element (j, c) at j * nc + c; c = b mod nc by magic division.
+template <typename R, int RAD, int SIGN>
+__device__ __forceinline__ void lpass(const typename Cplx<R>::T* in, typename Cplx<R>::T* out,
+                                      const typename Cplx<R>::T* tw, const LineFFT& f, int Ns,
+                                      unsigned int ns_magic) {
+  using C = typename Cplx<R>::T;
+  const int N = f.n, nc = f.nc;
+  const int L = N / RAD;
+  const int stride = L / Ns;
+  const int nb = L * nc;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    const int j = fast_div(b, f.nc_magic);
+    const int c = b - j * nc;
+    const int k = Ns == 1 ? 0 : j - fast_div(j, ns_magic) * Ns;
+    C v[RAD];
+#pragma unroll
+    for (int t = 0; t < RAD; ++t) v[t] = in[(j + t * L) * nc + c];
+    if (k > 0) {
+#pragma unroll
+      for (int t = 1; t < RAD; ++t) v[t] = ctw<SIGN>(v[t], tw[t * k * stride]);
+    }
+    dft_reg<R, RAD, SIGN>(v, tw, N);
+    const int d = (j - k) * RAD + k;
+#pragma unroll
+    for (int t = 0; t < RAD; ++t) out[(d + t * Ns) * nc + c] = v[t];
+  }
+}
+
+template <typename R, int SIGN>
+__device__ __forceinline__ void lpass_any(const typename Cplx<R>::T* in,
+                                          typename Cplx<R>::T* out,
+                                          const typename Cplx<R>::T* tw, const LineFFT& f,
+                                          int Ns, unsigned int ns_magic, int p) {
+  using C = typename Cplx<R>::T;
+  const int N = f.n, nc = f.nc;
+  const int L = N / p;
+  const int stride = L / Ns;
+  const int n = N * nc;
+  for (int o = threadIdx.x; o < n; o += blockDim.x) {
+    const int r = fast_div(o, f.nc_magic);
+    const int c = o - r * nc;
+    const int u = r / L, j = r - u * L;
+    const int k = Ns == 1 ? 0 : j - fast_div(j, ns_magic) * Ns;
+    C a = cmk<R>(R(0), R(0));
+    for (int t = 0; t < p; ++t) {
+      int idx = t * k * stride + ((u * t) % p) * L;
+      if (idx >= N) idx -= N;
+      const C z = ctw<SIGN>(in[(j + t * L) * nc + c], tw[idx]);
+      a.x += z.x;
+      a.y += z.y;
+    }
+    out[((j - k) * p + k + u * Ns) * nc + c] = a;
+  }
+}
+
+// All passes of one line transform; returns the buffer that holds the result.
+template <typename R, int SIGN>
+__device__ __forceinline__ typename Cplx<R>::T* lfft_lines(typename Cplx<R>::T* a,
+                                                           typename Cplx<R>::T* b,
+                                                           const typename Cplx<R>::T* tw,
+                                                           const LineFFT& f) {
+  int Ns = 1;
+  for (int s = 0; s < f.npass; ++s) {
+    const int rad = f.radix[s];
+    const unsigned int mg = f.ns_magic[s];
+    switch (rad) {
+      case 8: lpass<R, 8, SIGN>(a, b, tw, f, Ns, mg); break;
+      case 4: lpass<R, 4, SIGN>(a, b, tw, f, Ns, mg); break;
+      case 2: lpass<R, 2, SIGN>(a, b, tw, f, Ns, mg); break;
+      case 3: lpass<R, 3, SIGN>(a, b, tw, f, Ns, mg); break;
+      case 5: lpass<R, 5, SIGN>(a, b, tw, f, Ns, mg); break;
+      case 7: lpass<R, 7, SIGN>(a, b, tw, f, Ns, mg); break;
+      default: lpass_any<R, SIGN>(a, b, tw, f, Ns, mg, rad); break;
+    }
+    Ns *= rad;
+    __syncthreads();
+    typename Cplx<R>::T* t = a;
+    a = b;
+    b = t;
+  }
+  return a;
+}
+
 // Sums of 8 values over the 32 lanes of a warp in a fixed order.  Each of the first three
 // levels halves the values a lane keeps and sends the other half to its partner, so lane l
 // ends with the warp total of value c(l) = 4 ((l >> 4) & 1) + 2 ((l >> 3) & 1) + ((l >> 2)
@@ -1206,7 +1252,6 @@ __global__ void __launch_bounds__(kXThreads, std::is_same<R, float>::value ? 2 :
   // per column: k of (0, m1, m2), 1 / (w1^2 w2^2) times the Hermitian weight, m1, m2, flags
   __shared__ R ck[3][32], cw[32], cg[32];
   __shared__ int cm1[32], cm2[32], cflag[32];
-  static_assert(INV || !FWD, "the forward transform is only fused with the inverse one");
   const int f0 = order[blockIdx.x] * NC;
   const int total = M0 << lognc;
   const int64_t rowst = x.ncol;  // elements between rows i0 and i0 + 1
@@ -1216,8 +1261,9 @@ __global__ void __launch_bounds__(kXThreads, std::is_same<R, float>::value ? 2 :
     const int c = threadIdx.x, f = f0 + c;
     int flag = 0;
     if (f < x.ncol) {
-      const int i1 = f / s.H2, i2 = f - (f / s.H2) * s.H2;
-      const int m1 = (2 * i1 <= s.M[1]) ? i1 : i1 - s.M[1];
+      const int b1 = f / x.nb2, i2 = f - b1 * x.nb2;
+      const int m1 = (2 * b1 <= x.nb1) ? b1 : b1 - x.nb1;
+      const int i1 = m1 < 0 ? m1 + s.M[1] : m1;
       const int m2 = i2;
       flag = colact[f] ? 3 : 1;  // a column of the spectrum; 3: its line may meet the sphere
       const R f1 = R(m1), f2 = R(m2);
@@ -1357,6 +1403,185 @@ __global__ void __launch_bounds__(kXThreads, std::is_same<R, float>::value ? 2 :
 }
 
 // ---------------------------------------------------------------------------------------
+// Plane transforms over (i1, i2), one CTA per plane i0, pruned to the box of the sphere
+// |m1| <= mmax1, 0 <= m2 <= mmax2 (every mode with |k| <= c / r_c lies in it).  Shared
+// memory (complex elements): the M1 and M2 roots, T = M1 x ncb (the lines along i1, one
+// column per m2) and a work area of max(2 M2 nca, M1 ncb).
+template <typename R>
+__host__ __device__ constexpr int plane_threads() {
+  return std::is_same<R, float>::value ? 2 * kPThreads : kPThreads;
+}
+
+__host__ __device__ inline size_t plane_smem_elems(const PlaneGeom& pg) {
+  const size_t t = (size_t)pg.M1 * pg.b.nc;
+  const size_t w1 = 2 * (size_t)pg.M2 * pg.a.nc;
+  return (size_t)pg.M1 + pg.M2 + t + (w1 > t ? w1 : t);
+}
+
+// Forward: the real lines along i2 are taken two at a time as one complex line z = x_a +
+// i x_b; from its transform Z, X_a(m) = (Z(m) + conj Z(-m)) / 2 and X_b(m) = (Z(m) - conj
+// Z(-m)) / (2 i) for m2 = m < nb2.  Then the transform along i1 of those nb2 columns, of
+// which the nb1 rows of the box are written to box[i0][b1][m2].
+template <typename R>
+__global__ void __launch_bounds__(plane_threads<R>()) k_fplane(const R* __restrict__ grid,
+                                                      typename Cplx<R>::T* __restrict__ box,
+                                                      PlaneGeom pg,
+                                                      const typename Cplx<R>::T* __restrict__ twg) {
+  pdl_wait();
+  using C = typename Cplx<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int M1 = pg.M1, M2 = pg.M2, nca = pg.a.nc, ncb = pg.b.nc, nb2 = pg.nb2;
+  C* twB = reinterpret_cast<C*>(smem_raw);
+  C* twA = twB + M1;
+  C* T = twA + M2;
+  C* U = T + (size_t)M1 * ncb;
+  C* U2 = U + (size_t)M2 * nca;
+  for (int e = threadIdx.x; e < M1 + M2; e += blockDim.x) twB[e] = twg[e];
+  const R* plane = grid + (size_t)blockIdx.x * M1 * M2;
+  for (int p0 = 0; p0 < pg.npairs; p0 += pg.pairs_b) {
+    const int np = min(pg.pairs_b, pg.npairs - p0);
+    __syncthreads();  // the work area is free, the roots are in place
+    // kU elements per thread and round, all loads issued before the first store
+    constexpr int kU = 8;
+    for (int e0 = threadIdx.x; e0 < M2 * nca; e0 += kU * blockDim.x) {
+      R re[kU], im[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int e = e0 + u * blockDim.x;
+        const int c = fast_div(e, pg.m2_magic);
+        const int j = e - c * M2;
+        const int r = 2 * (p0 + c);
+        re[u] = (e < M2 * nca && c < np) ? plane[(size_t)r * M2 + j] : R(0);
+        im[u] = (e < M2 * nca && c < np && r + 1 < M1) ? plane[(size_t)(r + 1) * M2 + j] : R(0);
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e < M2 * nca) {
+          const int c = fast_div(e, pg.m2_magic);
+          const int j = e - c * M2;
+          U[j * nca + c] = cmk<R>(re[u], im[u]);
+        }
+      }
+    }
+    __syncthreads();
+    const C* Z = lfft_lines<R, -1>(U, U2, twA, pg.a);
+    for (int e = threadIdx.x; e < nb2 * np; e += blockDim.x) {
+      const int c = fast_div(e, pg.nb2_magic);
+      const int m = e - c * nb2;
+      const C z = Z[m * nca + c];
+      const C w = Z[(m == 0 ? 0 : M2 - m) * nca + c];
+      const int r = 2 * (p0 + c);
+      T[r * ncb + m] = cmk<R>(R(0.5) * (z.x + w.x), R(0.5) * (z.y - w.y));
+      if (r + 1 < M1) T[(r + 1) * ncb + m] = cmk<R>(R(0.5) * (z.y + w.y), R(0.5) * (w.x - z.x));
+    }
+  }
+  __syncthreads();
+  const C* Y = lfft_lines<R, -1>(T, U, twB, pg.b);
+  C* out = box + (size_t)blockIdx.x * pg.nb1 * nb2;
+  for (int e = threadIdx.x; e < pg.nb1 * nb2; e += blockDim.x) {
+    const int b1 = fast_div(e, pg.nb2_magic);
+    const int m = e - b1 * nb2;
+    const int m1 = (2 * b1 <= pg.nb1) ? b1 : b1 - pg.nb1;
+    out[e] = Y[(m1 < 0 ? m1 + M1 : m1) * ncb + m];
+  }
+}
+
+// Inverse (unnormalised, as the forward): the box columns (zero where colact = 0 and
+// outside the box) take the inverse transform along i1, then pairs of lines along i2 are
+// rebuilt as Z(m) = X_a(m) + i X_b(m) over the Hermitian extension X(-m) = conj X(m) (the
+// m = 0 term real) and transformed, x_a = Re, x_b = Im.  Inverse transforms are forward
+// ones between two conjugations.
+template <typename R>
+__global__ void __launch_bounds__(plane_threads<R>()) k_iplane(const typename Cplx<R>::T* __restrict__ box,
+                                                      const unsigned char* __restrict__ colact,
+                                                      R* __restrict__ grid, PlaneGeom pg,
+                                                      const typename Cplx<R>::T* __restrict__ twg) {
+  pdl_wait();
+  using C = typename Cplx<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int M1 = pg.M1, M2 = pg.M2, nca = pg.a.nc, ncb = pg.b.nc, nb2 = pg.nb2;
+  C* twB = reinterpret_cast<C*>(smem_raw);
+  C* twA = twB + M1;
+  C* T = twA + M2;
+  C* U = T + (size_t)M1 * ncb;
+  C* U2 = U + (size_t)M2 * nca;
+  for (int e = threadIdx.x; e < M1 + M2; e += blockDim.x) twB[e] = twg[e];
+  for (int e = threadIdx.x; e < M1 * ncb; e += blockDim.x) T[e] = cmk<R>(R(0), R(0));
+  __syncthreads();
+  const C* in = box + (size_t)blockIdx.x * pg.nb1 * nb2;
+  {
+    // the box columns, kU per thread and round with every load issued first (the
+    // inactive columns hold stale values and are replaced by zero)
+    constexpr int kU = 4;
+    const int nbox = pg.nb1 * nb2;
+    for (int e0 = threadIdx.x; e0 < nbox; e0 += kU * blockDim.x) {
+      C v[kU];
+      unsigned char a[kU];
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int e = e0 + u * blockDim.x;
+        a[u] = e < nbox ? colact[e] : 0;
+        v[u] = e < nbox ? in[e] : cmk<R>(R(0), R(0));
+      }
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+        const int e = e0 + u * blockDim.x;
+        if (e < nbox) {
+          const int b1 = fast_div(e, pg.nb2_magic);
+          const int m = e - b1 * nb2;
+          const int m1 = (2 * b1 <= pg.nb1) ? b1 : b1 - pg.nb1;
+          T[(m1 < 0 ? m1 + M1 : m1) * ncb + m] = a[u] ? cmk<R>(v[u].x, -v[u].y) : cmk<R>(R(0), R(0));
+        }
+      }
+    }
+  }
+  __syncthreads();
+  C* Yc = lfft_lines<R, -1>(T, U, twB, pg.b);  // conj of the inverse along i1
+  if (Yc != T) {
+    for (int e = threadIdx.x; e < M1 * ncb; e += blockDim.x) T[e] = Yc[e];
+  }
+  R* plane = grid + (size_t)blockIdx.x * M1 * M2;
+  for (int p0 = 0; p0 < pg.npairs; p0 += pg.pairs_b) {
+    const int np = min(pg.pairs_b, pg.npairs - p0);
+    __syncthreads();  // T complete; the work area is free
+    for (int e = threadIdx.x; e < M2 * nca; e += blockDim.x) {
+      const int c = fast_div(e, pg.m2_magic);
+      const int j = e - c * M2;
+      C z = cmk<R>(R(0), R(0));
+      if (c < np) {
+        const int r = 2 * (p0 + c);
+        const bool two = r + 1 < M1;
+        if (j < nb2) {
+          // a = X_a(j), b = X_b(j) (T holds their conjugates)
+          const C ta = T[r * ncb + j];
+          const C tb = two ? T[(r + 1) * ncb + j] : cmk<R>(R(0), R(0));
+          z = j == 0 ? cmk<R>(ta.x, tb.x) : cmk<R>(ta.x + tb.y, tb.x - ta.y);
+        } else if (j > M2 - nb2) {
+          // conj X_a(M2 - j) + i conj X_b(M2 - j)
+          const int m = M2 - j;
+          const C ta = T[r * ncb + m];
+          const C tb = two ? T[(r + 1) * ncb + m] : cmk<R>(R(0), R(0));
+          z = cmk<R>(ta.x - tb.y, ta.y + tb.x);
+        }
+      }
+      z.y = -z.y;
+      U[j * nca + c] = z;
+    }
+    __syncthreads();
+    const C* Zc = lfft_lines<R, -1>(U, U2, twA, pg.a);  // conj of the inverse along i2
+    for (int e = threadIdx.x; e < M2 * np; e += blockDim.x) {
+      const int c = fast_div(e, pg.m2_magic);
+      const int j = e - c * M2;
+      const C v = Zc[j * nca + c];
+      const int r = 2 * (p0 + c);
+      plane[(size_t)r * M2 + j] = v.x;
+      if (r + 1 < M1) plane[(size_t)(r + 1) * M2 + j] = -v.y;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // Persistent CTAs take tiles from a global work counter (work[1], zeroed every step).
 // The tile's padded block of the potential grid is staged in shared memory for all warps;
 // per chunk of its atoms: (A) window values and derivatives as in k_spread; (B) groups of
@@ -1365,12 +1590,13 @@ __global__ void __launch_bounds__(kXThreads, std::is_same<R, float>::value ? 2 :
 // sums the rows, and the group's first lane turns the sums into the atom's force.
 template <typename R, typename IO, int P>
 __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 4 : 2) k_gather(
-    const typename Vec4<R>::T* __restrict__ sorted_tq, const int* __restrict__ sorted_lb,
-    const int* __restrict__ sorted_idx, const int* __restrict__ toff, GatherGeom gg,
-    int ntiles, int* __restrict__ work, const R* __restrict__ wtab,
+    Bins bins, GatherGeom gg, int ntiles, const R* __restrict__ wtab,
     const R* __restrict__ grid, IO* __restrict__ forces) {
   pdl_wait();
   const TileGeom& g = gg.g;
+  const typename Vec4<R>::T* __restrict__ sorted_tq = static_cast<const typename Vec4<R>::T*>(bins.tq);
+  const int* __restrict__ sorted_lb = bins.lb;
+  const int* __restrict__ sorted_idx = bins.idx;
   using TC = TileC<P>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* phi = reinterpret_cast<R*>(smem_raw);
@@ -1383,7 +1609,7 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 4 : 
   V4* TQ = reinterpret_cast<V4*>(smem_raw + L.t);  // per atom (t0, t1, t2, q)
   int* B = reinterpret_cast<int*>(smem_raw + L.b);
   int* X = reinterpret_cast<int*>(smem_raw + L.x);  // per atom its index in the input
-  __shared__ int s_tile;
+  __shared__ int s_tile, s_cnt;
 
   constexpr int D = WinDeg<R>::value;
   constexpr int NP = kThreads / P;
@@ -1395,11 +1621,15 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 4 : 
 
   for (;;) {
     __syncthreads();  // the previous tile is done and s_tile consumed
-    if (threadIdx.x == 0) s_tile = atomicAdd(&work[1], 1);
+    if (threadIdx.x == 0) {
+      const int t = atomicAdd(&bins.ctrl[5], 1);
+      s_tile = t;
+      if (t < ntiles) s_cnt = bins.tcount[t];
+    }
     __syncthreads();
     const int tile = s_tile;
     if (tile >= ntiles) break;
-    const int start = toff[tile], end = toff[tile + 1];
+    const int start = tile * bins.cap, end = start + s_cnt;
     if (start == end) continue;
 
     const int t2 = tile % g.nt[2];
@@ -1572,6 +1802,60 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 4 : 
       __syncthreads();
     }
   }
+
+  // atoms past their tile's capacity: one warp per atom, straight from the global grid
+  {
+    const int novf = bins.ctrl[4];
+    R* Ww = W + warp * (6 * kMaxP);
+    const typename Vec4<R>::T* otq = static_cast<const typename Vec4<R>::T*>(bins.otq);
+    for (;;) {
+      int o = 0;
+      if (lane == 0) o = atomicAdd(&bins.ctrl[6], 1);
+      o = __shfl_sync(0xffffffffu, o, 0);
+      if (o >= novf) break;
+      const typename Vec4<R>::T v = otq[o];
+      const int b0 = bins.ob[3 * o], b1 = bins.ob[3 * o + 1], b2 = bins.ob[3 * o + 2];
+      for (int e = lane; e < 3 * P; e += 32) {
+        const int d = e / P, pp = e - d * P;
+        const R tau = tq_comp<R>(v, d) - R(0.5);
+        R w = wtab[D * P + pp], dw = wtab[(D + 1) * P + D * P + pp];
+        for (int k = D - 1; k >= 0; --k) {
+          w = fma(w, tau, wtab[k * P + pp]);
+          dw = fma(dw, tau, wtab[(D + 1) * P + k * P + pp]);
+        }
+        Ww[e] = w;
+        Ww[3 * P + e] = dw * dscale_of<R>(g, d);
+      }
+      __syncwarp();
+      R ax = R(0), ay = R(0), az = R(0);
+      for (int l = lane; l < P * P * P; l += 32) {
+        const int i = l / (P * P), r = l - i * (P * P), j = r / P, k = r - j * P;
+        const int gi = wrap_index(b0 + i, g.M[0]);
+        const int gj = wrap_index(b1 + j, g.M[1]);
+        const int gk = wrap_index(b2 + k, g.M[2]);
+        const R f = grid[((int64_t)gi * g.M[1] + gj) * g.M[2] + gk];
+        ax = fma(f, Ww[3 * P + i] * Ww[P + j] * Ww[2 * P + k], ax);
+        ay = fma(f, Ww[i] * Ww[4 * P + j] * Ww[2 * P + k], ay);
+        az = fma(f, Ww[i] * Ww[P + j] * Ww[5 * P + k], az);
+      }
+#pragma unroll
+      for (int sft = 16; sft > 0; sft >>= 1) {
+        ax += __shfl_xor_sync(0xffffffffu, ax, sft);
+        ay += __shfl_xor_sync(0xffffffffu, ay, sft);
+        az += __shfl_xor_sync(0xffffffffu, az, sft);
+      }
+      if (lane == 0) {
+        const int idx = bins.oidx[o];
+        const double f = (double)v.w * gg.fscale;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          forces[3 * (int64_t)idx + c] =
+              (IO)(f * (g.hinv[c] * (double)ax + g.hinv[3 + c] * (double)ay + g.hinv[6 + c] * (double)az));
+      }
+      __syncwarp();
+    }
+  }
+  last_cta_resets(bins.ctrl, 7, 5, 3);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -1681,6 +1965,32 @@ __global__ void __launch_bounds__(kThreads) k_near_bin(const IO* __restrict__ po
     v.w = (R)qi;
     xq[i] = v;
   }
+}
+
+// Exclusive scan of one value per thread over the CTA (kThreads threads); *total gets
+// the CTA's sum.  wsum: kThreads / 32 ints of shared memory.
+__device__ __forceinline__ int block_exclusive_scan(int v, int* wsum, int* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int t = lane < kThreads / 32 ? wsum[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += y;
+    }
+    if (lane < kThreads / 32) wsum[lane] = t;
+  }
+  __syncthreads();
+  *total = wsum[kThreads / 32 - 1];
+  return (wid > 0 ? wsum[wid - 1] : 0) + x - v;
 }
 
 __global__ void __launch_bounds__(kThreads) k_near_scan(int* __restrict__ ccount,
@@ -1983,12 +2293,13 @@ __global__ void __launch_bounds__(kThreads) k_fields(const typename Cplx<R>::T* 
 // out[idx * stride + off + f] = coef q_i sum_g field_f(g) w(g / M - s_i).
 template <typename R, typename IO, int P, int NF>
 __global__ void __launch_bounds__(kThreads, 2) k_gather_fields(
-    const typename Vec4<R>::T* __restrict__ sorted_tq, const int* __restrict__ sorted_lb,
-    const int* __restrict__ sorted_idx, const int* __restrict__ toff, TileGeom g, int ntiles,
-    int* __restrict__ work, const R* __restrict__ wtab, const R* __restrict__ fields,
+    Bins bins, TileGeom g, int ntiles, const R* __restrict__ wtab, const R* __restrict__ fields,
     int64_t field_stride, double coef, IO* __restrict__ out, int stride, int off) {
   using TC = TileC<P>;
   using V4 = typename Vec4<R>::T;
+  const V4* __restrict__ sorted_tq = static_cast<const V4*>(bins.tq);
+  const int* __restrict__ sorted_lb = bins.lb;
+  const int* __restrict__ sorted_idx = bins.idx;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   constexpr int E1 = TC::E1, E3p = TC::E3p, vol = TC::VOL, S1 = TC::S1;
   constexpr int PS = round_up4(P), RS = 3 * PS;
@@ -1998,7 +2309,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_gather_fields(
   V4* TQ = reinterpret_cast<V4*>(smem_raw + wo + align32((size_t)kChunk * RS * sizeof(R)));
   int* B = reinterpret_cast<int*>(reinterpret_cast<unsigned char*>(TQ) + align32((size_t)kChunk * sizeof(V4)));
   int* X = B + kChunk;
-  __shared__ int s_tile;
+  __shared__ int s_tile, s_cnt;
   const int E0 = g.E[0], E2 = g.E[2];
   constexpr int D = WinDeg<R>::value;
   constexpr int NP = kThreads / P;
@@ -2009,11 +2320,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_gather_fields(
   const bool evaluator = pair0 < NP;
   for (;;) {
     __syncthreads();
-    if (threadIdx.x == 0) s_tile = atomicAdd(&work[1], 1);
+    if (threadIdx.x == 0) {
+      const int t = atomicAdd(&bins.ctrl[5], 1);
+      s_tile = t;
+      if (t < ntiles) s_cnt = bins.tcount[t];
+    }
     __syncthreads();
     const int tile = s_tile;
     if (tile >= ntiles) break;
-    const int start = toff[tile], end = toff[tile + 1];
+    const int start = tile * bins.cap, end = start + s_cnt;
     if (start == end) continue;
     const int t2 = tile % g.nt[2];
     const int t1 = (tile / g.nt[2]) % g.nt[1];
@@ -2097,6 +2412,54 @@ __global__ void __launch_bounds__(kThreads, 2) k_gather_fields(
       __syncthreads();
     }
   }
+
+  // atoms past their tile's capacity: one warp per atom, straight from the global fields
+  {
+    const int novf = bins.ctrl[4];
+    R* Ww = W + warp * (3 * kMaxP);
+    const V4* otq = static_cast<const V4*>(bins.otq);
+    for (;;) {
+      int o = 0;
+      if (lane == 0) o = atomicAdd(&bins.ctrl[6], 1);
+      o = __shfl_sync(0xffffffffu, o, 0);
+      if (o >= novf) break;
+      const V4 v = otq[o];
+      const int b0 = bins.ob[3 * o], b1 = bins.ob[3 * o + 1], b2 = bins.ob[3 * o + 2];
+      for (int e = lane; e < 3 * P; e += 32) {
+        const int d = e / P, pp = e - d * P;
+        const R tau = tq_comp<R>(v, d) - R(0.5);
+        R w = wtab[D * P + pp];
+        for (int k = D - 1; k >= 0; --k) w = fma(w, tau, wtab[k * P + pp]);
+        Ww[e] = w;
+      }
+      __syncwarp();
+      R acc[NF];
+#pragma unroll
+      for (int f = 0; f < NF; ++f) acc[f] = R(0);
+      for (int l = lane; l < P * P * P; l += 32) {
+        const int i = l / (P * P), r = l - i * (P * P), j = r / P, k = r - j * P;
+        const int gi = wrap_index(b0 + i, g.M[0]);
+        const int gj = wrap_index(b1 + j, g.M[1]);
+        const int gk = wrap_index(b2 + k, g.M[2]);
+        const R w = Ww[i] * Ww[P + j] * Ww[2 * P + k];
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+          acc[f] = fma(fields[f * field_stride + ((int64_t)gi * g.M[1] + gj) * g.M[2] + gk], w, acc[f]);
+      }
+#pragma unroll
+      for (int sft = 16; sft > 0; sft >>= 1)
+#pragma unroll
+        for (int f = 0; f < NF; ++f) acc[f] += __shfl_xor_sync(0xffffffffu, acc[f], sft);
+      if (lane == 0) {
+        const int idx = bins.oidx[o];
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+          out[(int64_t)idx * stride + off + f] = (IO)(coef * (double)v.w * (double)acc[f]);
+      }
+      __syncwarp();
+    }
+  }
+  last_cta_resets(bins.ctrl, 7, 5, 3);
 }
 
 size_t fields_smem(bool fp64, int P, int NF) {
@@ -2159,9 +2522,8 @@ cudaError_t pdl_launch(void (*kern)(KArgs...), int grid, int block, size_t smem,
 }
 
 cudaError_t launch_bin(bool io_double, bool fp64, const void* pos, const void* q, int64_t n,
-                       const TileGeom& g, int* tile_count, int* ptile, int* prank, int* plb,
-                       void* tq, void* bin_part_v, void* zero_buf, size_t zero_bytes,
-                       cudaStream_t st) {
+                       const TileGeom& g, const Bins& b, void* bin_part_v, void* zero_buf,
+                       size_t zero_bytes, cudaStream_t st) {
   if (n <= 0 || zero_bytes % 16 != 0) {
     if (zero_bytes) {
       const cudaError_t e = cudaMemsetAsync(zero_buf, 0, zero_bytes, st);
@@ -2174,48 +2536,29 @@ cudaError_t launch_bin(bool io_double, bool fp64, const void* pos, const void* q
   int4* zero = (int4*)zero_buf;
   const int64_t nzero = (int64_t)(zero_bytes / 16);
   if (io_double && fp64)
-    k_bin<double, double><<<nb, kThreads, 0, st>>>((const double*)pos, (const double*)q, n, g,
-                                                    tile_count, ptile, prank, plb,
-                                                    (double4*)tq, bin_part, zero, nzero);
+    k_bin<double, double><<<nb, kThreads, 0, st>>>((const double*)pos, (const double*)q, n, g, b,
+                                                    bin_part, zero, nzero);
   else if (io_double)
-    k_bin<double, float><<<nb, kThreads, 0, st>>>((const double*)pos, (const double*)q, n, g,
-                                                   tile_count, ptile, prank, plb, (float4*)tq,
+    k_bin<double, float><<<nb, kThreads, 0, st>>>((const double*)pos, (const double*)q, n, g, b,
                                                    bin_part, zero, nzero);
   else if (fp64)
-    k_bin<float, double><<<nb, kThreads, 0, st>>>((const float*)pos, (const float*)q, n, g,
-                                                   tile_count, ptile, prank, plb, (double4*)tq,
+    k_bin<float, double><<<nb, kThreads, 0, st>>>((const float*)pos, (const float*)q, n, g, b,
                                                    bin_part, zero, nzero);
   else
-    k_bin<float, float><<<nb, kThreads, 0, st>>>((const float*)pos, (const float*)q, n, g,
-                                                  tile_count, ptile, prank, plb, (float4*)tq,
+    k_bin<float, float><<<nb, kThreads, 0, st>>>((const float*)pos, (const float*)q, n, g, b,
                                                   bin_part, zero, nzero);
   return cudaGetLastError();
 }
 
-cudaError_t launch_scan(int* count, int* suboff, int* toff, int* bsum, int ntiles, int ksub,
-                        int* work, cudaStream_t st) {
-  const int n = ntiles * ksub;
-  const int nb = (n + kScanBlock - 1) / kScanBlock;
-  cudaError_t e = pdl_launch(k_scan_local, nb, kThreads, 0, st, count, suboff, bsum, n);
-  if (e != cudaSuccess) return e;
-  return pdl_launch(k_scan_fix, nb, kThreads, 0, st, suboff, toff, (const int*)bsum, ntiles, ksub,
-                    work);
-}
-
-int scan_blocks(int ntiles, int ksub) { return (ntiles * ksub + kScanBlock - 1) / kScanBlock; }
-
 int bin_blocks(int64_t n) { return grid_blocks(n); }
 
-cudaError_t launch_scatter(bool fp64, int64_t n, int ksub, const int* ptile, const int* prank,
-                           const int* plb, const void* tq, const int* offset, void* sorted_tq,
-                           int* sorted_lb, int* sorted_idx, cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  const int nb = grid_blocks(n);
-  if (fp64)
-    return pdl_launch(k_scatter<double4>, nb, kThreads, 0, st, n, ksub, ptile, prank, plb,
-                      (const double4*)tq, offset, (double4*)sorted_tq, sorted_lb, sorted_idx);
-  return pdl_launch(k_scatter<float4>, nb, kThreads, 0, st, n, ksub, ptile, prank, plb,
-                    (const float4*)tq, offset, (float4*)sorted_tq, sorted_lb, sorted_idx);
+int bin_capacity(int64_t n, int ntiles) {
+  const double mean = (double)std::max<int64_t>(n, 0) / std::max(ntiles, 1);
+  int64_t cap = (int64_t)std::ceil(2.5 * mean) + 32;
+  cap = (cap + 31) / 32 * 32;
+  // slot indices stay within 32-bit ints; the overflow list takes the rest
+  const int64_t most = ((int64_t)1 << 31) / std::max(ntiles, 1) / 32 * 32;
+  return (int)std::max<int64_t>(32, std::min(cap, most));
 }
 
 size_t spread_smem_bytes(bool fp64, const TileGeom& g) {
@@ -2256,18 +2599,16 @@ cudaError_t configure_kernels(bool fp64, int P, size_t spread_smem, size_t gathe
   });
 }
 
-cudaError_t launch_spread(bool fp64, const TileGeom& g, int ntiles, int nblocks,
-                          const void* sorted_tq, const int* sorted_lb, const int* toff,
-                          int* work, const void* wtab, void* grid, cudaStream_t st) {
+cudaError_t launch_spread(bool fp64, const TileGeom& g, int ntiles, int nblocks, const Bins& b,
+                          const void* wtab, void* grid, cudaStream_t st) {
   const size_t smem = spread_smem_bytes(fp64, g);
   return with_P(g.P, [&](auto pc) -> cudaError_t {
     constexpr int PP = decltype(pc)::value;
     if (fp64)
-      return pdl_launch(k_spread<double, PP>, nblocks, kThreads, smem, st,
-                        (const double4*)sorted_tq, sorted_lb, toff, g, ntiles, work,
+      return pdl_launch(k_spread<double, PP>, nblocks, kThreads, smem, st, b, g, ntiles,
                         (const double*)wtab, (double*)grid);
-    return pdl_launch(k_spread<float, PP>, nblocks, kThreads, smem, st, (const float4*)sorted_tq,
-                      sorted_lb, toff, g, ntiles, work, (const float*)wtab, (float*)grid);
+    return pdl_launch(k_spread<float, PP>, nblocks, kThreads, smem, st, b, g, ntiles,
+                      (const float*)wtab, (float*)grid);
   });
 }
 
@@ -2288,6 +2629,8 @@ cudaError_t set_xfft_smem(size_t smem) {
     return e;
   if ((e = cudaFuncSetAttribute(k_xfft<R, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)))
     return e;
+  if ((e = cudaFuncSetAttribute(k_xfft<R, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)))
+    return e;
   return cudaFuncSetAttribute(k_xfft<R, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
 }
 template <typename R>
@@ -2305,7 +2648,8 @@ cudaError_t run_xfft(bool fwd, bool inv, const XGeom& x, const ScaleGeom& s, con
                                       nactive);
     return cudaGetLastError();
   };
-  if (fwd) return go(k_xfft<R, true, true>);
+  if (fwd && inv) return go(k_xfft<R, true, true>);
+  if (fwd) return go(k_xfft<R, true, false>);
   if (inv) return go(k_xfft<R, false, true>);
   return go(k_xfft<R, false, false>);
 }
@@ -2320,12 +2664,50 @@ cudaError_t launch_xfft(bool fp64, bool fwd, bool inv, const XGeom& x, const Sca
                         const void* radtab,
                         double* partials, const int* order, const unsigned char* colact,
                         int nactive, cudaStream_t st) {
-  if ((fwd && !inv) || nactive < 1) return cudaErrorInvalidValue;
+  if (nactive < 1) return cudaErrorInvalidValue;
   if (fp64)
     return run_xfft<double>(fwd, inv, x, s, spec, out, tw, invw2, radtab, partials, order, colact,
                             nactive, st);
   return run_xfft<float>(fwd, inv, x, s, spec, out, tw, invw2, radtab, partials, order, colact,
                          nactive, st);
+}
+
+size_t plane_smem_bytes(bool fp64, const PlaneGeom& pg) {
+  return plane_smem_elems(pg) * (fp64 ? sizeof(double2) : sizeof(float2));
+}
+
+cudaError_t configure_planes(bool fp64, size_t smem) {
+  const int b = (int)smem;
+  cudaError_t e;
+  if (fp64) {
+    if ((e = cudaFuncSetAttribute(k_fplane<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)))
+      return e;
+    return cudaFuncSetAttribute(k_iplane<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  }
+  if ((e = cudaFuncSetAttribute(k_fplane<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)))
+    return e;
+  return cudaFuncSetAttribute(k_iplane<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+}
+
+cudaError_t launch_fplane(bool fp64, const PlaneGeom& pg, const void* grid, void* box,
+                          const void* tw, cudaStream_t st) {
+  const size_t smem = plane_smem_bytes(fp64, pg);
+  if (fp64)
+    return pdl_launch(k_fplane<double>, pg.M0, plane_threads<double>(), smem, st, (const double*)grid,
+                      (double2*)box, pg, (const double2*)tw);
+  return pdl_launch(k_fplane<float>, pg.M0, plane_threads<float>(), smem, st, (const float*)grid,
+                    (float2*)box, pg, (const float2*)tw);
+}
+
+cudaError_t launch_iplane(bool fp64, const PlaneGeom& pg, const void* box,
+                          const unsigned char* colact, void* grid, const void* tw,
+                          cudaStream_t st) {
+  const size_t smem = plane_smem_bytes(fp64, pg);
+  if (fp64)
+    return pdl_launch(k_iplane<double>, pg.M0, plane_threads<double>(), smem, st, (const double2*)box, colact,
+                      (double*)grid, pg, (const double2*)tw);
+  return pdl_launch(k_iplane<float>, pg.M0, plane_threads<float>(), smem, st, (const float2*)box, colact,
+                    (float*)grid, pg, (const float2*)tw);
 }
 
 cudaError_t launch_xsum(bool fp64, const double* partials, int nblk, const void* bin_part,
@@ -2339,22 +2721,18 @@ cudaError_t launch_xsum(bool fp64, const double* partials, int nblk, const void*
 }
 
 cudaError_t launch_gather(bool fp64, bool io_double, const GatherGeom& gg, int ntiles,
-                          int nblocks, const void* sorted_tq, const int* sorted_lb,
-                          const int* sorted_idx, const int* toff, int* work, const void* wtab,
-                          const void* grid, void* forces, cudaStream_t st) {
+                          int nblocks, const Bins& b, const void* wtab, const void* grid,
+                          void* forces, cudaStream_t st) {
   const size_t smem = gather_smem_bytes(fp64, gg.g);
   return with_P(gg.g.P, [&](auto pc) -> cudaError_t {
     constexpr int PP = decltype(pc)::value;
     if (fp64)
-      return pdl_launch(k_gather<double, double, PP>, nblocks, kThreads, smem, st,
-                        (const double4*)sorted_tq, sorted_lb, sorted_idx, toff, gg, ntiles, work,
+      return pdl_launch(k_gather<double, double, PP>, nblocks, kThreads, smem, st, b, gg, ntiles,
                         (const double*)wtab, (const double*)grid, (double*)forces);
     if (io_double)
-      return pdl_launch(k_gather<float, double, PP>, nblocks, kThreads, smem, st,
-                        (const float4*)sorted_tq, sorted_lb, sorted_idx, toff, gg, ntiles, work,
+      return pdl_launch(k_gather<float, double, PP>, nblocks, kThreads, smem, st, b, gg, ntiles,
                         (const float*)wtab, (const float*)grid, (double*)forces);
-    return pdl_launch(k_gather<float, float, PP>, nblocks, kThreads, smem, st,
-                      (const float4*)sorted_tq, sorted_lb, sorted_idx, toff, gg, ntiles, work,
+    return pdl_launch(k_gather<float, float, PP>, nblocks, kThreads, smem, st, b, gg, ntiles,
                       (const float*)wtab, (const float*)grid, (float*)forces);
   });
 }
@@ -2454,29 +2832,27 @@ cudaError_t launch_fields(bool fp64, int kind, const ScaleGeom& s, const void* s
 }
 
 cudaError_t launch_gather_fields(bool fp64, bool io_double, const TileGeom& g, int ntiles,
-                                 int nblocks, int nf, const void* sorted_tq, const int* sorted_lb,
-                                 const int* sorted_idx, const int* toff, int* work,
-                                 const void* wtab, const void* fields, int64_t field_stride,
-                                 double coef, void* out, int stride, int off, cudaStream_t st) {
+                                 int nblocks, int nf, const Bins& b, const void* wtab,
+                                 const void* fields, int64_t field_stride, double coef,
+                                 void* out, int stride, int off, cudaStream_t st) {
   if (nf != 1 && nf != 3) return cudaErrorInvalidValue;
   const size_t smem = fields_smem(fp64, g.P, nf);
   return with_P(g.P, [&](auto pc) -> cudaError_t {
     constexpr int PP = decltype(pc)::value;
-    auto go = [&](auto kernel, auto tq, auto wt, auto fl, auto o) -> cudaError_t {
+    auto go = [&](auto kernel, int /*unused*/, auto wt, auto fl, auto o) -> cudaError_t {
       cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       if (e != cudaSuccess) return e;
-      kernel<<<nblocks, kThreads, smem, st>>>(tq, sorted_lb, sorted_idx, toff, g, ntiles, work, wt,
-                                              fl, field_stride, coef, o, stride, off);
+      kernel<<<nblocks, kThreads, smem, st>>>(b, g, ntiles, wt, fl, field_stride, coef, o, stride, off);
       return cudaGetLastError();
     };
     if (fp64) {
-      auto tq = (const double4*)sorted_tq;
+      const int tq = 0;
       auto wt = (const double*)wtab;
       auto fl = (const double*)fields;
       return nf == 1 ? go(k_gather_fields<double, double, PP, 1>, tq, wt, fl, (double*)out)
                      : go(k_gather_fields<double, double, PP, 3>, tq, wt, fl, (double*)out);
     }
-    auto tq = (const float4*)sorted_tq;
+    const int tq = 0;
     auto wt = (const float*)wtab;
     auto fl = (const float*)fields;
     if (io_double)

@@ -15,8 +15,6 @@ constexpr int kDegF32 = 13;
 constexpr int kDegF64 = 24;
 constexpr int kRadialPieces = 16;
 constexpr int kThreads = 256;
-constexpr int kSub = 8;    // binning sub-counters per tile (spreads same-address atomics)
-constexpr int kMaxScan = 1 << 24;  // most binning counters supported
 
 // Geometry shared by the binning, spreading and gathering kernels.
 struct TileGeom {
@@ -28,7 +26,6 @@ struct TileGeom {
   int E3p;      // shared-memory row pitch (TileC<P>::E3p)
   int deg;      // degree of the window polynomials
   int vec4;     // 1: rows move as aligned float4 between global and shared memory
-  int ksub;     // binning sub-counters per tile (kSub, or 1 for very many tiles)
   double hinv[9];    // h^{-1}, row-major
   float hinvf[9];    // the same in FP32 (FP32 force transform)
   double dscale[3];  // d u / d s factor of the window argument: 2 M_d / P
@@ -62,17 +59,69 @@ struct ScaleGeom {
 constexpr int kMaxPass = 32;
 struct XGeom {
   int M0;
-  int ncol;
+  int ncol;       // columns of the spectrum layout: nb1 * nb2
+  int nb1, nb2;   // layout [M0][nb1][nb2]: the full half spectrum (M1, H2) or the box of
+                  // the sphere (2 mmax1 + 1, mmax2 + 1); column (b1, m2) holds
+                  // m1 = b1 for 2 b1 <= nb1, else b1 - nb1
   int lognc;
   int npass;
   int radix[kMaxPass];
   unsigned int ns_magic[kMaxPass];  // ceil(2^32 / Ns) (unused for Ns = 1), Ns = product of the radices before
 };
 
+// A mixed-radix transform of length n over nc columns held in shared memory as
+// buf[j * nc + c] (j the transform index); nc is odd so that both orientations of access
+// stay clear of bank conflicts.
+struct LineFFT {
+  int n, nc;
+  int npass;
+  int radix[kMaxPass];
+  unsigned int ns_magic[kMaxPass];
+  unsigned int nc_magic;   // ceil(2^32 / nc)
+};
+
+// The plane transforms over (i1, i2) of every plane i0, pruned to the box of the sphere
+// (k_fplane forward: real grid -> box [M0][nb1][nb2]; k_iplane inverse: box -> real grid).
+// Rows are taken in pairs (two real lines as one complex line), npair_b pairs per batch.
+struct PlaneGeom {
+  int M0, M1, M2;
+  int nb1, nb2;     // the box (as XGeom)
+  int mmax1;
+  int npairs;       // ceil(M1 / 2)
+  int pairs_b;      // pairs per batch of the transform along i2
+  LineFFT a;        // along i2: n = M2, nc = pairs_b + (pairs_b even)
+  LineFFT b;        // along i1: n = M1, nc = nb2 + (nb2 even)
+  unsigned int m2_magic;   // ceil(2^32 / M2)
+  unsigned int nb2_magic;  // ceil(2^32 / nb2)
+};
+
 struct GatherGeom {
   TileGeom g;
   double fscale;  // 1 / (V Mtot^2)
   float fscalef;  // the same in FP32 (an FP64 conversion per atom is slow on this part)
+};
+
+// Atoms binned by tile into fixed-capacity slots: the binning kernel writes atom r of
+// tile t (in the order its atomics hand out) to slot t * cap + r; atoms past a tile's
+// capacity go to an overflow list that spread and gather treat one atom at a time with
+// global memory.  Control words (ctrl, kCtrl ints, zero between steps):
+//   [0] overflow atoms of this step (binning), [1] spread tile counter, [2] spread
+//   overflow counter, [3] spread CTAs done, [4] overflow atoms for the gather (set by the
+//   last spread CTA), [5] gather tile counter, [6] gather overflow counter, [7] gather
+//   CTAs done.  The last CTA of spread and of gather resets its own counters, and the
+//   spread moves count[t] to tcount[t] and zeroes count[t].
+constexpr int kCtrl = 16;
+struct Bins {
+  int cap;        // slots per tile
+  int* count;     // [ntiles] binning counters
+  int* tcount;    // [ntiles] atoms in the slots of each tile (min(count, cap))
+  void* tq;       // [ntiles * cap] Vec4 of the compute type: (t0, t1, t2, q)
+  int* lb;        // [ntiles * cap] stencil base relative to the tile, 10 bits per dimension
+  int* idx;       // [ntiles * cap] index of the atom in the input
+  void* otq;      // [n] overflow atoms (t, q)
+  int* ob;        // [3 n] their stencil bases
+  int* oidx;      // [n] their input indices
+  int* ctrl;      // [kCtrl]
 };
 
 // Near (real-space) part of the split: a cell list with nc[d] >= 1 bins per reduced axis
@@ -159,23 +208,17 @@ __host__ __device__ inline SmemLayout smem_layout(bool gather, size_t es, size_t
 // ---- launchers (return cudaGetLastError() of the launch) -----------------------------
 // io_double: pos/q/F are double (else float).  fp64: compute type double (else float).
 
-// Also clears zero_bytes of zero_buf (the spread target grid), by a memset when n <= 0.
+// Wrap, stencil base and slot of every atom (Bins); also clears zero_bytes of zero_buf
+// (the spread target grid), by a memset when n <= 0.  bin_part: per block 3 compensated
+// sums (sum q, sum q^2, skipped atoms) as float pairs.
 cudaError_t launch_bin(bool io_double, bool fp64, const void* pos, const void* q, int64_t n,
-                       const TileGeom& g, int* tile_count, int* ptile, int* prank, int* plb,
-                       void* tq, void* bin_part, void* zero_buf, size_t zero_bytes,
-                       cudaStream_t st);
+                       const TileGeom& g, const Bins& b, void* bin_part, void* zero_buf,
+                       size_t zero_bytes, cudaStream_t st);
 int bin_blocks(int64_t n);
-// count: zero on entry (bin adds into it), zero again on exit; work[0..1] zeroed too.
-// bsum: scan_blocks() ints.
-cudaError_t launch_scan(int* count, int* suboff, int* toff, int* bsum, int ntiles, int ksub,
-                        int* work, cudaStream_t st);
-int scan_blocks(int ntiles, int ksub);
-cudaError_t launch_scatter(bool fp64, int64_t n, int ksub, const int* ptile, const int* prank,
-                           const int* plb, const void* tq, const int* offset, void* sorted_tq,
-                           int* sorted_lb, int* sorted_idx, cudaStream_t st);
-cudaError_t launch_spread(bool fp64, const TileGeom& g, int ntiles, int nblocks,
-                          const void* sorted_tq, const int* sorted_lb, const int* toff,
-                          int* work, const void* wtab, void* grid, cudaStream_t st);
+// slots per tile for n atoms over ntiles tiles (about 2.5x the mean, at least 32)
+int bin_capacity(int64_t n, int ntiles);
+cudaError_t launch_spread(bool fp64, const TileGeom& g, int ntiles, int nblocks, const Bins& b,
+                          const void* wtab, void* grid, cudaStream_t st);
 // The transform along axis 0 fused with the scaling (k_xfft, kXThreads per CTA): the
 // sums of U_F and W_F over the sphere; fwd: the columns first take the forward transform
 // along axis 0 (the planes are transformed), else they hold the full 3D spectrum; inv: the
@@ -198,10 +241,21 @@ cudaError_t launch_xfft(bool fp64, bool fwd, bool inv, const XGeom& x, const Sca
                         int nactive, cudaStream_t st);
 cudaError_t launch_xsum(bool fp64, const double* partials, int nblk, const void* bin_part,
                         int nbin, double* accum, cudaStream_t st);
+// Plane transforms (2 kPThreads per CTA in FP32, kPThreads in FP64; one CTA per plane i0).  tw: M1 roots
+// e^{-2 pi i m / M1} then M2 roots e^{-2 pi i m / M2} of the compute type.  fplane: grid
+// (M0 x M1 x M2 real) -> box (M0 x nb1 x nb2 complex).  iplane: box -> grid, columns with
+// colact = 0 read as zero (k_xfft writes only the active ones).
+constexpr int kPThreads = 512;
+size_t plane_smem_bytes(bool fp64, const PlaneGeom& pg);
+cudaError_t configure_planes(bool fp64, size_t smem);
+cudaError_t launch_fplane(bool fp64, const PlaneGeom& pg, const void* grid, void* box,
+                          const void* tw, cudaStream_t st);
+cudaError_t launch_iplane(bool fp64, const PlaneGeom& pg, const void* box,
+                          const unsigned char* colact, void* grid, const void* tw,
+                          cudaStream_t st);
 cudaError_t launch_gather(bool fp64, bool io_double, const GatherGeom& gg, int ntiles,
-                          int nblocks, const void* sorted_tq, const int* sorted_lb,
-                          const int* sorted_idx, const int* toff, int* work, const void* wtab,
-                          const void* grid, void* forces, cudaStream_t st);
+                          int nblocks, const Bins& b, const void* wtab, const void* grid,
+                          void* forces, cudaStream_t st);
 // Near part.  bin: cell id, rank within the cell and the atom's position relative to its
 // cell corner (with q) in the input order; ccount (ncells ints) zero on entry.  scan:
 // coff[0..ncells] exclusive offsets, ccount zeroed again.  scatter: cell order.  pairs:
@@ -223,13 +277,12 @@ cudaError_t launch_near_pairs(bool fp64, bool io_double, const NearGeom& ng, int
 cudaError_t launch_fields(bool fp64, int kind, const ScaleGeom& s, const void* spec,
                           const void* invw2, const void* radtab, void* out, cudaStream_t st);
 // Window interpolation of nf (1 or 3) real grids at the atoms (grids field_stride apart):
-// out[idx * stride + off + f] = coef q_i sum_g field_f(g) w(g / M - s_i); work[1] zero on
-// entry (it is the gather's tile counter).
+// out[idx * stride + off + f] = coef q_i sum_g field_f(g) w(g / M - s_i); uses the gather's
+// control words.
 cudaError_t launch_gather_fields(bool fp64, bool io_double, const TileGeom& g, int ntiles,
-                                 int nblocks, int nf, const void* sorted_tq, const int* sorted_lb,
-                                 const int* sorted_idx, const int* toff, int* work,
-                                 const void* wtab, const void* fields, int64_t field_stride,
-                                 double coef, void* out, int stride, int off, cudaStream_t st);
+                                 int nblocks, int nf, const Bins& b, const void* wtab,
+                                 const void* fields, int64_t field_stride, double coef,
+                                 void* out, int stride, int off, cudaStream_t st);
 size_t fields_smem_bytes(bool fp64, int P, int NF);
 
 // dU/dh at fixed positions into grad[9] (row-major): -W h^{-T} + sum_i F_i (h^{-1} r_i)^T

@@ -24,9 +24,19 @@ import paper_2601_00161_gb300 as esp  # noqa: E402
 
 TOL = {"fp64": 1e-12, "fp32": 2e-6}
 TRI = np.array([[13.0, 1.3, -0.9], [0.0, 14.0, 1.1], [0.0, 0.0, 12.5]])
+def crowded():
+    # 500 of 700 atoms in a 1.5 A cube: most of them pass their tile's capacity and take
+    # the overflow path of the field gather
+    S = sy.small_random(700, TRI, seed=72, grid=(30, 26, 28), P=7, delta=1e-6, rc=4.0)
+    S.pos[:500] = np.array([3.0, 4.0, 5.0]) + 1.5 * np.random.default_rng(5).random((500, 3))
+    S.q[:] -= S.q.mean()
+    return S
+
+
 CASES = {
     "water648": lambda: sy.water_cubic(),
     "triclinic_P7": lambda: sy.small_random(700, TRI, seed=71, grid=(30, 26, 28), P=7, delta=1e-6, rc=4.0),
+    "crowded_P7": crowded,
 }
 
 

@@ -186,6 +186,35 @@ def test_energy_pressure_only_path(precision, case):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_crowded_tiles_overflow(precision):
+    """Tiles hold about 2.5x the mean number of atoms; atoms past that go to an overflow
+    list that spread and gather handle one atom at a time.  Here 700 of 1000 atoms sit in
+    a 1.5 A cube (inside one or two tiles), so most of them overflow; the energy path and
+    the kept-spectrum force path must still match the oracle."""
+    rng = np.random.default_rng(77)
+    cell = TRI
+    grid = (24, 26, 28)
+    n = 1000
+    pos = rng.random((n, 3)) @ cell.T
+    pos[:700] = np.array([4.0, 5.0, 6.0]) + 1.5 * rng.random((700, 3))
+    q = rng.normal(size=n)
+    q -= q.mean()
+    S = sy.System("crowded", pos, q, cell, grid, 6, 1e-5, fitting_rc(cell, grid, 1e-5))
+    check(S, precision)
+    res, _ = check(S, precision, forces=False)
+    # forces from the kept spectrum (the gather after an energy-only step)
+    c = c_from_tolerance(S.delta)
+    plan, r, _, pos_d, q_d = run_gpu(S, c, precision, forces=False)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    F = torch.empty((n, 3), dtype=dt, device="cuda")
+    esp.esp_forces_from_spectrum(plan.handle, F)
+    torch.cuda.synchronize()
+    ref = esp_grid(pos_d, q_d, S.cell, S.grid, S.P, c, S.rc)
+    assert rel(F.double().cpu().numpy(), ref["forces"]) < TOL[precision]
+    plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_wrapping_of_far_images(precision):
     S = sy.small_random(200, TRI, seed=3, grid=(24, 24, 24), P=6, rc=3.5)
     shift = (np.array([5, -3, 2])[None, :] * 1.0) @ TRI.T  # integer combination of cell vectors
