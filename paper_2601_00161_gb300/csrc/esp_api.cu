@@ -555,6 +555,10 @@ int setup_tile_geom(esp_plan_t p) {
     p->ntiles *= g.nt[d];
   }
   g.vec4 = (!p->fp64 && g.T[2] % 4 == 0 && p->M[2] % 4 == 0 && (g.E[2] + 3) / 4 * 4 <= g.E3p) ? 1 : 0;
+  {
+    const int v = p->fp64 ? 2 : 4;  // elements per 16 bytes
+    g.gvec = (g.T[2] % v == 0 && p->M[2] % v == 0) ? 1 : 0;
+  }
   auto magic = [](unsigned int d) {
     return (unsigned int)((((unsigned long long)1 << 32) + d - 1) / d);
   };

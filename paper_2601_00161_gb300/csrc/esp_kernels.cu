@@ -76,6 +76,21 @@ __device__ __forceinline__ int fast_div(int x, unsigned int m) {
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;"); }
 
+// Asynchronous copies global -> shared (cp.async; no register staging).  16 bytes need
+// 16-byte aligned addresses on both sides.
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem) : "memory");
+}
+template <int BYTES>
+__device__ __forceinline__ void cp_async_small(void* smem, const void* gmem) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(gmem), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
 __device__ __forceinline__ int wrap3(int x, int m) {
   x = x >= m ? x - m : x;
   return x >= m ? x - m : x;
@@ -517,24 +532,30 @@ __device__ __forceinline__ void spread_column2(unsigned addr,
 }
 
 // ---------------------------------------------------------------------------------------
-// Persistent CTAs take tiles from a global work counter (work[0], zeroed every step).
-// Per chunk of a tile's atoms: (A) thread t < (kThreads / P) P evaluates the window
-// polynomial of stencil point t % P (coefficients in registers) for (atom, dimension)
-// pairs t / P, t / P + kThreads / P, ...; (B) each warp takes one atom at a time and adds
-// its P^3 values into the padded block along the lane-fixed columns of Cols<P>, every
-// shared-memory add of the warp hitting 32 distinct banks.  The FP32 block holds 32-bit
-// fixed point with a power-of-two scale per tile: scale <= 2^30 / (sum |q| over the
-// tile's atoms x max |w|^3), so no partial sum can overflow; the rounding of each
-// contribution is at most half a unit of 2^-30 times that bound.  The block then goes to
-// the periodic grid with global atomics, and is cleared as it is read.
+// Five resident CTAs per SM where 48 registers hold the FP32 spread without spills.
 template <typename R, int P>
-__global__ void __launch_bounds__(kThreads) k_spread(Bins bins, TileGeom g, int ntiles,
+constexpr int spread_min_ctas() {
+  return (std::is_same<R, float>::value && (P == 3 || P == 4 || P == 6 || P == 8)) ? 5 : 1;
+}
+
+// Persistent CTAs take tiles from a global counter (ctrl[1]) two ahead of the one they
+// work on; the next tile's atom count and first chunk of atoms arrive by asynchronous
+// copies into the other half of a double buffer while the current tile is worked on.
+// Per chunk of a tile's atoms: (A) thread (p, a) evaluates the window at stencil point p
+// for the three dimensions of atom a (coefficients in registers); (B) each warp takes one
+// atom at a time and adds its P^3 values into the padded block along the lane-fixed
+// columns of Cols<P>, every shared-memory add of the warp hitting 32 distinct banks.  The
+// FP32 block holds 32-bit fixed point with a power-of-two scale per tile: scale <= 2^30 /
+// (sum |q| over the tile's atoms x max |w|^3), so no partial sum can overflow; the
+// rounding of each contribution is at most half a unit of 2^-30 times that bound.  The
+// block then goes to the periodic grid with global atomics, and is cleared as it is read.
+template <typename R, int P>
+__global__ void __launch_bounds__(kThreads, spread_min_ctas<R, P>()) k_spread(Bins bins, TileGeom g, int ntiles,
                                                      const R* __restrict__ wtab,
                                                      R* __restrict__ grid) {
   pdl_wait();
   using V4 = typename Vec4<R>::T;
-  const V4* __restrict__ sorted_tq = static_cast<const V4*>(bins.tq);
-  const int* __restrict__ sorted_lb = bins.lb;
+  const V4* __restrict__ slot_tq = static_cast<const V4*>(bins.tq);
   using TC = TileC<P>;
   using CM = Cols<P>;
   constexpr bool kFixed = std::is_same<R, float>::value;
@@ -544,33 +565,41 @@ __global__ void __launch_bounds__(kThreads) k_spread(Bins bins, TileGeom g, int 
   constexpr int E1 = TC::E1, E3p = TC::E3p, vol = TC::VOL, S1 = TC::S1;
   constexpr int RS = record_stride(false, P);
   const int E0 = g.E[0], E2 = g.E[2];  // this plan's tiles (<= TC)
-  const SmemLayout L = smem_layout(false, sizeof(R), (size_t)vol, P);
-  R* W = reinterpret_cast<R*>(smem_raw + L.w);  // per atom [w0 | q w1 | w2]
-  V4* TQ = reinterpret_cast<V4*>(smem_raw + L.t);  // per atom (t0, t1, t2, q)
-  int* B = reinterpret_cast<int*>(smem_raw + L.b);
-  __shared__ int s_tile, s_cnt;
+  const SpreadLayout L = spread_layout((int)sizeof(R), P);
+  R* W = reinterpret_cast<R*>(smem_raw + L.w);        // per atom [w0 | q w1 | w2]
+  V4* TQ_b = reinterpret_cast<V4*>(smem_raw + L.tq);  // 2 x kChunk (t0, t1, t2, q)
+  int* LB_b = reinterpret_cast<int*>(smem_raw + L.lb);
+  int* CNT_b = reinterpret_cast<int*>(smem_raw + L.cnt);
+  __shared__ int s_first[2], s_ahead[2];
   __shared__ float s_qsum[kThreads / 32];
   const unsigned acc_s = (unsigned)__cvta_generic_to_shared(acc);
-  // thread 0 takes the next tile and moves its atom count out of the binning counter
-  auto next_tile = [&]() {
-    const int t = atomicAdd(&bins.ctrl[1], 1);
-    s_tile = t;
-    if (t < ntiles) {
-      const int c = min(bins.count[t], bins.cap);
-      bins.tcount[t] = c;
-      bins.count[t] = 0;
-      s_cnt = c;
-    }
-  };
 
   constexpr int D = WinDeg<R>::value;
-  constexpr int NP = kThreads / P;  // pairs per sweep
-  const int p_t = threadIdx.x % P, pair0 = threadIdx.x / P;
-  const bool evaluator = pair0 < NP;
+  constexpr int NPA = kThreads / P;  // atoms per sweep of the window evaluation
+  const int p_t = threadIdx.x % P, a_t = threadIdx.x / P;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const LaneCols<P, S1, E3p> lc(lane, (int)sizeof(A));
+  const int ncopy = min(kChunk, bins.cap);
 
-  if (threadIdx.x == 0) next_tile();
+  // copies of tile t into buffer b: its binning count and first chunk of atoms
+  auto issue = [&](int t, int b) {
+    if (t < ntiles) {
+      const int64_t s0 = (int64_t)t * bins.cap;
+      constexpr int QV = (int)sizeof(V4) / 16;
+      for (int e = threadIdx.x; e < ncopy * QV; e += blockDim.x)
+        cp_async16(reinterpret_cast<unsigned char*>(TQ_b + b * kChunk) + 16 * e,
+                   reinterpret_cast<const unsigned char*>(slot_tq + s0) + 16 * e);
+      for (int e = threadIdx.x; e < ncopy / 4; e += blockDim.x)
+        cp_async16(LB_b + b * kChunk + 4 * e, bins.lb + s0 + 4 * e);
+      if (threadIdx.x == 0) cp_async_small<4>(CNT_b + b, bins.count + t);
+    }
+    cp_async_commit();
+  };
+
+  if (threadIdx.x == 0) {
+    s_first[0] = atomicAdd(&bins.ctrl[1], 1);
+    s_first[1] = atomicAdd(&bins.ctrl[1], 1);
+  }
   {
     // clear the block once; every flush clears what it reads
     using Z = typename std::conditional<kFixed, int4, double2>::type;
@@ -580,17 +609,31 @@ __global__ void __launch_bounds__(kThreads) k_spread(Bins bins, TileGeom g, int 
     for (int e = threadIdx.x; e < nz; e += blockDim.x) az[e] = zero;
   }
   __syncthreads();
+  int tile = s_first[0], nxt = s_first[1];
+  issue(tile, 0);
+  issue(nxt, 1);
 
-  for (;;) {
-    const int tile = s_tile;
-    if (tile >= ntiles) break;
-    const int start = tile * bins.cap, end = start + s_cnt;
-    if (start < end) {
+  for (int kt = 0; tile < ntiles; ++kt) {
+    const int bf = kt & 1;
+    if (threadIdx.x == 0) s_ahead[bf] = atomicAdd(&bins.ctrl[1], 1);
+    cp_async_wait<1>();
+    __syncthreads();  // tile's count and first atoms are in buffer bf
+    V4* TQ = TQ_b + bf * kChunk;
+    int* LB = LB_b + bf * kChunk;
+    const int cnt_all = min(CNT_b[bf], bins.cap);
+    if (threadIdx.x == 0) {
+      // the gather reads the tile's atom count from tcount; the counter is zero again
+      bins.tcount[tile] = cnt_all;
+      bins.count[tile] = 0;
+    }
+    const int64_t s0 = (int64_t)tile * bins.cap;
+    if (cnt_all > 0) {
       // fixed-point scale of this tile (FP32): a power of two, so scaling back is exact
       R scale = R(1), inv_scale = R(1);
       if constexpr (kFixed) {
         float sq = 0.f;
-        for (int j = start + threadIdx.x; j < end; j += blockDim.x) sq += fabsf(sorted_tq[j].w);
+        for (int j = threadIdx.x; j < cnt_all; j += blockDim.x)
+          sq += fabsf(j < kChunk ? TQ[j].w : slot_tq[s0 + j].w);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
         if (lane == 0) s_qsum[warp] = sq;
@@ -606,32 +649,42 @@ __global__ void __launch_bounds__(kThreads) k_spread(Bins bins, TileGeom g, int 
         scale = ldexpf(1.f, 30 - ex);
         inv_scale = ldexpf(1.f, ex - 30);
       }
-      for (int c0 = start; c0 < end; c0 += kChunk) {
-        const int cnt = min(kChunk, end - c0);
-        // the chunk's atoms into shared memory with one coalesced load each
-        for (int a = threadIdx.x; a < cnt; a += blockDim.x) {
-          TQ[a] = sorted_tq[c0 + a];
-          B[a] = local_base<S1, E3p>(sorted_lb[c0 + a]);
+      for (int c0 = 0; c0 < cnt_all; c0 += kChunk) {
+        const int cnt = min(kChunk, cnt_all - c0);
+        if (c0 > 0) {
+          // a tile with more atoms than a chunk: the later chunks are loaded here
+          for (int a = threadIdx.x; a < cnt; a += blockDim.x) {
+            TQ[a] = slot_tq[s0 + c0 + a];
+            LB[a] = bins.lb[s0 + c0 + a];
+          }
+          __syncthreads();
         }
-        __syncthreads();
-        if (evaluator) {
+        if (a_t < NPA) {
           // coefficients of stencil point p_t (a small table, L1-resident): loaded here so
           // the registers are free in the other phases
           R cw[D + 1];
 #pragma unroll
           for (int k = 0; k <= D; ++k) cw[k] = __ldg(wtab + k * P + p_t);
-          for (int pr = pair0; pr < 3 * cnt; pr += NP) {
-            const int a = pr / 3, d = pr - 3 * a;
+          for (int a = a_t; a < cnt; a += NPA) {
             const V4 v = TQ[a];
-            R w = horner_reg<R, D>(cw, tq_comp<R>(v, d));
-            if (d == 1) w *= v.w * scale;
-            W[a * RS + d * P + p_t] = w;
+            const R w0 = horner_reg<R, D>(cw, v.x);
+            const R w1 = horner_reg<R, D>(cw, v.y);
+            const R w2 = horner_reg<R, D>(cw, v.z);
+            R* Wa = W + a * RS + p_t;
+            Wa[0] = w0;
+            Wa[P] = w1 * (v.w * scale);
+            Wa[2 * P] = w2;
           }
         }
         __syncthreads();
-        for (int a = warp; a < cnt; a += kThreads / 32) {
+        // warp w takes a contiguous block of the chunk's atoms: the atoms the eight warps
+        // add at the same time lie about cnt / 8 slots apart, not next to each other (the
+        // binning fills slots molecule by molecule, whose stencils overlap)
+        const int per = (cnt + kThreads / 32 - 1) / (kThreads / 32);
+        const int aend = min(cnt, (warp + 1) * per);
+        for (int a = warp * per; a < aend; ++a) {
           const R* Wa = W + a * RS;
-          const unsigned base = acc_s + (unsigned)(B[a] * (int)sizeof(A));
+          const unsigned base = acc_s + (unsigned)(local_base<S1, E3p>(LB[a]) * (int)sizeof(A));
           if constexpr (kFixed) {
             // the record's w0 as packed pairs straight from the 16-byte aligned record
             unsigned long long w0p[(P + 1) / 2];
@@ -720,10 +773,14 @@ __global__ void __launch_bounds__(kThreads) k_spread(Bins bins, TileGeom g, int 
         }
       }
     }
-    __syncthreads();  // the block is read out and cleared; s_tile consumed
-    if (threadIdx.x == 0) next_tile();
-    __syncthreads();
+    __syncthreads();  // the block is read out and cleared; buffer bf is free
+    const int nn = s_ahead[bf];
+    issue(nn, bf);
+    tile = nxt;
+    nxt = nn;
   }
+  cp_async_wait<0>();
+  __syncthreads();
 
   // atoms past their tile's capacity: one warp per atom, window values in the warp's part
   // of the record area, global atomics with periodic wrap
@@ -1582,160 +1639,173 @@ __global__ void __launch_bounds__(plane_threads<R>()) k_iplane(const typename Cp
 }
 
 // ---------------------------------------------------------------------------------------
-// Persistent CTAs take tiles from a global work counter (work[1], zeroed every step).
-// The tile's padded block of the potential grid is staged in shared memory for all warps;
-// per chunk of its atoms: (A) window values and derivatives as in k_spread; (B) groups of
-// P lanes take one atom each (32 / P atoms per warp at a time): lane j of a group
-// contracts stencil row j (its P x P points) in registers, a segmented shuffle reduction
-// sums the rows, and the group's first lane turns the sums into the atom's force.
+// Force gather.  Persistent CTAs take tiles from a global counter (ctrl[5]) two ahead of
+// the one they work on, and copy the next tile's padded block of the potential grid, its
+// atom count and its first chunk of atoms into the other half of a double buffer with
+// asynchronous copies while the current tile is worked on.  Per chunk of a tile's atoms:
+// (A) thread (p, a) evaluates the window and its derivative at stencil point p for the
+// three dimensions of atom a (three packed Horner chains); (B) groups of P lanes take one
+// atom each (32 / P atoms per warp at a time): lane j of a group contracts stencil row j
+// (its P x P points) in registers, a segmented shuffle reduction sums the rows, and the
+// group's first lane turns the sums into the atom's force.
 template <typename R, typename IO, int P>
-__global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 4 : 2) k_gather(
+__global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 3 : 2) k_gather(
     Bins bins, GatherGeom gg, int ntiles, const R* __restrict__ wtab,
     const R* __restrict__ grid, IO* __restrict__ forces) {
   pdl_wait();
   const TileGeom& g = gg.g;
-  const typename Vec4<R>::T* __restrict__ sorted_tq = static_cast<const typename Vec4<R>::T*>(bins.tq);
-  const int* __restrict__ sorted_lb = bins.lb;
-  const int* __restrict__ sorted_idx = bins.idx;
-  using TC = TileC<P>;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* phi = reinterpret_cast<R*>(smem_raw);
-  constexpr int E1 = TC::E1, E3p = TC::E3p, vol = TC::VOL, S1 = TC::S1;
-  constexpr int PS = round_up4(P), RS = record_stride(true, P);
-  const int E0 = g.E[0], E2 = g.E[2];  // this plan's tiles (<= TC)
-  const SmemLayout L = smem_layout(true, sizeof(R), (size_t)vol, P);
-  R* W = reinterpret_cast<R*>(smem_raw + L.w);  // per atom [w0|w1|w2|w0'|w1'|w2'], slots of PS
   using V4 = typename Vec4<R>::T;
-  V4* TQ = reinterpret_cast<V4*>(smem_raw + L.t);  // per atom (t0, t1, t2, q)
-  int* B = reinterpret_cast<int*>(smem_raw + L.b);
-  int* X = reinterpret_cast<int*>(smem_raw + L.x);  // per atom its index in the input
-  __shared__ int s_tile, s_cnt;
+  constexpr int ES = (int)sizeof(R);
+  constexpr int CH = gather_chunk(ES);
+  constexpr int PS = round_up4(P), RS = record_stride(true, P);
+  constexpr int T2c = P <= 8 ? 16 : 8;
+  constexpr int E1 = 8 + P - 1, E3 = gather_pitch(T2c + P - 1, ES), S1 = E1 * E3;
+  constexpr int VOL = (8 + P - 1) * S1;
+  constexpr int VW = 16 / ES;  // elements per 16-byte copy
+  const GatherLayout L = gather_layout(ES, P);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* phi_b = reinterpret_cast<R*>(smem_raw + L.phi);  // 2 x VOL
+  R* W = reinterpret_cast<R*>(smem_raw + L.w);        // per atom [w0|w1|w2|w0'|w1'|w2']
+  V4* TQ_b = reinterpret_cast<V4*>(smem_raw + L.tq);  // 2 x CH
+  int* LB_b = reinterpret_cast<int*>(smem_raw + L.lb);
+  int* X_b = reinterpret_cast<int*>(smem_raw + L.idx);
+  int* CNT_b = reinterpret_cast<int*>(smem_raw + L.cnt);
+  const V4* __restrict__ slot_tq = static_cast<const V4*>(bins.tq);
+  __shared__ int s_first[2], s_ahead[2];
 
   constexpr int D = WinDeg<R>::value;
-  constexpr int NP = kThreads / P;
-  constexpr int G = 32 / P;  // atoms per warp at a time
+  constexpr int NPA = kThreads / P;  // atoms per sweep of the window evaluation
+  constexpr int G = 32 / P;          // atoms per warp at a time
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int slot = lane / P, jj = lane - slot * P;
-  const int p_t = threadIdx.x % P, pair0 = threadIdx.x / P;
-  const bool evaluator = pair0 < NP;
+  const int p_t = threadIdx.x % P, a_t = threadIdx.x / P;
+  const int E0 = g.E[0], E1r = g.E[1], E2 = g.E[2];
+  const int ncopy = min(CH, bins.cap);
 
-  for (;;) {
-    __syncthreads();  // the previous tile is done and s_tile consumed
-    if (threadIdx.x == 0) {
-      const int t = atomicAdd(&bins.ctrl[5], 1);
-      s_tile = t;
-      if (t < ntiles) s_cnt = bins.tcount[t];
-    }
-    __syncthreads();
-    const int tile = s_tile;
-    if (tile >= ntiles) break;
-    const int start = tile * bins.cap, end = start + s_cnt;
-    if (start == end) continue;
-
-    const int t2 = tile % g.nt[2];
-    const int t1 = (tile / g.nt[2]) % g.nt[1];
-    const int t0 = tile / (g.nt[2] * g.nt[1]);
-    const int o0 = t0 * g.T[0], o1 = t1 * g.T[1], o2 = t2 * g.T[2];
-    bool loaded = false;
-    if constexpr (std::is_same<R, float>::value) {
-      if (g.vec4) {
-        // rounds of kU float4 per thread: all loads issued before the first store
-        constexpr int kU = P <= 11 ? 4 : 2;
-        const int E2v = (E2 + 3) >> 2;
-        const int nload = E0 * E1 * E2v;
-        for (int e0 = threadIdx.x; e0 < nload; e0 += kU * blockDim.x) {
-          float4 v[kU];
-          int dst[kU];
-#pragma unroll
-          for (int u = 0; u < kU; ++u) {
-            const int e = e0 + u * blockDim.x;
-            dst[u] = -1;
-            if (e < nload) {
-              const int ab = fast_div(e, g.div_E2v);
-              const int c4 = e - ab * E2v;
-              const int a = ab / E1;
-              const int b = ab - a * E1;
-              if (b < g.E[1]) {
-                const int gi = wrap3(o0 + a, g.M[0]);
-                const int gj = wrap3(o1 + b, g.M[1]);
-                const int gk = wrap3(o2 + 4 * c4, g.M[2]);
-                v[u] = __ldcg(reinterpret_cast<const float4*>(
-                    grid + ((int64_t)gi * g.M[1] + gj) * g.M[2] + gk));
-                dst[u] = a * S1 + b * E3p + 4 * c4;
-              }
-            }
-          }
-#pragma unroll
-          for (int u = 0; u < kU; ++u) {
-            if (dst[u] >= 0) {
-              float* d = phi + dst[u];
-              d[0] = v[u].x;
-              d[1] = v[u].y;
-              d[2] = v[u].z;
-              d[3] = v[u].w;
-            }
-          }
+  // copies of tile t into buffer b: block, count, first chunk of atoms (one group)
+  auto issue = [&](int t, int b) {
+    if (t < ntiles) {
+      const int t2 = t % g.nt[2];
+      const int t1 = (t / g.nt[2]) % g.nt[1];
+      const int t0 = t / (g.nt[2] * g.nt[1]);
+      const int o0 = t0 * g.T[0], o1 = t1 * g.T[1], o2 = t2 * g.T[2];
+      R* phi = phi_b + b * VOL;
+      if (g.gvec) {
+        const int E2v = (E2 + VW - 1) / VW;
+        const int n = E0 * E1r * E2v;
+        for (int e = threadIdx.x; e < n; e += blockDim.x) {
+          const int ab = e / E2v, c4 = e - ab * E2v;
+          const int a = ab / E1r, bb = ab - a * E1r;
+          const int gi = wrap3(o0 + a, g.M[0]);
+          const int gj = wrap3(o1 + bb, g.M[1]);
+          const int gk = wrap3(o2 + VW * c4, g.M[2]);
+          cp_async16(phi + a * S1 + bb * E3 + VW * c4,
+                     grid + ((int64_t)gi * g.M[1] + gj) * g.M[2] + gk);
         }
-        loaded = true;
+      } else {
+        const int n = E0 * E1r * E2;
+        for (int e = threadIdx.x; e < n; e += blockDim.x) {
+          const int ab = e / E2, c = e - ab * E2;
+          const int a = ab / E1r, bb = ab - a * E1r;
+          const int gi = wrap_index(o0 + a, g.M[0]);
+          const int gj = wrap_index(o1 + bb, g.M[1]);
+          const int gk = wrap_index(o2 + c, g.M[2]);
+          cp_async_small<ES>(phi + a * S1 + bb * E3 + c,
+                             grid + ((int64_t)gi * g.M[1] + gj) * g.M[2] + gk);
+        }
       }
-    }
-    if (!loaded) {
-      const int E1r = g.E[1];
-      const int nload = E0 * E1r * E2;
-      for (int e = threadIdx.x; e < nload; e += blockDim.x) {
-        const int c = e % E2;
-        const int ab = e / E2;
-        const int b = ab % E1r;
-        const int a = ab / E1r;
-        const int gi = wrap_index(o0 + a, g.M[0]);
-        const int gj = wrap_index(o1 + b, g.M[1]);
-        const int gk = wrap_index(o2 + c, g.M[2]);
-        phi[a * S1 + b * E3p + c] = grid[((int64_t)gi * g.M[1] + gj) * g.M[2] + gk];
+      // atoms: the slot arrays are padded by a chunk, so whole chunks stay in bounds
+      const int64_t s0 = (int64_t)t * bins.cap;
+      constexpr int QV = (int)sizeof(V4) / 16;  // 16-byte pieces per (t, q) record
+      for (int e = threadIdx.x; e < ncopy * QV; e += blockDim.x)
+        cp_async16(reinterpret_cast<unsigned char*>(TQ_b + b * CH) + 16 * e,
+                   reinterpret_cast<const unsigned char*>(slot_tq + s0) + 16 * e);
+      const int ni = (ncopy + 3) / 4;
+      for (int e = threadIdx.x; e < 2 * ni; e += blockDim.x) {
+        if (e < ni)
+          cp_async16(LB_b + b * CH + 4 * e, bins.lb + s0 + 4 * e);
+        else
+          cp_async16(X_b + b * CH + 4 * (e - ni), bins.idx + s0 + 4 * (e - ni));
       }
+      if (threadIdx.x == 0) cp_async_small<4>(CNT_b + b, bins.tcount + t);
     }
+    cp_async_commit();
+  };
 
-    for (int c0 = start; c0 < end; c0 += kChunk) {
-      const int cnt = min(kChunk, end - c0);
-      // the chunk's atoms into shared memory with one coalesced load each
-      for (int a = threadIdx.x; a < cnt; a += blockDim.x) {
-        TQ[a] = sorted_tq[c0 + a];
-        B[a] = local_base<S1, E3p>(sorted_lb[c0 + a]);
-        X[a] = sorted_idx[c0 + a];
+  if (threadIdx.x == 0) {
+    s_first[0] = atomicAdd(&bins.ctrl[5], 1);
+    s_first[1] = atomicAdd(&bins.ctrl[5], 1);
+  }
+  __syncthreads();
+  int cur = s_first[0], nxt = s_first[1];
+  issue(cur, 0);
+  issue(nxt, 1);
+
+  for (int k = 0; cur < ntiles; ++k) {
+    const int b = k & 1;
+    if (threadIdx.x == 0) s_ahead[b] = atomicAdd(&bins.ctrl[5], 1);
+    cp_async_wait<1>();
+    __syncthreads();  // tile cur's block and atoms are in buffer b
+    const R* phi = phi_b + b * VOL;
+    V4* TQ = TQ_b + b * CH;
+    int* LB = LB_b + b * CH;
+    int* X = X_b + b * CH;
+    const int cnt_all = CNT_b[b];
+    const int64_t s0 = (int64_t)cur * bins.cap;
+    for (int c0 = 0; c0 < cnt_all; c0 += CH) {
+      const int cnt = min(CH, cnt_all - c0);
+      if (c0 > 0) {
+        // a tile with more atoms than a chunk: the later chunks are loaded here
+        __syncthreads();
+        for (int a = threadIdx.x; a < cnt; a += blockDim.x) {
+          TQ[a] = slot_tq[s0 + c0 + a];
+          LB[a] = bins.lb[s0 + c0 + a];
+          X[a] = bins.idx[s0 + c0 + a];
+        }
+        __syncthreads();
       }
-      __syncthreads();  // also covers the staging of phi for the first chunk
-      if (evaluator) {
-        // coefficients of stencil point p_t, window and derivative (L1-resident table)
+      // (A) window values and derivatives: thread (p_t, a) for the three dimensions
+      if (a_t < NPA) {
         if constexpr (std::is_same<R, float>::value) {
-          // window and derivative together as packed pairs
           unsigned long long cwd[D + 1];
 #pragma unroll
-          for (int k = 0; k <= D; ++k)
-            cwd[k] = pack2(__ldg(wtab + k * P + p_t), __ldg(wtab + (D + 1) * P + k * P + p_t));
-          for (int pr = pair0; pr < 3 * cnt; pr += NP) {
-            const int a = pr / 3, d = pr - 3 * a;
-            const float tau = tq_comp<R>(TQ[a], d) - 0.5f;  // the polynomials are in t - 1/2
-            float w, dw;
-            unpack2(horner2<D>(cwd, pack2(tau, tau)), w, dw);
-            W[a * RS + d * PS + p_t] = w;
-            W[a * RS + (3 + d) * PS + p_t] = dw * dscale_of<R>(g, d);
+          for (int kk = 0; kk <= D; ++kk)
+            cwd[kk] = pack2(__ldg(wtab + kk * P + p_t), __ldg(wtab + (D + 1) * P + kk * P + p_t));
+          for (int a = a_t; a < cnt; a += NPA) {
+            const V4 v = TQ[a];
+            float w0, d0, w1, d1, w2, d2;
+            unpack2(horner2<D>(cwd, pack2(v.x - 0.5f, v.x - 0.5f)), w0, d0);
+            unpack2(horner2<D>(cwd, pack2(v.y - 0.5f, v.y - 0.5f)), w1, d1);
+            unpack2(horner2<D>(cwd, pack2(v.z - 0.5f, v.z - 0.5f)), w2, d2);
+            R* Wa = W + a * RS + p_t;
+            Wa[0] = w0;
+            Wa[PS] = w1;
+            Wa[2 * PS] = w2;
+            Wa[3 * PS] = d0 * g.dscalef[0];
+            Wa[4 * PS] = d1 * g.dscalef[1];
+            Wa[5 * PS] = d2 * g.dscalef[2];
           }
         } else {
           R cw[D + 1], cd[D + 1];
 #pragma unroll
-          for (int k = 0; k <= D; ++k) {
-            cw[k] = __ldg(wtab + k * P + p_t);
-            cd[k] = __ldg(wtab + (D + 1) * P + k * P + p_t);
+          for (int kk = 0; kk <= D; ++kk) {
+            cw[kk] = __ldg(wtab + kk * P + p_t);
+            cd[kk] = __ldg(wtab + (D + 1) * P + kk * P + p_t);
           }
-          for (int pr = pair0; pr < 3 * cnt; pr += NP) {
-            const int a = pr / 3, d = pr - 3 * a;
-            const R t = tq_comp<R>(TQ[a], d);
-            W[a * RS + d * PS + p_t] = horner_reg<R, D>(cw, t);
-            W[a * RS + (3 + d) * PS + p_t] = horner_reg<R, D>(cd, t) * dscale_of<R>(g, d);
+          for (int a = a_t; a < cnt; a += NPA) {
+            const V4 v = TQ[a];
+            R* Wa = W + a * RS + p_t;
+            Wa[0] = horner_reg<R, D>(cw, v.x);
+            Wa[PS] = horner_reg<R, D>(cw, v.y);
+            Wa[2 * PS] = horner_reg<R, D>(cw, v.z);
+            Wa[3 * PS] = horner_reg<R, D>(cd, v.x) * g.dscale[0];
+            Wa[4 * PS] = horner_reg<R, D>(cd, v.y) * g.dscale[1];
+            Wa[5 * PS] = horner_reg<R, D>(cd, v.z) * g.dscale[2];
           }
         }
       }
       __syncthreads();
-      // lane j of an atom's group: the P x P points (i, k) of row j, contracted in registers
+      // (B) lane j of an atom's group: the P x P points (i, k) of row j in registers
       //   gx = w1[j] sum_k w2[k] sum_i phi w0'[i],  gy = w1'[j] sum_k w2[k] sum_i phi w0[i],
       //   gz = w1[j] sum_k w2'[k] sum_i phi w0[i]
       for (int a0 = warp * G; a0 < cnt; a0 += (kThreads / 32) * G) {
@@ -1749,7 +1819,8 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 4 : 
           load_record<R, P>(Wa + 2 * PS, w2);
           load_record<R, P>(Wa + 3 * PS, d0);
           load_record<R, P>(Wa + 5 * PS, d2);
-          const R* src = phi + B[a] + jj * E3p;
+          const int lb = LB[a];
+          const R* src = phi + (lb & 1023) * S1 + (((lb >> 10) & 1023) + jj) * E3 + ((lb >> 20) & 1023);
 #pragma unroll
           for (int kk = 0; kk < P; ++kk) {
             R sx = R(0), sw = R(0);
@@ -1770,11 +1841,11 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 4 : 
         }
         // segmented sum: lane j of a group ends with rows j .. P-1 of its atom
 #pragma unroll
-        for (int s = 1; s < P; s <<= 1) {
-          const R tx = __shfl_down_sync(0xffffffffu, ax, s);
-          const R ty = __shfl_down_sync(0xffffffffu, ay, s);
-          const R tz = __shfl_down_sync(0xffffffffu, az, s);
-          if (jj + s < P) {
+        for (int sft = 1; sft < P; sft <<= 1) {
+          const R tx = __shfl_down_sync(0xffffffffu, ax, sft);
+          const R ty = __shfl_down_sync(0xffffffffu, ay, sft);
+          const R tz = __shfl_down_sync(0xffffffffu, az, sft);
+          if (jj + sft < P) {
             ax += tx;
             ay += ty;
             az += tz;
@@ -1799,9 +1870,15 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 4 : 
           }
         }
       }
-      __syncthreads();
     }
+    __syncthreads();  // buffer b is free; s_ahead[b] is visible
+    const int nn = s_ahead[b];
+    issue(nn, b);
+    cur = nxt;
+    nxt = nn;
   }
+  cp_async_wait<0>();
+  __syncthreads();
 
   // atoms past their tile's capacity: one warp per atom, straight from the global grid
   {
@@ -2562,15 +2639,11 @@ int bin_capacity(int64_t n, int ntiles) {
 }
 
 size_t spread_smem_bytes(bool fp64, const TileGeom& g) {
-  int T[3], E3p, vol;
-  tile_shape(g.P, T, &E3p, &vol);
-  return smem_layout(false, fp64 ? 8 : 4, (size_t)vol, g.P).total;
+  return spread_layout(fp64 ? 8 : 4, g.P).total;
 }
 
 size_t gather_smem_bytes(bool fp64, const TileGeom& g) {
-  int T[3], E3p, vol;
-  tile_shape(g.P, T, &E3p, &vol);
-  return smem_layout(true, fp64 ? 8 : 4, (size_t)vol, g.P).total;
+  return gather_layout(fp64 ? 8 : 4, g.P).total;
 }
 
 cudaError_t configure_kernels(bool fp64, int P, size_t spread_smem, size_t gather_smem) {

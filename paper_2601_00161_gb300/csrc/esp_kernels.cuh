@@ -26,6 +26,8 @@ struct TileGeom {
   int E3p;      // shared-memory row pitch (TileC<P>::E3p)
   int deg;      // degree of the window polynomials
   int vec4;     // 1: rows move as aligned float4 between global and shared memory
+  int gvec;     // 1: the gather's block rows move as 16-byte copies (M3, T3 multiples of
+                // 16 bytes of the compute type)
   double hinv[9];    // h^{-1}, row-major
   float hinvf[9];    // the same in FP32 (FP32 force transform)
   double dscale[3];  // d u / d s factor of the window argument: 2 M_d / P
@@ -180,11 +182,67 @@ inline void tile_shape(int P, int T[3], int* E3p, int* vol) {
 // window values of a chunk, then share out its atoms.
 constexpr int kChunk = 128;
 
+// Gather tile block: rows of E3 = a multiple of 16 bytes, so the block moves with 16-byte
+// asynchronous copies; E3 in 16-byte units is odd, so the P rows an atom's lanes read in
+// one instruction fall on distinct banks (for P <= 8 in FP32).  Two blocks (double
+// buffering: the next tile's block arrives while the current one is worked on).
+__host__ __device__ constexpr int gather_pitch(int e2, int es) {
+  const int v = 16 / es;  // elements per 16 bytes
+  int x = (e2 + v - 1) / v * v;
+  if (((x / v) & 1) == 0) x += v;
+  return x;
+}
+// atoms per chunk of the gather (its records and atom buffers)
+__host__ __device__ constexpr int gather_chunk(int es) { return es == 4 ? 128 : 64; }
+struct GatherLayout {
+  int E3, S1, vol;           // row pitch, plane stride, block size (elements)
+  size_t phi, w, tq, lb, idx, cnt, total;  // byte offsets
+};
+__host__ __device__ inline GatherLayout gather_layout(int es, int P) {
+  GatherLayout L{};
+  const int T2 = P <= 8 ? 16 : 8;
+  const int E1 = 8 + P - 1, E0 = 8 + P - 1, E2 = T2 + P - 1;
+  const int ch = gather_chunk(es);
+  L.E3 = gather_pitch(E2, es);
+  L.S1 = E1 * L.E3;
+  L.vol = E0 * L.S1;
+  size_t o = 0;
+  L.phi = o;  o += 2 * (size_t)L.vol * es;                       o = (o + 31) & ~(size_t)31;
+  L.w = o;    o += (size_t)ch * (6 * ((P + 3) & ~3)) * es;        o = (o + 31) & ~(size_t)31;
+  L.tq = o;   o += 2 * (size_t)ch * 4 * es;                      o = (o + 31) & ~(size_t)31;
+  L.lb = o;   o += 2 * (size_t)ch * sizeof(int);                 o = (o + 31) & ~(size_t)31;
+  L.idx = o;  o += 2 * (size_t)ch * sizeof(int);                 o = (o + 31) & ~(size_t)31;
+  L.cnt = o;  o += 2 * sizeof(int);                              o = (o + 31) & ~(size_t)31;
+  L.total = o;
+  return L;
+}
+
 // Per-atom record of window values in shared memory, starting on a 16-byte boundary:
 // spread [w0 | q w1 | w2] (3P values, padded to a multiple of 4); gather
 // [w0 | w1 | w2 | w0' | w1' | w2'], each vector in a slot of round_up4(P) values.
 __host__ __device__ constexpr int record_stride(bool gather, int P) {
   return gather ? 6 * round_up4(P) : round_up4(3 * P);
+}
+
+// Spread: the padded tile block (TileC<P>, accumulators of the compute type's size), the
+// chunk's window records, and two buffers of atoms ((t, q), packed local base) and counts
+// for the tile worked on and the next one.
+struct SpreadLayout {
+  size_t w, tq, lb, cnt, total;
+};
+__host__ __device__ inline SpreadLayout spread_layout(int es, int P) {
+  SpreadLayout L{};
+  int T[3] = {8, 8, P <= 8 ? 16 : 8};
+  const int E3p = tile_pitch(T[2] + P - 1, P);
+  const int vol = round_up4((T[0] + P - 1) * plane_stride(T[1] + P - 1, E3p, P));
+  size_t o = (size_t)vol * es;
+  o = (o + 31) & ~(size_t)31;
+  L.w = o;   o += (size_t)kChunk * record_stride(false, P) * es;  o = (o + 31) & ~(size_t)31;
+  L.tq = o;  o += 2 * (size_t)kChunk * 4 * es;                    o = (o + 31) & ~(size_t)31;
+  L.lb = o;  o += 2 * (size_t)kChunk * sizeof(int);               o = (o + 31) & ~(size_t)31;
+  L.cnt = o; o += 2 * sizeof(int);                                o = (o + 31) & ~(size_t)31;
+  L.total = o;
+  return L;
 }
 
 // Shared-memory layout of spread / gather, byte offsets aligned to 32 bytes: the padded
