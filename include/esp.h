@@ -51,7 +51,12 @@ enum {
   ESP_FP64 = 0,      /* spread / FFT / scale / gather in FP64; pos, q, F are double */
   ESP_FP32 = 1,      /* spread, FFT, gather and per-mode math in FP32; energy and virial
                         sums in FP64; pos, q, F are float unless ESP_IO_F64 is given */
-  ESP_IO_F64 = 16    /* with ESP_FP32: pos, q and F are double */
+  ESP_IO_F64 = 16,   /* with ESP_FP32: pos, q and F are double */
+  ESP_BF16_GRID = 32 /* with ESP_FP32: the potential grid between the inverse transform and
+                        the force gather is stored in BF16 (8-bit mantissa); the gather
+                        computes in FP32.  Energy and virial are unchanged (they come from
+                        the spectrum); forces lose accuracy (Sec. 4.4 variants).  Needs the
+                        library's plane transforms and M3 a multiple of 8 (ESP_ERR_ARG) */
 };
 
 typedef struct esp_plan_s* esp_plan_t;

@@ -31,6 +31,7 @@ ESP_ERR_STATE = -9
 ESP_FP64 = 0
 ESP_FP32 = 1
 ESP_IO_F64 = 16
+ESP_BF16_GRID = 32
 ESP_ACCUM_LEN = 16
 
 # every symbol include/esp.h declares
@@ -267,14 +268,20 @@ class Plan:
     """Owns an esp_plan_t.  Positions / charges / forces are torch CUDA tensors."""
 
     def __init__(self, cell, n, grid, P, c, rc, precision="fp64", io_double=None, stream=None):
+        """precision: "fp64", "fp32", or "fp32_bf16grid" (FP32 with the potential grid
+        stored in BF16 between the inverse transform and the force gather)."""
         import torch
 
+        if precision not in ("fp64", "fp32", "fp32_bf16grid"):
+            raise ValueError("precision must be fp64, fp32 or fp32_bf16grid")
         self.torch = torch
         self.fp64 = precision == "fp64"
         self.io_double = self.fp64 if io_double is None else bool(io_double)
         flags = ESP_FP64 if self.fp64 else ESP_FP32
         if not self.fp64 and self.io_double:
             flags |= ESP_IO_F64
+        if precision == "fp32_bf16grid":
+            flags |= ESP_BF16_GRID
         self.io_dtype = torch.float64 if self.io_double else torch.float32
         self.n = int(n)
         self.grid = tuple(int(x) for x in grid)

@@ -33,6 +33,7 @@ struct esp_plan_s {
   // configuration
   bool fp64 = true;
   bool io_double = true;
+  bool bf16 = false;  // the potential grid is stored in BF16 (ESP_BF16_GRID)
   int64_t n = 0;
   int M[3] = {0, 0, 0};
   int H2 = 0;
@@ -64,6 +65,7 @@ struct esp_plan_s {
   bool box_mode = false;
   void* d_pbox = nullptr;  // planes transformed, the input of k_xfft (kept for forces)
   void* d_ptw = nullptr;   // M1 then M2 roots (compute type)
+  void* d_phi16 = nullptr; // the potential grid in BF16 (ESP_BF16_GRID)
   int xactive = 0;       // groups whose lines may meet the sphere (ordered first)
   int* d_xorder = nullptr;           // group order, active first
   unsigned char* d_xcol = nullptr;   // per column: line may meet the sphere
@@ -418,7 +420,7 @@ void release(esp_plan_t p) {
   if (!p) return;
   if (p->stream) cudaStreamSynchronize(p->stream);
   void* bufs[] = {p->d_wtab,      p->d_radtab,    p->d_invw2,    p->d_grid,      p->d_spec,  p->d_spec2, p->d_xtw, p->d_xorder, p->d_xcol,
-                  p->d_pbox,      p->d_ptw,
+                  p->d_pbox,      p->d_ptw,       p->d_phi16,
                   p->bins.count,  p->bins.tcount, p->bins.tq,    p->bins.lb,     p->bins.idx, p->bins.otq, p->bins.ob, p->bins.oidx,
                   p->bins.ctrl,   p->d_binpart,   p->d_accum,   p->d_partials,
                   p->d_io_pos,    p->d_io_q,     p->d_io_f,
@@ -516,6 +518,9 @@ int setup_planes(esp_plan_t p) {
   }
   (void)ce;
   esp::XGeom& x = p->xg;
+  if (!ok && p->bf16)
+    return fail(p, ESP_ERR_ARG, "ESP_BF16_GRID needs the library's plane transforms, which "
+                                "do not fit this grid");
   p->box_mode = ok;
   if (ok) {
     x.nb1 = pg.nb1;
@@ -556,7 +561,7 @@ int setup_tile_geom(esp_plan_t p) {
   }
   g.vec4 = (!p->fp64 && g.T[2] % 4 == 0 && p->M[2] % 4 == 0 && (g.E[2] + 3) / 4 * 4 <= g.E3p) ? 1 : 0;
   {
-    const int v = p->fp64 ? 2 : 4;  // elements per 16 bytes
+    const int v = p->fp64 ? 2 : (p->bf16 ? 8 : 4);  // elements per 16 bytes
     g.gvec = (g.T[2] % v == 0 && p->M[2] % v == 0) ? 1 : 0;
   }
   auto magic = [](unsigned int d) {
@@ -599,6 +604,9 @@ inline void mark(esp_plan_t p, int i) {
   }
 }
 
+// The potential grid the inverse transform writes and the gather reads.
+void* phi_grid(esp_plan_t p) { return p->bf16 ? p->d_phi16 : p->d_grid; }
+
 // Forward plane transforms: the grid into d_pbox (the box of the sphere, or the full half
 // spectrum through cuFFT).
 int planes_forward(esp_plan_t p) {
@@ -616,7 +624,7 @@ int planes_forward(esp_plan_t p) {
 // Inverse plane transforms: the scaled columns of d_spec2 into the grid (the potential).
 int planes_inverse(esp_plan_t p) {
   if (p->box_mode) {
-    ESP_CUDA(p, esp::launch_iplane(p->fp64, p->pg, p->d_spec2, p->d_xcol, p->d_grid, p->d_ptw,
+    ESP_CUDA(p, esp::launch_iplane(p->fp64, p->bf16, p->pg, p->d_spec2, p->d_xcol, phi_grid(p), p->d_ptw,
                                    p->stream));
     return ESP_OK;
   }
@@ -681,8 +689,8 @@ int run_step(esp_plan_t p, const void* pos, const void* q, void* forces, double*
   if (want_f) {
     if ((rc = planes_inverse(p)) != ESP_OK) return rc;
     mark(p, kGather);
-    ESP_CUDA(p, esp::launch_gather(fp64, p->io_double, p->gg, p->ntiles, p->gather_blocks,
-                                   p->bins, p->d_wtab, p->d_grid, forces, st));
+    ESP_CUDA(p, esp::launch_gather(fp64, p->io_double, p->bf16, p->gg, p->ntiles, p->gather_blocks,
+                                   p->bins, p->d_wtab, phi_grid(p), forces, st));
   }
   ESP_CUDA(p, cudaStreamWaitEvent(st, p->ev_join, 0));
   mark(p, kNStage);
@@ -770,6 +778,8 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
     return fail(nullptr, ESP_ERR_ARG, "alpha (= r_c) must be positive");
   const int base = precision & 0xf;
   if (base != ESP_FP64 && base != ESP_FP32) return fail(nullptr, ESP_ERR_ARG, "bad precision");
+  if ((precision & ESP_BF16_GRID) && (base != ESP_FP32 || grid[2] % 8 != 0))
+    return fail(nullptr, ESP_ERR_ARG, "ESP_BF16_GRID needs ESP_FP32 and M3 a multiple of 8");
   for (int d = 0; d < 3; ++d) {
     if (grid[d] < 2 || grid[d] > 4096) return fail(nullptr, ESP_ERR_ARG, "grid size out of range");
     if (w >= grid[d]) return fail(nullptr, ESP_ERR_SUPPORT, "stencil width must be below every M_d");
@@ -780,6 +790,7 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
   esp_plan_t p = new esp_plan_s();
   p->fp64 = (base == ESP_FP64);
   p->io_double = p->fp64 || (precision & ESP_IO_F64);
+  p->bf16 = !p->fp64 && (precision & ESP_BF16_GRID);
   p->n = n;
   for (int d = 0; d < 3; ++d) p->M[d] = grid[d];
   p->H2 = grid[2] / 2 + 1;
@@ -875,6 +886,7 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
   ALLOC(p->d_spec2, 2 * es * nspec);
   ALLOC(p->d_pbox, 2 * es * nspec);
   ALLOC(p->d_ptw, 2 * es * (size_t)(p->M[1] + p->M[2]));
+  if (p->bf16) ALLOC(p->d_phi16, 2 * Mtot);
   p->bin_blocks = esp::bin_blocks(n);
   {
     esp::Bins& b = p->bins;
@@ -966,13 +978,14 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
       return bail(fail(p, ESP_ERR_CUFFT, "cufftSetStream failed"));
   }
   {
-    const size_t ss = esp::spread_smem_bytes(p->fp64, g), gs = esp::gather_smem_bytes(p->fp64, g);
+    const size_t ss = esp::spread_smem_bytes(p->fp64, g),
+                 gs = esp::gather_smem_bytes(p->fp64, g, p->bf16);
     if (ss > 227 * 1024 || gs > 227 * 1024)
       return bail(fail(p, ESP_ERR_ARG, "tile does not fit in shared memory"));
-    cudaError_t e = esp::configure_kernels(p->fp64, w, ss, gs);
+    cudaError_t e = esp::configure_kernels(p->fp64, w, ss, gs, p->bf16);
     if (e != cudaSuccess) return bail(cuda_fail(p, e, "cudaFuncSetAttribute"));
     int occ_s = 1, occ_g = 1;
-    e = esp::occupancy(p->fp64, p->io_double, w, ss, gs, &occ_s, &occ_g);
+    e = esp::occupancy(p->fp64, p->io_double, w, ss, gs, &occ_s, &occ_g, p->bf16);
     if (e != cudaSuccess) return bail(cuda_fail(p, e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor"));
     p->spread_blocks = std::max(1, std::min(p->ntiles, sms * std::max(occ_s, 1)));
     p->gather_blocks = std::max(1, std::min(p->ntiles, sms * std::max(occ_g, 1)));
@@ -1060,8 +1073,8 @@ int esp_forces_from_spectrum(esp_plan_t p, void* forces) {
                                p->n > 0 ? p->bin_blocks : 0, p->d_accum, st));
   int rc;
   if ((rc = planes_inverse(p)) != ESP_OK) return rc;
-  ESP_CUDA(p, esp::launch_gather(fp64, p->io_double, p->gg, p->ntiles, p->gather_blocks,
-                                 p->bins, p->d_wtab, p->d_grid, forces, st));
+  ESP_CUDA(p, esp::launch_gather(fp64, p->io_double, p->bf16, p->gg, p->ntiles, p->gather_blocks,
+                                 p->bins, p->d_wtab, phi_grid(p), forces, st));
   p->spectrum_kept = false;
   return ESP_OK;
 }

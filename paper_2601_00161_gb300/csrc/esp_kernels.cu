@@ -25,6 +25,7 @@
 // (i, reversed j, k) never share a bank.
 #include "esp_kernels.cuh"
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -57,6 +58,17 @@ template <>
 struct Cplx<double> {
   using T = double2;
 };
+
+// Elements of the potential grid: the compute type, or BF16 (read into FP32).
+__device__ __forceinline__ float grid_val(float x) { return x; }
+__device__ __forceinline__ double grid_val(double x) { return x; }
+__device__ __forceinline__ float grid_val(__nv_bfloat16 x) { return __bfloat162float(x); }
+template <typename G, typename R>
+__device__ __forceinline__ G grid_elem(R x) { return x; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 grid_elem<__nv_bfloat16, float>(float x) {
+  return __float2bfloat16_rn(x);
+}
 
 __device__ __forceinline__ int wrap_index(int i, int m) {
   i %= m;
@@ -1549,10 +1561,10 @@ __global__ void __launch_bounds__(plane_threads<R>()) k_fplane(const R* __restri
 // rebuilt as Z(m) = X_a(m) + i X_b(m) over the Hermitian extension X(-m) = conj X(m) (the
 // m = 0 term real) and transformed, x_a = Re, x_b = Im.  Inverse transforms are forward
 // ones between two conjugations.
-template <typename R>
+template <typename R, typename G>
 __global__ void __launch_bounds__(plane_threads<R>()) k_iplane(const typename Cplx<R>::T* __restrict__ box,
                                                       const unsigned char* __restrict__ colact,
-                                                      R* __restrict__ grid, PlaneGeom pg,
+                                                      G* __restrict__ grid, PlaneGeom pg,
                                                       const typename Cplx<R>::T* __restrict__ twg) {
   pdl_wait();
   using C = typename Cplx<R>::T;
@@ -1598,7 +1610,7 @@ __global__ void __launch_bounds__(plane_threads<R>()) k_iplane(const typename Cp
   if (Yc != T) {
     for (int e = threadIdx.x; e < M1 * ncb; e += blockDim.x) T[e] = Yc[e];
   }
-  R* plane = grid + (size_t)blockIdx.x * M1 * M2;
+  G* plane = grid + (size_t)blockIdx.x * M1 * M2;
   for (int p0 = 0; p0 < pg.npairs; p0 += pg.pairs_b) {
     const int np = min(pg.pairs_b, pg.npairs - p0);
     __syncthreads();  // T complete; the work area is free
@@ -1632,8 +1644,8 @@ __global__ void __launch_bounds__(plane_threads<R>()) k_iplane(const typename Cp
       const int j = e - c * M2;
       const C v = Zc[j * nca + c];
       const int r = 2 * (p0 + c);
-      plane[(size_t)r * M2 + j] = v.x;
-      if (r + 1 < M1) plane[(size_t)(r + 1) * M2 + j] = -v.y;
+      plane[(size_t)r * M2 + j] = grid_elem<G>(v.x);
+      if (r + 1 < M1) plane[(size_t)(r + 1) * M2 + j] = grid_elem<G>(-v.y);
     }
   }
 }
@@ -1648,23 +1660,24 @@ __global__ void __launch_bounds__(plane_threads<R>()) k_iplane(const typename Cp
 // atom each (32 / P atoms per warp at a time): lane j of a group contracts stencil row j
 // (its P x P points) in registers, a segmented shuffle reduction sums the rows, and the
 // group's first lane turns the sums into the atom's force.
-template <typename R, typename IO, int P>
+template <typename R, typename IO, int P, typename G>
 __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 3 : 2) k_gather(
     Bins bins, GatherGeom gg, int ntiles, const R* __restrict__ wtab,
-    const R* __restrict__ grid, IO* __restrict__ forces) {
+    const G* __restrict__ grid, IO* __restrict__ forces) {
   pdl_wait();
   const TileGeom& g = gg.g;
   using V4 = typename Vec4<R>::T;
   constexpr int ES = (int)sizeof(R);
+  constexpr int GS = (int)sizeof(G);  // potential grid element: the compute type or BF16
   constexpr int CH = gather_chunk(ES);
   constexpr int PS = round_up4(P), RS = record_stride(true, P);
   constexpr int T2c = P <= 8 ? 16 : 8;
-  constexpr int E1 = 8 + P - 1, E3 = gather_pitch(T2c + P - 1, ES), S1 = E1 * E3;
+  constexpr int E1 = 8 + P - 1, E3 = gather_pitch(T2c + P - 1, GS), S1 = E1 * E3;
   constexpr int VOL = (8 + P - 1) * S1;
-  constexpr int VW = 16 / ES;  // elements per 16-byte copy
-  const GatherLayout L = gather_layout(ES, P);
+  constexpr int VW = 16 / GS;  // elements per 16-byte copy
+  const GatherLayout L = gather_layout(ES, P, GS);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* phi_b = reinterpret_cast<R*>(smem_raw + L.phi);  // 2 x VOL
+  G* phi_b = reinterpret_cast<G*>(smem_raw + L.phi);  // 2 x VOL
   R* W = reinterpret_cast<R*>(smem_raw + L.w);        // per atom [w0|w1|w2|w0'|w1'|w2']
   V4* TQ_b = reinterpret_cast<V4*>(smem_raw + L.tq);  // 2 x CH
   int* LB_b = reinterpret_cast<int*>(smem_raw + L.lb);
@@ -1675,7 +1688,7 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 3 : 
 
   constexpr int D = WinDeg<R>::value;
   constexpr int NPA = kThreads / P;  // atoms per sweep of the window evaluation
-  constexpr int G = 32 / P;          // atoms per warp at a time
+  constexpr int GA = 32 / P;         // atoms per warp at a time
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int slot = lane / P, jj = lane - slot * P;
   const int p_t = threadIdx.x % P, a_t = threadIdx.x / P;
@@ -1689,7 +1702,7 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 3 : 
       const int t1 = (t / g.nt[2]) % g.nt[1];
       const int t0 = t / (g.nt[2] * g.nt[1]);
       const int o0 = t0 * g.T[0], o1 = t1 * g.T[1], o2 = t2 * g.T[2];
-      R* phi = phi_b + b * VOL;
+      G* phi = phi_b + b * VOL;
       if (g.gvec) {
         const int E2v = (E2 + VW - 1) / VW;
         const int n = E0 * E1r * E2v;
@@ -1702,7 +1715,8 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 3 : 
           cp_async16(phi + a * S1 + bb * E3 + VW * c4,
                      grid + ((int64_t)gi * g.M[1] + gj) * g.M[2] + gk);
         }
-      } else {
+      } else if constexpr (GS >= 4) {
+        // (a BF16 grid always takes the 16-byte path: the plan requires it)
         const int n = E0 * E1r * E2;
         for (int e = threadIdx.x; e < n; e += blockDim.x) {
           const int ab = e / E2, c = e - ab * E2;
@@ -1710,7 +1724,7 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 3 : 
           const int gi = wrap_index(o0 + a, g.M[0]);
           const int gj = wrap_index(o1 + bb, g.M[1]);
           const int gk = wrap_index(o2 + c, g.M[2]);
-          cp_async_small<ES>(phi + a * S1 + bb * E3 + c,
+          cp_async_small<GS>(phi + a * S1 + bb * E3 + c,
                              grid + ((int64_t)gi * g.M[1] + gj) * g.M[2] + gk);
         }
       }
@@ -1746,7 +1760,7 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 3 : 
     if (threadIdx.x == 0) s_ahead[b] = atomicAdd(&bins.ctrl[5], 1);
     cp_async_wait<1>();
     __syncthreads();  // tile cur's block and atoms are in buffer b
-    const R* phi = phi_b + b * VOL;
+    const G* phi = phi_b + b * VOL;
     V4* TQ = TQ_b + b * CH;
     int* LB = LB_b + b * CH;
     int* X = X_b + b * CH;
@@ -1808,9 +1822,9 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 3 : 
       // (B) lane j of an atom's group: the P x P points (i, k) of row j in registers
       //   gx = w1[j] sum_k w2[k] sum_i phi w0'[i],  gy = w1'[j] sum_k w2[k] sum_i phi w0[i],
       //   gz = w1[j] sum_k w2'[k] sum_i phi w0[i]
-      for (int a0 = warp * G; a0 < cnt; a0 += (kThreads / 32) * G) {
+      for (int a0 = warp * GA; a0 < cnt; a0 += (kThreads / 32) * GA) {
         const int a = a0 + slot;
-        const bool valid = slot < G && a < cnt;
+        const bool valid = slot < GA && a < cnt;
         R ax = R(0), ay = R(0), az = R(0);
         if (valid) {
           const R* Wa = W + a * RS;
@@ -1820,13 +1834,13 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 3 : 
           load_record<R, P>(Wa + 3 * PS, d0);
           load_record<R, P>(Wa + 5 * PS, d2);
           const int lb = LB[a];
-          const R* src = phi + (lb & 1023) * S1 + (((lb >> 10) & 1023) + jj) * E3 + ((lb >> 20) & 1023);
+          const G* src = phi + (lb & 1023) * S1 + (((lb >> 10) & 1023) + jj) * E3 + ((lb >> 20) & 1023);
 #pragma unroll
           for (int kk = 0; kk < P; ++kk) {
             R sx = R(0), sw = R(0);
 #pragma unroll
             for (int i = 0; i < P; ++i) {
-              const R f = src[i * S1 + kk];
+              const R f = grid_val(src[i * S1 + kk]);
               sx = fma(f, d0[i], sx);
               sw = fma(f, w0[i], sw);
             }
@@ -1910,7 +1924,7 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 3 : 
         const int gi = wrap_index(b0 + i, g.M[0]);
         const int gj = wrap_index(b1 + j, g.M[1]);
         const int gk = wrap_index(b2 + k, g.M[2]);
-        const R f = grid[((int64_t)gi * g.M[1] + gj) * g.M[2] + gk];
+        const R f = grid_val(grid[((int64_t)gi * g.M[1] + gj) * g.M[2] + gk]);
         ax = fma(f, Ww[3 * P + i] * Ww[P + j] * Ww[2 * P + k], ax);
         ay = fma(f, Ww[i] * Ww[4 * P + j] * Ww[2 * P + k], ay);
         az = fma(f, Ww[i] * Ww[P + j] * Ww[5 * P + k], az);
@@ -2642,33 +2656,38 @@ size_t spread_smem_bytes(bool fp64, const TileGeom& g) {
   return spread_layout(fp64 ? 8 : 4, g.P).total;
 }
 
-size_t gather_smem_bytes(bool fp64, const TileGeom& g) {
-  return gather_layout(fp64 ? 8 : 4, g.P).total;
+size_t gather_smem_bytes(bool fp64, const TileGeom& g, bool bf16) {
+  return gather_layout(fp64 ? 8 : 4, g.P, fp64 ? 8 : (bf16 ? 2 : 4)).total;
 }
 
-cudaError_t configure_kernels(bool fp64, int P, size_t spread_smem, size_t gather_smem) {
+cudaError_t configure_kernels(bool fp64, int P, size_t spread_smem, size_t gather_smem,
+                              bool bf16) {
   return with_P(P, [&](auto pc) -> cudaError_t {
     constexpr int PP = decltype(pc)::value;
+    const int gs = (int)gather_smem;
     cudaError_t e;
     if (fp64) {
       e = cudaFuncSetAttribute(k_spread<double, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)spread_smem);
       if (e != cudaSuccess) return e;
-      e = cudaFuncSetAttribute(k_gather<double, double, PP>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gather_smem);
-      if (e != cudaSuccess) return e;
-    } else {
-      e = cudaFuncSetAttribute(k_spread<float, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)spread_smem);
-      if (e != cudaSuccess) return e;
-      e = cudaFuncSetAttribute(k_gather<float, float, PP>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gather_smem);
-      if (e != cudaSuccess) return e;
-      e = cudaFuncSetAttribute(k_gather<float, double, PP>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)gather_smem);
-      if (e != cudaSuccess) return e;
+      return cudaFuncSetAttribute(k_gather<double, double, PP, double>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, gs);
     }
-    return cudaSuccess;
+    e = cudaFuncSetAttribute(k_spread<float, PP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)spread_smem);
+    if (e != cudaSuccess) return e;
+    if (bf16) {
+      e = cudaFuncSetAttribute(k_gather<float, float, PP, __nv_bfloat16>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, gs);
+      if (e != cudaSuccess) return e;
+      return cudaFuncSetAttribute(k_gather<float, double, PP, __nv_bfloat16>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, gs);
+    }
+    e = cudaFuncSetAttribute(k_gather<float, float, PP, float>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, gs);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_gather<float, double, PP, float>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, gs);
   });
 }
 
@@ -2755,11 +2774,13 @@ cudaError_t configure_planes(bool fp64, size_t smem) {
   if (fp64) {
     if ((e = cudaFuncSetAttribute(k_fplane<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)))
       return e;
-    return cudaFuncSetAttribute(k_iplane<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+    return cudaFuncSetAttribute(k_iplane<double, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
   }
   if ((e = cudaFuncSetAttribute(k_fplane<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)))
     return e;
-  return cudaFuncSetAttribute(k_iplane<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
+  if ((e = cudaFuncSetAttribute(k_iplane<float, __nv_bfloat16>, cudaFuncAttributeMaxDynamicSharedMemorySize, b)))
+    return e;
+  return cudaFuncSetAttribute(k_iplane<float, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, b);
 }
 
 cudaError_t launch_fplane(bool fp64, const PlaneGeom& pg, const void* grid, void* box,
@@ -2772,15 +2793,18 @@ cudaError_t launch_fplane(bool fp64, const PlaneGeom& pg, const void* grid, void
                     (float2*)box, pg, (const float2*)tw);
 }
 
-cudaError_t launch_iplane(bool fp64, const PlaneGeom& pg, const void* box,
+cudaError_t launch_iplane(bool fp64, bool bf16, const PlaneGeom& pg, const void* box,
                           const unsigned char* colact, void* grid, const void* tw,
                           cudaStream_t st) {
   const size_t smem = plane_smem_bytes(fp64, pg);
   if (fp64)
-    return pdl_launch(k_iplane<double>, pg.M0, plane_threads<double>(), smem, st, (const double2*)box, colact,
-                      (double*)grid, pg, (const double2*)tw);
-  return pdl_launch(k_iplane<float>, pg.M0, plane_threads<float>(), smem, st, (const float2*)box, colact,
-                    (float*)grid, pg, (const float2*)tw);
+    return pdl_launch(k_iplane<double, double>, pg.M0, plane_threads<double>(), smem, st,
+                      (const double2*)box, colact, (double*)grid, pg, (const double2*)tw);
+  if (bf16)
+    return pdl_launch(k_iplane<float, __nv_bfloat16>, pg.M0, plane_threads<float>(), smem, st,
+                      (const float2*)box, colact, (__nv_bfloat16*)grid, pg, (const float2*)tw);
+  return pdl_launch(k_iplane<float, float>, pg.M0, plane_threads<float>(), smem, st,
+                    (const float2*)box, colact, (float*)grid, pg, (const float2*)tw);
 }
 
 cudaError_t launch_xsum(bool fp64, const double* partials, int nblk, const void* bin_part,
@@ -2793,19 +2817,27 @@ cudaError_t launch_xsum(bool fp64, const double* partials, int nblk, const void*
   return cudaGetLastError();
 }
 
-cudaError_t launch_gather(bool fp64, bool io_double, const GatherGeom& gg, int ntiles,
+cudaError_t launch_gather(bool fp64, bool io_double, bool bf16, const GatherGeom& gg, int ntiles,
                           int nblocks, const Bins& b, const void* wtab, const void* grid,
                           void* forces, cudaStream_t st) {
-  const size_t smem = gather_smem_bytes(fp64, gg.g);
+  const size_t smem = gather_smem_bytes(fp64, gg.g, bf16);
   return with_P(gg.g.P, [&](auto pc) -> cudaError_t {
     constexpr int PP = decltype(pc)::value;
     if (fp64)
-      return pdl_launch(k_gather<double, double, PP>, nblocks, kThreads, smem, st, b, gg, ntiles,
-                        (const double*)wtab, (const double*)grid, (double*)forces);
+      return pdl_launch(k_gather<double, double, PP, double>, nblocks, kThreads, smem, st, b, gg,
+                        ntiles, (const double*)wtab, (const double*)grid, (double*)forces);
+    if (bf16) {
+      const __nv_bfloat16* gb = (const __nv_bfloat16*)grid;
+      if (io_double)
+        return pdl_launch(k_gather<float, double, PP, __nv_bfloat16>, nblocks, kThreads, smem, st,
+                          b, gg, ntiles, (const float*)wtab, gb, (double*)forces);
+      return pdl_launch(k_gather<float, float, PP, __nv_bfloat16>, nblocks, kThreads, smem, st, b,
+                        gg, ntiles, (const float*)wtab, gb, (float*)forces);
+    }
     if (io_double)
-      return pdl_launch(k_gather<float, double, PP>, nblocks, kThreads, smem, st, b, gg, ntiles,
-                        (const float*)wtab, (const float*)grid, (double*)forces);
-    return pdl_launch(k_gather<float, float, PP>, nblocks, kThreads, smem, st, b, gg, ntiles,
+      return pdl_launch(k_gather<float, double, PP, float>, nblocks, kThreads, smem, st, b, gg,
+                        ntiles, (const float*)wtab, (const float*)grid, (double*)forces);
+    return pdl_launch(k_gather<float, float, PP, float>, nblocks, kThreads, smem, st, b, gg, ntiles,
                       (const float*)wtab, (const float*)grid, (float*)forces);
   });
 }
@@ -2938,24 +2970,23 @@ cudaError_t launch_gather_fields(bool fp64, bool io_double, const TileGeom& g, i
 
 // resident CTAs per SM for the spread and gather kernels of this configuration
 cudaError_t occupancy(bool fp64, bool io_double, int P, size_t spread_smem, size_t gather_smem,
-                      int* spread_ctas, int* gather_ctas) {
+                      int* spread_ctas, int* gather_ctas, bool bf16) {
   return with_P(P, [&](auto pc) -> cudaError_t {
     constexpr int PP = decltype(pc)::value;
     cudaError_t e;
     if (fp64) {
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(spread_ctas, k_spread<double, PP>, kThreads, spread_smem);
       if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(gather_ctas, k_gather<double, double, PP>, kThreads, gather_smem);
-    } else {
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(spread_ctas, k_spread<float, PP>, kThreads, spread_smem);
-      if (e == cudaSuccess) {
-        if (io_double)
-          e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(gather_ctas, k_gather<float, double, PP>, kThreads, gather_smem);
-        else
-          e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(gather_ctas, k_gather<float, float, PP>, kThreads, gather_smem);
-      }
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(gather_ctas, k_gather<double, double, PP, double>, kThreads, gather_smem);
+      return e;
     }
-    return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(spread_ctas, k_spread<float, PP>, kThreads, spread_smem);
+    if (e != cudaSuccess) return e;
+    if (bf16)
+      return io_double ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(gather_ctas, k_gather<float, double, PP, __nv_bfloat16>, kThreads, gather_smem)
+                       : cudaOccupancyMaxActiveBlocksPerMultiprocessor(gather_ctas, k_gather<float, float, PP, __nv_bfloat16>, kThreads, gather_smem);
+    return io_double ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(gather_ctas, k_gather<float, double, PP, float>, kThreads, gather_smem)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(gather_ctas, k_gather<float, float, PP, float>, kThreads, gather_smem);
   });
 }
 

@@ -27,7 +27,7 @@ struct TileGeom {
   int deg;      // degree of the window polynomials
   int vec4;     // 1: rows move as aligned float4 between global and shared memory
   int gvec;     // 1: the gather's block rows move as 16-byte copies (M3, T3 multiples of
-                // 16 bytes of the compute type)
+                // 16 bytes of the potential grid's element type)
   double hinv[9];    // h^{-1}, row-major
   float hinvf[9];    // the same in FP32 (FP32 force transform)
   double dscale[3];  // d u / d s factor of the window argument: 2 M_d / P
@@ -198,16 +198,17 @@ struct GatherLayout {
   int E3, S1, vol;           // row pitch, plane stride, block size (elements)
   size_t phi, w, tq, lb, idx, cnt, total;  // byte offsets
 };
-__host__ __device__ inline GatherLayout gather_layout(int es, int P) {
+// es: compute type size; gs: size of the potential grid's element (4, 8, or 2 for BF16)
+__host__ __device__ inline GatherLayout gather_layout(int es, int P, int gs) {
   GatherLayout L{};
   const int T2 = P <= 8 ? 16 : 8;
   const int E1 = 8 + P - 1, E0 = 8 + P - 1, E2 = T2 + P - 1;
   const int ch = gather_chunk(es);
-  L.E3 = gather_pitch(E2, es);
+  L.E3 = gather_pitch(E2, gs);
   L.S1 = E1 * L.E3;
   L.vol = E0 * L.S1;
   size_t o = 0;
-  L.phi = o;  o += 2 * (size_t)L.vol * es;                       o = (o + 31) & ~(size_t)31;
+  L.phi = o;  o += 2 * (size_t)L.vol * gs;                       o = (o + 31) & ~(size_t)31;
   L.w = o;    o += (size_t)ch * (6 * ((P + 3) & ~3)) * es;        o = (o + 31) & ~(size_t)31;
   L.tq = o;   o += 2 * (size_t)ch * 4 * es;                      o = (o + 31) & ~(size_t)31;
   L.lb = o;   o += 2 * (size_t)ch * sizeof(int);                 o = (o + 31) & ~(size_t)31;
@@ -308,10 +309,11 @@ size_t plane_smem_bytes(bool fp64, const PlaneGeom& pg);
 cudaError_t configure_planes(bool fp64, size_t smem);
 cudaError_t launch_fplane(bool fp64, const PlaneGeom& pg, const void* grid, void* box,
                           const void* tw, cudaStream_t st);
-cudaError_t launch_iplane(bool fp64, const PlaneGeom& pg, const void* box,
+cudaError_t launch_iplane(bool fp64, bool bf16, const PlaneGeom& pg, const void* box,
                           const unsigned char* colact, void* grid, const void* tw,
                           cudaStream_t st);
-cudaError_t launch_gather(bool fp64, bool io_double, const GatherGeom& gg, int ntiles,
+// bf16: the potential grid is BF16 (FP32 compute only)
+cudaError_t launch_gather(bool fp64, bool io_double, bool bf16, const GatherGeom& gg, int ntiles,
                           int nblocks, const Bins& b, const void* wtab, const void* grid,
                           void* forces, cudaStream_t st);
 // Near part.  bin: cell id, rank within the cell and the atom's position relative to its
@@ -348,10 +350,11 @@ cudaError_t launch_cell_grad(bool io_double, const void* pos, const void* forces
                              const CellGradArgs& c, const double* accum, double* grad,
                              cudaStream_t st);
 cudaError_t occupancy(bool fp64, bool io_double, int P, size_t spread_smem, size_t gather_smem,
-                      int* spread_ctas, int* gather_ctas);
+                      int* spread_ctas, int* gather_ctas, bool bf16 = false);
 
 size_t spread_smem_bytes(bool fp64, const TileGeom& g);
-size_t gather_smem_bytes(bool fp64, const TileGeom& g);
-cudaError_t configure_kernels(bool fp64, int P, size_t spread_smem, size_t gather_smem);
+size_t gather_smem_bytes(bool fp64, const TileGeom& g, bool bf16 = false);
+cudaError_t configure_kernels(bool fp64, int P, size_t spread_smem, size_t gather_smem,
+                              bool bf16 = false);
 
 }  // namespace esp
