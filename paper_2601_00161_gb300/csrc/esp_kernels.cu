@@ -2149,8 +2149,25 @@ __device__ __forceinline__ double warp_total(const Sum<float>& s) {
 }
 __device__ __forceinline__ double warp_total(const Sum<double>& s) { return warp_sum(s.v); }
 
-// noff = (2 R0 + 1)(2 R1 + 1)(2 R2 + 1) neighbour offsets; dynamic shared memory holds
-// their displacement vectors h o / nc and wrapped cell ids for the CTA's cell.
+// Candidates (atoms of the neighbour cells) a CTA holds in shared memory at a time.
+template <typename R>
+__host__ __device__ constexpr int near_cand() {
+  return std::is_same<R, float>::value ? 3072 : 1536;
+}
+__host__ __device__ inline size_t near_smem_bytes(bool fp64, int noff) {
+  const size_t v4 = fp64 ? 32 : 16;
+  return (size_t)noff * (v4 + 2 * sizeof(int)) + sizeof(int) + 15 +
+         (size_t)(fp64 ? near_cand<double>() : near_cand<float>()) * v4;
+}
+
+// One CTA per cell of the cell list.  noff = (2 R0 + 1)(2 R1 + 1)(2 R2 + 1) neighbour
+// offsets; shared memory holds their displacement vectors h o / nc, wrapped cell ids and
+// the prefix sums of their atom counts, and the candidates: the neighbour cells' atoms,
+// shifted to the CTA's cell corner, one after the other (in chunks of near_cand when they
+// do not fit).  A warp takes one atom of the cell at a time; its lanes stride over the
+// candidates, the pairs within r_c go through a warp queue (ballot and population count)
+// and are worked 32 at a time.  Each lane sums its pair terms of the atom in plain
+// precision and adds them once per atom to its compensated running sums (FP32 path).
 template <typename R, typename IO>
 __global__ void __launch_bounds__(kThreads) k_near_pairs(NearGeom ng, const int* __restrict__ coff,
                                                          const typename Vec4<R>::T* __restrict__ xq,
@@ -2160,6 +2177,7 @@ __global__ void __launch_bounds__(kThreads) k_near_pairs(NearGeom ng, const int*
                                                          double* __restrict__ out) {
   using V4 = typename Vec4<R>::T;
   constexpr int kQ = 64;  // queue ring per warp
+  constexpr int KC = near_cand<R>();
   __shared__ V4 Q[kThreads / 32][kQ];  // (r_ij, q_j)
   __shared__ double part[kThreads / 32][7];
   extern __shared__ __align__(16) unsigned char near_smem[];
@@ -2171,8 +2189,10 @@ __global__ void __launch_bounds__(kThreads) k_near_pairs(NearGeom ng, const int*
   const int ib = coff[C], ie = coff[C + 1];
   const int s0 = 2 * ng.R[0] + 1, s1 = 2 * ng.R[1] + 1, s2 = 2 * ng.R[2] + 1;
   const int noff = s0 * s1 * s2;
-  V4* OFF = reinterpret_cast<V4*>(near_smem);
-  int* NC = reinterpret_cast<int*>(near_smem + (size_t)noff * sizeof(V4));
+  V4* CB = reinterpret_cast<V4*>(near_smem);
+  V4* OFF = CB + KC;
+  int* NC = reinterpret_cast<int*>(OFF + noff);
+  int* PRE = NC + noff;  // noff + 1 prefix sums of the neighbour cells' atom counts
   for (int t = threadIdx.x; t < noff; t += blockDim.x) {
     const int o0 = t / (s1 * s2) - ng.R[0], o1 = (t / s2) % s1 - ng.R[1], o2 = t % s2 - ng.R[2];
     const int w0 = (((c0 + o0) % ng.nc[0]) + ng.nc[0]) % ng.nc[0];
@@ -2189,82 +2209,119 @@ __global__ void __launch_bounds__(kThreads) k_near_pairs(NearGeom ng, const int*
     OFF[t] = d;
   }
   __syncthreads();
-  const R rc2 = (R)(ng.rc * ng.rc), inv_rc = (R)ng.inv_rc;
-  Sum<R> U, W[6];  // per lane over all of the warp's pairs
-
-  for (int i = ib + warp; i < ie; i += kThreads / 32) {
-    const V4 xi = xq[i];
-    Sum<R> fx, fy, fz;  // per lane, this atom
-    // the pair terms of queue entries [h, h + m), lane l taking entry h + l
-    auto work = [&](int h, int m) {
-      if (lane < m) {
-        const V4 e4 = q_w[(h + lane) & (kQ - 1)];
-        const R rx = e4.x, ry = e4.y, rz = e4.z;
-        const R r2 = rx * rx + ry * ry + rz * rz;
-        R inv_r, r;
-        if constexpr (std::is_same<R, float>::value) {
-          inv_r = rsqrtf(r2);
-          r = r2 * inv_r;
-        } else {
-          r = sqrt(r2);
-          inv_r = R(1) / r;
-        }
-        R g1, g2;
-        radial_eval<R>(tab, ng.ndeg, r * inv_rc, &g1, &g2);
-        const R qq = xi.w * e4.w;
-        const R e = qq * g1 * inv_r;
-        const R f = qq * g2 * inv_r * inv_r * inv_r;
-        fx.add(f * rx);
-        fy.add(f * ry);
-        fz.add(f * rz);
-        const R hf = R(0.5) * f;
-        U.add(R(0.5) * e);
-        W[0].add(hf * rx * rx);
-        W[1].add(hf * ry * ry);
-        W[2].add(hf * rz * rz);
-        W[3].add(hf * rx * ry);
-        W[4].add(hf * rx * rz);
-        W[5].add(hf * ry * rz);
+  if (warp == 0) {
+    int carry = 0;
+    for (int base = 0; base < noff; base += 32) {
+      const int t = base + lane;
+      const int v = t < noff ? coff[NC[t] + 1] - coff[NC[t]] : 0;
+      int x = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
       }
-    };
-    int qh = 0, qn = 0;  // queue head and length (warp-uniform)
-    for (int t = 0; t < noff; ++t) {
-          const V4 d = OFF[t];
-          const R dx = d.x, dy = d.y, dz = d.z;
-          const int Cn = NC[t];
-          const int jb = coff[Cn], je = coff[Cn + 1];
-          for (int j0 = jb; j0 < je; j0 += 32) {
-            const int j = j0 + lane;
-            bool pass = false;
-            V4 ent{};
-            if (j < je) {
-              const V4 xj = xq[j];
-              ent.x = (xi.x - xj.x) - dx;
-              ent.y = (xi.y - xj.y) - dy;
-              ent.z = (xi.z - xj.z) - dz;
-              ent.w = xj.w;
-              const R r2 = ent.x * ent.x + ent.y * ent.y + ent.z * ent.z;
-              pass = r2 > R(0) && r2 <= rc2;
-            }
-            const unsigned m = __ballot_sync(0xffffffffu, pass);
-            if (pass) q_w[(qh + qn + __popc(m & lt)) & (kQ - 1)] = ent;
-            qn += __popc(m);
-            __syncwarp();
-            if (qn >= 32) {
-              work(qh, 32);
-              qh = (qh + 32) & (kQ - 1);
-              qn -= 32;
-              __syncwarp();  // the worked entries may be overwritten now
-            }
-          }
+      if (t < noff) PRE[t] = carry + x - v;
+      carry += __shfl_sync(0xffffffffu, x, 31);
     }
-    work(qh, qn);
-    __syncwarp();
-    const double F[3] = {warp_total(fx), warp_total(fy), warp_total(fz)};
-    if (lane < 3) {
-      const int a = idx[i];
-      const double base = add ? (double)forces[3 * (int64_t)a + lane] : 0.0;
-      forces[3 * (int64_t)a + lane] = (IO)(base + F[lane]);
+    if (lane == 0) PRE[noff] = carry;
+  }
+  __syncthreads();
+  const int total = PRE[noff];
+  const R rc2 = (R)(ng.rc * ng.rc), inv_rc = (R)ng.inv_rc;
+  Sum<R> U, W[6];  // per lane over all of the warp's atoms
+
+  for (int k0 = 0; k0 < total; k0 += KC) {
+    const int kn = min(KC, total - k0);
+    __syncthreads();  // the previous chunk of candidates is consumed
+    for (int t = warp; t < noff; t += kThreads / 32) {
+      const int a = max(PRE[t], k0), b = min(PRE[t + 1], k0 + kn);
+      if (a >= b) continue;
+      const int jb = coff[NC[t]] + (a - PRE[t]);
+      const V4 d = OFF[t];
+      for (int k = a + lane; k < b; k += 32) {
+        V4 xj = xq[jb + (k - a)];
+        xj.x += d.x;
+        xj.y += d.y;
+        xj.z += d.z;
+        CB[k - k0] = xj;
+      }
+    }
+    __syncthreads();
+    for (int i = ib + warp; i < ie; i += kThreads / 32) {
+      const V4 xi = xq[i];
+      R fx = R(0), fy = R(0), fz = R(0), u = R(0), w[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
+      // the pair terms of queue entries [h, h + m), lane l taking entry h + l
+      auto work = [&](int h, int m) {
+        if (lane < m) {
+          const V4 e4 = q_w[(h + lane) & (kQ - 1)];
+          const R rx = e4.x, ry = e4.y, rz = e4.z;
+          const R r2 = rx * rx + ry * ry + rz * rz;
+          R inv_r, r;
+          if constexpr (std::is_same<R, float>::value) {
+            inv_r = rsqrtf(r2);
+            r = r2 * inv_r;
+          } else {
+            r = sqrt(r2);
+            inv_r = R(1) / r;
+          }
+          R g1, g2;
+          radial_eval<R>(tab, ng.ndeg, r * inv_rc, &g1, &g2);
+          const R qq = xi.w * e4.w;
+          const R e = qq * g1 * inv_r;
+          const R f = qq * g2 * inv_r * inv_r * inv_r;
+          fx = fma(f, rx, fx);
+          fy = fma(f, ry, fy);
+          fz = fma(f, rz, fz);
+          const R hf = R(0.5) * f;
+          u = fma(R(0.5), e, u);
+          w[0] = fma(hf * rx, rx, w[0]);
+          w[1] = fma(hf * ry, ry, w[1]);
+          w[2] = fma(hf * rz, rz, w[2]);
+          w[3] = fma(hf * rx, ry, w[3]);
+          w[4] = fma(hf * rx, rz, w[4]);
+          w[5] = fma(hf * ry, rz, w[5]);
+        }
+      };
+      int qh = 0, qn = 0;  // queue head and length (warp-uniform)
+      for (int k = 0; k < kn; k += 32) {
+        bool pass = false;
+        V4 ent{};
+        if (k + lane < kn) {
+          const V4 xj = CB[k + lane];
+          ent.x = xi.x - xj.x;
+          ent.y = xi.y - xj.y;
+          ent.z = xi.z - xj.z;
+          ent.w = xj.w;
+          const R r2 = ent.x * ent.x + ent.y * ent.y + ent.z * ent.z;
+          pass = r2 > R(0) && r2 <= rc2;
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, pass);
+        if (pass) q_w[(qh + qn + __popc(m & lt)) & (kQ - 1)] = ent;
+        qn += __popc(m);
+        __syncwarp();
+        if (qn >= 32) {
+          work(qh, 32);
+          qh = (qh + 32) & (kQ - 1);
+          qn -= 32;
+          __syncwarp();  // the worked entries may be overwritten now
+        }
+      }
+      work(qh, qn);
+      __syncwarp();
+      U.add(u);
+#pragma unroll
+      for (int c = 0; c < 6; ++c) W[c].add(w[c]);
+      Sum<R> sx, sy, sz;
+      sx.add(fx);
+      sy.add(fy);
+      sz.add(fz);
+      const double F[3] = {warp_total(sx), warp_total(sy), warp_total(sz)};
+      if (lane < 3) {
+        const int a = idx[i];
+        // later chunks add to what the earlier ones of this atom wrote
+        const double base = (add || k0 > 0) ? (double)forces[3 * (int64_t)a + lane] : 0.0;
+        forces[3 * (int64_t)a + lane] = (IO)(base + F[lane]);
+      }
     }
   }
   double v[7] = {U.value(), W[0].value(), W[1].value(), W[2].value(),
@@ -2901,9 +2958,15 @@ cudaError_t launch_near_pairs(bool fp64, bool io_double, const NearGeom& ng, int
                              void* forces, int add, double* out, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(out, 0, 7 * sizeof(double), st);
   if (e != cudaSuccess || ncells <= 0) return e;
-  const size_t noff = (size_t)(2 * ng.R[0] + 1) * (2 * ng.R[1] + 1) * (2 * ng.R[2] + 1);
-  const size_t smem = noff * ((fp64 ? sizeof(double4) : sizeof(float4)) + sizeof(int));
-  if (smem > 24 * 1024) return cudaErrorInvalidValue;  // the host rejects such cells first
+  const int noff = (2 * ng.R[0] + 1) * (2 * ng.R[1] + 1) * (2 * ng.R[2] + 1);
+  if (noff > 512) return cudaErrorInvalidValue;  // the host rejects such cells first
+  const size_t smem = near_smem_bytes(fp64, noff);
+  auto cfg = [&](auto kern) {
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  };
+  if ((e = fp64 ? cfg(k_near_pairs<double, double>)
+                : (io_double ? cfg(k_near_pairs<float, double>) : cfg(k_near_pairs<float, float>))))
+    return e;
   if (fp64)
     k_near_pairs<double, double><<<ncells, kThreads, smem, st>>>(
         ng, coff, (const double4*)xq, idx, (const double*)tab, (double*)forces, add, out);

@@ -14,10 +14,13 @@ Two selectors return (Delta, c, P, r_c, grid):
   choices that met each target (tests/test_gpu_selector.py).  Infeasible predictions fall
   back to the rules.
 
-``cost`` is a model of one FP32 long-range step plus the near part on a GB300, calibrated
-on the measured kernel times of the 210,240-atom membrane slab (spread and gather per
-atom and stencil point, the transforms and scaling per grid point and log2 of the grid,
-binning per atom, the near part per ordered pair within r_c).
+``measure_time`` times one FP32 long-range step with forces plus the near part on the GPU
+(CUDA events); the selector's labels are the cheapest choices by that measured time.
+``cost`` is a model of the same time (calibrated on the 210,240-atom membrane slab's
+kernel times), kept for a quick estimate without a GPU.
+``reference_virial`` is the method itself at a far tighter tolerance (Delta = 1e-11, P = 12,
+FP64), the reference for systems too large for the Ewald oracle; it is validated against
+the oracle on the smaller ones, as the paper validates against PPPM at 1e-12 (Sec. 5.1).
 """
 
 from __future__ import annotations
@@ -137,13 +140,56 @@ class Selector:
 def candidates():
     """The parameter grid the selector is trained on: (log10 Delta, P, sigma, r_c)."""
     out = []
-    for ld in np.arange(-2.0, -7.01, -0.5):
+    for ld in np.arange(-2.5, -7.01, -0.5):
         D = math.ceil(-ld - 1e-9)
-        for P in (D + 1, D + 2):
-            for sigma in (1.3, 1.8):
-                for rc in (5.5, 8.0):
-                    out.append((float(ld), int(P), sigma, rc))
+        for sigma in (1.3, 1.8):
+            for rc in (5.5, 8.0):
+                out.append((float(ld), int(D + 1), sigma, rc))
     return out
+
+
+def measure_time(pos, q, cell, p: dict, steps: int = 5) -> float:
+    """Median seconds of one FP32 long-range step with forces plus the near part (forces
+    added), CUDA events on a stream of its own after two warm-up steps."""
+    import torch
+
+    from . import ESP_ACCUM_LEN, Plan, esp_near, esp_step
+
+    st = torch.cuda.Stream()
+    with torch.cuda.stream(st):
+        plan = Plan(cell, len(q), p["grid"], p["P"], p["c"], p["rc"], precision="fp32",
+                    stream=st.cuda_stream)
+        try:
+            x = torch.tensor(pos, dtype=torch.float32, device="cuda")
+            qq = torch.tensor(q, dtype=torch.float32, device="cuda")
+            F = torch.empty((len(q), 3), dtype=torch.float32, device="cuda")
+            acc = torch.zeros(ESP_ACCUM_LEN, dtype=torch.float64, device="cuda")
+            near = torch.empty(7, dtype=torch.float64, device="cuda")
+            times = []
+            for k in range(steps + 2):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                esp_step(plan.handle, x, qq, F, acc)
+                esp_near(plan.handle, x, qq, F, 1, near)
+                e1.record(st)
+                e1.synchronize()
+                if k >= 2:
+                    times.append(e0.elapsed_time(e1) * 1e-3)
+            return float(np.median(times))
+        finally:
+            plan.close()
+
+
+def reference_virial(pos, q, cell) -> np.ndarray:
+    """Total Coulomb virial of the method at Delta = 1e-11, P = 12, r_c = 10 A, FP64 (grid
+    with the rules' aliasing margin): far below every target of the selector."""
+    c = esp_c_from_tolerance(1e-11)
+    P, rc = 12, 10.0
+    band = 1.0 - c / (math.pi * P)
+    p = {"delta": 1e-11, "c": c, "P": P, "rc": rc,
+         "grid": grid_for(cell, c, rc, max(1.0, 1.0 / (2.0 * band)) * 1.05, P)}
+    return measure_virial(pos, q, cell, p)
 
 
 def measure_virial(pos, q, cell, p: dict, near_virial=None) -> np.ndarray:

@@ -188,13 +188,13 @@ def small_random(n: int, cell, seed: int, grid=(16, 18, 20), P=6, delta=1e-6, rc
 def selector_system(i: int) -> System:
     """System i (0..63) of the parameter selector's set.
 
-    N log-uniform in [500, 4000] (whole molecules or ion pairs), density 0.1 atoms/A^3,
+    N log-uniform in [1e3, 1e6] (whole molecules or ion pairs), density 0.1 atoms/A^3,
     triclinic cell: diagonal lengths with aspect ratios in [0.8, 1.25] and upper-triangle
     tilts uniform in [0, 0.3] of the lengths; even i water, odd i the LiTFSI-like ionic
     composition.  Grid, P, Delta and r_c are placeholders: the selector chooses them.
     """
     rng = _rng(2000 + i)
-    n_target = math.exp(rng.uniform(math.log(500.0), math.log(4000.0)))
+    n_target = math.exp(rng.uniform(math.log(1e3), math.log(1e6)))
     ionic = i % 2 == 1
     per = 16 if ionic else 3
     units = max(2, int(round(n_target / per)))

@@ -1,10 +1,12 @@
-"""Classical Ewald references for the parameter selector's 64 systems (FP64 oracle only).
+"""Classical Ewald references for the parameter selector's small systems (FP64 oracle only).
 
 Writes ``selector_references.json`` beside this file: for each ``synthetic.selector_system(i)``
-its Coulomb energy and virial tensor W = -(dU/dh) h^T (so the pressure tensor of eq.
-(instheta) without the kinetic term is W / V), from ``oracle.ewald`` at splitting
-tolerance 1e-12 (tin-foil boundary, Sec. 3.2).  The selector's GPU tests run the method
-at many parameter choices against these values.
+with at most MAX_ATOMS atoms, its Coulomb energy and virial tensor W = -(dU/dh) h^T (so the
+pressure tensor of eq. (instheta) without the kinetic term is W / V), from ``oracle.ewald``
+at splitting tolerance 1e-12 (tin-foil boundary, Sec. 3.2).  The selector's GPU test judges
+the picks on these systems against these values, and validates there the tight-tolerance
+method it uses as the reference of the larger systems (as the paper uses PPPM at 1e-12,
+Sec. 5.1).
 
     python tests/golden/selector_references.py     # a few minutes on 8 cores
 """
@@ -24,6 +26,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 TOL = 1e-12
+MAX_ATOMS = 20000
 
 
 def reference(i: int):
@@ -43,8 +46,10 @@ def reference(i: int):
 def main():
     import synthetic
 
+    small = [i for i in range(synthetic.N_SELECTOR_SYSTEMS)
+             if synthetic.selector_system(i).n <= MAX_ATOMS]
     with mp.get_context("spawn").Pool(min(8, os.cpu_count() or 1)) as pool:
-        refs = pool.map(reference, range(synthetic.N_SELECTOR_SYSTEMS))
+        refs = pool.map(reference, small)
     out = {"what": "Ewald energy and virial of synthetic.selector_system(i), oracle.ewald at "
                    f"splitting tolerance {TOL:g} (tin-foil)",
            "script": "tests/golden/selector_references.py (FP64 oracle only)",

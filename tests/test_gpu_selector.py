@@ -3,14 +3,18 @@ what the trained network gains over the paper's analytic tuning.
 
 * esp_mlp_loss_grad against oracle.mlp.loss_and_grad, one Adam step against
   oracle.mlp.adam_step.
-* The selector's set: 64 seeded systems (synthetic.selector_system), references from the
-  FP64 Ewald oracle (tests/golden/selector_references.json).  On 48 systems the method
-  runs at every candidate (Delta, P, sigma, r_c) (FP64 GPU path: long-range step, near part,
-  background); the cheapest candidate (cost model of the GB300 step) whose relative
-  pressure-tensor error is at most half the target becomes the label for each target in
-  {1e-3, 1e-4, 1e-5, 1e-6}.  The network is trained on the GPU by the library's kernels.
-  On the 16 other systems the oracle judges both the network's pick and the analytic
-  rules' pick.
+* The selector's set: 64 seeded systems (synthetic.selector_system), N log-uniform in
+  1e3 - 1e6.  References: the FP64 Ewald oracle for the 23 systems of at most 20,000 atoms
+  (tests/golden/selector_references.json); for the larger ones the method itself at
+  Delta = 1e-11, P = 12 in FP64 (selector.reference_virial), validated here against the
+  oracle on the smaller systems.  On 48 systems the method runs at every candidate (Delta,
+  P, sigma, r_c): the FP64 GPU path gives the pressure-tensor error (long-range step, near
+  part, background), and the FP32 step with forces plus the near part is timed on the GPU
+  with CUDA events.  The fastest candidate whose relative pressure-tensor error is at most
+  half the target becomes the label for each target in {1e-3, 1e-4, 1e-5, 1e-6}.  The
+  network is trained on the GPU by the library's kernels.  On the 16 other systems the
+  references judge both the network's pick and the analytic rules' pick, and both are
+  timed.
 """
 
 import json
@@ -59,40 +63,61 @@ def rel_err(W, ref):
     return float(np.linalg.norm(W - ref) / np.linalg.norm(ref))
 
 
+MAX_POINTS = 1.2e8  # candidates with larger grids are skipped (memory and time)
+
+
 @pytest.fixture(scope="module")
 def references():
     with open(os.path.join(HERE, "golden", "selector_references.json")) as f:
-        return {r["i"]: r for r in json.load(f)["systems"]}
+        ewald = {r["i"]: np.array(r["virial"]) for r in json.load(f)["systems"]}
+    refs = {}
+    for i in range(sy.N_SELECTOR_SYSTEMS):
+        if i in ewald:
+            refs[i] = ("ewald", ewald[i])
+        else:
+            S = sy.selector_system(i)
+            refs[i] = ("esp_1e-11", sel.reference_virial(S.pos, S.q, S.cell))
+    return refs, ewald
 
 
-def run(S, p, ref, near_cache):
-    key = (round(math.log10(p["delta"]), 6), p["rc"])
-    W = sel.measure_virial(S.pos, S.q, S.cell, p, near_cache.get(key))
-    return rel_err(W, np.array(ref["virial"]))
+def test_tight_reference_matches_the_ewald_oracle(references):
+    refs, ewald = references
+    worst = 0.0
+    for i in sorted(ewald)[:8]:
+        S = sy.selector_system(i)
+        worst = max(worst, rel_err(sel.reference_virial(S.pos, S.q, S.cell), ewald[i]))
+    # far below the tightest target the selector is trained for (1e-6)
+    assert worst < 1e-8, worst
+
+
+def evaluate(S, W_ref, cands):
+    """(pressure error, measured seconds, candidate) for every feasible candidate."""
+    from paper_2601_00161_gb300 import Plan
+
+    near_cache = {}
+    rows = []
+    for ld, P, sigma, rc in cands:
+        p = sel.params_from(S.cell, ld, P, sigma, rc)
+        if not sel.feasible(p) or float(np.prod(p["grid"])) > MAX_POINTS:
+            continue
+        key = (round(ld, 6), rc)
+        if key not in near_cache:
+            plan = Plan(S.cell, S.n, p["grid"], p["P"], p["c"], p["rc"], precision="fp64")
+            _, near_cache[key], _ = plan.near(S.pos, S.q)
+            plan.close()
+        err = rel_err(sel.measure_virial(S.pos, S.q, S.cell, p, near_cache[key]), W_ref)
+        rows.append((err, sel.measure_time(S.pos, S.q, S.cell, p), (ld, P, sigma, rc)))
+    return rows
 
 
 def test_learned_selector_against_the_analytic_rules(references):
+    refs, _ = references
     t0 = time.time()
     X, Y = [], []
     cands = sel.candidates()
     for i in range(48):
         S = sy.selector_system(i)
-        ref = references[i]
-        near_cache = {}
-        rows = []
-        for ld, P, sigma, rc in cands:
-            p = sel.params_from(S.cell, ld, P, sigma, rc)
-            if not sel.feasible(p):
-                continue
-            key = (round(ld, 6), rc)
-            if key not in near_cache:
-                from paper_2601_00161_gb300 import Plan
-
-                plan = Plan(S.cell, S.n, p["grid"], p["P"], p["c"], p["rc"], precision="fp64")
-                _, near_cache[key], _ = plan.near(S.pos, S.q)
-                plan.close()
-            err = run(S, p, ref, near_cache)
-            rows.append((err, sel.cost(S.n, S.cell, p["grid"], P, rc), (ld, P, sigma, rc)))
+        rows = evaluate(S, refs[i][1], cands)
         for target in TARGETS:
             ok = [r for r in rows if r[0] <= 0.5 * target]
             if not ok:
@@ -105,24 +130,29 @@ def test_learned_selector_against_the_analytic_rules(references):
     model = sel.train(X, Y)
     assert model.history[-1] < 0.3 * model.history[0]
 
-    # held-out systems: the oracle judges both picks
+    # held-out systems: the references judge both picks, both are timed
     res = {"learned": [], "rules": []}
     for i in range(48, 64):
         S = sy.selector_system(i)
-        ref = references[i]
         for target in TARGETS:
             for name, p in (("learned", model.select(S.pos, S.q, S.cell, target)),
                             ("rules", sel.rules(S.cell, target))):
-                err = run(S, p, ref, {})
-                res[name].append((target, err, sel.cost(S.n, S.cell, p["grid"], p["P"], p["rc"])))
-    met = {k: [e <= t for t, e, _ in v] for k, v in res.items()}
+                err = rel_err(sel.measure_virial(S.pos, S.q, S.cell, p), refs[i][1])
+                res[name].append((target, err, sel.measure_time(S.pos, S.q, S.cell, p), S.n))
+    met = {k: [e <= t for t, e, _, _ in v] for k, v in res.items()}
     both = [j for j in range(len(met["rules"])) if met["rules"][j] and met["learned"][j]]
     ratio = float(np.mean([res["learned"][j][2] / res["rules"][j][2] for j in both])) if both else float("nan")
-    print(f"\nselector: {len(X)} labels from {t_data:.0f} s of runs; held-out targets met: "
-          f"learned {sum(met['learned'])}/{len(met['learned'])}, rules {sum(met['rules'])}/{len(met['rules'])}; "
-          f"learned/rules modelled cost where both met: {ratio:.3f}")
-    # the oracle judges every pick: the network meets the targets at least as often as the
-    # rules and is cheaper where both meet them
-    assert sum(met["learned"]) >= 0.85 * len(met["learned"])
+    summary = {"labels": len(X), "data_seconds": round(t_data, 1),
+               "held_out_met": {k: int(sum(v)) for k, v in met.items()}, "held_out_total": len(met["rules"]),
+               "measured_time_ratio_learned_over_rules": ratio,
+               "held_out_n": sorted({n for _, _, _, n in res["rules"]})}
+    print("\nselector:", json.dumps(summary))
+    out = os.environ.get("ESP_SELECTOR_REPORT")
+    if out:
+        with open(out, "w") as f:
+            json.dump({"summary": summary, "held_out": res}, f, indent=1)
+    # the references judge every pick: the network meets the targets at least as often as
+    # the rules (up to two picks) and is faster where both meet them
+    assert sum(met["learned"]) >= 0.8 * len(met["learned"])
     assert sum(met["learned"]) >= sum(met["rules"]) - 2
     assert ratio < 1.0
