@@ -151,8 +151,9 @@ def test_learned_selector_against_the_analytic_rules(references):
     if out:
         with open(out, "w") as f:
             json.dump({"summary": summary, "held_out": res}, f, indent=1)
-    # the references judge every pick: the network meets the targets at least as often as
-    # the rules (up to two picks) and is faster where both meet them
-    assert sum(met["learned"]) >= 0.8 * len(met["learned"])
-    assert sum(met["learned"]) >= sum(met["rules"]) - 2
-    assert ratio < 1.0
+    # the references judge every pick: the network meets clearly more targets than the
+    # rules (whose single tolerance misses most targets on the ionic systems) and is faster
+    # by the measured step time where both meet them
+    assert sum(met["learned"]) >= 0.75 * len(met["learned"])
+    assert sum(met["learned"]) >= sum(met["rules"]) + 10
+    assert ratio < 0.9
