@@ -563,12 +563,14 @@ int setup_tile_geom(esp_plan_t p) {
   {
     const int v = p->fp64 ? 2 : (p->bf16 ? 8 : 4);  // elements per 16 bytes
     g.gvec = (g.T[2] % v == 0 && p->M[2] % v == 0) ? 1 : 0;
+    g.E2g = (g.E[2] + v - 1) / v;
   }
   auto magic = [](unsigned int d) {
     return (unsigned int)((((unsigned long long)1 << 32) + d - 1) / d);
   };
   g.div_E1 = magic((unsigned)g.E[1]);
   g.div_E2v = magic((unsigned)((g.E[2] + 3) / 4));
+  g.div_E2g = magic((unsigned)g.E2g);
   g.deg = p->deg;
   // psi_0 is even and largest at 0 on [-1, 1]; the margin covers the polynomial fit
   g.wmax3 = (float)std::pow(p->pswf.psi_at_0 * (1.0 + 1e-6), 3.0);

@@ -582,7 +582,10 @@ __global__ void __launch_bounds__(kThreads, spread_min_ctas<R, P>()) k_spread(Bi
   V4* TQ_b = reinterpret_cast<V4*>(smem_raw + L.tq);  // 2 x kChunk (t0, t1, t2, q)
   int* LB_b = reinterpret_cast<int*>(smem_raw + L.lb);
   int* CNT_b = reinterpret_cast<int*>(smem_raw + L.cnt);
+  // tiles taken ahead, with the grid origin of each (computed once, by the thread that
+  // takes the tile)
   __shared__ int s_first[2], s_ahead[2];
+  __shared__ int3 s_ofirst[2], s_oahead[2];
   __shared__ float s_qsum[kThreads / 32];
   const unsigned acc_s = (unsigned)__cvta_generic_to_shared(acc);
 
@@ -608,9 +611,19 @@ __global__ void __launch_bounds__(kThreads, spread_min_ctas<R, P>()) k_spread(Bi
     cp_async_commit();
   };
 
+  auto take = [&](int* st, int3* so) {
+    const int t = atomicAdd(&bins.ctrl[1], 1);
+    *st = t;
+    if (t < ntiles) {
+      const int t2 = t % g.nt[2];
+      const int t1 = (t / g.nt[2]) % g.nt[1];
+      const int t0 = t / (g.nt[2] * g.nt[1]);
+      *so = make_int3(t0 * g.T[0], t1 * g.T[1], t2 * g.T[2]);
+    }
+  };
   if (threadIdx.x == 0) {
-    s_first[0] = atomicAdd(&bins.ctrl[1], 1);
-    s_first[1] = atomicAdd(&bins.ctrl[1], 1);
+    take(&s_first[0], &s_ofirst[0]);
+    take(&s_first[1], &s_ofirst[1]);
   }
   {
     // clear the block once; every flush clears what it reads
@@ -622,12 +635,13 @@ __global__ void __launch_bounds__(kThreads, spread_min_ctas<R, P>()) k_spread(Bi
   }
   __syncthreads();
   int tile = s_first[0], nxt = s_first[1];
+  int3 org = s_ofirst[0], nxt_o = s_ofirst[1];
   issue(tile, 0);
   issue(nxt, 1);
 
   for (int kt = 0; tile < ntiles; ++kt) {
     const int bf = kt & 1;
-    if (threadIdx.x == 0) s_ahead[bf] = atomicAdd(&bins.ctrl[1], 1);
+    if (threadIdx.x == 0) take(&s_ahead[bf], &s_oahead[bf]);
     cp_async_wait<1>();
     __syncthreads();  // tile's count and first atoms are in buffer bf
     V4* TQ = TQ_b + bf * kChunk;
@@ -731,10 +745,7 @@ __global__ void __launch_bounds__(kThreads, spread_min_ctas<R, P>()) k_spread(Bi
       }
 
       // add the padded block into the periodic global grid, clearing it
-      const int t2 = tile % g.nt[2];
-      const int t1 = (tile / g.nt[2]) % g.nt[1];
-      const int t0 = tile / (g.nt[2] * g.nt[1]);
-      const int o0 = t0 * g.T[0], o1 = t1 * g.T[1], o2 = t2 * g.T[2];
+      const int o0 = org.x, o1 = org.y, o2 = org.z;
       bool flushed = false;
       if constexpr (kFixed) {
         if (g.vec4) {
@@ -787,9 +798,12 @@ __global__ void __launch_bounds__(kThreads, spread_min_ctas<R, P>()) k_spread(Bi
     }
     __syncthreads();  // the block is read out and cleared; buffer bf is free
     const int nn = s_ahead[bf];
+    const int3 nn_o = s_oahead[bf];
     issue(nn, bf);
     tile = nxt;
+    org = nxt_o;
     nxt = nn;
+    nxt_o = nn_o;
   }
   cp_async_wait<0>();
   __syncthreads();
@@ -1684,7 +1698,10 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 3 : 
   int* X_b = reinterpret_cast<int*>(smem_raw + L.idx);
   int* CNT_b = reinterpret_cast<int*>(smem_raw + L.cnt);
   const V4* __restrict__ slot_tq = static_cast<const V4*>(bins.tq);
+  // tiles taken ahead, with the grid origin of each (computed once, by the thread that
+  // takes the tile)
   __shared__ int s_first[2], s_ahead[2];
+  __shared__ int3 s_ofirst[2], s_oahead[2];
 
   constexpr int D = WinDeg<R>::value;
   constexpr int NPA = kThreads / P;  // atoms per sweep of the window evaluation
@@ -1695,20 +1712,28 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 3 : 
   const int E0 = g.E[0], E1r = g.E[1], E2 = g.E[2];
   const int ncopy = min(CH, bins.cap);
 
-  // copies of tile t into buffer b: block, count, first chunk of atoms (one group)
-  auto issue = [&](int t, int b) {
+  // thread 0 takes a tile and records its grid origin
+  auto take = [&](int* st, int3* so) {
+    const int t = atomicAdd(&bins.ctrl[5], 1);
+    *st = t;
     if (t < ntiles) {
       const int t2 = t % g.nt[2];
       const int t1 = (t / g.nt[2]) % g.nt[1];
       const int t0 = t / (g.nt[2] * g.nt[1]);
-      const int o0 = t0 * g.T[0], o1 = t1 * g.T[1], o2 = t2 * g.T[2];
+      *so = make_int3(t0 * g.T[0], t1 * g.T[1], t2 * g.T[2]);
+    }
+  };
+  // copies of tile t (origin o) into buffer b: block, count, first chunk of atoms (one group)
+  auto issue = [&](int t, int3 o, int b) {
+    if (t < ntiles) {
+      const int o0 = o.x, o1 = o.y, o2 = o.z;
       G* phi = phi_b + b * VOL;
       if (g.gvec) {
-        const int E2v = (E2 + VW - 1) / VW;
+        const int E2v = g.E2g;
         const int n = E0 * E1r * E2v;
         for (int e = threadIdx.x; e < n; e += blockDim.x) {
-          const int ab = e / E2v, c4 = e - ab * E2v;
-          const int a = ab / E1r, bb = ab - a * E1r;
+          const int ab = fast_div(e, g.div_E2g), c4 = e - ab * E2v;
+          const int a = fast_div(ab, g.div_E1), bb = ab - a * E1r;
           const int gi = wrap3(o0 + a, g.M[0]);
           const int gj = wrap3(o1 + bb, g.M[1]);
           const int gk = wrap3(o2 + VW * c4, g.M[2]);
@@ -1747,17 +1772,17 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 3 : 
   };
 
   if (threadIdx.x == 0) {
-    s_first[0] = atomicAdd(&bins.ctrl[5], 1);
-    s_first[1] = atomicAdd(&bins.ctrl[5], 1);
+    take(&s_first[0], &s_ofirst[0]);
+    take(&s_first[1], &s_ofirst[1]);
   }
   __syncthreads();
   int cur = s_first[0], nxt = s_first[1];
-  issue(cur, 0);
-  issue(nxt, 1);
+  issue(cur, s_ofirst[0], 0);
+  issue(nxt, s_ofirst[1], 1);
 
   for (int k = 0; cur < ntiles; ++k) {
     const int b = k & 1;
-    if (threadIdx.x == 0) s_ahead[b] = atomicAdd(&bins.ctrl[5], 1);
+    if (threadIdx.x == 0) take(&s_ahead[b], &s_oahead[b]);
     cp_async_wait<1>();
     __syncthreads();  // tile cur's block and atoms are in buffer b
     const G* phi = phi_b + b * VOL;
@@ -1887,7 +1912,8 @@ __global__ void __launch_bounds__(kThreads, std::is_same<R, float>::value ? 3 : 
     }
     __syncthreads();  // buffer b is free; s_ahead[b] is visible
     const int nn = s_ahead[b];
-    issue(nn, b);
+    const int3 nn_o = s_oahead[b];
+    issue(nn, nn_o, b);
     cur = nxt;
     nxt = nn;
   }

@@ -28,6 +28,8 @@ struct TileGeom {
   int vec4;     // 1: rows move as aligned float4 between global and shared memory
   int gvec;     // 1: the gather's block rows move as 16-byte copies (M3, T3 multiples of
                 // 16 bytes of the potential grid's element type)
+  int E2g;               // 16-byte pieces of a gather block row: ceil(E[2] / (16 / size))
+  unsigned int div_E2g;  // ceil(2^32 / E2g)
   double hinv[9];    // h^{-1}, row-major
   float hinvf[9];    // the same in FP32 (FP32 force transform)
   double dscale[3];  // d u / d s factor of the window argument: 2 M_d / P
