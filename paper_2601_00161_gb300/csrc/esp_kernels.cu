@@ -1032,20 +1032,24 @@ __device__ __forceinline__ void xpass(const typename Cplx<R>::T* in, typename Cp
   const int stride = L / Ns;  // M0 / (Ns RAD)
   const int ncm = (1 << lognc) - 1;
   const int nb = L << lognc;
+  const int Lnc = L << lognc, Nsnc = Ns << lognc;  // element strides of inputs and outputs
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
     const int c = b & ncm, j = b >> lognc;
     const int k = Ns == 1 ? 0 : j - fast_div(j, ns_magic) * Ns;
     C v[RAD];
+    const C* src = in + b;  // b = (j << lognc) + c
 #pragma unroll
-    for (int t = 0; t < RAD; ++t) v[t] = in[((j + t * L) << lognc) + c];
+    for (int t = 0; t < RAD; ++t) v[t] = src[t * Lnc];
     if (k > 0) {
+      const int ks = k * stride;
+      const C* w = tw + ks;
 #pragma unroll
-      for (int t = 1; t < RAD; ++t) v[t] = ctw<SIGN>(v[t], tw[t * k * stride]);
+      for (int t = 1; t < RAD; ++t) v[t] = ctw<SIGN>(v[t], w[(t - 1) * ks]);
     }
     dft_reg<R, RAD, SIGN>(v, tw, M0);
-    const int d = (j - k) * RAD + k;
+    C* dst = out + (((j - k) * RAD + k) << lognc) + c;
 #pragma unroll
-    for (int t = 0; t < RAD; ++t) out[((d + t * Ns) << lognc) + c] = v[t];
+    for (int t = 0; t < RAD; ++t) dst[t * Nsnc] = v[t];
   }
 }
 
@@ -1116,21 +1120,26 @@ __device__ __forceinline__ void lpass(const typename Cplx<R>::T* in, typename Cp
   const int L = N / RAD;
   const int stride = L / Ns;
   const int nb = L * nc;
+  const int Lnc = L * nc, Nsnc = Ns * nc;  // element strides of the RAD inputs and outputs
   for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    // b = j nc + c: input t of butterfly j in column c is in[b + t L nc]
     const int j = fast_div(b, f.nc_magic);
     const int c = b - j * nc;
     const int k = Ns == 1 ? 0 : j - fast_div(j, ns_magic) * Ns;
     C v[RAD];
+    const C* src = in + b;
 #pragma unroll
-    for (int t = 0; t < RAD; ++t) v[t] = in[(j + t * L) * nc + c];
+    for (int t = 0; t < RAD; ++t) v[t] = src[t * Lnc];
     if (k > 0) {
+      const int ks = k * stride;
+      const C* w = tw + ks;
 #pragma unroll
-      for (int t = 1; t < RAD; ++t) v[t] = ctw<SIGN>(v[t], tw[t * k * stride]);
+      for (int t = 1; t < RAD; ++t) v[t] = ctw<SIGN>(v[t], w[(t - 1) * ks]);
     }
     dft_reg<R, RAD, SIGN>(v, tw, N);
-    const int d = (j - k) * RAD + k;
+    C* dst = out + ((j - k) * RAD + k) * nc + c;
 #pragma unroll
-    for (int t = 0; t < RAD; ++t) out[(d + t * Ns) * nc + c] = v[t];
+    for (int t = 0; t < RAD; ++t) dst[t * Nsnc] = v[t];
   }
 }
 
