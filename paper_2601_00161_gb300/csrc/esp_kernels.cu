@@ -1198,6 +1198,140 @@ __device__ __forceinline__ typename Cplx<R>::T* lfft_lines(typename Cplx<R>::T* 
   return a;
 }
 
+// ---------------------------------------------------------------------------------------
+// Line transforms of lengths known at compile time (the common grid sizes): the same
+// Stockham passes with the pass lengths, strides and twiddle steps as constants, and the
+// radix-3 and radix-5 butterflies from their closed forms.
+struct CPlan {
+  int npass;
+  int radix[kMaxPass];
+};
+__host__ __device__ constexpr CPlan cplan(int n) {
+  CPlan p{0, {}};
+  while (n % 8 == 0) {
+    p.radix[p.npass++] = 8;
+    n /= 8;
+  }
+  if (n % 4 == 0) {
+    p.radix[p.npass++] = 4;
+    n /= 4;
+  }
+  if (n % 2 == 0) {
+    p.radix[p.npass++] = 2;
+    n /= 2;
+  }
+  while (n % 3 == 0) {
+    p.radix[p.npass++] = 3;
+    n /= 3;
+  }
+  while (n % 5 == 0) {
+    p.radix[p.npass++] = 5;
+    n /= 5;
+  }
+  if (n > 1) p.npass = -1;  // other factors: no compile-time plan
+  return p;
+}
+
+// RAD-point DFT y_u = sum_t v_t e^{SIGN 2 pi i u t / RAD} for RAD = 2, 4, 8, 3, 5.
+// Radix 3: with w = -1/2 + i SIGN sqrt(3)/2, y_1,2 = a - (b + c)/2 +- i SIGN sqrt(3)/2 (b - c).
+// Radix 5: with s1 = v1 + v4, d1 = v1 - v4, s2 = v2 + v3, d2 = v2 - v3 and th = 2 pi / 5,
+//   y_1,4 = v0 + cos(th) s1 + cos(2 th) s2 +- i SIGN (sin(th) d1 + sin(2 th) d2),
+//   y_2,3 = v0 + cos(2 th) s1 + cos(th) s2 +- i SIGN (sin(2 th) d1 - sin(th) d2).
+template <typename R, int RAD, int SIGN>
+__device__ __forceinline__ void dft_fixed(typename Cplx<R>::T (&v)[RAD]) {
+  using C = typename Cplx<R>::T;
+  if constexpr (RAD == 2 || RAD == 4 || RAD == 8) {
+    dft_reg<R, RAD, SIGN>(v, nullptr, 0);
+  } else if constexpr (RAD == 3) {
+    const R h = R(0.866025403784438646763723170753);  // sqrt(3) / 2
+    const C t1 = cadd(v[1], v[2]);
+    const C t2 = cmk<R>(v[0].x - R(0.5) * t1.x, v[0].y - R(0.5) * t1.y);
+    const C d = cmk<R>(R(SIGN) * h * (v[1].x - v[2].x), R(SIGN) * h * (v[1].y - v[2].y));
+    v[0] = cadd(v[0], t1);
+    v[1] = cmk<R>(t2.x - d.y, t2.y + d.x);
+    v[2] = cmk<R>(t2.x + d.y, t2.y - d.x);
+  } else if constexpr (RAD == 5) {
+    const R c1 = R(0.309016994374947424102293417183), c2 = R(-0.809016994374947424102293417183);
+    const R s1 = R(0.951056516295153572116439333379), s2 = R(0.587785252292473129168705954639);
+    const C p1 = cadd(v[1], v[4]), m1 = csub(v[1], v[4]);
+    const C p2 = cadd(v[2], v[3]), m2 = csub(v[2], v[3]);
+    const C a1 = cmk<R>(v[0].x + c1 * p1.x + c2 * p2.x, v[0].y + c1 * p1.y + c2 * p2.y);
+    const C a2 = cmk<R>(v[0].x + c2 * p1.x + c1 * p2.x, v[0].y + c2 * p1.y + c1 * p2.y);
+    const C b1 = cmk<R>(R(SIGN) * (s1 * m1.x + s2 * m2.x), R(SIGN) * (s1 * m1.y + s2 * m2.y));
+    const C b2 = cmk<R>(R(SIGN) * (s2 * m1.x - s1 * m2.x), R(SIGN) * (s2 * m1.y - s1 * m2.y));
+    v[0] = cadd(v[0], cadd(p1, p2));
+    v[1] = cmk<R>(a1.x - b1.y, a1.y + b1.x);  // a1 + i b1
+    v[4] = cmk<R>(a1.x + b1.y, a1.y - b1.x);  // a1 - i b1
+    v[2] = cmk<R>(a2.x - b2.y, a2.y + b2.x);
+    v[3] = cmk<R>(a2.x + b2.y, a2.y - b2.x);
+  }
+}
+
+template <typename R, int RAD, int SIGN, int N, int NS>
+__device__ __forceinline__ void lpass_fixed(const typename Cplx<R>::T* in, typename Cplx<R>::T* out,
+                                            const typename Cplx<R>::T* tw, int nc,
+                                            unsigned int nc_magic) {
+  using C = typename Cplx<R>::T;
+  constexpr int L = N / RAD;
+  constexpr int stride = L / NS;
+  const int nb = L * nc;
+  const int Lnc = L * nc, Nsnc = NS * nc;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    const int j = fast_div(b, nc_magic);
+    const int c = b - j * nc;
+    const int k = NS == 1 ? 0 : j % NS;
+    C v[RAD];
+    const C* src = in + b;
+#pragma unroll
+    for (int t = 0; t < RAD; ++t) v[t] = src[t * Lnc];
+    if (k > 0) {
+      const C* w = tw + k * stride;
+#pragma unroll
+      for (int t = 1; t < RAD; ++t) v[t] = ctw<SIGN>(v[t], w[(t - 1) * k * stride]);
+    }
+    dft_fixed<R, RAD, SIGN>(v);
+    C* dst = out + ((j - k) * RAD + k) * nc + c;
+#pragma unroll
+    for (int t = 0; t < RAD; ++t) dst[t * Nsnc] = v[t];
+  }
+}
+
+template <typename R, int SIGN, int N, int S, int NS>
+__device__ __forceinline__ typename Cplx<R>::T* lfft_fixed(typename Cplx<R>::T* a,
+                                                           typename Cplx<R>::T* b,
+                                                           const typename Cplx<R>::T* tw, int nc,
+                                                           unsigned int nc_magic) {
+  constexpr CPlan pl = cplan(N);
+  if constexpr (S >= pl.npass) {
+    return a;
+  } else {
+    constexpr int RAD = pl.radix[S];
+    lpass_fixed<R, RAD, SIGN, N, NS>(a, b, tw, nc, nc_magic);
+    __syncthreads();
+    return lfft_fixed<R, SIGN, N, S + 1, NS * RAD>(b, a, tw, nc, nc_magic);
+  }
+}
+
+// The line transform of f: a compile-time version for the common lengths, else the
+// generic passes.
+template <typename R, int SIGN>
+__device__ __forceinline__ typename Cplx<R>::T* lfft_any(typename Cplx<R>::T* a,
+                                                         typename Cplx<R>::T* b,
+                                                         const typename Cplx<R>::T* tw,
+                                                         const LineFFT& f) {
+  switch (f.n) {
+    case 24: return lfft_fixed<R, SIGN, 24, 0, 1>(a, b, tw, f.nc, f.nc_magic);
+    case 32: return lfft_fixed<R, SIGN, 32, 0, 1>(a, b, tw, f.nc, f.nc_magic);
+    case 64: return lfft_fixed<R, SIGN, 64, 0, 1>(a, b, tw, f.nc, f.nc_magic);
+    case 72: return lfft_fixed<R, SIGN, 72, 0, 1>(a, b, tw, f.nc, f.nc_magic);
+    case 96: return lfft_fixed<R, SIGN, 96, 0, 1>(a, b, tw, f.nc, f.nc_magic);
+    case 128: return lfft_fixed<R, SIGN, 128, 0, 1>(a, b, tw, f.nc, f.nc_magic);
+    case 160: return lfft_fixed<R, SIGN, 160, 0, 1>(a, b, tw, f.nc, f.nc_magic);
+    case 256: return lfft_fixed<R, SIGN, 256, 0, 1>(a, b, tw, f.nc, f.nc_magic);
+    default: return lfft_lines<R, SIGN>(a, b, tw, f);
+  }
+}
+
 // Sums of 8 values over the 32 lanes of a warp in a fixed order.  Each of the first three
 // levels halves the values a lane keeps and sends the other half to its partner, so lane l
 // ends with the warp total of value c(l) = 4 ((l >> 4) & 1) + 2 ((l >> 3) & 1) + ((l >> 2)
@@ -1557,7 +1691,7 @@ __global__ void __launch_bounds__(plane_threads<R>()) k_fplane(const R* __restri
       }
     }
     __syncthreads();
-    const C* Z = lfft_lines<R, -1>(U, U2, twA, pg.a);
+    const C* Z = lfft_any<R, -1>(U, U2, twA, pg.a);
     for (int e = threadIdx.x; e < nb2 * np; e += blockDim.x) {
       const int c = fast_div(e, pg.nb2_magic);
       const int m = e - c * nb2;
@@ -1569,7 +1703,7 @@ __global__ void __launch_bounds__(plane_threads<R>()) k_fplane(const R* __restri
     }
   }
   __syncthreads();
-  const C* Y = lfft_lines<R, -1>(T, U, twB, pg.b);
+  const C* Y = lfft_any<R, -1>(T, U, twB, pg.b);
   C* out = box + (size_t)blockIdx.x * pg.nb1 * nb2;
   for (int e = threadIdx.x; e < pg.nb1 * nb2; e += blockDim.x) {
     const int b1 = fast_div(e, pg.nb2_magic);
@@ -1629,7 +1763,7 @@ __global__ void __launch_bounds__(plane_threads<R>()) k_iplane(const typename Cp
     }
   }
   __syncthreads();
-  C* Yc = lfft_lines<R, -1>(T, U, twB, pg.b);  // conj of the inverse along i1
+  C* Yc = lfft_any<R, -1>(T, U, twB, pg.b);  // conj of the inverse along i1
   if (Yc != T) {
     for (int e = threadIdx.x; e < M1 * ncb; e += blockDim.x) T[e] = Yc[e];
   }
@@ -1661,7 +1795,7 @@ __global__ void __launch_bounds__(plane_threads<R>()) k_iplane(const typename Cp
       U[j * nca + c] = z;
     }
     __syncthreads();
-    const C* Zc = lfft_lines<R, -1>(U, U2, twA, pg.a);  // conj of the inverse along i2
+    const C* Zc = lfft_any<R, -1>(U, U2, twA, pg.a);  // conj of the inverse along i2
     for (int e = threadIdx.x; e < M2 * np; e += blockDim.x) {
       const int c = fast_div(e, pg.m2_magic);
       const int j = e - c * M2;
