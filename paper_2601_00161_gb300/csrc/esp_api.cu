@@ -571,6 +571,7 @@ int setup_tile_geom(esp_plan_t p) {
   g.div_E1 = magic((unsigned)g.E[1]);
   g.div_E2v = magic((unsigned)((g.E[2] + 3) / 4));
   g.div_E2g = magic((unsigned)g.E2g);
+  for (int d = 0; d < 3; ++d) g.div_T[d] = magic((unsigned)g.T[d]);
   g.deg = p->deg;
   // psi_0 is even and largest at 0 on [-1, 1]; the margin covers the polynomial fit
   g.wmax3 = (float)std::pow(p->pswf.psi_at_0 * (1.0 + 1e-6), 3.0);

@@ -187,8 +187,10 @@ __device__ __forceinline__ bool stencil_base_df(const TileGeom& g, int d, const 
   if (t < 1e-6f || t > 1.f - 1e-6f) return false;
   const int M = g.M[d];
   int b = (int)fl - ((g.P & 1) ? (g.P - 1) / 2 : g.P / 2 - 1);
-  b %= M;
-  if (b < 0) b += M;
+  if ((unsigned)b >= (unsigned)M) {  // an atom outside the primary cell (rare): wrap
+    b %= M;
+    if (b < 0) b += M;
+  }
   *base = b;
   *t_out = t;
   return true;
@@ -257,7 +259,7 @@ __global__ void __launch_bounds__(kThreads) k_bin(const IO* __restrict__ pos,
             stencil_base(reduced_coord(&g.hinv[3 * d], r), g.M[d], g.P, &b[d], &td);
             t[d] = (R)td;
           }
-          tc[d] = b[d] / g.T[d];
+          tc[d] = fast_div(b[d], g.div_T[d]);  // b < 4096, T <= 16
           lb[d] = b[d] - tc[d] * g.T[d];
         }
         tile = (tc[0] * g.nt[1] + tc[1]) * g.nt[2] + tc[2];

@@ -36,8 +36,8 @@ struct TileGeom {
   float dscalef[3];
   // M_d h^{-1}[d][e] split into two floats (hi + lo) for the compensated FP32 transform
   float Ahi[9], Alo[9];
-  // magic multipliers for division by E[1] and by ceil(E[2] / 4)
-  unsigned int div_E1, div_E2v;
+  // magic multipliers for division by E[1], by ceil(E[2] / 4) and by T[d]
+  unsigned int div_E1, div_E2v, div_T[3];
   // (max |w|)^3 over the window, with a small margin: bounds |q w0 w1 w2| / |q|
   float wmax3;
 };
