@@ -1162,24 +1162,23 @@ int esp_near(esp_plan_t p, const void* pos, const void* q, void* forces, int add
   if (!d_out || (p->n > 0 && (!pos || !q || !forces)))
     return fail(p, ESP_ERR_ARG, "pos, q, forces or d_out is NULL");
   DeviceGuard guard(p->device);
-  // cell list of the current cell: nc bins of at least r_c per axis, R neighbours each side
+  // cell list of the current cell: nc bins of at least r_c / 2 per axis, R neighbours each
+  // side, blocks of up to 2 x 2 x 2 bins per CTA
   esp::NearGeom& ng = p->ng;
   int ncells = 1;
   for (int d = 0; d < 3; ++d) {
     // perpendicular width of the cell along reduced axis d: 1 / |row d of h^{-1}|
     const double* r = p->hinv + 3 * d;
     const double width = 1.0 / std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
-    ng.nc[d] = std::max(1, (int)std::min(1024.0, std::floor(width / p->rc)));
+    ng.nc[d] = std::max(1, (int)std::min(1024.0, std::floor(2.0 * width / p->rc)));
     ng.R[d] = std::max(1, (int)std::ceil(p->rc * ng.nc[d] / width));
+    ng.B[d] = std::min(2, ng.nc[d]);
+    ng.nb[d] = (ng.nc[d] + ng.B[d] - 1) / ng.B[d];
     ncells *= ng.nc[d];
   }
-  {
-    // neighbour offsets (2R+1)^3: the kernel keeps their vectors in shared memory
-    const long noff = (long)(2 * ng.R[0] + 1) * (2 * ng.R[1] + 1) * (2 * ng.R[2] + 1);
-    if (noff > 512)
-      return fail(p, ESP_ERR_SUPPORT, "cell too narrow for the near-part cell list (more than "
-                                      "512 neighbour images): r_c is many cell widths");
-  }
+  if (esp::near_region_cells(ng) > esp::kNearMaxRegion)
+    return fail(p, ESP_ERR_SUPPORT, "cell too narrow for the near-part cell list (a block's "
+                                    "neighbourhood exceeds 2048 cells): r_c is many cell widths");
   for (int i = 0; i < 9; ++i) {
     ng.h[i] = p->h[i];
     ng.hinv[i] = p->hinv[i];
@@ -1218,7 +1217,8 @@ int esp_near(esp_plan_t p, const void* pos, const void* q, void* forces, int add
   ESP_CUDA(p, esp::launch_near_scatter(p->fp64, p->n, p->d_ncell, p->d_nrank, p->d_ncoff,
                                        p->d_nxq_tmp, p->d_nxq, p->d_nidx, st));
   ESP_CUDA(p, esp::launch_near_pairs(p->fp64, p->io_double, ng, ncells, p->d_ncoff, p->d_nxq,
-                                     p->d_nidx, p->d_neartab, forces, add, d_out, st));
+                                     p->d_nidx, p->d_neartab, p->d_nxq_tmp, forces, add, p->n,
+                                     d_out, st));
   return ESP_OK;
 }
 

@@ -2286,26 +2286,21 @@ template <typename V>
 __global__ void __launch_bounds__(kThreads) k_near_scatter(int64_t n, const int* __restrict__ cell,
                                                            const int* __restrict__ rank,
                                                            const int* __restrict__ coff,
-                                                           const V* __restrict__ xq_tmp,
+                                                           V* __restrict__ xq_tmp,
                                                            V* __restrict__ xq,
                                                            int* __restrict__ idx) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int c = cell[i];
+    const V v = xq_tmp[i];
+    xq_tmp[i] = V{};  // the array is the pair kernel's force accumulator next
     if (c < 0) continue;
     const int dst = coff[c] + rank[i];
-    xq[dst] = xq_tmp[i];
+    xq[dst] = v;
     idx[dst] = (int)i;
   }
 }
 
-// One CTA per cell, one warp per atom of the cell at a time.  The lanes stride over the
-// atoms of the neighbour cells (coalesced, shared through L1 by the CTA's warps); the
-// pair vector of an atom in cell c and an image in the unwrapped neighbour c + o is
-// x_i - x_j - h o / nc, x the positions relative to the cell corners, so FP32 differences
-// stay small.  Pairs within r_c go through a warp queue (ballot + population count) and
-// are worked 32 at a time, every lane busy.  A full list: each pair is met from both
-// ends, the energy and virial take half of each.
 // sum over the warp of a compensated FP32 value (or a double on the FP64 path)
 __device__ __forceinline__ double warp_total(const Sum<float>& s) {
   DF v = s.d;
@@ -2320,58 +2315,113 @@ __device__ __forceinline__ double warp_total(const Sum<float>& s) {
 }
 __device__ __forceinline__ double warp_total(const Sum<double>& s) { return warp_sum(s.v); }
 
-// Candidates (atoms of the neighbour cells) a CTA holds in shared memory at a time.
+// Candidates (atoms of the block's neighbourhood) a CTA holds in shared memory at a time.
 template <typename R>
 __host__ __device__ constexpr int near_cand() {
-  return std::is_same<R, float>::value ? 3072 : 1536;
+  return std::is_same<R, float>::value ? 2048 : 1024;
 }
-__host__ __device__ inline size_t near_smem_bytes(bool fp64, int noff) {
-  const size_t v4 = fp64 ? 32 : 16;
-  return (size_t)noff * (v4 + 2 * sizeof(int)) + sizeof(int) + 15 +
-         (size_t)(fp64 ? near_cand<double>() : near_cand<float>()) * v4;
+// dynamic shared memory of k_near_pairs for a neighbourhood of nreg cells: candidates
+// (position, charge), their force sums (3 per candidate), and per cell its displacement,
+// wrapped id and the prefix sum of the atom counts
+__host__ __device__ inline size_t near_smem_bytes(bool fp64, int nreg) {
+  const size_t es = fp64 ? 8 : 4;
+  const size_t kc = fp64 ? near_cand<double>() : near_cand<float>();
+  return kc * (4 * es + 3 * es) + (size_t)nreg * (4 * es + sizeof(int)) +
+         ((size_t)nreg + 1) * sizeof(int);
 }
 
-// One CTA per cell of the cell list.  noff = (2 R0 + 1)(2 R1 + 1)(2 R2 + 1) neighbour
-// offsets; shared memory holds their displacement vectors h o / nc, wrapped cell ids and
-// the prefix sums of their atom counts, and the candidates: the neighbour cells' atoms,
-// shifted to the CTA's cell corner, one after the other (in chunks of near_cand when they
-// do not fit).  A warp takes one atom of the cell at a time; its lanes stride over the
-// candidates, the pairs within r_c go through a warp queue (ballot and population count)
-// and are worked 32 at a time.  Each lane sums its pair terms of the atom in plain
-// precision and adds them once per atom to its compensated running sums (FP32 path).
-template <typename R, typename IO>
+// psi pair of the near kernel: N-part factor g1 = 1 - phi_0(u) and force factor
+// g2 = 1 - phi_0(u) + u psi_0(u) / C_0 from a shared-memory table of kRadialPieces pieces
+// with interleaved coefficients (g1_k, g2_k) of (u - centre)^k.  FP32: both polynomials in
+// step as packed pairs.
+__device__ __forceinline__ void near_eval(const float2* __restrict__ t2, int nd, float u,
+                                          float* g1, float* g2) {
+  int piece = (int)(u * (float)kRadialPieces);
+  piece = piece < 0 ? 0 : (piece >= kRadialPieces ? kRadialPieces - 1 : piece);
+  const float tau = u - ((float)piece + 0.5f) / (float)kRadialPieces;
+  const unsigned long long* c = reinterpret_cast<const unsigned long long*>(t2 + piece * (nd + 1));
+  const unsigned long long tt = pack2(tau, tau);
+  unsigned long long v = c[nd];
+  for (int k = nd - 1; k >= 0; --k) asm("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(v) : "l"(tt), "l"(c[k]));
+  unpack2(v, *g1, *g2);
+}
+__device__ __forceinline__ void near_eval(const double2* __restrict__ t2, int nd, double u,
+                                          double* g1, double* g2) {
+  int piece = (int)(u * (double)kRadialPieces);
+  piece = piece < 0 ? 0 : (piece >= kRadialPieces ? kRadialPieces - 1 : piece);
+  const double tau = u - ((double)piece + 0.5) / (double)kRadialPieces;
+  const double2* c = t2 + piece * (nd + 1);
+  double a = c[nd].x, b = c[nd].y;
+  for (int k = nd - 1; k >= 0; --k) {
+    a = fma(a, tau, c[k].x);
+    b = fma(b, tau, c[k].y);
+  }
+  *g1 = a;
+  *g2 = b;
+}
+
+// Half-shell pair sum of the near part.  A CTA takes a block of B0 x B1 x B2 cells of the
+// cell list (cells at least r_c / 2 wide, reach R cells per side).  Each pair of atoms and
+// periodic image is met once: from the cell c of atom i, the offsets o in [-R, R]^3 that
+// come after (0, 0, 0) in the order (o0, o1, o2), and within c itself the atoms after i.
+// The CTA's neighbourhood is the (hb0 + R0) x (hb1 + 2 R1) x (hb2 + 2 R2) cells that these
+// offsets reach from its block, held in shared memory as rows along axis 2 (a row of
+// consecutive cells is one contiguous range of candidates), positions relative to the
+// block's corner cell.  A warp takes one atom of the block at a time, its lanes stride
+// over the 2 R2 + 1 cells of each forward row, and the pairs within r_c go through a warp
+// queue (ballot and population count) and are worked 32 at a time.  The pair force goes
+// to atom i in registers (summed over the warp once per atom) and, with the opposite
+// sign, to the candidate's sums in shared memory; those are added once per chunk to the
+// sorted-order accumulator fsort (vector atomics).  Energy and virial count each pair
+// once; the FP32 path sums them per lane in plain precision per atom and adds that to
+// compensated running sums.
+template <typename R>
 __global__ void __launch_bounds__(kThreads) k_near_pairs(NearGeom ng, const int* __restrict__ coff,
                                                          const typename Vec4<R>::T* __restrict__ xq,
-                                                         const int* __restrict__ idx,
                                                          const R* __restrict__ tab,
-                                                         IO* __restrict__ forces, int add,
+                                                         typename Vec4<R>::T* __restrict__ fsort,
                                                          double* __restrict__ out) {
   using V4 = typename Vec4<R>::T;
+  using R2 = typename std::conditional<std::is_same<R, float>::value, float2, double2>::type;
   constexpr int kQ = 64;  // queue ring per warp
   constexpr int KC = near_cand<R>();
-  __shared__ V4 Q[kThreads / 32][kQ];  // (r_ij, q_j)
-  __shared__ double part[kThreads / 32][7];
+  constexpr int NW = kThreads / 32;
+  __shared__ V4 Q[NW][kQ];   // (r_ij, q_j)
+  __shared__ int QJ[NW][kQ];  // candidate slot of the entry
+  __shared__ R2 TAB[kRadialPieces * (kMaxDeg + 1)];
+  __shared__ double part[NW][7];
+  __shared__ int HPRE[9];  // prefix sums of the home cells' atom counts
+  __shared__ int HT[8];    // neighbourhood index of each home cell
   extern __shared__ __align__(16) unsigned char near_smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
   V4* q_w = Q[warp];
-  const int C = blockIdx.x;
-  const int c2 = C % ng.nc[2], c1 = (C / ng.nc[2]) % ng.nc[1], c0 = C / (ng.nc[2] * ng.nc[1]);
-  const int ib = coff[C], ie = coff[C + 1];
-  const int s0 = 2 * ng.R[0] + 1, s1 = 2 * ng.R[1] + 1, s2 = 2 * ng.R[2] + 1;
-  const int noff = s0 * s1 * s2;
+  int* qj_w = QJ[warp];
+
+  const int blk = blockIdx.x;
+  const int k2 = blk % ng.nb[2], k1 = (blk / ng.nb[2]) % ng.nb[1], k0b = blk / (ng.nb[2] * ng.nb[1]);
+  const int hb0 = min(ng.B[0], ng.nc[0] - k0b * ng.B[0]);
+  const int hb1 = min(ng.B[1], ng.nc[1] - k1 * ng.B[1]);
+  const int hb2 = min(ng.B[2], ng.nc[2] - k2 * ng.B[2]);
+  const int R0 = ng.R[0], R1 = ng.R[1], R2c = ng.R[2];
+  const int RY = hb1 + 2 * R1, RZ = hb2 + 2 * R2c;
+  const int nreg = (hb0 + R0) * RY * RZ;
+
   V4* CB = reinterpret_cast<V4*>(near_smem);
-  V4* OFF = CB + KC;
-  int* NC = reinterpret_cast<int*>(OFF + noff);
-  int* PRE = NC + noff;  // noff + 1 prefix sums of the neighbour cells' atom counts
-  for (int t = threadIdx.x; t < noff; t += blockDim.x) {
-    const int o0 = t / (s1 * s2) - ng.R[0], o1 = (t / s2) % s1 - ng.R[1], o2 = t % s2 - ng.R[2];
-    const int w0 = (((c0 + o0) % ng.nc[0]) + ng.nc[0]) % ng.nc[0];
-    const int w1 = (((c1 + o1) % ng.nc[1]) + ng.nc[1]) % ng.nc[1];
-    const int w2 = (((c2 + o2) % ng.nc[2]) + ng.nc[2]) % ng.nc[2];
+  R* FJ = reinterpret_cast<R*>(CB + KC);  // x, y, z sums: FJ[e * KC + k]
+  V4* OFF = reinterpret_cast<V4*>(FJ + 3 * KC);
+  int* NC = reinterpret_cast<int*>(OFF + nreg);
+  int* PRE = NC + nreg;  // nreg + 1 prefix sums of the cells' atom counts
+
+  for (int t = threadIdx.x; t < nreg; t += blockDim.x) {
+    const int r0 = t / (RY * RZ), r1 = (t / RZ) % RY - R1, r2 = t % RZ - R2c;
+    const int u0 = k0b * ng.B[0] + r0, u1 = k1 * ng.B[1] + r1, u2 = k2 * ng.B[2] + r2;
+    const int w0 = ((u0 % ng.nc[0]) + ng.nc[0]) % ng.nc[0];
+    const int w1 = ((u1 % ng.nc[1]) + ng.nc[1]) % ng.nc[1];
+    const int w2 = ((u2 % ng.nc[2]) + ng.nc[2]) % ng.nc[2];
     NC[t] = (w0 * ng.nc[1] + w1) * ng.nc[2] + w2;
-    // h o / nc: the corner of the unwrapped neighbour relative to this cell's corner
-    const double f0 = (double)o0 / ng.nc[0], f1 = (double)o1 / ng.nc[1], f2 = (double)o2 / ng.nc[2];
+    // the corner of unwrapped cell u relative to the block's corner cell: h (u - u_0) / nc
+    const double f0 = (double)r0 / ng.nc[0], f1 = (double)r1 / ng.nc[1], f2 = (double)r2 / ng.nc[2];
     V4 d;
     d.x = (R)(ng.h[0] * f0 + ng.h[1] * f1 + ng.h[2] * f2);
     d.y = (R)(ng.h[3] * f0 + ng.h[4] * f1 + ng.h[5] * f2);
@@ -2379,33 +2429,65 @@ __global__ void __launch_bounds__(kThreads) k_near_pairs(NearGeom ng, const int*
     d.w = R(0);
     OFF[t] = d;
   }
+  const int nd = ng.ndeg;
+  for (int e = threadIdx.x; e < kRadialPieces * (nd + 1); e += blockDim.x) {
+    const int pc = e / (nd + 1), k = e - pc * (nd + 1);
+    R2 v;
+    v.x = tab[pc * (nd + 1) + k];
+    v.y = tab[(kRadialPieces + pc) * (nd + 1) + k];
+    TAB[e] = v;
+  }
+  for (int e = threadIdx.x; e < 3 * KC; e += blockDim.x) FJ[e] = R(0);
   __syncthreads();
   if (warp == 0) {
     int carry = 0;
-    for (int base = 0; base < noff; base += 32) {
+    for (int base = 0; base < nreg; base += 32) {
       const int t = base + lane;
-      const int v = t < noff ? coff[NC[t] + 1] - coff[NC[t]] : 0;
+      const int v = t < nreg ? coff[NC[t] + 1] - coff[NC[t]] : 0;
       int x = v;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const int y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
       }
-      if (t < noff) PRE[t] = carry + x - v;
+      if (t < nreg) PRE[t] = carry + x - v;
       carry += __shfl_sync(0xffffffffu, x, 31);
     }
-    if (lane == 0) PRE[noff] = carry;
+    if (lane == 0) PRE[nreg] = carry;
+    // home cells (h0, h1, h2) of the block in that order: their neighbourhood index and
+    // the prefix sums of their atom counts
+    const int nh = hb0 * hb1 * hb2;
+    int v = 0, th = 0;
+    if (lane < nh) {
+      const int h0 = lane / (hb1 * hb2), h1 = (lane / hb2) % hb1, h2 = lane % hb2;
+      th = (h0 * RY + h1 + R1) * RZ + h2 + R2c;
+      v = coff[NC[th] + 1] - coff[NC[th]];
+    }
+    int x = v;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane < nh) {
+      HT[lane] = th;
+      HPRE[lane] = x - v;
+    }
+    if (lane == nh - 1) HPRE[nh] = x;
   }
   __syncthreads();
-  const int total = PRE[noff];
+  const int total = PRE[nreg];
+  const int nh = hb0 * hb1 * hb2;
+  const int nhome = HPRE[nh];
+  if (nhome == 0) return;  // CTA-uniform
   const R rc2 = (R)(ng.rc * ng.rc), inv_rc = (R)ng.inv_rc;
   Sum<R> U, W[6];  // per lane over all of the warp's atoms
 
-  for (int k0 = 0; k0 < total; k0 += KC) {
-    const int kn = min(KC, total - k0);
-    __syncthreads();  // the previous chunk of candidates is consumed
-    for (int t = warp; t < noff; t += kThreads / 32) {
-      const int a = max(PRE[t], k0), b = min(PRE[t + 1], k0 + kn);
+  for (int c0 = 0; c0 < total; c0 += KC) {
+    const int kn = min(KC, total - c0);
+    if (c0 > 0) __syncthreads();  // the previous chunk's sums are flushed
+    for (int t = warp; t < nreg; t += NW) {
+      const int a = max(PRE[t], c0), b = min(PRE[t + 1], c0 + kn);
       if (a >= b) continue;
       const int jb = coff[NC[t]] + (a - PRE[t]);
       const V4 d = OFF[t];
@@ -2414,17 +2496,32 @@ __global__ void __launch_bounds__(kThreads) k_near_pairs(NearGeom ng, const int*
         xj.x += d.x;
         xj.y += d.y;
         xj.z += d.z;
-        CB[k - k0] = xj;
+        CB[k - c0] = xj;
       }
     }
     __syncthreads();
-    for (int i = ib + warp; i < ie; i += kThreads / 32) {
-      const V4 xi = xq[i];
+    for (int hi = warp; hi < nhome; hi += NW) {
+      int h = 0;
+      while (h + 1 < nh && HPRE[h + 1] <= hi) ++h;
+      const int th = HT[h];
+      const int rank = hi - HPRE[h];
+      const int si = coff[NC[th]] + rank;  // sorted index of atom i
+      const int ib = PRE[th] + rank;       // its slot in the neighbourhood
+      const int h0 = h / (hb1 * hb2), h1 = (h / hb2) % hb1, h2 = h - (h / hb2) * hb2;
+      V4 xi = xq[si];
+      {
+        const V4 d = OFF[th];
+        xi.x += d.x;
+        xi.y += d.y;
+        xi.z += d.z;
+      }
       R fx = R(0), fy = R(0), fz = R(0), u = R(0), w[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
-      // the pair terms of queue entries [h, h + m), lane l taking entry h + l
-      auto work = [&](int h, int m) {
+      // the pair terms of queue entries [qs, qs + m), lane l taking entry qs + l
+      auto work = [&](int qs, int m) {
         if (lane < m) {
-          const V4 e4 = q_w[(h + lane) & (kQ - 1)];
+          const int e = (qs + lane) & (kQ - 1);
+          const V4 e4 = q_w[e];
+          const int js = qj_w[e];
           const R rx = e4.x, ry = e4.y, rz = e4.z;
           const R r2 = rx * rx + ry * ry + rz * rz;
           R inv_r, r;
@@ -2436,45 +2533,70 @@ __global__ void __launch_bounds__(kThreads) k_near_pairs(NearGeom ng, const int*
             inv_r = R(1) / r;
           }
           R g1, g2;
-          radial_eval<R>(tab, ng.ndeg, r * inv_rc, &g1, &g2);
+          near_eval(TAB, nd, r * inv_rc, &g1, &g2);
           const R qq = xi.w * e4.w;
-          const R e = qq * g1 * inv_r;
+          const R en = qq * g1 * inv_r;
           const R f = qq * g2 * inv_r * inv_r * inv_r;
-          fx = fma(f, rx, fx);
-          fy = fma(f, ry, fy);
-          fz = fma(f, rz, fz);
-          const R hf = R(0.5) * f;
-          u = fma(R(0.5), e, u);
-          w[0] = fma(hf * rx, rx, w[0]);
-          w[1] = fma(hf * ry, ry, w[1]);
-          w[2] = fma(hf * rz, rz, w[2]);
-          w[3] = fma(hf * rx, ry, w[3]);
-          w[4] = fma(hf * rx, rz, w[4]);
-          w[5] = fma(hf * ry, rz, w[5]);
+          const R px = f * rx, py = f * ry, pz = f * rz;
+          fx += px;
+          fy += py;
+          fz += pz;
+          atomicAdd(FJ + js, -px);
+          atomicAdd(FJ + KC + js, -py);
+          atomicAdd(FJ + 2 * KC + js, -pz);
+          u += en;
+          w[0] = fma(px, rx, w[0]);
+          w[1] = fma(py, ry, w[1]);
+          w[2] = fma(pz, rz, w[2]);
+          w[3] = fma(px, ry, w[3]);
+          w[4] = fma(px, rz, w[4]);
+          w[5] = fma(py, rz, w[5]);
         }
       };
       int qh = 0, qn = 0;  // queue head and length (warp-uniform)
-      for (int k = 0; k < kn; k += 32) {
-        bool pass = false;
-        V4 ent{};
-        if (k + lane < kn) {
-          const V4 xj = CB[k + lane];
-          ent.x = xi.x - xj.x;
-          ent.y = xi.y - xj.y;
-          ent.z = xi.z - xj.z;
-          ent.w = xj.w;
-          const R r2 = ent.x * ent.x + ent.y * ent.y + ent.z * ent.z;
-          pass = r2 > R(0) && r2 <= rc2;
+      // candidates [a, b) of the neighbourhood (clipped to this chunk)
+      auto scan = [&](int a, int b) {
+        a = max(a, c0);
+        b = min(b, c0 + kn);
+        for (int k = a; k < b; k += 32) {
+          bool pass = false;
+          V4 ent{};
+          const int kk = k + lane - c0;
+          if (k + lane < b) {
+            const V4 xj = CB[kk];
+            ent.x = xi.x - xj.x;
+            ent.y = xi.y - xj.y;
+            ent.z = xi.z - xj.z;
+            ent.w = xj.w;
+            const R r2 = ent.x * ent.x + ent.y * ent.y + ent.z * ent.z;
+            pass = r2 > R(0) && r2 <= rc2;
+          }
+          const unsigned m = __ballot_sync(0xffffffffu, pass);
+          if (pass) {
+            const int e = (qh + qn + __popc(m & lt)) & (kQ - 1);
+            q_w[e] = ent;
+            qj_w[e] = kk;
+          }
+          qn += __popc(m);
+          __syncwarp();
+          if (qn >= 32) {
+            work(qh, 32);
+            qh = (qh + 32) & (kQ - 1);
+            qn -= 32;
+            __syncwarp();  // the worked entries may be overwritten now
+          }
         }
-        const unsigned m = __ballot_sync(0xffffffffu, pass);
-        if (pass) q_w[(qh + qn + __popc(m & lt)) & (kQ - 1)] = ent;
-        qn += __popc(m);
-        __syncwarp();
-        if (qn >= 32) {
-          work(qh, 32);
-          qh = (qh + 32) & (kQ - 1);
-          qn -= 32;
-          __syncwarp();  // the worked entries may be overwritten now
+      };
+      // forward rows: (o0, o1) after (0, 0); in row (0, 0) the atoms after i up to the
+      // cell R2 ahead
+      for (int o0 = 0; o0 <= R0; ++o0) {
+        for (int o1 = (o0 == 0 ? 0 : -R1); o1 <= R1; ++o1) {
+          const int row = ((h0 + o0) * RY + h1 + o1 + R1) * RZ;
+          const int last = PRE[row + h2 + 2 * R2c + 1];
+          if (o0 == 0 && o1 == 0)
+            scan(ib + 1, last);
+          else
+            scan(PRE[row + h2], last);
         }
       }
       work(qh, qn);
@@ -2482,16 +2604,45 @@ __global__ void __launch_bounds__(kThreads) k_near_pairs(NearGeom ng, const int*
       U.add(u);
 #pragma unroll
       for (int c = 0; c < 6; ++c) W[c].add(w[c]);
-      Sum<R> sx, sy, sz;
-      sx.add(fx);
-      sy.add(fy);
-      sz.add(fz);
-      const double F[3] = {warp_total(sx), warp_total(sy), warp_total(sz)};
-      if (lane < 3) {
-        const int a = idx[i];
-        // later chunks add to what the earlier ones of this atom wrote
-        const double base = (add || k0 > 0) ? (double)forces[3 * (int64_t)a + lane] : 0.0;
-        forces[3 * (int64_t)a + lane] = (IO)(base + F[lane]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        fx += __shfl_xor_sync(0xffffffffu, fx, o);
+        fy += __shfl_xor_sync(0xffffffffu, fy, o);
+        fz += __shfl_xor_sync(0xffffffffu, fz, o);
+      }
+      if (lane == 0) {
+        if constexpr (std::is_same<R, float>::value) {
+          atomicAdd(fsort + si, make_float4(fx, fy, fz, 0.f));
+        } else {
+          R* fs = reinterpret_cast<R*>(fsort + si);
+          atomicAdd(fs, fx);
+          atomicAdd(fs + 1, fy);
+          atomicAdd(fs + 2, fz);
+        }
+      }
+    }
+    __syncthreads();
+    // the candidates' sums of this chunk go to the sorted-order accumulator
+    for (int t = warp; t < nreg; t += NW) {
+      const int a = max(PRE[t], c0), b = min(PRE[t + 1], c0 + kn);
+      if (a >= b) continue;
+      const int jb = coff[NC[t]] + (a - PRE[t]);
+      for (int k = a + lane; k < b; k += 32) {
+        const int s = k - c0;
+        const R vx = FJ[s], vy = FJ[KC + s], vz = FJ[2 * KC + s];
+        if (vx != R(0) || vy != R(0) || vz != R(0)) {
+          FJ[s] = R(0);
+          FJ[KC + s] = R(0);
+          FJ[2 * KC + s] = R(0);
+          if constexpr (std::is_same<R, float>::value) {
+            atomicAdd(fsort + jb + (k - a), make_float4(vx, vy, vz, 0.f));
+          } else {
+            R* fs = reinterpret_cast<R*>(fsort + jb + (k - a));
+            atomicAdd(fs, vx);
+            atomicAdd(fs + 1, vy);
+            atomicAdd(fs + 2, vz);
+          }
+        }
       }
     }
   }
@@ -2505,8 +2656,31 @@ __global__ void __launch_bounds__(kThreads) k_near_pairs(NearGeom ng, const int*
   __syncthreads();
   if (threadIdx.x < 7) {
     double t = 0.0;
-    for (int w = 0; w < kThreads / 32; ++w) t += part[w][threadIdx.x];
+    for (int w = 0; w < NW; ++w) t += part[w][threadIdx.x];
     if (t != 0.0) atomicAdd(out + threadIdx.x, t);
+  }
+}
+
+// Near forces from the sorted-order accumulator to the caller's array (input order):
+// overwritten, or added to when add != 0.
+template <typename R, typename IO>
+__global__ void __launch_bounds__(kThreads) k_near_out(const int* __restrict__ coff, int ncells,
+                                                       const int* __restrict__ idx,
+                                                       const typename Vec4<R>::T* __restrict__ fsort,
+                                                       IO* __restrict__ forces, int add) {
+  const int ns = coff[ncells];
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < ns; s += gridDim.x * blockDim.x) {
+    const typename Vec4<R>::T f = fsort[s];
+    IO* dst = forces + 3 * (int64_t)idx[s];
+    if (add) {
+      dst[0] = (IO)((double)dst[0] + (double)f.x);
+      dst[1] = (IO)((double)dst[1] + (double)f.y);
+      dst[2] = (IO)((double)dst[2] + (double)f.z);
+    } else {
+      dst[0] = (IO)f.x;
+      dst[1] = (IO)f.y;
+      dst[2] = (IO)f.z;
+    }
   }
 }
 
@@ -3111,42 +3285,54 @@ cudaError_t launch_near_scan(int* ccount, int* coff, int ncells, cudaStream_t st
 }
 
 cudaError_t launch_near_scatter(bool fp64, int64_t n, const int* cell, const int* rank,
-                                const int* coff, const void* xq_tmp, void* xq, int* idx,
+                                const int* coff, void* xq_tmp, void* xq, int* idx,
                                 cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const int nb = grid_blocks(n);
   if (fp64)
-    k_near_scatter<double4><<<nb, kThreads, 0, st>>>(n, cell, rank, coff, (const double4*)xq_tmp,
+    k_near_scatter<double4><<<nb, kThreads, 0, st>>>(n, cell, rank, coff, (double4*)xq_tmp,
                                                      (double4*)xq, idx);
   else
-    k_near_scatter<float4><<<nb, kThreads, 0, st>>>(n, cell, rank, coff, (const float4*)xq_tmp,
+    k_near_scatter<float4><<<nb, kThreads, 0, st>>>(n, cell, rank, coff, (float4*)xq_tmp,
                                                     (float4*)xq, idx);
   return cudaGetLastError();
 }
 
+int near_region_cells(const NearGeom& ng) {
+  return (ng.B[0] + ng.R[0]) * (ng.B[1] + 2 * ng.R[1]) * (ng.B[2] + 2 * ng.R[2]);
+}
+
 cudaError_t launch_near_pairs(bool fp64, bool io_double, const NearGeom& ng, int ncells,
-                             const int* coff, const void* xq, const int* idx, const void* tab,
-                             void* forces, int add, double* out, cudaStream_t st) {
+                              const int* coff, const void* xq, const int* idx, const void* tab,
+                              void* fsort, void* forces, int add, int64_t n, double* out,
+                              cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(out, 0, 7 * sizeof(double), st);
-  if (e != cudaSuccess || ncells <= 0) return e;
-  const int noff = (2 * ng.R[0] + 1) * (2 * ng.R[1] + 1) * (2 * ng.R[2] + 1);
-  if (noff > 512) return cudaErrorInvalidValue;  // the host rejects such cells first
-  const size_t smem = near_smem_bytes(fp64, noff);
+  if (e != cudaSuccess || ncells <= 0 || n <= 0) return e;
+  const int nreg = near_region_cells(ng);
+  if (nreg > kNearMaxRegion) return cudaErrorInvalidValue;  // the host rejects such cells first
+  const int nblocks = ng.nb[0] * ng.nb[1] * ng.nb[2];
+  const size_t smem = near_smem_bytes(fp64, nreg);
   auto cfg = [&](auto kern) {
     return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   };
-  if ((e = fp64 ? cfg(k_near_pairs<double, double>)
-                : (io_double ? cfg(k_near_pairs<float, double>) : cfg(k_near_pairs<float, float>))))
-    return e;
+  if ((e = fp64 ? cfg(k_near_pairs<double>) : cfg(k_near_pairs<float>))) return e;
   if (fp64)
-    k_near_pairs<double, double><<<ncells, kThreads, smem, st>>>(
-        ng, coff, (const double4*)xq, idx, (const double*)tab, (double*)forces, add, out);
-  else if (io_double)
-    k_near_pairs<float, double><<<ncells, kThreads, smem, st>>>(
-        ng, coff, (const float4*)xq, idx, (const float*)tab, (double*)forces, add, out);
+    k_near_pairs<double><<<nblocks, kThreads, smem, st>>>(ng, coff, (const double4*)xq,
+                                                          (const double*)tab, (double4*)fsort, out);
   else
-    k_near_pairs<float, float><<<ncells, kThreads, smem, st>>>(
-        ng, coff, (const float4*)xq, idx, (const float*)tab, (float*)forces, add, out);
+    k_near_pairs<float><<<nblocks, kThreads, smem, st>>>(ng, coff, (const float4*)xq,
+                                                         (const float*)tab, (float4*)fsort, out);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int nb = grid_blocks(n);
+  if (fp64)
+    k_near_out<double, double><<<nb, kThreads, 0, st>>>(coff, ncells, idx, (const double4*)fsort,
+                                                        (double*)forces, add);
+  else if (io_double)
+    k_near_out<float, double><<<nb, kThreads, 0, st>>>(coff, ncells, idx, (const float4*)fsort,
+                                                       (double*)forces, add);
+  else
+    k_near_out<float, float><<<nb, kThreads, 0, st>>>(coff, ncells, idx, (const float4*)fsort,
+                                                      (float*)forces, add);
   return cudaGetLastError();
 }
 

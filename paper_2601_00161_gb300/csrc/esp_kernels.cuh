@@ -132,8 +132,10 @@ struct Bins {
 // (each bin at least r_c thick when nc[d] > 1) and R[d] neighbour bins on either side, so
 // every pair and periodic image within r_c is found exactly once.
 struct NearGeom {
-  int nc[3];
-  int R[3];
+  int nc[3];  // cells per axis, each at least r_c / 2 wide
+  int R[3];   // reach: cells per side that cover r_c
+  int B[3];   // cells per block (one CTA), at most 2 per axis
+  int nb[3];  // blocks per axis
   double h[9];     // row-major
   double hinv[9];  // row-major
   double rc, inv_rc;
@@ -320,19 +322,24 @@ cudaError_t launch_gather(bool fp64, bool io_double, bool bf16, const GatherGeom
                           void* forces, cudaStream_t st);
 // Near part.  bin: cell id, rank within the cell and the atom's position relative to its
 // cell corner (with q) in the input order; ccount (ncells ints) zero on entry.  scan:
-// coff[0..ncells] exclusive offsets, ccount zeroed again.  scatter: cell order.  pairs:
-// forces (overwritten, or added to when add != 0) and out[0..6] = U_N, W_N xx yy zz xy xz
-// yz (overwritten).
+// coff[0..ncells] exclusive offsets, ccount zeroed again.  scatter: cell order, and
+// xq_tmp zeroed (it is the pairs' sorted-order force accumulator fsort).  pairs: half-shell
+// pair sums over blocks of B cells, then the forces to the caller's array in input order
+// (overwritten, or added to when add != 0), out[0..6] = U_N, W_N xx yy zz xy xz yz
+// (overwritten).
+constexpr int kNearMaxRegion = 2048;  // cells of one block's neighbourhood
+int near_region_cells(const NearGeom& ng);
 cudaError_t launch_near_bin(bool io_double, bool fp64, const void* pos, const void* q,
                             int64_t n, const NearGeom& ng, int* ccount, int* cell, int* rank,
                             void* xq_tmp, cudaStream_t st);
 cudaError_t launch_near_scan(int* ccount, int* coff, int ncells, cudaStream_t st);
 cudaError_t launch_near_scatter(bool fp64, int64_t n, const int* cell, const int* rank,
-                                const int* coff, const void* xq_tmp, void* xq, int* idx,
+                                const int* coff, void* xq_tmp, void* xq, int* idx,
                                 cudaStream_t st);
 cudaError_t launch_near_pairs(bool fp64, bool io_double, const NearGeom& ng, int ncells,
-                             const int* coff, const void* xq, const int* idx, const void* tab,
-                             void* forces, int add, double* out, cudaStream_t st);
+                              const int* coff, const void* xq, const int* idx, const void* tab,
+                              void* fsort, void* forces, int add, int64_t n, double* out,
+                              cudaStream_t st);
 
 // Fields from the kept spectrum (kind 0: G X; 1: i k_d G X; 2: K_ab X / w^2), written as
 // 1, 3 or 6 half spectra one after the other.
