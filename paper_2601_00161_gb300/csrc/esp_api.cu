@@ -119,6 +119,7 @@ struct esp_plan_s {
   void* d_nxq_tmp = nullptr;
   void* d_nxq = nullptr;
   int* d_nidx = nullptr;
+  void* d_noff = nullptr;  // displacements of a block's neighbourhood cells
   // field variants (allocated on first use): up to 6 half spectra and 6 real grids, batched
   // inverse transforms for 3 and 6 fields
   void* d_fspec = nullptr;
@@ -425,7 +426,7 @@ void release(esp_plan_t p) {
                   p->bins.ctrl,   p->d_binpart,   p->d_accum,   p->d_partials,
                   p->d_io_pos,    p->d_io_q,     p->d_io_f,
                   p->d_neartab,   p->d_ncount,    p->d_ncoff,    p->d_ncell,     p->d_nrank,
-                  p->d_nxq_tmp,   p->d_nxq,       p->d_nidx,     p->d_fspec,     p->d_fgrid};
+                  p->d_nxq_tmp,   p->d_nxq,       p->d_nidx,     p->d_noff,      p->d_fspec,     p->d_fgrid};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (p->h_accum) cudaFreeHost(p->h_accum);
@@ -1163,7 +1164,7 @@ int esp_near(esp_plan_t p, const void* pos, const void* q, void* forces, int add
     return fail(p, ESP_ERR_ARG, "pos, q, forces or d_out is NULL");
   DeviceGuard guard(p->device);
   // cell list of the current cell: nc bins of at least r_c / 2 per axis, R neighbours each
-  // side, blocks of up to 2 x 2 x 2 bins per CTA
+  // side, blocks of up to 2 x 2 x 4 bins per CTA
   esp::NearGeom& ng = p->ng;
   int ncells = 1;
   for (int d = 0; d < 3; ++d) {
@@ -1172,13 +1173,15 @@ int esp_near(esp_plan_t p, const void* pos, const void* q, void* forces, int add
     const double width = 1.0 / std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
     ng.nc[d] = std::max(1, (int)std::min(1024.0, std::floor(2.0 * width / p->rc)));
     ng.R[d] = std::max(1, (int)std::ceil(p->rc * ng.nc[d] / width));
-    ng.B[d] = std::min(2, ng.nc[d]);
+    ng.B[d] = std::min(d == 2 ? 4 : 2, ng.nc[d]);
     ng.nb[d] = (ng.nc[d] + ng.B[d] - 1) / ng.B[d];
     ncells *= ng.nc[d];
   }
-  if (esp::near_region_cells(ng) > esp::kNearMaxRegion)
+  if (esp::near_region_cells(ng) > esp::kNearMaxRegion ||
+      esp::near_pairs_smem(p->fp64, ng) > esp::kNearMaxSmem)
     return fail(p, ESP_ERR_SUPPORT, "cell too narrow for the near-part cell list (a block's "
-                                    "neighbourhood exceeds 2048 cells): r_c is many cell widths");
+                                    "neighbourhood exceeds 2048 cells or the shared memory of "
+                                    "the pair kernel): r_c is many cell widths");
   for (int i = 0; i < 9; ++i) {
     ng.h[i] = p->h[i];
     ng.hinv[i] = p->hinv[i];
@@ -1197,6 +1200,7 @@ int esp_near(esp_plan_t p, const void* pos, const void* q, void* forces, int add
     ESP_CUDA(p, cudaMalloc(&p->d_nidx, nn * sizeof(int)));
     ESP_CUDA(p, cudaMalloc(&p->d_nxq_tmp, nn * 4 * es));
     ESP_CUDA(p, cudaMalloc(&p->d_nxq, nn * 4 * es));
+    ESP_CUDA(p, cudaMalloc(&p->d_noff, (size_t)esp::kNearMaxRegion * 4 * es));
   }
   ng.ndeg = p->near_ndeg;
   if (ncells > p->near_cells_alloc) {
@@ -1217,8 +1221,8 @@ int esp_near(esp_plan_t p, const void* pos, const void* q, void* forces, int add
   ESP_CUDA(p, esp::launch_near_scatter(p->fp64, p->n, p->d_ncell, p->d_nrank, p->d_ncoff,
                                        p->d_nxq_tmp, p->d_nxq, p->d_nidx, st));
   ESP_CUDA(p, esp::launch_near_pairs(p->fp64, p->io_double, ng, ncells, p->d_ncoff, p->d_nxq,
-                                     p->d_nidx, p->d_neartab, p->d_nxq_tmp, forces, add, p->n,
-                                     d_out, st));
+                                     p->d_nidx, p->d_neartab, p->d_noff, p->d_nxq_tmp, forces,
+                                     add, p->n, d_out, st));
   return ESP_OK;
 }
 

@@ -2292,12 +2292,13 @@ __global__ void __launch_bounds__(kThreads) k_near_scatter(int64_t n, const int*
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int c = cell[i];
-    const V v = xq_tmp[i];
-    xq_tmp[i] = V{};  // the array is the pair kernel's force accumulator next
-    if (c < 0) continue;
-    const int dst = coff[c] + rank[i];
-    xq[dst] = v;
-    idx[dst] = (int)i;
+    if (c >= 0) {
+      const int dst = coff[c] + rank[i];
+      xq[dst] = xq_tmp[i];
+      idx[dst] = (int)i;
+    }
+    // the array is the pair kernel's force accumulator next
+    memset(static_cast<void*>(xq_tmp + i), 0, sizeof(V));
   }
 }
 
@@ -2320,33 +2321,43 @@ template <typename R>
 __host__ __device__ constexpr int near_cand() {
   return std::is_same<R, float>::value ? 2048 : 1024;
 }
-// dynamic shared memory of k_near_pairs for a neighbourhood of nreg cells: candidates
-// (position, charge), their force sums (3 per candidate), and per cell its displacement,
-// wrapped id and the prefix sum of the atom counts
-__host__ __device__ inline size_t near_smem_bytes(bool fp64, int nreg) {
+// dynamic shared memory of k_near_pairs for a neighbourhood of nreg cells and nh x nrow
+// home-cell rows: candidates (position, charge) and their force sums (3 per candidate),
+// per cell its displacement, first sorted index and the prefix sum of the atom counts,
+// and the row ranges
+__host__ __device__ inline size_t near_smem_bytes(bool fp64, int nreg, int nrows) {
   const size_t es = fp64 ? 8 : 4;
   const size_t kc = fp64 ? near_cand<double>() : near_cand<float>();
-  return kc * (4 * es + 3 * es) + (size_t)nreg * (4 * es + sizeof(int)) +
-         ((size_t)nreg + 1) * sizeof(int);
+  return kc * (4 * es + 3 * es) + (size_t)nreg * (4 * es + 2 * sizeof(int)) +
+         2 * sizeof(int) + (size_t)nrows * 2 * sizeof(int);
 }
 
 // psi pair of the near kernel: N-part factor g1 = 1 - phi_0(u) and force factor
 // g2 = 1 - phi_0(u) + u psi_0(u) / C_0 from a shared-memory table of kRadialPieces pieces
-// with interleaved coefficients (g1_k, g2_k) of (u - centre)^k.  FP32: both polynomials in
-// step as packed pairs.
+// with interleaved coefficients (g1_k, g2_k) of (u - centre)^k, degree ND (compile time)
+// or nd (ND = 0).  FP32: both polynomials in step as packed pairs.
+template <int ND>
 __device__ __forceinline__ void near_eval(const float2* __restrict__ t2, int nd, float u,
                                           float* g1, float* g2) {
+  if constexpr (ND > 0) nd = ND;
   int piece = (int)(u * (float)kRadialPieces);
   piece = piece < 0 ? 0 : (piece >= kRadialPieces ? kRadialPieces - 1 : piece);
   const float tau = u - ((float)piece + 0.5f) / (float)kRadialPieces;
   const unsigned long long* c = reinterpret_cast<const unsigned long long*>(t2 + piece * (nd + 1));
   const unsigned long long tt = pack2(tau, tau);
   unsigned long long v = c[nd];
-  for (int k = nd - 1; k >= 0; --k) asm("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(v) : "l"(tt), "l"(c[k]));
+  if constexpr (ND > 0) {
+#pragma unroll
+    for (int k = ND - 1; k >= 0; --k) asm("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(v) : "l"(tt), "l"(c[k]));
+  } else {
+    for (int k = nd - 1; k >= 0; --k) asm("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(v) : "l"(tt), "l"(c[k]));
+  }
   unpack2(v, *g1, *g2);
 }
+template <int ND>
 __device__ __forceinline__ void near_eval(const double2* __restrict__ t2, int nd, double u,
                                           double* g1, double* g2) {
+  if constexpr (ND > 0) nd = ND;
   int piece = (int)(u * (double)kRadialPieces);
   piece = piece < 0 ? 0 : (piece >= kRadialPieces ? kRadialPieces - 1 : piece);
   const double tau = u - ((double)piece + 0.5) / (double)kRadialPieces;
@@ -2360,6 +2371,26 @@ __device__ __forceinline__ void near_eval(const double2* __restrict__ t2, int nd
   *g2 = b;
 }
 
+// Displacements of a block's neighbourhood cells: entry ((r0 Y) + r1) Z + r2 of the
+// largest neighbourhood (Y = B1 + 2 R1, Z = B2 + 2 R2) is h (r0, r1 - R1, r2 - R2) / nc,
+// the corner of that cell relative to the block's corner cell.
+template <typename R>
+__global__ void __launch_bounds__(kThreads) k_near_offsets(NearGeom ng,
+                                                           typename Vec4<R>::T* __restrict__ off) {
+  const int Y = ng.B[1] + 2 * ng.R[1], Z = ng.B[2] + 2 * ng.R[2];
+  const int n = (ng.B[0] + ng.R[0]) * Y * Z;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    const int r0 = t / (Y * Z), r1 = (t / Z) % Y - ng.R[1], r2 = t % Z - ng.R[2];
+    const double f0 = (double)r0 / ng.nc[0], f1 = (double)r1 / ng.nc[1], f2 = (double)r2 / ng.nc[2];
+    typename Vec4<R>::T d;
+    d.x = (R)(ng.h[0] * f0 + ng.h[1] * f1 + ng.h[2] * f2);
+    d.y = (R)(ng.h[3] * f0 + ng.h[4] * f1 + ng.h[5] * f2);
+    d.z = (R)(ng.h[6] * f0 + ng.h[7] * f1 + ng.h[8] * f2);
+    d.w = R(0);
+    off[t] = d;
+  }
+}
+
 // Half-shell pair sum of the near part.  A CTA takes a block of B0 x B1 x B2 cells of the
 // cell list (cells at least r_c / 2 wide, reach R cells per side).  Each pair of atoms and
 // periodic image is met once: from the cell c of atom i, the offsets o in [-R, R]^3 that
@@ -2367,18 +2398,19 @@ __device__ __forceinline__ void near_eval(const double2* __restrict__ t2, int nd
 // The CTA's neighbourhood is the (hb0 + R0) x (hb1 + 2 R1) x (hb2 + 2 R2) cells that these
 // offsets reach from its block, held in shared memory as rows along axis 2 (a row of
 // consecutive cells is one contiguous range of candidates), positions relative to the
-// block's corner cell.  A warp takes one atom of the block at a time, its lanes stride
+// block's corner cell.  A warp takes one atom of the block at a time; its lanes stride
 // over the 2 R2 + 1 cells of each forward row, and the pairs within r_c go through a warp
-// queue (ballot and population count) and are worked 32 at a time.  The pair force goes
+// queue of candidate slots (ballot and population count) and are worked 32 at a time.  The pair force goes
 // to atom i in registers (summed over the warp once per atom) and, with the opposite
 // sign, to the candidate's sums in shared memory; those are added once per chunk to the
 // sorted-order accumulator fsort (vector atomics).  Energy and virial count each pair
-// once; the FP32 path sums them per lane in plain precision per atom and adds that to
+// once; the FP32 path sums them per lane in plain precision over a chunk and adds that to
 // compensated running sums.
-template <typename R>
-__global__ void __launch_bounds__(kThreads) k_near_pairs(NearGeom ng, const int* __restrict__ coff,
+template <typename R, int ND>
+__global__ void __launch_bounds__(kThreads, 3) k_near_pairs(NearGeom ng, const int* __restrict__ coff,
                                                          const typename Vec4<R>::T* __restrict__ xq,
                                                          const R* __restrict__ tab,
+                                                         const typename Vec4<R>::T* __restrict__ offtab,
                                                          typename Vec4<R>::T* __restrict__ fsort,
                                                          double* __restrict__ out) {
   using V4 = typename Vec4<R>::T;
@@ -2386,16 +2418,15 @@ __global__ void __launch_bounds__(kThreads) k_near_pairs(NearGeom ng, const int*
   constexpr int kQ = 64;  // queue ring per warp
   constexpr int KC = near_cand<R>();
   constexpr int NW = kThreads / 32;
-  __shared__ V4 Q[NW][kQ];   // (r_ij, q_j)
-  __shared__ int QJ[NW][kQ];  // candidate slot of the entry
+  __shared__ int QJ[NW][kQ];  // candidate slots of the queued pairs
   __shared__ R2 TAB[kRadialPieces * (kMaxDeg + 1)];
   __shared__ double part[NW][7];
-  __shared__ int HPRE[9];  // prefix sums of the home cells' atom counts
-  __shared__ int HT[8];    // neighbourhood index of each home cell
+  __shared__ int HPRE[kNearMaxHome + 1];  // prefix sums of the home cells' atom counts
+  __shared__ int HT[kNearMaxHome];        // neighbourhood index of each home cell
+  __shared__ int HD[kNearMaxHome];        // its (h0, h1, h2) as h0 << 20 | h1 << 10 | h2
   extern __shared__ __align__(16) unsigned char near_smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned lt = (1u << lane) - 1u;
-  V4* q_w = Q[warp];
   int* qj_w = QJ[warp];
 
   const int blk = blockIdx.x;
@@ -2406,12 +2437,15 @@ __global__ void __launch_bounds__(kThreads) k_near_pairs(NearGeom ng, const int*
   const int R0 = ng.R[0], R1 = ng.R[1], R2c = ng.R[2];
   const int RY = hb1 + 2 * R1, RZ = hb2 + 2 * R2c;
   const int nreg = (hb0 + R0) * RY * RZ;
+  const int nh = hb0 * hb1 * hb2;
+  const int nrow = 1 + R1 + R0 * (2 * R1 + 1);  // forward rows of a home cell
 
   V4* CB = reinterpret_cast<V4*>(near_smem);
   R* FJ = reinterpret_cast<R*>(CB + KC);  // x, y, z sums: FJ[e * KC + k]
   V4* OFF = reinterpret_cast<V4*>(FJ + 3 * KC);
-  int* NC = reinterpret_cast<int*>(OFF + nreg);
-  int* PRE = NC + nreg;  // nreg + 1 prefix sums of the cells' atom counts
+  int* CS = reinterpret_cast<int*>(OFF + nreg);  // first sorted index of each cell
+  int* PRE = CS + nreg;                          // nreg + 1 prefix sums of the atom counts
+  int2* ROWS = reinterpret_cast<int2*>(PRE + nreg + 2);  // [home cell][row]: candidates [a, b)
 
   for (int t = threadIdx.x; t < nreg; t += blockDim.x) {
     const int r0 = t / (RY * RZ), r1 = (t / RZ) % RY - R1, r2 = t % RZ - R2c;
@@ -2419,15 +2453,11 @@ __global__ void __launch_bounds__(kThreads) k_near_pairs(NearGeom ng, const int*
     const int w0 = ((u0 % ng.nc[0]) + ng.nc[0]) % ng.nc[0];
     const int w1 = ((u1 % ng.nc[1]) + ng.nc[1]) % ng.nc[1];
     const int w2 = ((u2 % ng.nc[2]) + ng.nc[2]) % ng.nc[2];
-    NC[t] = (w0 * ng.nc[1] + w1) * ng.nc[2] + w2;
-    // the corner of unwrapped cell u relative to the block's corner cell: h (u - u_0) / nc
-    const double f0 = (double)r0 / ng.nc[0], f1 = (double)r1 / ng.nc[1], f2 = (double)r2 / ng.nc[2];
-    V4 d;
-    d.x = (R)(ng.h[0] * f0 + ng.h[1] * f1 + ng.h[2] * f2);
-    d.y = (R)(ng.h[3] * f0 + ng.h[4] * f1 + ng.h[5] * f2);
-    d.z = (R)(ng.h[6] * f0 + ng.h[7] * f1 + ng.h[8] * f2);
-    d.w = R(0);
-    OFF[t] = d;
+    const int wc = (w0 * ng.nc[1] + w1) * ng.nc[2] + w2;
+    const int cs = coff[wc];
+    CS[t] = cs;
+    PRE[t] = coff[wc + 1] - cs;  // the count, scanned below
+    OFF[t] = offtab[((r0 * (ng.B[1] + 2 * R1)) + r1 + R1) * (ng.B[2] + 2 * R2c) + r2 + R2c];
   }
   const int nd = ng.ndeg;
   for (int e = threadIdx.x; e < kRadialPieces * (nd + 1); e += blockDim.x) {
@@ -2443,41 +2473,57 @@ __global__ void __launch_bounds__(kThreads) k_near_pairs(NearGeom ng, const int*
     int carry = 0;
     for (int base = 0; base < nreg; base += 32) {
       const int t = base + lane;
-      const int v = t < nreg ? coff[NC[t] + 1] - coff[NC[t]] : 0;
+      const int v = t < nreg ? PRE[t] : 0;
       int x = v;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const int y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
       }
+      __syncwarp();
       if (t < nreg) PRE[t] = carry + x - v;
       carry += __shfl_sync(0xffffffffu, x, 31);
     }
     if (lane == 0) PRE[nreg] = carry;
-    // home cells (h0, h1, h2) of the block in that order: their neighbourhood index and
-    // the prefix sums of their atom counts
-    const int nh = hb0 * hb1 * hb2;
+    __syncwarp();
+    // home cells in the order (h0, h1, h2): neighbourhood index and prefix sums of counts
     int v = 0, th = 0;
     if (lane < nh) {
       const int h0 = lane / (hb1 * hb2), h1 = (lane / hb2) % hb1, h2 = lane % hb2;
       th = (h0 * RY + h1 + R1) * RZ + h2 + R2c;
-      v = coff[NC[th] + 1] - coff[NC[th]];
+      v = PRE[th + 1] - PRE[th];
+      HT[lane] = th;
+      HD[lane] = h0 << 20 | h1 << 10 | h2;
     }
     int x = v;
 #pragma unroll
-    for (int o = 1; o < 8; o <<= 1) {
+    for (int o = 1; o < kNearMaxHome; o <<= 1) {
       const int y = __shfl_up_sync(0xffffffffu, x, o);
       if (lane >= o) x += y;
     }
-    if (lane < nh) {
-      HT[lane] = th;
-      HPRE[lane] = x - v;
-    }
+    if (lane < nh) HPRE[lane] = x - v;
     if (lane == nh - 1) HPRE[nh] = x;
   }
   __syncthreads();
+  // forward rows of each home cell, numbered ro = 0 .. nrow - 1: row (0, 0) first (its
+  // range starts after atom i), then (0, 1 .. R1), then (o0 >= 1, -R1 .. R1)
+  for (int e = threadIdx.x; e < nh * nrow; e += blockDim.x) {
+    const int h = e / nrow, ro = e - h * nrow;
+    const int hd = HD[h];
+    const int h0 = hd >> 20, h1 = (hd >> 10) & 1023, h2 = hd & 1023;
+    int o0, o1;
+    if (ro <= R1) {
+      o0 = 0;
+      o1 = ro;
+    } else {
+      o0 = 1 + (ro - R1 - 1) / (2 * R1 + 1);
+      o1 = (ro - R1 - 1) % (2 * R1 + 1) - R1;
+    }
+    const int base = ((h0 + o0) * RY + h1 + o1 + R1) * RZ;
+    ROWS[e] = make_int2(PRE[base + h2], PRE[base + h2 + 2 * R2c + 1]);
+  }
+  __syncthreads();
   const int total = PRE[nreg];
-  const int nh = hb0 * hb1 * hb2;
   const int nhome = HPRE[nh];
   if (nhome == 0) return;  // CTA-uniform
   const R rc2 = (R)(ng.rc * ng.rc), inv_rc = (R)ng.inv_rc;
@@ -2485,11 +2531,12 @@ __global__ void __launch_bounds__(kThreads) k_near_pairs(NearGeom ng, const int*
 
   for (int c0 = 0; c0 < total; c0 += KC) {
     const int kn = min(KC, total - c0);
+    const int c1 = c0 + kn;
     if (c0 > 0) __syncthreads();  // the previous chunk's sums are flushed
     for (int t = warp; t < nreg; t += NW) {
-      const int a = max(PRE[t], c0), b = min(PRE[t + 1], c0 + kn);
+      const int a = max(PRE[t], c0), b = min(PRE[t + 1], c1);
       if (a >= b) continue;
-      const int jb = coff[NC[t]] + (a - PRE[t]);
+      const int jb = CS[t] + (a - PRE[t]);
       const V4 d = OFF[t];
       for (int k = a + lane; k < b; k += 32) {
         V4 xj = xq[jb + (k - a)];
@@ -2500,14 +2547,15 @@ __global__ void __launch_bounds__(kThreads) k_near_pairs(NearGeom ng, const int*
       }
     }
     __syncthreads();
+    R u = R(0), w[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};  // plain sums over the chunk
     for (int hi = warp; hi < nhome; hi += NW) {
-      int h = 0;
-      while (h + 1 < nh && HPRE[h + 1] <= hi) ++h;
+      const unsigned hm = __ballot_sync(0xffffffffu, lane < nh && HPRE[lane + 1] <= hi);
+      const int h = __popc(hm);
       const int th = HT[h];
       const int rank = hi - HPRE[h];
-      const int si = coff[NC[th]] + rank;  // sorted index of atom i
-      const int ib = PRE[th] + rank;       // its slot in the neighbourhood
-      const int h0 = h / (hb1 * hb2), h1 = (h / hb2) % hb1, h2 = h - (h / hb2) * hb2;
+      const int si = CS[th] + rank;  // sorted index of atom i
+      const int ib = PRE[th] + rank;  // its slot in the neighbourhood
+      const int2* rows = ROWS + h * nrow;
       V4 xi = xq[si];
       {
         const V4 d = OFF[th];
@@ -2515,14 +2563,41 @@ __global__ void __launch_bounds__(kThreads) k_near_pairs(NearGeom ng, const int*
         xi.y += d.y;
         xi.z += d.z;
       }
-      R fx = R(0), fy = R(0), fz = R(0), u = R(0), w[6] = {R(0), R(0), R(0), R(0), R(0), R(0)};
-      // the pair terms of queue entries [qs, qs + m), lane l taking entry qs + l
-      auto work = [&](int qs, int m) {
-        if (lane < m) {
-          const int e = (qs + lane) & (kQ - 1);
-          const V4 e4 = q_w[e];
-          const int js = qj_w[e];
-          const R rx = e4.x, ry = e4.y, rz = e4.z;
+      R fx = R(0), fy = R(0), fz = R(0);
+      // the warp alternates between filling its queue from the rows (until it holds 32
+      // entries or the rows are done) and working 32 (or the last) entries
+      int ro = 0;
+      int ka = max(ib + 1, c0), kb = min(rows[0].y, c1);
+      int qh = 0, qn = 0;  // queue head and length (warp-uniform)
+      for (;;) {
+        while (qn < 32) {
+          if (ka >= kb) {
+            if (++ro >= nrow) break;
+            const int2 rr = rows[ro];
+            ka = max(rr.x, c0);
+            kb = min(rr.y, c1);
+            continue;
+          }
+          const int k = ka + lane;
+          bool pass = false;
+          if (k < kb) {
+            const V4 xj = CB[k - c0];
+            const R dx = xi.x - xj.x, dy = xi.y - xj.y, dz = xi.z - xj.z;
+            const R r2 = dx * dx + dy * dy + dz * dz;
+            pass = r2 > R(0) && r2 <= rc2;
+          }
+          const unsigned m = __ballot_sync(0xffffffffu, pass);
+          if (pass) qj_w[(qh + qn + __popc(m & lt)) & (kQ - 1)] = k - c0;
+          qn += __popc(m);
+          ka += 32;
+        }
+        if (qn == 0) break;
+        __syncwarp();
+        const int mq = min(qn, 32);
+        if (lane < mq) {
+          const int js = qj_w[(qh + lane) & (kQ - 1)];
+          const V4 e4 = CB[js];  // the same FP32 differences as the test above
+          const R rx = xi.x - e4.x, ry = xi.y - e4.y, rz = xi.z - e4.z;
           const R r2 = rx * rx + ry * ry + rz * rz;
           R inv_r, r;
           if constexpr (std::is_same<R, float>::value) {
@@ -2533,7 +2608,7 @@ __global__ void __launch_bounds__(kThreads) k_near_pairs(NearGeom ng, const int*
             inv_r = R(1) / r;
           }
           R g1, g2;
-          near_eval(TAB, nd, r * inv_rc, &g1, &g2);
+          near_eval<ND>(TAB, nd, r * inv_rc, &g1, &g2);
           const R qq = xi.w * e4.w;
           const R en = qq * g1 * inv_r;
           const R f = qq * g2 * inv_r * inv_r * inv_r;
@@ -2552,58 +2627,10 @@ __global__ void __launch_bounds__(kThreads) k_near_pairs(NearGeom ng, const int*
           w[4] = fma(px, rz, w[4]);
           w[5] = fma(py, rz, w[5]);
         }
-      };
-      int qh = 0, qn = 0;  // queue head and length (warp-uniform)
-      // candidates [a, b) of the neighbourhood (clipped to this chunk)
-      auto scan = [&](int a, int b) {
-        a = max(a, c0);
-        b = min(b, c0 + kn);
-        for (int k = a; k < b; k += 32) {
-          bool pass = false;
-          V4 ent{};
-          const int kk = k + lane - c0;
-          if (k + lane < b) {
-            const V4 xj = CB[kk];
-            ent.x = xi.x - xj.x;
-            ent.y = xi.y - xj.y;
-            ent.z = xi.z - xj.z;
-            ent.w = xj.w;
-            const R r2 = ent.x * ent.x + ent.y * ent.y + ent.z * ent.z;
-            pass = r2 > R(0) && r2 <= rc2;
-          }
-          const unsigned m = __ballot_sync(0xffffffffu, pass);
-          if (pass) {
-            const int e = (qh + qn + __popc(m & lt)) & (kQ - 1);
-            q_w[e] = ent;
-            qj_w[e] = kk;
-          }
-          qn += __popc(m);
-          __syncwarp();
-          if (qn >= 32) {
-            work(qh, 32);
-            qh = (qh + 32) & (kQ - 1);
-            qn -= 32;
-            __syncwarp();  // the worked entries may be overwritten now
-          }
-        }
-      };
-      // forward rows: (o0, o1) after (0, 0); in row (0, 0) the atoms after i up to the
-      // cell R2 ahead
-      for (int o0 = 0; o0 <= R0; ++o0) {
-        for (int o1 = (o0 == 0 ? 0 : -R1); o1 <= R1; ++o1) {
-          const int row = ((h0 + o0) * RY + h1 + o1 + R1) * RZ;
-          const int last = PRE[row + h2 + 2 * R2c + 1];
-          if (o0 == 0 && o1 == 0)
-            scan(ib + 1, last);
-          else
-            scan(PRE[row + h2], last);
-        }
+        qh = (qh + mq) & (kQ - 1);
+        qn -= mq;
+        __syncwarp();  // the worked entries may be overwritten now
       }
-      work(qh, qn);
-      __syncwarp();
-      U.add(u);
-#pragma unroll
-      for (int c = 0; c < 6; ++c) W[c].add(w[c]);
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         fx += __shfl_xor_sync(0xffffffffu, fx, o);
@@ -2621,12 +2648,15 @@ __global__ void __launch_bounds__(kThreads) k_near_pairs(NearGeom ng, const int*
         }
       }
     }
+    U.add(u);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) W[c].add(w[c]);
     __syncthreads();
     // the candidates' sums of this chunk go to the sorted-order accumulator
     for (int t = warp; t < nreg; t += NW) {
-      const int a = max(PRE[t], c0), b = min(PRE[t + 1], c0 + kn);
+      const int a = max(PRE[t], c0), b = min(PRE[t + 1], c1);
       if (a >= b) continue;
-      const int jb = coff[NC[t]] + (a - PRE[t]);
+      const int jb = CS[t] + (a - PRE[t]);
       for (int k = a + lane; k < b; k += 32) {
         const int s = k - c0;
         const R vx = FJ[s], vy = FJ[KC + s], vz = FJ[2 * KC + s];
@@ -3302,26 +3332,48 @@ int near_region_cells(const NearGeom& ng) {
   return (ng.B[0] + ng.R[0]) * (ng.B[1] + 2 * ng.R[1]) * (ng.B[2] + 2 * ng.R[2]);
 }
 
+size_t near_pairs_smem(bool fp64, const NearGeom& ng) {
+  const int nrows = ng.B[0] * ng.B[1] * ng.B[2] * (1 + ng.R[1] + ng.R[0] * (2 * ng.R[1] + 1));
+  return near_smem_bytes(fp64, near_region_cells(ng), nrows);
+}
+
 cudaError_t launch_near_pairs(bool fp64, bool io_double, const NearGeom& ng, int ncells,
                               const int* coff, const void* xq, const int* idx, const void* tab,
-                              void* fsort, void* forces, int add, int64_t n, double* out,
-                              cudaStream_t st) {
+                              void* offtab, void* fsort, void* forces, int add, int64_t n,
+                              double* out, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(out, 0, 7 * sizeof(double), st);
   if (e != cudaSuccess || ncells <= 0 || n <= 0) return e;
   const int nreg = near_region_cells(ng);
   if (nreg > kNearMaxRegion) return cudaErrorInvalidValue;  // the host rejects such cells first
   const int nblocks = ng.nb[0] * ng.nb[1] * ng.nb[2];
-  const size_t smem = near_smem_bytes(fp64, nreg);
-  auto cfg = [&](auto kern) {
-    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  };
-  if ((e = fp64 ? cfg(k_near_pairs<double>) : cfg(k_near_pairs<float>))) return e;
+  const size_t smem = near_pairs_smem(fp64, ng);
+  if (smem > kNearMaxSmem) return cudaErrorInvalidValue;  // the host rejects such cells first
   if (fp64)
-    k_near_pairs<double><<<nblocks, kThreads, smem, st>>>(ng, coff, (const double4*)xq,
-                                                          (const double*)tab, (double4*)fsort, out);
+    k_near_offsets<double><<<(nreg + kThreads - 1) / kThreads, kThreads, 0, st>>>(ng, (double4*)offtab);
   else
-    k_near_pairs<float><<<nblocks, kThreads, smem, st>>>(ng, coff, (const float4*)xq,
-                                                         (const float*)tab, (float4*)fsort, out);
+    k_near_offsets<float><<<(nreg + kThreads - 1) / kThreads, kThreads, 0, st>>>(ng, (float4*)offtab);
+  auto run = [&](auto kern, const auto* xqp, const auto* tabp, const auto* offp, auto* fsp) {
+    cudaError_t r = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (r != cudaSuccess) return r;
+    kern<<<nblocks, kThreads, smem, st>>>(ng, coff, xqp, tabp, offp, fsp, out);
+    return cudaGetLastError();
+  };
+  if (fp64) {
+    e = run(k_near_pairs<double, 0>, (const double4*)xq, (const double*)tab, (const double4*)offtab,
+            (double4*)fsort);
+  } else {
+    const float4* x4 = (const float4*)xq;
+    const float* t = (const float*)tab;
+    const float4* o4 = (const float4*)offtab;
+    float4* f4 = (float4*)fsort;
+    // the table degree as a compile-time constant where the FP32 fit usually lands
+    switch (ng.ndeg) {
+      case 6: e = run(k_near_pairs<float, 6>, x4, t, o4, f4); break;
+      case 7: e = run(k_near_pairs<float, 7>, x4, t, o4, f4); break;
+      case 8: e = run(k_near_pairs<float, 8>, x4, t, o4, f4); break;
+      default: e = run(k_near_pairs<float, 0>, x4, t, o4, f4); break;
+    }
+  }
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int nb = grid_blocks(n);
   if (fp64)

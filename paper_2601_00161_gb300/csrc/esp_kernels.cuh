@@ -328,7 +328,10 @@ cudaError_t launch_gather(bool fp64, bool io_double, bool bf16, const GatherGeom
 // (overwritten, or added to when add != 0), out[0..6] = U_N, W_N xx yy zz xy xz yz
 // (overwritten).
 constexpr int kNearMaxRegion = 2048;  // cells of one block's neighbourhood
+constexpr int kNearMaxHome = 16;      // cells of one block (at most 2 x 2 x 4)
+constexpr size_t kNearMaxSmem = 200 * 1024;  // dynamic shared memory of the pair kernel
 int near_region_cells(const NearGeom& ng);
+size_t near_pairs_smem(bool fp64, const NearGeom& ng);
 cudaError_t launch_near_bin(bool io_double, bool fp64, const void* pos, const void* q,
                             int64_t n, const NearGeom& ng, int* ccount, int* cell, int* rank,
                             void* xq_tmp, cudaStream_t st);
@@ -336,10 +339,11 @@ cudaError_t launch_near_scan(int* ccount, int* coff, int ncells, cudaStream_t st
 cudaError_t launch_near_scatter(bool fp64, int64_t n, const int* cell, const int* rank,
                                 const int* coff, void* xq_tmp, void* xq, int* idx,
                                 cudaStream_t st);
+// offtab: kNearMaxRegion vec4 of the compute type (device scratch, written here)
 cudaError_t launch_near_pairs(bool fp64, bool io_double, const NearGeom& ng, int ncells,
                               const int* coff, const void* xq, const int* idx, const void* tab,
-                              void* fsort, void* forces, int add, int64_t n, double* out,
-                              cudaStream_t st);
+                              void* offtab, void* fsort, void* forces, int add, int64_t n,
+                              double* out, cudaStream_t st);
 
 // Fields from the kept spectrum (kind 0: G X; 1: i k_d G X; 2: K_ab X / w^2), written as
 // 1, 3 or 6 half spectra one after the other.
