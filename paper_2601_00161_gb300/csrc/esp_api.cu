@@ -1164,7 +1164,7 @@ int esp_near(esp_plan_t p, const void* pos, const void* q, void* forces, int add
     return fail(p, ESP_ERR_ARG, "pos, q, forces or d_out is NULL");
   DeviceGuard guard(p->device);
   // cell list of the current cell: nc bins of at least r_c / 2 per axis, R neighbours each
-  // side, blocks of up to 2 x 2 x 4 bins per CTA
+  // side, blocks of up to 2 x 2 x 2 bins per CTA
   esp::NearGeom& ng = p->ng;
   int ncells = 1;
   for (int d = 0; d < 3; ++d) {
@@ -1173,8 +1173,9 @@ int esp_near(esp_plan_t p, const void* pos, const void* q, void* forces, int add
     const double width = 1.0 / std::sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]);
     ng.nc[d] = std::max(1, (int)std::min(1024.0, std::floor(2.0 * width / p->rc)));
     ng.R[d] = std::max(1, (int)std::ceil(p->rc * ng.nc[d] / width));
-    ng.B[d] = std::min(d == 2 ? 4 : 2, ng.nc[d]);
+    ng.B[d] = std::min(2, ng.nc[d]);
     ng.nb[d] = (ng.nc[d] + ng.B[d] - 1) / ng.B[d];
+    ng.inv_nc[d] = 1.0 / ng.nc[d];
     ncells *= ng.nc[d];
   }
   if (esp::near_region_cells(ng) > esp::kNearMaxRegion ||

@@ -2214,8 +2214,9 @@ __global__ void __launch_bounds__(kThreads) k_near_bin(const IO* __restrict__ po
       double sd = ng.hinv[3 * d] * r[0] + ng.hinv[3 * d + 1] * r[1] + ng.hinv[3 * d + 2] * r[2];
       sd -= floor(sd);
       if (sd >= 1.0) sd = 0.0;
-      c[d] = min((int)(sd * ng.nc[d]), ng.nc[d] - 1);
-      f[d] = sd - (double)c[d] / ng.nc[d];  // reduced offset from the cell corner
+      const double td = sd * ng.nc[d];
+      c[d] = min((int)td, ng.nc[d] - 1);
+      f[d] = (td - (double)c[d]) * ng.inv_nc[d];  // reduced offset from the cell corner
     }
     const int id = (c[0] * ng.nc[1] + c[1]) * ng.nc[2] + c[2];
     cell[i] = id;
@@ -2229,54 +2230,50 @@ __global__ void __launch_bounds__(kThreads) k_near_bin(const IO* __restrict__ po
   }
 }
 
-// Exclusive scan of one value per thread over the CTA (kThreads threads); *total gets
-// the CTA's sum.  wsum: kThreads / 32 ints of shared memory.
-__device__ __forceinline__ int block_exclusive_scan(int v, int* wsum, int* total) {
+// Exclusive scan of the cell counts by one CTA of kScanThreads threads, kScanPer counts
+// per thread and pass; ccount is zeroed for the next call.
+constexpr int kScanThreads = 1024, kScanPer = 8;
+__global__ void __launch_bounds__(kScanThreads) k_near_scan(int* __restrict__ ccount,
+                                                            int* __restrict__ coff, int ncells) {
+  __shared__ int wsum[kScanThreads / 32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  int x = v;
+  int carry = 0;
+  for (int base = 0; base < ncells; base += kScanPer * kScanThreads) {
+    int v[kScanPer], sum = 0;
+    const int i0 = base + kScanPer * threadIdx.x;
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
-  }
-  if (lane == 31) wsum[wid] = x;
-  __syncthreads();
-  if (wid == 0) {
-    int t = lane < kThreads / 32 ? wsum[lane] : 0;
+    for (int k = 0; k < kScanPer; ++k) {
+      v[k] = i0 + k < ncells ? ccount[i0 + k] : 0;
+      sum += v[k];
+    }
+#pragma unroll
+    for (int k = 0; k < kScanPer; ++k)
+      if (i0 + k < ncells) ccount[i0 + k] = 0;
+    int x = sum;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, t, o);
-      if (lane >= o) t += y;
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
     }
-    if (lane < kThreads / 32) wsum[lane] = t;
-  }
-  __syncthreads();
-  *total = wsum[kThreads / 32 - 1];
-  return (wid > 0 ? wsum[wid - 1] : 0) + x - v;
-}
-
-__global__ void __launch_bounds__(kThreads) k_near_scan(int* __restrict__ ccount,
-                                                        int* __restrict__ coff, int ncells) {
-  __shared__ int wsum[kThreads / 32];
-  int carry = 0;
-  for (int base = 0; base < ncells; base += 4 * kThreads) {
-    int v[4], s = 0;
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int t = wsum[lane];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int i = base + 4 * threadIdx.x + k;
-      v[k] = i < ncells ? ccount[i] : 0;
-      if (i < ncells) ccount[i] = 0;
-      s += v[k];
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, t, o);
+        if (lane >= o) t += y;
+      }
+      wsum[lane] = t;
     }
-    int total;
-    int o = block_exclusive_scan(s, wsum, &total) + carry;
+    __syncthreads();
+    int o = carry + (wid > 0 ? wsum[wid - 1] : 0) + x - sum;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int i = base + 4 * threadIdx.x + k;
-      if (i < ncells) coff[i] = o;
+    for (int k = 0; k < kScanPer; ++k) {
+      if (i0 + k < ncells) coff[i0 + k] = o;
       o += v[k];
     }
-    carry += total;
+    carry += wsum[kScanThreads / 32 - 1];
     __syncthreads();  // wsum is reused
   }
   if (threadIdx.x == 0) coff[ncells] = carry;
@@ -2319,7 +2316,7 @@ __device__ __forceinline__ double warp_total(const Sum<double>& s) { return warp
 // Candidates (atoms of the block's neighbourhood) a CTA holds in shared memory at a time.
 template <typename R>
 __host__ __device__ constexpr int near_cand() {
-  return std::is_same<R, float>::value ? 2048 : 1024;
+  return std::is_same<R, float>::value ? 1536 : 1024;
 }
 // dynamic shared memory of k_near_pairs for a neighbourhood of nreg cells and nh x nrow
 // home-cell rows: candidates (position, charge) and their force sums (3 per candidate),
@@ -2407,7 +2404,7 @@ __global__ void __launch_bounds__(kThreads) k_near_offsets(NearGeom ng,
 // once; the FP32 path sums them per lane in plain precision over a chunk and adds that to
 // compensated running sums.
 template <typename R, int ND>
-__global__ void __launch_bounds__(kThreads, 3) k_near_pairs(NearGeom ng, const int* __restrict__ coff,
+__global__ void __launch_bounds__(kThreads, 4) k_near_pairs(NearGeom ng, const int* __restrict__ coff,
                                                          const typename Vec4<R>::T* __restrict__ xq,
                                                          const R* __restrict__ tab,
                                                          const typename Vec4<R>::T* __restrict__ offtab,
@@ -3310,7 +3307,7 @@ cudaError_t launch_near_bin(bool io_double, bool fp64, const void* pos, const vo
 }
 
 cudaError_t launch_near_scan(int* ccount, int* coff, int ncells, cudaStream_t st) {
-  k_near_scan<<<1, kThreads, 0, st>>>(ccount, coff, ncells);
+  k_near_scan<<<1, kScanThreads, 0, st>>>(ccount, coff, ncells);
   return cudaGetLastError();
 }
 

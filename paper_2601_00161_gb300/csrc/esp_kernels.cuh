@@ -134,8 +134,9 @@ struct Bins {
 struct NearGeom {
   int nc[3];  // cells per axis, each at least r_c / 2 wide
   int R[3];   // reach: cells per side that cover r_c
-  int B[3];   // cells per block (one CTA), at most 2 per axis
+  int B[3];   // cells per block (one CTA): up to 2 x 2 x 2
   int nb[3];  // blocks per axis
+  double inv_nc[3];
   double h[9];     // row-major
   double hinv[9];  // row-major
   double rc, inv_rc;
@@ -328,7 +329,7 @@ cudaError_t launch_gather(bool fp64, bool io_double, bool bf16, const GatherGeom
 // (overwritten, or added to when add != 0), out[0..6] = U_N, W_N xx yy zz xy xz yz
 // (overwritten).
 constexpr int kNearMaxRegion = 2048;  // cells of one block's neighbourhood
-constexpr int kNearMaxHome = 16;      // cells of one block (at most 2 x 2 x 4)
+constexpr int kNearMaxHome = 8;       // cells of one block (at most 2 x 2 x 2)
 constexpr size_t kNearMaxSmem = 200 * 1024;  // dynamic shared memory of the pair kernel
 int near_region_cells(const NearGeom& ng);
 size_t near_pairs_smem(bool fp64, const NearGeom& ng);
