@@ -371,6 +371,14 @@ struct WinDeg<double> {
   static constexpr int value = kDegF64;
 };
 
+// Vector reduction of four floats into global memory (no value returned, so no register
+// waits for the atomic to complete).  addr: 16-byte aligned.
+__device__ __forceinline__ void red_add4(void* addr, float a, float b, float c, float d) {
+  asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(addr), "f"(a), "f"(b),
+               "f"(c), "f"(d)
+               : "memory");
+}
+
 // Horner with the coefficients of (t - 1/2)^k held in registers
 template <typename R, int D>
 __device__ __forceinline__ R horner_reg(const R (&c)[D + 1], R t) {
@@ -766,12 +774,11 @@ __global__ void __launch_bounds__(kThreads, spread_min_ctas<R, P>()) k_spread(Bi
               src[1] = 0;
               src[2] = 0;
               src[3] = 0;
-              const float4 v = make_float4((float)iv.x * inv_scale, (float)iv.y * inv_scale,
-                                           (float)iv.z * inv_scale, (float)iv.w * inv_scale);
               const int gi = wrap3(o0 + a, g.M[0]);
               const int gj = wrap3(o1 + b, g.M[1]);
               const int gk = wrap3(o2 + 4 * c4, g.M[2]);
-              atomicAdd(reinterpret_cast<float4*>(grid + ((int64_t)gi * g.M[1] + gj) * g.M[2] + gk), v);
+              red_add4(grid + ((int64_t)gi * g.M[1] + gj) * g.M[2] + gk, (float)iv.x * inv_scale,
+                       (float)iv.y * inv_scale, (float)iv.z * inv_scale, (float)iv.w * inv_scale);
             }
           }
           flushed = true;
@@ -2636,7 +2643,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_near_pairs(NearGeom ng, const i
       }
       if (lane == 0) {
         if constexpr (std::is_same<R, float>::value) {
-          atomicAdd(fsort + si, make_float4(fx, fy, fz, 0.f));
+          red_add4(fsort + si, fx, fy, fz, 0.f);
         } else {
           R* fs = reinterpret_cast<R*>(fsort + si);
           atomicAdd(fs, fx);
@@ -2662,7 +2669,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_near_pairs(NearGeom ng, const i
           FJ[KC + s] = R(0);
           FJ[2 * KC + s] = R(0);
           if constexpr (std::is_same<R, float>::value) {
-            atomicAdd(fsort + jb + (k - a), make_float4(vx, vy, vz, 0.f));
+            red_add4(fsort + jb + (k - a), vx, vy, vz, 0.f);
           } else {
             R* fs = reinterpret_cast<R*>(fsort + jb + (k - a));
             atomicAdd(fs, vx);
