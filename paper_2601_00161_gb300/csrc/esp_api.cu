@@ -423,7 +423,7 @@ void release(esp_plan_t p) {
   void* bufs[] = {p->d_wtab,      p->d_radtab,    p->d_invw2,    p->d_grid,      p->d_spec,  p->d_spec2, p->d_xtw, p->d_xorder, p->d_xcol,
                   p->d_pbox,      p->d_ptw,       p->d_phi16,
                   p->bins.count,  p->bins.tcount, p->bins.tq,    p->bins.lb,     p->bins.idx, p->bins.otq, p->bins.ob, p->bins.oidx,
-                  p->bins.ctrl,   p->d_binpart,   p->d_accum,   p->d_partials,
+                  p->bins.ctrl,   p->bins.hq,     p->d_binpart,   p->d_accum,   p->d_partials,
                   p->d_io_pos,    p->d_io_q,     p->d_io_f,
                   p->d_neartab,   p->d_ncount,    p->d_ncoff,    p->d_ncell,     p->d_nrank,
                   p->d_nxq_tmp,   p->d_nxq,       p->d_nidx,     p->d_noff,      p->d_fspec,     p->d_fgrid};
@@ -905,6 +905,7 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
     ALLOC(b.ob, 3 * sizeof(int) * nn);
     ALLOC(b.oidx, sizeof(int) * nn);
     ALLOC(b.ctrl, sizeof(int) * esp::kCtrl);
+    ALLOC(b.hq, sizeof(float) * esp::kHQ * (size_t)p->ntiles);
   }
   ALLOC(p->d_binpart, sizeof(double) * 3 * p->bin_blocks);
   ALLOC(p->d_accum, sizeof(double) * ESP_ACCUM_LEN);
@@ -918,6 +919,7 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
     cudaError_t e = cudaMemset(p->bins.count, 0, sizeof(int) * (size_t)p->ntiles);
     if (e == cudaSuccess) e = cudaMemset(p->bins.tcount, 0, sizeof(int) * (size_t)p->ntiles);
     if (e == cudaSuccess) e = cudaMemset(p->bins.ctrl, 0, sizeof(int) * esp::kCtrl);
+    if (e == cudaSuccess) e = cudaMemset(p->bins.hq, 0, sizeof(float) * esp::kHQ * (size_t)p->ntiles);
     if (e == cudaSuccess) e = cudaMemset(p->d_accum, 0, sizeof(double) * ESP_ACCUM_LEN);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_accum, sizeof(double) * ESP_ACCUM_LEN);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&p->h_xorder, sizeof(int) * (size_t)p->xblocks);
@@ -1401,7 +1403,7 @@ constexpr size_t kNoAllocSlots = 2 * (size_t)ESP_NOALLOC_MAX_ATOMS > 32 * (size_
                                      : 32 * (size_t)ESP_NOALLOC_MAX_TILES;
 
 struct NoAllocLayout {
-  size_t count, tcount, ctrl, binpart, tq, lb, idx, otq, ob, oidx, wtab, total;
+  size_t count, tcount, ctrl, hq, binpart, tq, lb, idx, otq, ob, oidx, wtab, total;
 };
 
 constexpr NoAllocLayout noalloc_layout() {
@@ -1412,6 +1414,7 @@ constexpr NoAllocLayout noalloc_layout() {
   L.count = o;   o = al256(o + sizeof(int) * T);
   L.tcount = o;  o = al256(o + sizeof(int) * T);
   L.ctrl = o;    o = al256(o + sizeof(int) * esp::kCtrl);
+  L.hq = o;      o = al256(o + sizeof(float) * esp::kHQ * T);
   L.binpart = o; o = al256(o + 3 * 8 * nbin);
   L.tq = o;      o = al256(o + 32 * S);
   L.lb = o;      o = al256(o + sizeof(int) * S);
@@ -1556,6 +1559,7 @@ extern "C" int esp_spread_noalloc(const double cell[9], int64_t n, const int gri
   bins.count = reinterpret_cast<int*>(S + kNoAlloc.count);
   bins.tcount = reinterpret_cast<int*>(S + kNoAlloc.tcount);
   bins.ctrl = reinterpret_cast<int*>(S + kNoAlloc.ctrl);
+  bins.hq = reinterpret_cast<float*>(S + kNoAlloc.hq);
   bins.tq = S + kNoAlloc.tq;
   bins.lb = reinterpret_cast<int*>(S + kNoAlloc.lb);
   bins.idx = reinterpret_cast<int*>(S + kNoAlloc.idx);
@@ -1584,6 +1588,7 @@ extern "C" int esp_spread_noalloc(const double cell[9], int64_t n, const int gri
   // at zero (a completed call leaves them zero, a failed one may not)
   ESP_CUDA(nullptr, cudaMemsetAsync(bins.count, 0, sizeof(int) * (size_t)p->ntiles, st));
   ESP_CUDA(nullptr, cudaMemsetAsync(bins.ctrl, 0, sizeof(int) * esp::kCtrl, st));
+  ESP_CUDA(nullptr, cudaMemsetAsync(bins.hq, 0, sizeof(float) * esp::kHQ * (size_t)p->ntiles, st));
   ESP_CUDA(nullptr, esp::launch_bin(p->io_double, p->fp64, pos, q, n, g, bins, binpart,
                                     nullptr, 0, st));
   ESP_CUDA(nullptr, cudaMemsetAsync(grid_out, 0, es * Mtot, st));

@@ -296,6 +296,9 @@ __global__ void __launch_bounds__(kThreads) k_bin(const IO* __restrict__ pos,
         slot_tq[sl] = v;
         bins.lb[sl] = lbp;
         bins.idx[sl] = (int)i;
+        // the FP32 spread's fixed-point bound: sum |q| per tile and base b2
+        if constexpr (std::is_same<R, float>::value)
+          atomicAdd(bins.hq + (int64_t)tile * kHQ + (lbp >> 20), fabsf(v.w));
       } else {
         const int o = atomicAdd(&bins.ctrl[0], 1);
         static_cast<V4*>(bins.otq)[o] = v;
@@ -568,9 +571,10 @@ constexpr int spread_min_ctas() {
 // atom at a time and adds its P^3 values into the padded block along the lane-fixed
 // columns of Cols<P>, every shared-memory add of the warp hitting 32 distinct banks.  The
 // FP32 block holds 32-bit fixed point with a power-of-two scale per tile: scale <= 2^30 /
-// (sum |q| over the tile's atoms x max |w|^3), so no partial sum can overflow; the
-// rounding of each contribution is at most half a unit of 2^-30 times that bound.  The
-// block then goes to the periodic grid with global atomics, and is cleared as it is read.
+// (max |w|^3 x the largest sum of |q| over the atoms whose bases fall in a window of P
+// positions along axis 2), so no partial sum can overflow; the rounding of each
+// contribution is at most half a unit of 2^-30 times that bound.  The block then goes to
+// the periodic grid with global vector reductions, and is cleared as it is read.
 template <typename R, int P>
 __global__ void __launch_bounds__(kThreads, spread_min_ctas<R, P>()) k_spread(Bins bins, TileGeom g, int ntiles,
                                                      const R* __restrict__ wtab,
@@ -589,6 +593,7 @@ __global__ void __launch_bounds__(kThreads, spread_min_ctas<R, P>()) k_spread(Bi
   const int E0 = g.E[0], E2 = g.E[2];  // this plan's tiles (<= TC)
   const SpreadLayout L = spread_layout((int)sizeof(R), P);
   R* W = reinterpret_cast<R*>(smem_raw + L.w);        // per atom [w0 | q w1 | w2]
+  float* HQ_b = reinterpret_cast<float*>(smem_raw + L.hq);  // 2 x kHQ: the tile's sum |q| per b2
   V4* TQ_b = reinterpret_cast<V4*>(smem_raw + L.tq);  // 2 x kChunk (t0, t1, t2, q)
   int* LB_b = reinterpret_cast<int*>(smem_raw + L.lb);
   int* CNT_b = reinterpret_cast<int*>(smem_raw + L.cnt);
@@ -596,7 +601,7 @@ __global__ void __launch_bounds__(kThreads, spread_min_ctas<R, P>()) k_spread(Bi
   // takes the tile)
   __shared__ int s_first[2], s_ahead[2];
   __shared__ int3 s_ofirst[2], s_oahead[2];
-  __shared__ float s_qsum[kThreads / 32];
+  __shared__ float s_bound;  // FP32: the tile's bound of sum |q|
   const unsigned acc_s = (unsigned)__cvta_generic_to_shared(acc);
 
   constexpr int D = WinDeg<R>::value;
@@ -617,6 +622,8 @@ __global__ void __launch_bounds__(kThreads, spread_min_ctas<R, P>()) k_spread(Bi
       for (int e = threadIdx.x; e < ncopy / 4; e += blockDim.x)
         cp_async16(LB_b + b * kChunk + 4 * e, bins.lb + s0 + 4 * e);
       if (threadIdx.x == 0) cp_async_small<4>(CNT_b + b, bins.count + t);
+      if (kFixed && threadIdx.x < kHQ / 4)
+        cp_async16(HQ_b + b * kHQ + 4 * threadIdx.x, bins.hq + (int64_t)t * kHQ + 4 * threadIdx.x);
     }
     cp_async_commit();
   };
@@ -662,22 +669,36 @@ __global__ void __launch_bounds__(kThreads, spread_min_ctas<R, P>()) k_spread(Bi
       bins.tcount[tile] = cnt_all;
       bins.count[tile] = 0;
     }
+    if (kFixed && threadIdx.x < kHQ) bins.hq[(int64_t)tile * kHQ + threadIdx.x] = 0.f;
     const int64_t s0 = (int64_t)tile * bins.cap;
     if (cnt_all > 0) {
       // fixed-point scale of this tile (FP32): a power of two, so scaling back is exact
       R scale = R(1), inv_scale = R(1);
       if constexpr (kFixed) {
-        float sq = 0.f;
-        for (int j = threadIdx.x; j < cnt_all; j += blockDim.x)
-          sq += fabsf(j < kChunk ? TQ[j].w : slot_tq[s0 + j].w);
+        // A point (x0, x1, x2) of the block receives only from the atoms whose stencil base
+        // b has x_2 - P < b_2 <= x_2, so the largest sum of |q| over such windows along axis
+        // 2 (any b0, b1), times max |w|^3, bounds every partial sum.  HQ holds the tile's
+        // sum |q| per base b2 (from the binning); lane x2 of warp 0 sums window x2.
+        if (warp == 0) {
+          const float* HQ = HQ_b + bf * kHQ;
+          const int T2 = g.T[2];
+          float mx = 0.f;
+          for (int x2 = lane; x2 < E2; x2 += 32) {
+            float sw = 0.f;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
-        if (lane == 0) s_qsum[warp] = sq;
+            for (int d2 = 0; d2 < P; ++d2) {
+              const int b2 = x2 - d2;
+              if (b2 >= 0 && b2 < T2) sw += HQ[b2];
+            }
+            mx = fmaxf(mx, sw);
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+          if (lane == 0) s_bound = mx;
+        }
         __syncthreads();
-        float tot = 0.f;
-#pragma unroll
-        for (int w = 0; w < kThreads / 32; ++w) tot += s_qsum[w];
-        // an upper bound of every |partial sum| in the block, with margin for the float sums
+        const float tot = s_bound;
+        // with margin for the float sums
         const float bound = tot * g.wmax3 * 1.0001f + 1e-30f;
         int ex;
         frexpf(bound, &ex);  // bound < 2^ex

@@ -126,11 +126,14 @@ struct Bins {
   int* ob;        // [3 n] their stencil bases
   int* oidx;      // [n] their input indices
   int* ctrl;      // [kCtrl]
+  float* hq;      // [ntiles * kHQ] FP32: sum |q| of the slotted atoms per tile and base b2
+                  // (zero between steps: the spread reads and clears it)
 };
+constexpr int kHQ = 16;  // b2 bins per tile (T2 <= 16)
 
 // Near (real-space) part of the split: a cell list with nc[d] >= 1 bins per reduced axis
-// (each bin at least r_c thick when nc[d] > 1) and R[d] neighbour bins on either side, so
-// every pair and periodic image within r_c is found exactly once.
+// (each bin at least r_c / 2 thick when nc[d] > 1) and R[d] neighbour bins on either side,
+// so every pair and periodic image within r_c is found exactly once.
 struct NearGeom {
   int nc[3];  // cells per axis, each at least r_c / 2 wide
   int R[3];   // reach: cells per side that cover r_c
@@ -234,7 +237,7 @@ __host__ __device__ constexpr int record_stride(bool gather, int P) {
 // chunk's window records, and two buffers of atoms ((t, q), packed local base) and counts
 // for the tile worked on and the next one.
 struct SpreadLayout {
-  size_t w, tq, lb, cnt, total;
+  size_t w, tq, lb, cnt, hq, total;
 };
 __host__ __device__ inline SpreadLayout spread_layout(int es, int P) {
   SpreadLayout L{};
@@ -247,6 +250,7 @@ __host__ __device__ inline SpreadLayout spread_layout(int es, int P) {
   L.tq = o;  o += 2 * (size_t)kChunk * 4 * es;                    o = (o + 31) & ~(size_t)31;
   L.lb = o;  o += 2 * (size_t)kChunk * sizeof(int);               o = (o + 31) & ~(size_t)31;
   L.cnt = o; o += 2 * sizeof(int);                                o = (o + 31) & ~(size_t)31;
+  L.hq = o;  o += 2 * (size_t)kHQ * sizeof(float);                 o = (o + 31) & ~(size_t)31;
   L.total = o;
   return L;
 }
