@@ -259,8 +259,9 @@ const char* esp_last_error(esp_plan_t plan);
  * with a device-memory budget fixed at start-up, or a loop that must not pay the implicit
  * device synchronisation a cudaMalloc or cudaFree may cost.  It runs the plan path's
  * bin/sort and spread kernels with their scratch (binning counters, binned atoms, the
- * window table) in one static device array of the library, about 8.4 MB, which every GPU
- * that loads the library holds until the process exits.
+ * window table, the per-tile charge sums of the fixed-point bound) in one static device
+ * array of the library, about 8.7 MB, which every GPU that loads the library holds until
+ * the process exits.
  *   cell, grid, w, c, precision: as for esp_plan (no split radius is needed here).
  *   n <= ESP_NOALLOC_MAX_ATOMS, and the grid at most ESP_NOALLOC_MAX_TILES tiles of
  *        8 x 8 x 16 points (8 x 8 x 8 for w > 8); larger inputs return ESP_ERR_ARG.
