@@ -36,10 +36,10 @@ FEATURES = ("log10_n", "log10_density", "log_aspect_21", "log_aspect_31", "tilt"
 OUTPUTS = ("log10_delta", "P", "sigma", "rc")
 
 # cost model coefficients (seconds), GB300, FP32 path
-COST_ATOM = 1.6e-10         # bin, scan, scatter per atom
+COST_ATOM = 1.6e-10         # binning per atom
 COST_ATOM_P3 = 1.83e-12     # spread + gather per atom and stencil point
 COST_POINT_LOG = 1.18e-12   # forward + inverse FFT and scaling per grid point and log2(Mtot)
-COST_PAIR = 3.32e-11        # near part per ordered pair within r_c
+COST_PAIR = 9.8e-12         # near part per ordered pair within r_c (half-shell kernel)
 
 
 def fft_size(n: int) -> int:
