@@ -216,7 +216,7 @@ __device__ __forceinline__ double dscale_of<double>(const TileGeom& g, int d) {
 
 // ---------------------------------------------------------------------------------------
 template <typename IO, typename R>
-__global__ void __launch_bounds__(kThreads) k_bin(const IO* __restrict__ pos,
+__global__ void __launch_bounds__(kThreads, 6) k_bin(const IO* __restrict__ pos,
                                                   const IO* __restrict__ q, int64_t n,
                                                   TileGeom g, Bins bins,
                                                   float2* __restrict__ bin_part,
