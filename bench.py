@@ -406,14 +406,21 @@ def esp_arm(args):
     F_h = torch.empty((S.n, 3), dtype=dt).pin_memory().numpy()
     for _ in range(3):
         esp.esp_compute_host(plan.handle, pos_h, q_h, F_h)
+    # each call timed on the host clock (the call returns with its results on the host),
+    # the L2 flushed before it outside the timed interval
     n_e2e = max(10, min(args.steps, 50))
-    t0 = time.perf_counter()
+    e2e_tot = 0.0
     for _ in range(n_e2e):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
         esp.esp_compute_host(plan.handle, pos_h, q_h, F_h)
-    e2e_s = (time.perf_counter() - t0) / n_e2e
+        e2e_tot += time.perf_counter() - t0
+    e2e_s = e2e_tot / n_e2e
     e2e = {"value": round(world / e2e_s, 2), "unit": "steps/s",
            "h2d_bytes_per_step": int(pos_h.nbytes + q_h.nbytes),
-           "d2h_bytes_per_step": int(F_h.nbytes + 8 * esp.ESP_ACCUM_LEN)}
+           "d2h_bytes_per_step": int(F_h.nbytes + 8 * esp.ESP_ACCUM_LEN),
+           "l2": "flushed before every call (512 MB write, outside the timed call)"}
 
     fp64_value = None
     if not fp64 and not args.no_fp64_compare:

@@ -76,6 +76,7 @@ struct esp_plan_s {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_start = nullptr, ev_zero = nullptr;
   int bin_blocks = 0;
   int spread_blocks = 0, gather_blocks = 0;
+  int sms = 152;  // SMs of the plan's device
   // device buffers
   void* d_wtab = nullptr;
   void* d_radtab = nullptr;
@@ -835,6 +836,7 @@ int esp_plan(esp_plan_t* out, const double cell[9], int64_t n, const int grid[3]
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   }
+  p->sms = sms;
   if ((rc = setup_tile_geom(p)) != ESP_OK) return bail(rc);
   esp::TileGeom& g = p->tg;
 
@@ -1287,10 +1289,21 @@ int esp_compute_host(esp_plan_t p, const void* pos, const void* q, void* forces,
   // input buffers (plain launches on the legacy default stream)
   int rc = run_step_graph(p, dpos, dq, forces ? p->d_io_f : nullptr, p->d_accum);
   if (rc != ESP_OK) return rc;
-  ESP_CUDA(p, cudaMemcpyAsync(p->h_accum, p->d_accum, sizeof(double) * ESP_ACCUM_LEN,
-                              cudaMemcpyDeviceToHost, st));
-  if (forces && p->n > 0)
-    ESP_CUDA(p, cudaMemcpyAsync(forces, p->d_io_f, 3 * io_es * p->n, cudaMemcpyDeviceToHost, st));
+  // Results back: into page-locked, 16-byte aligned host forces a kernel writes through
+  // the device mapping with coalesced 16-byte stores (faster over the CPU-GPU link than a
+  // copy-engine transfer of this size); otherwise two copies.
+  void* fmap = (forces && p->n > 0) ? const_cast<void*>(mapped_host(forces)) : nullptr;
+  void* amap = const_cast<void*>(mapped_host(p->h_accum));
+  const size_t fbytes = 3 * io_es * (size_t)p->n;
+  if (fmap && amap && ((uintptr_t)fmap & 15) == 0) {
+    ESP_CUDA(p, esp::launch_copy_out(p->d_io_f, fmap, (int64_t)(fbytes / 4), p->d_accum,
+                                     (double*)amap, ESP_ACCUM_LEN, p->sms, st));
+  } else {
+    ESP_CUDA(p, cudaMemcpyAsync(p->h_accum, p->d_accum, sizeof(double) * ESP_ACCUM_LEN,
+                                cudaMemcpyDeviceToHost, st));
+    if (forces && p->n > 0)
+      ESP_CUDA(p, cudaMemcpyAsync(forces, p->d_io_f, fbytes, cudaMemcpyDeviceToHost, st));
+  }
   ESP_CUDA(p, cudaStreamSynchronize(st));
   fill_result(p, p->h_accum, out);
   if (p->h_accum[9] > 0.0) return fail(p, ESP_ERR_NONFINITE, "non-finite position or charge");

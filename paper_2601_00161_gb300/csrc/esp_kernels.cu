@@ -2716,6 +2716,22 @@ __global__ void __launch_bounds__(kThreads, 4) k_near_pairs(NearGeom ng, const i
   }
 }
 
+// The step's results to page-locked host memory through its device mapping: nf floats
+// (the first 4 * n16 as 16-byte words, coalesced) and nacc doubles of the accumulator.
+__global__ void __launch_bounds__(kThreads) k_copy_out(const float* __restrict__ src,
+                                                       float* __restrict__ dst, int64_t nf,
+                                                       const double* __restrict__ acc,
+                                                       double* __restrict__ acc_dst, int nacc) {
+  const int64_t n16 = nf / 4;
+  const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+  const int4* s4 = reinterpret_cast<const int4*>(src);
+  int4* d4 = reinterpret_cast<int4*>(dst);
+  for (int64_t i = tid; i < n16; i += nth) d4[i] = s4[i];
+  for (int64_t i = 4 * n16 + tid; i < nf; i += nth) dst[i] = src[i];
+  if (tid < nacc) acc_dst[tid] = acc[tid];
+}
+
 // Near forces from the sorted-order accumulator to the caller's array (input order):
 // overwritten, or added to when add != 0.
 template <typename R, typename IO>
@@ -3262,6 +3278,12 @@ cudaError_t launch_iplane(bool fp64, bool bf16, const PlaneGeom& pg, const void*
                       (const float2*)box, colact, (__nv_bfloat16*)grid, pg, (const float2*)tw);
   return pdl_launch(k_iplane<float, float>, pg.M0, plane_threads<float>(), smem, st,
                     (const float2*)box, colact, (float*)grid, pg, (const float2*)tw);
+}
+
+cudaError_t launch_copy_out(const void* src, void* dst, int64_t nf, const double* acc,
+                            double* acc_dst, int nacc, int sms, cudaStream_t st) {
+  k_copy_out<<<2 * sms, kThreads, 0, st>>>((const float*)src, (float*)dst, nf, acc, acc_dst, nacc);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_xsum(bool fp64, const double* partials, int nblk, const void* bin_part,

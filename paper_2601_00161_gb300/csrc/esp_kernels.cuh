@@ -307,6 +307,10 @@ cudaError_t launch_xfft(bool fp64, bool fwd, bool inv, const XGeom& x, const Sca
                         const void* radtab,
                         double* partials, const int* order, const unsigned char* colact,
                         int nactive, cudaStream_t st);
+// nf floats src -> dst (dst: the device mapping of page-locked host memory; both 16-byte
+// aligned) and nacc doubles acc -> acc_dst, on 2 sms CTAs.
+cudaError_t launch_copy_out(const void* src, void* dst, int64_t nf, const double* acc,
+                            double* acc_dst, int nacc, int sms, cudaStream_t st);
 cudaError_t launch_xsum(bool fp64, const double* partials, int nblk, const void* bin_part,
                         int nbin, double* accum, cudaStream_t st);
 // Plane transforms (2 kPThreads per CTA in FP32, kPThreads in FP64; one CTA per plane i0).  tw: M1 roots
