@@ -206,7 +206,9 @@ int esp_forces_from_spectrum(esp_plan_t plan, void* forces);
 /* End-to-end call with HOST buffers: copies pos, q (I/O type) to the device, runs the
  * full step, copies forces (may be NULL) back and fills *out (may be NULL).
  * Synchronous.  pos/q/forces may be pageable or pinned host memory; page-locked pos and
- * q are read in place by the binning kernel (no staging copy), others are copied first. */
+ * q are read in place by the binning kernel (no staging copy), others are copied first.
+ * Page-locked, 16-byte aligned forces are written by a kernel through their device
+ * mapping; other forces buffers receive a copy-engine transfer. */
 int esp_compute_host(esp_plan_t plan, const void* pos, const void* q, void* forces,
                      esp_result* out);
 
