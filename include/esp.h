@@ -239,8 +239,8 @@ int esp_plan_info(esp_plan_t plan, double* info, int len);
  * esp_profile_read synchronises the stream and writes the last step's stage durations
  * in ms, in the order: [0] set-up, [1] bin (which also clears the spread grid and writes
  * the atoms straight into their tiles' slots), [2], [3] unused (0), [4] unused (0),
- * [5] spread, [6] forward FFT (the plane transforms on the force path, the full 3D
- * transform on the energy and pressure path), [7] transform along the first axis fused
+ * [5] spread, [6] forward plane transforms (cuFFT's for grids whose plane transforms do
+ * not fit in shared memory), [7] transform along the first axis fused
  * with the scaling and the sums, [8] inverse plane transforms, [9] gather (stages that
  * did not run read 0).  Writes min(len, 10) values. */
 int esp_profile(esp_plan_t plan, int enable);
