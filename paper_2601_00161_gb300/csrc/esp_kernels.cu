@@ -7,17 +7,26 @@
 //   k_spread   eq. (gridding): persistent CTAs stage a tile's padded block in shared
 //              memory; a warp adds one atom's P^3 footprint at a time along lane-fixed
 //              stencil columns (32 distinct banks per add), as 32-bit fixed point with
-//              the native shared-memory integer add; the block then goes to the periodic
-//              grid with float4 global reductions
+//              the native shared-memory integer add and a per-tile scale from the binned
+//              charge sums; the block then goes to the periodic grid with vector
+//              reductions
+//   k_fplane   the plane transforms over (i1, i2) of one plane i0 per CTA, pruned to the
+//              box of the sphere (two real lines as one complex line along i2, then the
+//              kept columns along i1)
 //   k_xfft     the transform along the first grid axis of the column groups whose lines
 //              meet the sphere |k| <= c / r_c (mixed-radix Stockham passes in shared
 //              memory), fused with eqs. (diag)/(PFfinal): per mode the deconvolved weight,
 //              the Fourier kernel and the 3x3 pressure kernel, summed per CTA (compensated
 //              FP32 on the FP32 path), and for forces G X and the inverse transform
 //   k_xsum     the fixed-order final sums of k_xfft's partials and of the charge sums
+//   k_iplane   the inverse of k_fplane from the scaled box into the potential grid
 //   k_gather   eq. (AD): the CTA stages its tile's padded block of the potential grid in
 //              shared memory; P lanes per atom contract its P^3 points with the window
 //              and its gradient, a segmented shuffle sums them
+// Around the step: k_cell_grad (cell gradient, Sec. 2.2), k_fields and k_gather_fields
+// (ik forces, local virial, per-atom energy: Sec. 4.4, Appendix C), the near part of the
+// split (k_near_bin, k_near_scan, k_near_scatter, k_near_offsets, k_near_pairs,
+// k_near_out: Sec. 3, eq. (UN)) and k_copy_out (results to page-locked host memory).
 //
 // Shared-memory layout of a tile block: row pitch E3p = -P (mod 32) and plane stride
 // S1 = P^2 (mod 32), so the stencil point (i, j, k) of an atom lies in bank
