@@ -13,7 +13,9 @@
  *    first cell vector h_1, cell[3..5] is h_2, cell[6..8] is h_3 (Angstrom).  det h > 0.
  *  - Positions are Cartesian (Angstrom), N x 3 row-major; charges N (e).  They may lie
  *    anywhere; they are wrapped into the cell through reduced coordinates s = h^{-1} r.
- *  - Units are Gaussian: energies in e^2/Angstrom, as the paper's 1/r kernel.
+ *  - Units are Gaussian: energies in e^2/Angstrom, as the paper's 1/r kernel.  Multiply
+ *    energies, virials, pressures and forces by the caller's Coulomb constant (for example
+ *    332.0637 kcal Angstrom / (mol e^2)) to convert.
  *  - Tensors are 3x3 row-major.  The virial is W = -(dU/dh) h^T at fixed reduced
  *    coordinates (eq. (instheta) without the kinetic term), so P = W / det h.
  *  - Device pointers belong to the caller, must stay valid until the stream has
@@ -287,6 +289,28 @@ int esp_spread_noalloc(const double cell[9], int64_t n, const int grid[3], int w
 /* PSWF shape parameter c with psi_0^c(1) / psi_0^c(0) = delta (Sec. 5.1 tuning rule,
  * read as a ratio to psi_0(0)), 0 < delta < 1; returns a negative value on bad input. */
 double esp_c_from_tolerance(double delta);
+
+/* Pressure seen by a barostat's cell coupling (Sec. 2.2), from a 3x3 row-major pressure
+ * tensor P, for example pressure_recip of esp_result plus pressure_bg on the diagonal
+ * plus the near part's W_N / det h.  Sec. 2.2 defines each coupling's pressure as minus
+ * the derivative of the energy with respect to its cell variables at fixed reduced
+ * coordinates; for the potential energy those derivatives are these combinations of
+ * P = -(dU/dh) h^T / det h (eq. (instheta)):
+ *   ESP_COUPLE_ISO       out[0] = tr P / 3                         (isotropic, eq. (Pins))
+ *   ESP_COUPLE_SEMI      out[0] = (Pxx + Pyy) / 2, out[1] = Pzz    (semi-isotropic: the
+ *                        lateral area A in the x-y plane and the height L along z)
+ *   ESP_COUPLE_ANISO     out[0..2] = Pxx, Pyy, Pzz                 (eq. (diagona))
+ *   ESP_COUPLE_FLEXIBLE  out[0..5] = Pxx Pyy Pzz Pxy Pxz Pyz        (eq. (instheta); P is
+ *                        symmetric for pair potentials)
+ * Returns the number of values written, or ESP_ERR_ARG for a NULL pointer or an unknown
+ * mode.  Host only; needs no plan and no GPU. */
+enum {
+  ESP_COUPLE_ISO = 0,
+  ESP_COUPLE_SEMI = 1,
+  ESP_COUPLE_ANISO = 2,
+  ESP_COUPLE_FLEXIBLE = 3
+};
+int esp_pressure_coupling(const double P[9], int mode, double* out);
 
 #ifdef __cplusplus
 }

@@ -41,7 +41,10 @@ EXPORTS = (
     "esp_copy_grid", "esp_copy_spectrum", "esp_plan_info", "esp_destroy", "esp_last_error",
     "esp_c_from_tolerance", "esp_profile", "esp_profile_read", "esp_spread_noalloc",
     "esp_cell_gradient", "esp_near", "esp_forces_ik", "esp_local_virial", "esp_atom_energy",
+    "esp_pressure_coupling",
 )
+
+ESP_COUPLE_ISO, ESP_COUPLE_SEMI, ESP_COUPLE_ANISO, ESP_COUPLE_FLEXIBLE = 0, 1, 2, 3
 
 ESP_NOALLOC_MAX_ATOMS = 65536
 ESP_NOALLOC_MAX_TILES = 4096
@@ -107,6 +110,7 @@ def _load():
         "esp_destroy": (ci, [vp]),
         "esp_last_error": (ctypes.c_char_p, [vp]),
         "esp_c_from_tolerance": (cd, [cd]),
+        "esp_pressure_coupling": (ci, [dptr, ci, dptr]),
         "esp_profile": (ci, [vp, ci]),
         "esp_profile_read": (ci, [vp, dptr, ci]),
         "esp_spread_noalloc": (ci, [dptr, i64, ctypes.POINTER(ci), ci, cd, ci, vp, vp, vp, vp]),
@@ -243,6 +247,19 @@ def esp_c_from_tolerance(delta: float) -> float:
     if c < 0:
         raise ESPError(ESP_ERR_ARG, "delta must lie in (0, 1)")
     return c
+
+
+def esp_pressure_coupling(P, mode: int):
+    """The pressure a barostat's cell coupling sees (ESP_COUPLE_*) from a 3x3 tensor."""
+    import numpy as np
+
+    a = np.ascontiguousarray(np.asarray(P, dtype=np.float64).reshape(9))
+    out = np.zeros(6)
+    k = _lib.esp_pressure_coupling(a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(mode),
+                                   out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if k < 0:
+        raise ESPError(k, esp_last_error(None))
+    return out[:k].copy()
 
 
 def esp_profile(plan, enable: bool):

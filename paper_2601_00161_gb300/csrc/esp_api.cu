@@ -1400,6 +1400,34 @@ const char* esp_last_error(esp_plan_t p) {
 
 double esp_c_from_tolerance(double delta) { return esp::c_from_tolerance(delta); }
 
+int esp_pressure_coupling(const double P[9], int mode, double* out) {
+  if (!P || !out) return fail(nullptr, ESP_ERR_ARG, "NULL argument");
+  switch (mode) {
+    case ESP_COUPLE_ISO:
+      out[0] = (P[0] + P[4] + P[8]) / 3.0;
+      return 1;
+    case ESP_COUPLE_SEMI:
+      out[0] = 0.5 * (P[0] + P[4]);
+      out[1] = P[8];
+      return 2;
+    case ESP_COUPLE_ANISO:
+      out[0] = P[0];
+      out[1] = P[4];
+      out[2] = P[8];
+      return 3;
+    case ESP_COUPLE_FLEXIBLE:
+      out[0] = P[0];
+      out[1] = P[4];
+      out[2] = P[8];
+      out[3] = P[1];
+      out[4] = P[2];
+      out[5] = P[5];
+      return 6;
+    default:
+      return fail(nullptr, ESP_ERR_ARG, "unknown pressure coupling mode");
+  }
+}
+
 }  // extern "C"
 
 // ---- allocation-free spreading ------------------------------------------------------------
