@@ -515,6 +515,11 @@ def esp_arm(args):
             "clocks": clk,
             "fp64_path_value": fp64_value,
             "energy_recip": res["energy_recip"],
+            # the long-range pressure (Fourier part plus background) a barostat's
+            # semi-isotropic coupling sees: lateral P_A and normal P_L, e^2/A^4
+            "pressure_semi_long_range": dict(zip(("P_A", "P_L"), (float(v) for v in esp.esp_pressure_coupling(
+                np.asarray(res["pressure_recip"]).reshape(3, 3) + res["pressure_bg"] * np.eye(3),
+                esp.ESP_COUPLE_SEMI)))),
         }
         if not args.no_cpu_baseline and world == 1:
             out["cpu_baseline"] = cpu_baseline_oracle(S, c)
