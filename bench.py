@@ -533,7 +533,7 @@ def esp_arm(args):
 def reference_arm(args):
     """FP64 CPU oracle on the host, one thread: each step is one full oracle step of the
     workload (spread, FFT, scaling, inverse FFT, gather of every atom), about 3 s for the
-    210,240-atom slab, so W + K steps of the driver's default run finish in minutes."""
+    210,240-atom slab, so W + K steps of a default run finish in minutes."""
     from oracle.esp_grid import esp_grid
     from oracle.pswf import c_from_tolerance
 
